@@ -1,0 +1,397 @@
+"""FP64 CPU oracle — TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s cpu_baseline /
+reference leg may import this package.  It shares no code with the CUDA
+library (``paper_2608_16940_gb300``) and never imports it.
+
+Contents
+--------
+* ``qsa_oracle.c`` (built into ``liboracle.so`` by :func:`build`): the plain
+  single-threaded FP64 state-vector update, probabilities, <Z>, Philox4x64-10
+  and the fixed-point CDF sampler.
+* this module: ctypes wrappers plus plain numpy restatements of
+  - the Kronecker embedding and block product used by fusion (§IV-C: "within a
+    block, matrices remain in circuit order, with later gates multiplied on
+    the left"),
+  - the fusion partition dynamic program (§IV-C, Eq. dp-recurrence) and the
+    plain width-limit greedy partition,
+  - the cost-model network (37 -> 64 -> 64 -> 1, ReLU, MSE on log-seconds)
+    forward, backward and one Adam step (Kingma & Ba 2015, Algorithm 1),
+  - fidelity metrics.
+
+Pins for every function live in ``tests/test_oracle_*.py``.  Functions with no
+pin beyond their definition say so in their docstring ("parity unpinned").
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Iterable, List, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qsa_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc.  ``-ffp-contract=off`` keeps every
+    product and sum rounded separately (no fused multiply-add), which the
+    sampler's fixed-point weights rely on."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
+               _SRC, "-o", _LIB_PATH]
+        subprocess.check_call(cmd)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB_PATH)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        L.orc_apply.argtypes = [dp, ctypes.c_int, ip, ctypes.c_int, dp]
+        L.orc_apply.restype = ctypes.c_int
+        L.orc_probabilities.argtypes = [dp, ctypes.c_int, dp]
+        L.orc_probabilities.restype = None
+        L.orc_expect_z.argtypes = [dp, ctypes.c_int, ctypes.c_uint64]
+        L.orc_expect_z.restype = ctypes.c_double
+        L.orc_philox4x64_10.argtypes = [u64p, u64p, u64p]
+        L.orc_philox4x64_10.restype = None
+        L.orc_sample.argtypes = [dp, ctypes.c_int, ip, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                 ctypes.c_double, u64p, ctypes.POINTER(ctypes.c_uint8)]
+        L.orc_sample.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# ---------------------------------------------------------------------------
+# State-vector operations (C)
+# ---------------------------------------------------------------------------
+
+def zero_state(n: int) -> np.ndarray:
+    """|0...0>: psi_0 = 1 (§II)."""
+    psi = np.zeros(1 << n, dtype=np.complex128)
+    psi[0] = 1.0
+    return psi
+
+
+def apply(psi: np.ndarray, targets: Sequence[int], mat: np.ndarray) -> None:
+    """In place: apply the 2^k x 2^k matrix ``mat`` on the ordered tuple
+    ``targets`` (little-endian, §II) of the canonical-order state ``psi``."""
+    assert psi.dtype == np.complex128 and psi.flags.c_contiguous
+    n = int(psi.size).bit_length() - 1
+    k = len(targets)
+    m = np.ascontiguousarray(mat, dtype=np.complex128)
+    assert m.shape == (1 << k, 1 << k)
+    t = (ctypes.c_int * k)(*[int(q) for q in targets])
+    rc = lib().orc_apply(_dptr(psi.view(np.float64)), n, t, k, _dptr(m.view(np.float64)))
+    if rc != 0:
+        raise ValueError("oracle apply: invalid arguments")
+
+
+def run_circuit(n: int, ops: Iterable, psi: np.ndarray | None = None) -> np.ndarray:
+    """Apply ``ops`` (objects with ``.targets`` and ``.matrix``) in order."""
+    if psi is None:
+        psi = zero_state(n)
+    for op in ops:
+        apply(psi, op.targets, op.matrix)
+    return psi
+
+
+def probabilities(psi: np.ndarray) -> np.ndarray:
+    n = int(psi.size).bit_length() - 1
+    p = np.empty(psi.size, dtype=np.float64)
+    lib().orc_probabilities(_dptr(np.ascontiguousarray(psi).view(np.float64)), n, _dptr(p))
+    return p
+
+
+def expect_z(psi: np.ndarray, mask: int) -> float:
+    n = int(psi.size).bit_length() - 1
+    return float(lib().orc_expect_z(_dptr(np.ascontiguousarray(psi).view(np.float64)), n, ctypes.c_uint64(mask)))
+
+
+def philox4x64_10(ctr: Sequence[int], key: Sequence[int]) -> List[int]:
+    c = (ctypes.c_uint64 * 4)(*[int(v) & (2**64 - 1) for v in ctr])
+    k = (ctypes.c_uint64 * 2)(*[int(v) & (2**64 - 1) for v in key])
+    o = (ctypes.c_uint64 * 4)()
+    lib().orc_philox4x64_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def sample(psi_logical: np.ndarray, phys_of_logical: Sequence[int], shots: int, seed: int, stream: int = 0,
+           near_frac: float = 0.0) -> Tuple[np.ndarray, np.ndarray]:
+    """Per-shot logical outcomes and near-boundary flags (see qsa_oracle.c)."""
+    psi = np.ascontiguousarray(psi_logical, dtype=np.complex128)
+    n = int(psi.size).bit_length() - 1
+    lay = (ctypes.c_int * n)(*[int(v) for v in phys_of_logical])
+    out = np.empty(shots, dtype=np.uint64)
+    flg = np.empty(shots, dtype=np.uint8)
+    rc = lib().orc_sample(_dptr(psi.view(np.float64)), n, lay, shots, seed, stream, near_frac,
+                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                          flg.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    if rc != 0:
+        raise ValueError("oracle sample: all weights are zero")
+    return out, flg.astype(bool)
+
+
+def sample_counts(psi_logical, phys_of_logical, shots, seed, stream=0):
+    out, _ = sample(psi_logical, phys_of_logical, shots, seed, stream)
+    vals, cnts = np.unique(out, return_counts=True)
+    return vals.astype(np.uint64), cnts.astype(np.uint64)
+
+
+# ---------------------------------------------------------------------------
+# Independent full-matrix construction (for pins at N <= 8)
+# ---------------------------------------------------------------------------
+
+def full_operator(n: int, targets: Sequence[int], mat: np.ndarray) -> np.ndarray:
+    """The 2^n x 2^n operator of ``mat`` on ``targets`` built as
+    P^T (I_{2^(n-k)} kron G) P, where P is the basis permutation that moves
+    qubit q_j to bit j and the remaining qubits, in increasing order, to bits
+    k..n-1.  Built from np.kron and an explicit permutation matrix, not from
+    the gather/scatter loop of ``apply``."""
+    k = len(targets)
+    rest = [q for q in range(n) if q not in targets]
+    order = list(targets) + rest  # new bit i holds old qubit order[i]
+    dim = 1 << n
+    P = np.zeros((dim, dim))
+    for x in range(dim):
+        y = 0
+        for i, q in enumerate(order):
+            if (x >> q) & 1:
+                y |= 1 << i
+        P[y, x] = 1.0
+    big = np.kron(np.eye(1 << (n - k)), np.asarray(mat, dtype=np.complex128))
+    return P.T @ big @ P
+
+
+# ---------------------------------------------------------------------------
+# Fusion: embedding, block product, partitions (§IV-C)
+# ---------------------------------------------------------------------------
+
+def kron_embed(mat: np.ndarray, gate_targets: Sequence[int], block_targets: Sequence[int]) -> np.ndarray:
+    """Matrix of a gate on ``gate_targets`` as an operator on the ordered
+    tuple ``block_targets`` (⊇ gate_targets), entry by entry from the
+    definition: E[r][c] = G[r_g][c_g] when r and c agree on every block bit
+    that is not a gate target, else 0, where r_g collects the bits of r at the
+    block positions of the gate's targets, in the gate's order."""
+    u = len(block_targets)
+    pos = [list(block_targets).index(q) for q in gate_targets]
+    other = [i for i in range(u) if i not in pos]
+    D = 1 << u
+    E = np.zeros((D, D), dtype=np.complex128)
+    for r in range(D):
+        for c in range(D):
+            if any(((r >> i) & 1) != ((c >> i) & 1) for i in other):
+                continue
+            rg = sum(((r >> p) & 1) << j for j, p in enumerate(pos))
+            cg = sum(((c >> p) & 1) << j for j, p in enumerate(pos))
+            E[r, c] = mat[rg, cg]
+    return E
+
+
+def block_product(gates: Sequence, block_targets: Sequence[int]) -> np.ndarray:
+    """Product of the gates of one block in circuit order, later gates on the
+    left (§IV-C)."""
+    D = 1 << len(block_targets)
+    M = np.eye(D, dtype=np.complex128)
+    for g in gates:
+        M = kron_embed(g.matrix, g.targets, block_targets) @ M
+    return M
+
+
+def gamma_score(width: int, diag: bool) -> float:
+    """gamma(k, dense) = 4^k, gamma(k, diag) = 1 (§IV-C)."""
+    return 1.0 if diag else float(4 ** width)
+
+
+def _block_width(gates, j, i):
+    s = set()
+    for g in gates[j:i]:
+        s.update(g.targets)
+    return len(s)
+
+
+def dp_window(gates: Sequence, kmax: int, kmax_diag: int, score=None) -> List[Tuple[int, int]]:
+    """Eq. dp-recurrence on one window g_0..g_{h-1}:
+        D_0 = 0,  D_i = min_{j in J_i} D_j + Gamma(B(j, i)),
+    J_i = {j < i : width(B(j,i)) <= cap(mode(B(j,i)))} ∪ {i-1}.  Ties take the
+    smallest j (longest final block).  Returns the blocks as (start, end)
+    half-open gate ranges, in order.  ``score(width, diag, gates_slice)``
+    replaces Gamma when given."""
+    h = len(gates)
+    INF = float("inf")
+    D = [0.0] + [INF] * h
+    arg = [0] * (h + 1)
+    for i in range(1, h + 1):
+        best, bj = INF, None
+        for j in range(0, i):
+            blk = gates[j:i]
+            w = _block_width(gates, j, i)
+            diag = all(g.diag for g in blk)
+            cap = kmax_diag if diag else kmax
+            if w > cap and j != i - 1:
+                continue
+            sc = gamma_score(w, diag) if score is None else score(w, diag, blk)
+            val = D[j] + sc
+            if val < best:  # strict: keeps the smallest j on ties
+                best, bj = val, j
+        D[i], arg[i] = best, bj
+    blocks = []
+    i = h
+    while i > 0:
+        j = arg[i]
+        blocks.append((j, i))
+        i = j
+    return blocks[::-1]
+
+
+def greedy_partition(gates: Sequence, kmax: int) -> List[Tuple[int, int]]:
+    """Plain width-limit heuristic: walk the gates in circuit order and extend
+    the current block while the union of targets stays within kmax; otherwise
+    close it.  A gate wider than kmax is a singleton."""
+    blocks = []
+    start, cur = 0, set()
+    for i, g in enumerate(gates):
+        nxt = cur | set(g.targets)
+        if i > start and len(nxt) > kmax:
+            blocks.append((start, i))
+            start, cur = i, set(g.targets)
+        else:
+            cur = nxt
+    if gates:
+        blocks.append((start, len(gates)))
+    return blocks
+
+
+# ---------------------------------------------------------------------------
+# Cost-model network (FP64): 37 -> 64 -> ReLU -> 64 -> ReLU -> 1
+# ---------------------------------------------------------------------------
+
+MLP_SHAPES = [(64, 37), (64,), (64, 64), (64,), (1, 64), (1,)]
+
+
+def mlp_forward(params: Sequence[np.ndarray], X: np.ndarray):
+    """y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 for each row x of X."""
+    W1, b1, W2, b2, W3, b3 = params
+    z1 = X @ W1.T + b1
+    a1 = np.maximum(z1, 0.0)
+    z2 = a1 @ W2.T + b2
+    a2 = np.maximum(z2, 0.0)
+    y = a2 @ W3.T + b3
+    return y[:, 0], (X, z1, a1, z2, a2)
+
+
+def mlp_loss_grad(params, X, t):
+    """L = mean((y - t)^2); returns L and dL/dparams by the chain rule."""
+    W1, b1, W2, b2, W3, b3 = params
+    y, (X, z1, a1, z2, a2) = mlp_forward(params, X)
+    n = X.shape[0]
+    L = float(np.mean((y - t) ** 2))
+    dy = 2.0 * (y - t) / n                  # (n,)
+    dW3 = dy[None, :] @ a2                   # (1,64)
+    db3 = np.array([dy.sum()])
+    da2 = dy[:, None] * W3                   # (n,64)
+    dz2 = da2 * (z2 > 0)
+    dW2 = dz2.T @ a1
+    db2 = dz2.sum(axis=0)
+    da1 = dz2 @ W2
+    dz1 = da1 * (z1 > 0)
+    dW1 = dz1.T @ X
+    db1 = dz1.sum(axis=0)
+    return L, [dW1, db1, dW2, db2, dW3, db3]
+
+
+def adam_step(params, grads, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2015, Algorithm 1), step number t >= 1."""
+    new_p, new_m, new_v = [], [], []
+    for p, g, mm, vv in zip(params, grads, m, v):
+        mm = b1 * mm + (1 - b1) * g
+        vv = b2 * vv + (1 - b2) * g * g
+        mh = mm / (1 - b1 ** t)
+        vh = vv / (1 - b2 ** t)
+        new_p.append(p - lr * mh / (np.sqrt(vh) + eps))
+        new_m.append(mm)
+        new_v.append(vv)
+    return new_p, new_m, new_v
+
+
+# ---------------------------------------------------------------------------
+# Fidelity metrics
+# ---------------------------------------------------------------------------
+
+def fidelity(psi_ref: np.ndarray, psi: np.ndarray) -> float:
+    """F = |<psi_ref|psi>|^2 in FP64."""
+    a = np.asarray(psi_ref, dtype=np.complex128)
+    b = np.asarray(psi, dtype=np.complex128)
+    return float(abs(np.vdot(a, b)) ** 2)
+
+
+def max_abs_diff(psi_ref: np.ndarray, psi: np.ndarray) -> float:
+    return float(np.max(np.abs(np.asarray(psi_ref, np.complex128) - np.asarray(psi, np.complex128))))
+
+
+# ---------------------------------------------------------------------------
+# Layout map (§II, §IV-B Alg. 2, §IV-D Theorem 1)
+# ---------------------------------------------------------------------------
+
+def decode_state(stored: np.ndarray, phys_of_logical: Sequence[int]) -> np.ndarray:
+    """Canonical logical state from a stored one: psi_x = stored[y] with
+    y_{L(q)} = x_q for every logical qubit q (Theorem 1, component form)."""
+    n = int(stored.size).bit_length() - 1
+    x = np.arange(stored.size, dtype=np.uint64)
+    y = np.zeros_like(x)
+    for q in range(n):
+        y |= ((x >> np.uint64(q)) & np.uint64(1)) << np.uint64(phys_of_logical[q])
+    return stored[y]
+
+
+def encode_state(psi: np.ndarray, phys_of_logical: Sequence[int]) -> np.ndarray:
+    """Inverse of decode_state: stored[y] = psi_x with y_{L(q)} = x_q."""
+    n = int(psi.size).bit_length() - 1
+    x = np.arange(psi.size, dtype=np.uint64)
+    y = np.zeros_like(x)
+    for q in range(n):
+        y |= ((x >> np.uint64(q)) & np.uint64(1)) << np.uint64(phys_of_logical[q])
+    out = np.empty_like(psi)
+    out[y] = psi
+    return out
+
+
+def lazy_ttgt(stored: np.ndarray, phys_of_logical: Sequence[int], targets: Sequence[int], mat: np.ndarray):
+    """Dense branch of Alg. 2 (lazy TTGT), out of place:
+    A = (L(q_0)..L(q_{k-1})); alpha_A sends A_j to position N-k+j and the
+    other positions, in increasing order, to 0..N-k-1; the data permutation
+    Pi_A moves bit b of every index to bit alpha_A(b); the result is viewed
+    as M (2^k x 2^(N-k), row = the top k bits), M' = G M, and L' = alpha_A∘L.
+    Returns (L', stored')."""
+    n = int(stored.size).bit_length() - 1
+    k = len(targets)
+    A = [phys_of_logical[q] for q in targets]
+    alpha = {}
+    for j, b in enumerate(A):
+        alpha[b] = n - k + j
+    rest = [b for b in range(n) if b not in A]
+    for i, b in enumerate(rest):
+        alpha[b] = i
+    y = np.arange(stored.size, dtype=np.uint64)
+    yp = np.zeros_like(y)
+    for b in range(n):
+        yp |= ((y >> np.uint64(b)) & np.uint64(1)) << np.uint64(alpha[b])
+    perm = np.empty_like(stored)
+    perm[yp] = stored
+    M = perm.reshape(1 << k, 1 << (n - k))
+    Mp = np.asarray(mat, dtype=np.complex128) @ M
+    Lp = [alpha[phys_of_logical[q]] for q in range(n)]
+    return Lp, Mp.reshape(-1).copy()
