@@ -1,0 +1,266 @@
+/*
+ * qsa.h — C ABI of libqsa, a GB300 (sm_103a) state-vector library that applies
+ * ordered fused k-qubit operators (k = 1..6) to a complex64 state vector whose
+ * qubits are placed by a logical-to-physical layout map.
+ *
+ * Paper: "QSimAdv" (arxiv 2608.16940).  Cited passages:
+ *   §II   "State and layout notation", "Fused gates and requests"
+ *   §III  (R2) apply(L, Psi, G, V) -> (L', Psi')
+ *   §IV-B Alg. 2 (axis-shifted / lazy-TTGT lowering), Eqs. cost-perm, cost-formal
+ *   §IV-C fusion score gamma, Eq. dp-recurrence, window W = 64, cross-window merge
+ *   §IV-D Theorem 1 (placement invariant), Alg. 3 (promotion dispatch), first-free
+ *   §IV-E "Sampling" (hierarchical CDF, strict upper bound), App. B numerics
+ *
+ * Conventions shared by every call
+ *   - A state of N qubits holds 2^N amplitudes; amplitude y is stored as two
+ *     floats (Re, Im) at byte offset 8*y of one device buffer.  Bit p of y is
+ *     physical position p, position 0 least significant (§II).
+ *   - The layout map L sends logical qubit q to physical position L(q); it is
+ *     a bijection on 0..N-1.  The stored amplitude at y equals the logical one
+ *     at x with x_q = y_{L(q)} (Theorem 1).  New states have L = identity.
+ *   - A k-qubit matrix G acts on the ordered logical tuple V = (q_0..q_{k-1});
+ *     q_j supplies bit j of G's row and column index (little-endian in V, §II).
+ *     Matrices are passed as 2*4^k doubles, row-major G[r][c], interleaved
+ *     (Re, Im); the library rounds them once to FP32.
+ *   - Host pointers are read before the call returns (the caller keeps
+ *     ownership).  Device pointers are borrowed, never freed by the library.
+ *   - Kernels run on the state's CUDA stream (a cudaStream_t passed as void*;
+ *     NULL = legacy default stream).  apply / permute calls are asynchronous;
+ *     calls that return numbers to host memory synchronise that stream.
+ *   - Every call returns qsa_status; on failure qsa_last_error() gives a
+ *     message (thread-local).  Arguments are validated before any launch.
+ *     After QSA_E_CUDA the state is marked failed and later calls on it
+ *     return QSA_E_STATE.
+ */
+#ifndef QSA_H
+#define QSA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QSA_OK = 0,
+    QSA_E_ARG = 1,          /* invalid argument (range, duplicate target, NULL, non-bijection) */
+    QSA_E_RANGE = 2,        /* output capacity too small; the needed size is reported */
+    QSA_E_NOMEM = 3,        /* device allocation failed */
+    QSA_E_CUDA = 4,         /* a CUDA call or kernel failed; the state is marked failed */
+    QSA_E_TIMEOUT = 5,      /* a device-side work budget ran out (the kernel returned early) */
+    QSA_E_UNSUPPORTED = 6,  /* valid request this build does not implement (e.g. complex128) */
+    QSA_E_STATE = 7         /* call not allowed in the state's current condition */
+} qsa_status;
+
+typedef enum { QSA_C64 = 0, QSA_C128 = 1 /* reserved: QSA_E_UNSUPPORTED */ } qsa_dtype;
+
+typedef struct qsa_state_s* qsa_state;
+
+#define QSA_MAX_QUBITS 34
+#define QSA_MAX_K 6
+
+/* Lowering of one fused dense operator (§III R4: the backend picks the
+ * concrete kernel once the physical targets are known). */
+typedef enum {
+    QSA_LOWER_AUTO = 0,     /* strided in-place gather unless the cost model says otherwise */
+    QSA_LOWER_STRIDED = 1,  /* gather the 2^k group straight from any physical positions */
+    QSA_LOWER_PERMUTE = 2   /* first promote targets outside the in-block bits by bit swaps
+                               (first-free victims, §IV-D), keep the new layout, then apply */
+} qsa_lowering;
+
+typedef enum {
+    QSA_PREC_FP32 = 0,      /* FP32 CUDA-core complex matvec */
+    QSA_PREC_TF32X3 = 1     /* k = 5, 6: split-TF32 (3 products) on tcgen05 tensor cores with
+                               FP32 accumulation; k < 5 falls back to FP32 */
+} qsa_precision;
+
+typedef enum {
+    QSA_PLAN_PER_GATE = 0,  /* no fusion: one pass per input op */
+    QSA_PLAN_GREEDY = 1,    /* width-limit greedy in circuit order */
+    QSA_PLAN_DP = 2,        /* Eq. dp-recurrence with gamma = 4^k (dense) / 1 (diag) */
+    QSA_PLAN_DP_MLP = 3     /* the same DP scored by the cost model's predicted seconds;
+                               falls back to QSA_PLAN_GREEDY when no model is loaded */
+} qsa_planner;
+
+#define QSA_OP_DIAG 1u      /* op is diagonal (eligible for the diagonal block mode, §IV-C) */
+
+/* One circuit operation: G on the ordered logical targets[0..k-1]. */
+typedef struct {
+    int32_t k;              /* 1..6 */
+    int32_t targets[QSA_MAX_K];
+    const double* matrix;   /* host, 2*4^k doubles, layout as above */
+    uint32_t flags;         /* QSA_OP_DIAG or 0 */
+} qsa_op;
+
+typedef struct {
+    int32_t planner;        /* qsa_planner */
+    int32_t kmax;           /* dense fusion cap, 1..6 */
+    int32_t kmax_diag;      /* diagonal-block cap, 1..kmax */
+    int32_t window;         /* DP window W (§IV-C uses 64) */
+    int32_t rounds;         /* fuse pipeline repeats, 1..4 (§IV-C: at most four) */
+    int32_t precision;      /* qsa_precision for k >= 5 blocks */
+    int32_t lowering;       /* qsa_lowering */
+    int32_t timing;         /* 1: time every launch with CUDA events (fills *_seconds) */
+} qsa_plan_opts;
+
+typedef struct {
+    double seconds;         /* device time of all launches (timing = 1), else 0 */
+    double apply_seconds;   /* device time of fused-operator kernels */
+    double permute_seconds; /* device time of permutation kernels */
+    double hbm_bytes;       /* algorithmic HBM bytes: 16 B x 2^N per full-state pass */
+    uint64_t blocks;        /* fused blocks applied */
+    uint64_t passes;        /* full-state passes (applies + permutations) */
+    uint64_t permutes;      /* permutation passes */
+    uint64_t tc_blocks;     /* blocks run on the tensor-core path */
+    uint64_t launches;      /* kernel launches issued */
+    double h2d_bytes;       /* host-to-device bytes copied by the call (fused matrices) */
+} qsa_run_stats;
+
+/* A compiled circuit: the planner's blocks with their fused FP32 matrices. */
+typedef struct qsa_plan_s* qsa_plan;
+
+/* ---- state lifecycle (§II; §III R2) ---------------------------------------- */
+
+/* Allocate a 2^N-amplitude state (library-owned device memory) set to |0..0>
+ * with identity layout, on the legacy default stream.  N in 1..34.
+ * Errors: QSA_E_ARG (N, out NULL), QSA_E_UNSUPPORTED (dtype != QSA_C64),
+ * QSA_E_NOMEM. */
+qsa_status qsa_state_create(int n_qubits, qsa_dtype dtype, qsa_state* out);
+
+/* Wrap a caller-owned device buffer of >= 8*2^N bytes (16-byte aligned) that
+ * must outlive the state.  init_zero = 1 writes |0..0>; 0 keeps the buffer's
+ * contents as the initial stored state (identity layout).  cuda_stream is
+ * the stream all kernels of this state run on. */
+qsa_status qsa_state_create_ex(int n_qubits, qsa_dtype dtype, void* dev_buf, size_t bytes,
+                               void* cuda_stream, int init_zero, qsa_state* out);
+
+/* Free library-owned memory and the handle (synchronises its stream). */
+qsa_status qsa_state_destroy(qsa_state s);
+
+/* Change the stream used by later calls. */
+qsa_status qsa_set_stream(qsa_state s, void* cuda_stream);
+
+/* |0..0> and identity layout (clears a failed mark only if the device is healthy). */
+qsa_status qsa_state_reset(qsa_state s);
+
+/* Number of qubits, and the device address of the amplitudes. */
+qsa_status qsa_state_info(qsa_state s, int* n_qubits, void** dev_amplitudes);
+
+/* ---- layout map (§II, §IV-D Theorem 1) ------------------------------------- */
+
+/* Install layout phys_of_logical[q] = L(q) (N entries, a bijection, else
+ * QSA_E_ARG).  materialise = 1 moves the amplitudes so the logical state is
+ * unchanged (permutation passes).  materialise = 0 only relabels, which is
+ * valid only while the state is known to be |0..0> (§IV-D: a metadata-only
+ * relabel is valid for the permutation-invariant initial state); otherwise
+ * QSA_E_STATE. */
+qsa_status qsa_set_layout(qsa_state s, const int32_t* phys_of_logical, int materialise);
+
+/* Copy the current layout into phys_of_logical[0..N-1]. */
+qsa_status qsa_get_layout(qsa_state s, int32_t* phys_of_logical);
+
+/* The qubit-permutation kernel (single-GPU promotion, Alg. 3 with rank bits
+ * read as out-of-block bits; Lemma "distributed promotion swap"): swap
+ * physical bit positions phys_a[i] <-> phys_b[i] for i < n_pairs in place and
+ * compose the layout with the same transpositions.  Positions must be
+ * distinct across all pairs (QSA_E_ARG).  Pure data movement: bit-exact. */
+qsa_status qsa_permute_bits(qsa_state s, const int32_t* phys_a, const int32_t* phys_b, int n_pairs);
+
+/* ---- fused operator (§III R2, Alg. 2) --------------------------------------- */
+
+/* apply(L, Psi, G, V) -> (L', Psi'): resolve A = (L(q_0)..L(q_{k-1})) and
+ * apply G in V's little-endian order.  targets: k distinct logical qubits
+ * (host); matrix: host, 2*4^k doubles.  Uses QSA_LOWER_AUTO and FP32.
+ * Errors: QSA_E_ARG (k outside 1..6 or > N, bad / repeated target, NULL). */
+qsa_status qsa_apply_fused(qsa_state s, const int32_t* targets, int k, const double* matrix);
+
+/* As qsa_apply_fused with an explicit lowering (qsa_lowering) and precision
+ * (qsa_precision).  QSA_LOWER_PERMUTE may change the layout (L' = tau o L). */
+qsa_status qsa_apply_fused_ex(qsa_state s, const int32_t* targets, int k, const double* matrix,
+                              int lowering, int precision);
+
+/* ---- circuits: fusion planning + execution (§IV-C) ------------------------- */
+
+/* Fill *opts with the defaults: DP planner, kmax 4, kmax_diag 4, window 64,
+ * rounds 4, FP32, AUTO lowering, timing off. */
+void qsa_plan_opts_default(qsa_plan_opts* opts);
+
+/* Host only (no GPU needed): partition ops[0..n_ops-1] into consecutive
+ * fused blocks with the planner in *opts (NULL = defaults).  block_start
+ * receives the first op index of each block (capacity n_ops entries);
+ * *n_blocks the number of blocks.  Blocks may cover several input ops after
+ * the merge / repeat rounds.  Errors: QSA_E_ARG. */
+qsa_status qsa_plan_circuit(const qsa_op* ops, size_t n_ops, int n_qubits, const qsa_plan_opts* opts,
+                            size_t* block_start, size_t* n_blocks);
+
+/* Host only: the fused matrix of ops[0..n_ops-1] in circuit order (later ops
+ * multiplied on the left, §IV-C), on the ordered logical tuple
+ * block_targets_out (the union of the ops' targets, ascending; at most 6).
+ * matrix_out: 2*4^u doubles.  *width_out = u.  Errors: QSA_E_ARG (union > 6). */
+qsa_status qsa_fuse_ops(const qsa_op* ops, size_t n_ops, int32_t* block_targets_out, int* width_out,
+                        double* matrix_out);
+
+/* Plan (as qsa_plan_circuit), fuse and apply the circuit to s.  stats may be
+ * NULL.  With opts->timing = 1 the call synchronises at the end and fills the
+ * device times.  Equivalent to qsa_plan_create + qsa_plan_execute +
+ * qsa_plan_destroy with the state's current layout. */
+qsa_status qsa_apply_circuit(qsa_state s, const qsa_op* ops, size_t n_ops, const qsa_plan_opts* opts,
+                             qsa_run_stats* stats);
+
+/* Host only: plan and fuse once (§IV-C; the paper's timer excludes plan
+ * construction, App. B).  layout (N entries, nullable = identity) is the
+ * layout the DP-MLP scores assume.  The plan copies everything it needs from
+ * ops.  Errors: as qsa_plan_circuit. */
+qsa_status qsa_plan_create(const qsa_op* ops, size_t n_ops, int n_qubits, const qsa_plan_opts* opts,
+                           const int32_t* layout, qsa_plan* out);
+
+/* Number of fused blocks and input ops, widest block, bytes of fused FP32 matrices. */
+qsa_status qsa_plan_info(qsa_plan p, size_t* n_blocks, size_t* n_ops, int* max_width, size_t* matrix_bytes);
+
+/* First input op and width of every block (capacity >= n_blocks, else QSA_E_RANGE). */
+qsa_status qsa_plan_blocks(qsa_plan p, size_t* first_op, int32_t* widths, size_t capacity);
+
+/* Apply the plan's blocks to s in order (asynchronous unless opts.timing).
+ * The first execution on a device uploads the fused matrices once
+ * (stats->h2d_bytes).  Errors: QSA_E_ARG if the plan's N differs from s. */
+qsa_status qsa_plan_execute(qsa_state s, qsa_plan p, qsa_run_stats* stats);
+
+/* Free the plan (synchronises the device if matrices were uploaded). */
+qsa_status qsa_plan_destroy(qsa_plan p);
+
+/* Total kernels launched on this state since creation. */
+qsa_status qsa_state_counters(qsa_state s, uint64_t* launches);
+
+/* ---- outputs (§IV-E "Sampling", App. B "Numerical configuration") ----------- */
+
+/* p_x = |psi_x|^2 in FP64 for every LOGICAL index x (decoded through L),
+ * written to out_host (2^N doubles, may be NULL), and the FP64 norm
+ * sum_x p_x to *norm_out (may be NULL).  Synchronises. */
+qsa_status qsa_probabilities(qsa_state s, double* out_host, double* norm_out);
+
+/* As qsa_probabilities but writes to a device buffer of 2^N doubles. */
+qsa_status qsa_probabilities_device(qsa_state s, double* out_dev, double* norm_out);
+
+/* <Z_mask> = sum_x (-1)^{popcount(x & logical_mask)} p_x (FP64 accumulation);
+ * logical_mask = 0 gives the norm.  Synchronises. */
+qsa_status qsa_expectation_z(qsa_state s, uint64_t logical_mask, double* out);
+
+/* Draw `shots` outcomes (§IV-E): weights P_y = trunc(p_y * 2^62) (integer,
+ * so the CDF does not depend on summation order) over physical indices in
+ * 2^10-amplitude blocks; shot i draws Philox4x64-10(ctr = (i, 0, 0, 0),
+ * key = (seed, 0)).word0 mod total and takes the first physical index whose
+ * cumulative weight is strictly greater (a zero-weight bin is never drawn);
+ * the outcome is decoded to the logical bitstring through L (§IV-D).
+ * Results: distinct logical outcomes ascending in outcomes[], their counts in
+ * counts[], *n_distinct.  If capacity < n_distinct: QSA_E_RANGE with
+ * *n_distinct set and nothing written.  shots in 1..2^26.  Synchronises. */
+qsa_status qsa_sample_counts(qsa_state s, uint64_t shots, uint64_t seed, uint64_t* outcomes, uint64_t* counts,
+                             size_t capacity, size_t* n_distinct);
+
+const char* qsa_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSA_H */

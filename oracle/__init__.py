@@ -395,3 +395,58 @@ def lazy_ttgt(stored: np.ndarray, phys_of_logical: Sequence[int], targets: Seque
     Mp = np.asarray(mat, dtype=np.complex128) @ M
     Lp = [alpha[phys_of_logical[q]] for q in range(n)]
     return Lp, Mp.reshape(-1).copy()
+
+
+def merge_adjacent(blocks, kmax: int, kmax_diag: int, score=None):
+    """Cross-window greedy merge (§IV-C, reading: merge neighbours a, b when
+    width(a ∪ b) fits the cap of the merged mode and
+    Gamma(a ∪ b) <= Gamma(a) + Gamma(b)).  ``blocks`` are dicts with keys
+    targets (set), diag, s, e (input op range)."""
+    sc = score if score is not None else (lambda w, d, t: gamma_score(w, d))
+    out = []
+    cur = None
+    for b in blocks:
+        if cur is None:
+            cur = dict(b)
+            continue
+        t = cur["targets"] | b["targets"]
+        d = cur["diag"] and b["diag"]
+        cap = kmax_diag if d else kmax
+        if len(t) <= cap and sc(len(t), d, t) <= sc(len(cur["targets"]), cur["diag"], cur["targets"]) + \
+                sc(len(b["targets"]), b["diag"], b["targets"]):
+            cur = {"targets": t, "diag": d, "s": cur["s"], "e": b["e"]}
+        else:
+            out.append(cur)
+            cur = dict(b)
+    if cur is not None:
+        out.append(cur)
+    return out
+
+
+def fuse_pipeline(gates, kmax: int, kmax_diag: int, window: int = 64, rounds: int = 4, score=None):
+    """Windows of ``window`` units partitioned by Eq. dp-recurrence, then the
+    cross-window merge; the pipeline is repeated on the resulting blocks at
+    most ``rounds`` times and stops when the block count no longer falls
+    (§IV-C).  Returns the first input-op index of every block."""
+
+    class U:
+        def __init__(self, targets, diag, s, e):
+            self.targets, self.diag, self.s, self.e = tuple(sorted(targets)), diag, s, e
+
+    units = [U(g.targets, bool(g.diag), i, i + 1) for i, g in enumerate(gates)]
+    wscore = None if score is None else (lambda w, d, blk: score(w, d, set().union(*[set(b.targets) for b in blk])))
+    for rnd in range(rounds):
+        blocks = []
+        for b0 in range(0, len(units), window):
+            win = units[b0:b0 + window]
+            for j, i in dp_window(win, kmax, kmax_diag, score=wscore):
+                t = set()
+                for u in win[j:i]:
+                    t |= set(u.targets)
+                blocks.append({"targets": t, "diag": all(u.diag for u in win[j:i]), "s": win[j].s,
+                               "e": win[i - 1].e})
+        blocks = merge_adjacent(blocks, kmax, kmax_diag, score)
+        if rnd > 0 and len(blocks) >= len(units):
+            break
+        units = [U(b["targets"], b["diag"], b["s"], b["e"]) for b in blocks]
+    return [u.s for u in units]

@@ -25,6 +25,7 @@
 #include <stddef.h>
 #include <stdlib.h>
 #include <string.h>
+#include <math.h>
 
 #define ORC_OK 0
 #define ORC_EARG 1
@@ -136,9 +137,11 @@ void orc_philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2], uint6
  * never chosen, then decode the logical outcome through the layout map.
  *
  * Reading fixed here (the paper keeps FP64 block sums, whose value depends on
- * the summation order): the weight of a physical index is the fixed-point
- * integer P_y = trunc((re^2 + im^2) * 2^62), each square and the sum rounded
- * once in FP64; the CDF is the integer prefix sum C_y = sum_{y' <= y} P_y'.
+ * the summation order): the weight of a physical index is the integer
+ * P_y = floor(re^2 * 2^60) + floor(im^2 * 2^60), each term the exact square
+ * truncated to 60 fractional bits (|amplitude| < 2 assumed); the CDF is the
+ * integer prefix sum C_y = sum_{y' <= y} P_y', so it is exact and independent
+ * of summation order.
  * Shot s of stream t draws r = Philox4x64-10(ctr = (s, t, 0, 0),
  * key = (seed, 0)).word0, u = r mod C_last, and takes the first y with
  * C_y > u.  The logical outcome x has x_q = y_{L(q)}.
@@ -146,10 +149,24 @@ void orc_philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2], uint6
  *   amps_logical: FP64 interleaved amplitudes in canonical logical order;
  *   phys_of_logical: L(q) for q < n; the physical amplitude at index y is the
  *                    logical one at decode(y).
- *   near_frac: a draw is flagged when u lies within near_frac * 2^62 of the
+ *   near_frac: a draw is flagged when u lies within near_frac * 2^60 of the
  *              cumulative value on either side of the chosen bin.
  * Returns ORC_OK, or ORC_EARG if every weight is zero.
  */
+/* floor(v^2 * 2^60) exactly: v = M * 2^(e-53) with a 53-bit integer M, so
+ * v^2 * 2^60 = M^2 * 2^(2e-46), formed in 128-bit integers. */
+static uint64_t sq_fixed60(double v) {
+    if (v == 0.0) return 0;
+    int e;
+    double fr = frexp(fabs(v), &e);                 /* fr in [0.5, 1) */
+    uint64_t M = (uint64_t)ldexp(fr, 53);           /* exact */
+    unsigned __int128 sq = (unsigned __int128)M * (unsigned __int128)M;
+    int s = 2 * e - 46;
+    if (s >= 0) return (uint64_t)(sq << s);
+    if (-s >= 128) return 0;
+    return (uint64_t)(sq >> (-s));
+}
+
 static uint64_t decode_phys(uint64_t y, const int* phys_of_logical, int n) {
     uint64_t x = 0;
     for (int q = 0; q < n; ++q)
@@ -163,18 +180,16 @@ int orc_sample(const double* amps_logical, int n, const int* phys_of_logical,
     const uint64_t dim = (uint64_t)1 << n;
     uint64_t* cum = (uint64_t*)malloc(sizeof(uint64_t) * dim);
     if (!cum) return ORC_EARG;
-    const double two62 = 4611686018427387904.0; /* 2^62 */
+    const double two60 = 1152921504606846976.0; /* 2^60 */
     uint64_t run = 0;
     for (uint64_t y = 0; y < dim; ++y) {
         uint64_t x = decode_phys(y, phys_of_logical, n);
-        double re = amps_logical[2 * x], im = amps_logical[2 * x + 1];
-        double p = re * re + im * im;
-        run += (uint64_t)(p * two62);
+        run += sq_fixed60(amps_logical[2 * x]) + sq_fixed60(amps_logical[2 * x + 1]);
         cum[y] = run;
     }
     const uint64_t total = run;
     if (total == 0) { free(cum); return ORC_EARG; }
-    const double near_abs = near_frac * two62;
+    const double near_abs = near_frac * two60;
     for (uint64_t s = 0; s < shots; ++s) {
         uint64_t ctr[4] = {s, stream, 0, 0}, key[2] = {seed, 0}, out[4];
         orc_philox4x64_10(ctr, key, out);

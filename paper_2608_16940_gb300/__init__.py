@@ -1,0 +1,364 @@
+"""Thin ctypes binding of libqsa (include/qsa.h).
+
+Each function has the name of the C entry point it wraps and only marshals
+arguments: numpy arrays become host pointers, integers stand for device
+pointers and CUDA streams (for example ``tensor.data_ptr()`` and
+``torch.cuda.current_stream().cuda_stream``).  All arithmetic runs in the
+library's CUDA kernels; there is no fallback.  Importing this package raises
+if libqsa.so has not been built (``paper_2608_16940_gb300.build.build()``).
+
+Status codes other than QSA_OK raise :class:`QsaError` carrying the code and
+``qsa_last_error()``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Iterable, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqsa.so")
+
+QSA_OK, QSA_E_ARG, QSA_E_RANGE, QSA_E_NOMEM, QSA_E_CUDA, QSA_E_TIMEOUT, QSA_E_UNSUPPORTED, QSA_E_STATE = range(8)
+QSA_C64, QSA_C128 = 0, 1
+QSA_LOWER_AUTO, QSA_LOWER_STRIDED, QSA_LOWER_PERMUTE = 0, 1, 2
+QSA_PREC_FP32, QSA_PREC_TF32X3 = 0, 1
+QSA_PLAN_PER_GATE, QSA_PLAN_GREEDY, QSA_PLAN_DP, QSA_PLAN_DP_MLP = 0, 1, 2, 3
+QSA_OP_DIAG = 1
+MLP_PARAMS = 6657
+MLP_IN = 37
+
+
+class QsaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"qsa status {code}: {msg}")
+        self.code = code
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_2608_16940_gb300.build.build()")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_c = ctypes
+_dp = _c.POINTER(_c.c_double)
+_fp = _c.POINTER(_c.c_float)
+_i32p = _c.POINTER(_c.c_int32)
+_u64p = _c.POINTER(_c.c_uint64)
+_szp = _c.POINTER(_c.c_size_t)
+
+
+class qsa_op(_c.Structure):
+    _fields_ = [("k", _c.c_int32), ("targets", _c.c_int32 * 6), ("matrix", _dp), ("flags", _c.c_uint32)]
+
+
+class qsa_plan_opts(_c.Structure):
+    _fields_ = [("planner", _c.c_int32), ("kmax", _c.c_int32), ("kmax_diag", _c.c_int32), ("window", _c.c_int32),
+                ("rounds", _c.c_int32), ("precision", _c.c_int32), ("lowering", _c.c_int32),
+                ("timing", _c.c_int32)]
+
+
+class qsa_run_stats(_c.Structure):
+    _fields_ = [("seconds", _c.c_double), ("apply_seconds", _c.c_double), ("permute_seconds", _c.c_double),
+                ("hbm_bytes", _c.c_double), ("blocks", _c.c_uint64), ("passes", _c.c_uint64),
+                ("permutes", _c.c_uint64), ("tc_blocks", _c.c_uint64), ("launches", _c.c_uint64),
+                ("h2d_bytes", _c.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def _sig(name, args, res=_c.c_int):
+    f = getattr(_lib, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+_vp = _c.c_void_p
+_f = {
+    "qsa_state_create": _sig("qsa_state_create", [_c.c_int, _c.c_int, _c.POINTER(_vp)]),
+    "qsa_state_create_ex": _sig("qsa_state_create_ex", [_c.c_int, _c.c_int, _vp, _c.c_size_t, _vp, _c.c_int,
+                                                        _c.POINTER(_vp)]),
+    "qsa_state_destroy": _sig("qsa_state_destroy", [_vp]),
+    "qsa_set_stream": _sig("qsa_set_stream", [_vp, _vp]),
+    "qsa_state_reset": _sig("qsa_state_reset", [_vp]),
+    "qsa_state_info": _sig("qsa_state_info", [_vp, _c.POINTER(_c.c_int), _c.POINTER(_vp)]),
+    "qsa_set_layout": _sig("qsa_set_layout", [_vp, _i32p, _c.c_int]),
+    "qsa_get_layout": _sig("qsa_get_layout", [_vp, _i32p]),
+    "qsa_permute_bits": _sig("qsa_permute_bits", [_vp, _i32p, _i32p, _c.c_int]),
+    "qsa_apply_fused": _sig("qsa_apply_fused", [_vp, _i32p, _c.c_int, _dp]),
+    "qsa_apply_fused_ex": _sig("qsa_apply_fused_ex", [_vp, _i32p, _c.c_int, _dp, _c.c_int, _c.c_int]),
+    "qsa_plan_opts_default": _sig("qsa_plan_opts_default", [_c.POINTER(qsa_plan_opts)], None),
+    "qsa_plan_circuit": _sig("qsa_plan_circuit", [_c.POINTER(qsa_op), _c.c_size_t, _c.c_int,
+                                                  _c.POINTER(qsa_plan_opts), _szp, _szp]),
+    "qsa_fuse_ops": _sig("qsa_fuse_ops", [_c.POINTER(qsa_op), _c.c_size_t, _i32p, _c.POINTER(_c.c_int), _dp]),
+    "qsa_apply_circuit": _sig("qsa_apply_circuit", [_vp, _c.POINTER(qsa_op), _c.c_size_t,
+                                                    _c.POINTER(qsa_plan_opts), _c.POINTER(qsa_run_stats)]),
+    "qsa_plan_create": _sig("qsa_plan_create", [_c.POINTER(qsa_op), _c.c_size_t, _c.c_int,
+                                                _c.POINTER(qsa_plan_opts), _i32p, _c.POINTER(_vp)]),
+    "qsa_plan_info": _sig("qsa_plan_info", [_vp, _szp, _szp, _c.POINTER(_c.c_int), _szp]),
+    "qsa_plan_blocks": _sig("qsa_plan_blocks", [_vp, _szp, _i32p, _c.c_size_t]),
+    "qsa_plan_execute": _sig("qsa_plan_execute", [_vp, _vp, _c.POINTER(qsa_run_stats)]),
+    "qsa_plan_destroy": _sig("qsa_plan_destroy", [_vp]),
+    "qsa_state_counters": _sig("qsa_state_counters", [_vp, _u64p]),
+    "qsa_probabilities": _sig("qsa_probabilities", [_vp, _dp, _dp]),
+    "qsa_probabilities_device": _sig("qsa_probabilities_device", [_vp, _vp, _dp]),
+    "qsa_expectation_z": _sig("qsa_expectation_z", [_vp, _c.c_uint64, _dp]),
+    "qsa_sample_counts": _sig("qsa_sample_counts", [_vp, _c.c_uint64, _c.c_uint64, _u64p, _u64p, _c.c_size_t,
+                                                    _szp]),
+    "qsa_last_error": _sig("qsa_last_error", [], _c.c_char_p),
+    "qsa_costmodel_features": _sig("qsa_costmodel_features", [_c.c_int, _c.c_uint64, _c.c_int, _c.c_int, _fp]),
+    "qsa_costmodel_set": _sig("qsa_costmodel_set", [_fp]),
+    "qsa_costmodel_predict": _sig("qsa_costmodel_predict", [_fp, _c.c_size_t, _dp]),
+}
+
+
+def _optional(name, args, res=_c.c_int):
+    if hasattr(_lib, name):
+        _f[name] = _sig(name, args, res)
+
+
+def qsa_last_error() -> str:
+    v = _f["qsa_last_error"]()
+    return v.decode() if v else ""
+
+
+def _check(code: int) -> None:
+    if code != QSA_OK:
+        raise QsaError(code, qsa_last_error())
+
+
+def _i32(seq) -> Tuple[object, object]:
+    a = np.ascontiguousarray(np.asarray(seq, dtype=np.int32))
+    return a, a.ctypes.data_as(_i32p)
+
+
+def _cmat(m) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(m, dtype=np.complex128))
+
+
+# ---- state ----------------------------------------------------------------
+
+def qsa_state_create(n_qubits: int, dtype: int = QSA_C64) -> int:
+    h = _vp()
+    _check(_f["qsa_state_create"](n_qubits, dtype, _c.byref(h)))
+    return h.value
+
+
+def qsa_state_create_ex(n_qubits: int, dev_ptr: int, nbytes: int, stream: int = 0, init_zero: int = 1,
+                        dtype: int = QSA_C64) -> int:
+    h = _vp()
+    _check(_f["qsa_state_create_ex"](n_qubits, dtype, _vp(dev_ptr), nbytes, _vp(stream), init_zero, _c.byref(h)))
+    return h.value
+
+
+def qsa_state_destroy(s: int) -> None:
+    _check(_f["qsa_state_destroy"](_vp(s)))
+
+
+def qsa_set_stream(s: int, stream: int) -> None:
+    _check(_f["qsa_set_stream"](_vp(s), _vp(stream)))
+
+
+def qsa_state_reset(s: int) -> None:
+    _check(_f["qsa_state_reset"](_vp(s)))
+
+
+def qsa_state_info(s: int) -> Tuple[int, int]:
+    n = _c.c_int()
+    p = _vp()
+    _check(_f["qsa_state_info"](_vp(s), _c.byref(n), _c.byref(p)))
+    return n.value, p.value
+
+
+def qsa_set_layout(s: int, phys_of_logical: Sequence[int], materialise: int = 1) -> None:
+    a, p = _i32(phys_of_logical)
+    _check(_f["qsa_set_layout"](_vp(s), p, materialise))
+
+
+def qsa_get_layout(s: int) -> List[int]:
+    n, _ = qsa_state_info(s)
+    a = np.zeros(n, dtype=np.int32)
+    _check(_f["qsa_get_layout"](_vp(s), a.ctypes.data_as(_i32p)))
+    return [int(v) for v in a]
+
+
+def qsa_permute_bits(s: int, phys_a: Sequence[int], phys_b: Sequence[int]) -> None:
+    a, pa = _i32(phys_a)
+    b, pb = _i32(phys_b)
+    _check(_f["qsa_permute_bits"](_vp(s), pa, pb, len(a)))
+
+
+def qsa_apply_fused(s: int, targets: Sequence[int], matrix) -> None:
+    t, pt = _i32(targets)
+    m = _cmat(matrix)
+    _check(_f["qsa_apply_fused"](_vp(s), pt, len(t), m.view(np.float64).ctypes.data_as(_dp)))
+
+
+def qsa_apply_fused_ex(s: int, targets: Sequence[int], matrix, lowering: int, precision: int) -> None:
+    t, pt = _i32(targets)
+    m = _cmat(matrix)
+    _check(_f["qsa_apply_fused_ex"](_vp(s), pt, len(t), m.view(np.float64).ctypes.data_as(_dp), lowering,
+                                    precision))
+
+
+# ---- circuits ---------------------------------------------------------------
+
+class OpArray:
+    """A qsa_op[] built from objects with ``targets``, ``matrix`` (complex,
+    2^k x 2^k) and optional ``diag``; keeps the matrices alive."""
+
+    def __init__(self, ops: Iterable):
+        ops = list(ops)
+        self.mats = [_cmat(o.matrix) for o in ops]
+        self.arr = (qsa_op * max(1, len(ops)))()
+        for i, o in enumerate(ops):
+            t = list(o.targets)
+            self.arr[i].k = len(t)
+            for j, q in enumerate(t):
+                self.arr[i].targets[j] = int(q)
+            self.arr[i].matrix = self.mats[i].view(np.float64).ctypes.data_as(_dp)
+            self.arr[i].flags = QSA_OP_DIAG if getattr(o, "diag", False) else 0
+        self.n = len(ops)
+
+
+def qsa_plan_opts_default() -> qsa_plan_opts:
+    o = qsa_plan_opts()
+    _f["qsa_plan_opts_default"](_c.byref(o))
+    return o
+
+
+def make_opts(**kw) -> qsa_plan_opts:
+    o = qsa_plan_opts_default()
+    for k, v in kw.items():
+        setattr(o, k, int(v))
+    return o
+
+
+def qsa_plan_circuit(ops, n_qubits: int, opts: Optional[qsa_plan_opts] = None) -> List[int]:
+    oa = ops if isinstance(ops, OpArray) else OpArray(ops)
+    starts = (_c.c_size_t * max(1, oa.n))()
+    nb = _c.c_size_t()
+    _check(_f["qsa_plan_circuit"](oa.arr, oa.n, n_qubits, _c.byref(opts) if opts else None, starts, _c.byref(nb)))
+    return [int(starts[i]) for i in range(nb.value)]
+
+
+def qsa_fuse_ops(ops) -> Tuple[List[int], np.ndarray]:
+    oa = ops if isinstance(ops, OpArray) else OpArray(ops)
+    t = (_c.c_int32 * 6)()
+    w = _c.c_int()
+    m = np.zeros(2 * 4096, dtype=np.float64)
+    _check(_f["qsa_fuse_ops"](oa.arr, oa.n, t, _c.byref(w), m.ctypes.data_as(_dp)))
+    u = w.value
+    M = m[: 2 * 4 ** u].view(np.complex128).reshape(1 << u, 1 << u).copy()
+    return [int(t[j]) for j in range(u)], M
+
+
+def qsa_apply_circuit(s: int, ops, opts: Optional[qsa_plan_opts] = None) -> dict:
+    oa = ops if isinstance(ops, OpArray) else OpArray(ops)
+    st = qsa_run_stats()
+    _check(_f["qsa_apply_circuit"](_vp(s), oa.arr, oa.n, _c.byref(opts) if opts else None, _c.byref(st)))
+    return st.as_dict()
+
+
+def qsa_plan_create(ops, n_qubits: int, opts: Optional[qsa_plan_opts] = None, layout=None) -> int:
+    oa = ops if isinstance(ops, OpArray) else OpArray(ops)
+    h = _vp()
+    lay = None
+    if layout is not None:
+        la, lay = _i32(layout)
+    _check(_f["qsa_plan_create"](oa.arr, oa.n, n_qubits, _c.byref(opts) if opts else None, lay, _c.byref(h)))
+    return h.value
+
+
+def qsa_plan_info(p: int) -> dict:
+    nb, no, mb = _c.c_size_t(), _c.c_size_t(), _c.c_size_t()
+    mw = _c.c_int()
+    _check(_f["qsa_plan_info"](_vp(p), _c.byref(nb), _c.byref(no), _c.byref(mw), _c.byref(mb)))
+    return {"blocks": nb.value, "ops": no.value, "max_width": mw.value, "matrix_bytes": mb.value}
+
+
+def qsa_plan_blocks(p: int) -> Tuple[List[int], List[int]]:
+    nb = qsa_plan_info(p)["blocks"]
+    fo = (_c.c_size_t * max(1, nb))()
+    w = np.zeros(max(1, nb), dtype=np.int32)
+    _check(_f["qsa_plan_blocks"](_vp(p), fo, w.ctypes.data_as(_i32p), nb))
+    return [int(fo[i]) for i in range(nb)], [int(v) for v in w[:nb]]
+
+
+def qsa_plan_execute(s: int, p: int) -> dict:
+    st = qsa_run_stats()
+    _check(_f["qsa_plan_execute"](_vp(s), _vp(p), _c.byref(st)))
+    return st.as_dict()
+
+
+def qsa_plan_destroy(p: int) -> None:
+    _check(_f["qsa_plan_destroy"](_vp(p)))
+
+
+def qsa_state_counters(s: int) -> int:
+    v = _c.c_uint64()
+    _check(_f["qsa_state_counters"](_vp(s), _c.byref(v)))
+    return v.value
+
+
+# ---- outputs ------------------------------------------------------------------
+
+def qsa_probabilities(s: int, want_probs: bool = True) -> Tuple[Optional[np.ndarray], float]:
+    n, _ = qsa_state_info(s)
+    norm = _c.c_double()
+    out = np.empty(1 << n, dtype=np.float64) if want_probs else None
+    _check(_f["qsa_probabilities"](_vp(s), out.ctypes.data_as(_dp) if want_probs else None, _c.byref(norm)))
+    return out, norm.value
+
+
+def qsa_probabilities_device(s: int, out_dev_ptr: int) -> float:
+    norm = _c.c_double()
+    _check(_f["qsa_probabilities_device"](_vp(s), _vp(out_dev_ptr), _c.byref(norm)))
+    return norm.value
+
+
+def qsa_expectation_z(s: int, logical_mask: int) -> float:
+    out = _c.c_double()
+    _check(_f["qsa_expectation_z"](_vp(s), _c.c_uint64(logical_mask), _c.byref(out)))
+    return out.value
+
+
+def qsa_sample_counts(s: int, shots: int, seed: int, capacity: Optional[int] = None) -> Tuple[np.ndarray, np.ndarray]:
+    cap = shots if capacity is None else capacity
+    outc = np.zeros(max(1, cap), dtype=np.uint64)
+    cnt = np.zeros(max(1, cap), dtype=np.uint64)
+    nd = _c.c_size_t()
+    _check(_f["qsa_sample_counts"](_vp(s), shots, _c.c_uint64(seed), outc.ctypes.data_as(_u64p),
+                                   cnt.ctypes.data_as(_u64p), cap, _c.byref(nd)))
+    return outc[: nd.value].copy(), cnt[: nd.value].copy()
+
+
+# ---- cost model -------------------------------------------------------------
+
+def qsa_costmodel_features(k: int, phys_mask: int, n_qubits: int, batch: int = 1) -> np.ndarray:
+    x = np.zeros(MLP_IN, dtype=np.float32)
+    _check(_f["qsa_costmodel_features"](k, _c.c_uint64(phys_mask), n_qubits, batch, x.ctypes.data_as(_fp)))
+    return x
+
+
+def qsa_costmodel_set(params: Optional[np.ndarray]) -> None:
+    if params is None:
+        _check(_f["qsa_costmodel_set"](None))
+        return
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert p.size == MLP_PARAMS
+    _check(_f["qsa_costmodel_set"](p.ctypes.data_as(_fp)))
+
+
+def qsa_costmodel_predict(features: np.ndarray) -> np.ndarray:
+    X = np.ascontiguousarray(features, dtype=np.float32).reshape(-1, MLP_IN)
+    out = np.zeros(X.shape[0], dtype=np.float64)
+    _check(_f["qsa_costmodel_predict"](X.ctypes.data_as(_fp), X.shape[0], out.ctypes.data_as(_dp)))
+    return out
+
+
+def exported_symbols() -> List[str]:
+    return sorted(k for k in _f)

@@ -1,0 +1,422 @@
+// FP32 fused dense update and qubit-permutation kernels (sm_103a).
+//
+// Both kernels share one tile engine: a persistent CTA walks tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...; each tile (2^T amplitudes = 2^nx
+// contiguous runs of 2^m amplitudes) is staged into shared memory with 16-byte
+// cp.async copies in an S-deep ring, transformed, and written back in place.
+// Tiles partition the index space, so the in-place update needs no second
+// state buffer (the paper's CUDA path holds two, App. C "Capacity").
+//
+//   apply  (§IV-B, R2 apply; Eq. cost-formal): for every group of 2^k
+//          amplitudes that differ only in the target bits,
+//          psi'[x|spread(r)] = sum_c G[r][c] psi[x|spread(c)];
+//   permute (§IV-D, Lemma "distributed promotion swap" with the rank bits read
+//          as out-of-block bits): psi'[tau(y)] = psi[y] for a product tau of
+//          disjoint bit transpositions.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "qsa_internal.h"
+
+namespace qsa {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Insert a zero bit at position p (positions handled in ascending order).
+__device__ __forceinline__ uint64_t insert_zero(uint64_t v, int p) {
+    uint64_t lo = v & ((1ull << p) - 1ull);
+    return ((v >> p) << (p + 1)) | lo;
+}
+
+struct TileArgs {
+    float2* psi;
+    uint64_t ntiles;
+    int T, m, nx;
+    int xpos[6];
+};
+
+__device__ __forceinline__ uint64_t tile_base(const TileArgs& a, uint64_t t) {
+    uint64_t b = t << a.m;
+#pragma unroll
+    for (int e = 0; e < 6; ++e)
+        if (e < a.nx) b = insert_zero(b, a.xpos[e]);
+    return b;
+}
+
+// Global index of tile-local index j.
+__device__ __forceinline__ uint64_t tile_global(const TileArgs& a, const uint64_t* runoff, uint64_t base,
+                                                uint32_t j) {
+    return base | (j & ((1u << a.m) - 1u)) | runoff[j >> a.m];
+}
+
+__device__ __forceinline__ void build_runoff(const TileArgs& a, uint64_t* runoff) {
+    for (int r = threadIdx.x; r < (1 << a.nx); r += blockDim.x) {
+        uint64_t off = 0;
+#pragma unroll
+        for (int e = 0; e < 6; ++e)
+            if (e < a.nx && ((r >> e) & 1)) off |= 1ull << a.xpos[e];
+        runoff[r] = off;
+    }
+}
+
+// Issue the 16-byte copies of tile t into stage buffer `st`.
+__device__ __forceinline__ void load_tile(const TileArgs& a, const uint64_t* runoff, uint64_t t, float2* st) {
+    const uint64_t base = tile_base(a, t);
+    const uint32_t chunks = 1u << (a.T - 1);
+    for (uint32_t q = threadIdx.x; q < chunks; q += blockDim.x) {
+        uint32_t j = q << 1;
+        cp_async16(st + j, a.psi + tile_global(a, runoff, base, j));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Apply
+// ---------------------------------------------------------------------------
+struct ApplyArgs {
+    TileArgs t;
+    const float* mat;   // 2 * 4^K floats
+    int tl[6];          // tile-local position of target j (V order)
+    int tls[6];         // the same positions, ascending
+};
+
+template <int K, int R, int S>
+__global__ void __launch_bounds__(kThreads) k_apply_fp32(ApplyArgs a) {
+    constexpr int D = 1 << K;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tileAmps = 1 << a.t.T;
+    float2* stage = reinterpret_cast<float2*>(smem_raw);
+    float2* Ms = stage + S * tileAmps;
+    uint64_t* runoff = reinterpret_cast<uint64_t*>(Ms + D * D);
+    int* loff = reinterpret_cast<int*>(runoff + 64);
+
+    const float2* gm = reinterpret_cast<const float2*>(a.mat);
+    for (int i = threadIdx.x; i < D * D; i += blockDim.x) Ms[i] = gm[i];
+    build_runoff(a.t, runoff);
+    for (int c = threadIdx.x; c < D; c += blockDim.x) {
+        int o = 0;
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if ((c >> j) & 1) o |= 1 << a.tl[j];
+        loff[c] = o;
+    }
+    __syncthreads();
+
+    const uint64_t stride = gridDim.x;
+    // prologue: S-1 tiles in flight
+#pragma unroll
+    for (int s = 0; s < S - 1; ++s) {
+        uint64_t t = blockIdx.x + s * stride;
+        if (t < a.t.ntiles) load_tile(a.t, runoff, t, stage + s * tileAmps);
+        cp_async_commit();
+    }
+    const int G = tileAmps >> K;                  // groups per tile
+    const int gshift = a.t.T - K;
+    const int items = G * (D / R);
+    int it_stage = 0;
+    for (uint64_t t = blockIdx.x; t < a.t.ntiles; t += stride) {
+        uint64_t tn = t + (S - 1) * stride;
+        int ld_stage = it_stage + (S - 1);
+        if (ld_stage >= S) ld_stage -= S;
+        if (tn < a.t.ntiles) load_tile(a.t, runoff, tn, stage + ld_stage * tileAmps);
+        cp_async_commit();
+        cp_async_wait<S - 1>();
+        __syncthreads();
+
+        const float2* st = stage + it_stage * tileAmps;
+        const uint64_t base = tile_base(a.t, t);
+        for (int it = threadIdx.x; it < items; it += blockDim.x) {
+            const int g = it & (G - 1);
+            const int rb = it >> gshift;
+            uint32_t lb = static_cast<uint32_t>(g);
+#pragma unroll
+            for (int j = 0; j < K; ++j) lb = static_cast<uint32_t>(insert_zero(lb, a.tls[j]));
+            float2 v[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) v[c] = st[lb | loff[c]];
+#pragma unroll
+            for (int rr = 0; rr < R; ++rr) {
+                const int r = rb * R + rr;
+                const float4* mrow = reinterpret_cast<const float4*>(Ms + r * D);
+                float ar = 0.f, ai = 0.f;
+#pragma unroll
+                for (int c = 0; c < D; c += 2) {
+                    float4 m2 = mrow[c >> 1];  // G[r][c], G[r][c+1]
+                    ar = fmaf(m2.x, v[c].x, ar);
+                    ar = fmaf(-m2.y, v[c].y, ar);
+                    ai = fmaf(m2.x, v[c].y, ai);
+                    ai = fmaf(m2.y, v[c].x, ai);
+                    ar = fmaf(m2.z, v[c + 1].x, ar);
+                    ar = fmaf(-m2.w, v[c + 1].y, ar);
+                    ai = fmaf(m2.z, v[c + 1].y, ai);
+                    ai = fmaf(m2.w, v[c + 1].x, ai);
+                }
+                const uint32_t lj = lb | loff[r];
+                __stcs(a.t.psi + tile_global(a.t, runoff, base, lj), make_float2(ar, ai));
+            }
+        }
+        __syncthreads();
+        if (++it_stage == S) it_stage = 0;
+    }
+    cp_async_wait<0>();
+}
+
+template <int K>
+struct ApplyCfg;
+template <> struct ApplyCfg<1> { static constexpr int T = 11, R = 2, S = 3; };
+template <> struct ApplyCfg<2> { static constexpr int T = 11, R = 4, S = 3; };
+template <> struct ApplyCfg<3> { static constexpr int T = 11, R = 8, S = 3; };
+template <> struct ApplyCfg<4> { static constexpr int T = 11, R = 8, S = 3; };
+template <> struct ApplyCfg<5> { static constexpr int T = 12, R = 8, S = 2; };
+template <> struct ApplyCfg<6> { static constexpr int T = 12, R = 8, S = 2; };
+
+template <int K>
+cudaError_t launch_apply_k(float2* psi, int n, const int* phys, const float* d_mat, cudaStream_t st,
+                           uint64_t* launches) {
+    using C = ApplyCfg<K>;
+    TileGeom g;
+    if (!make_geom(n, phys, K, C::T, &g)) return cudaErrorInvalidValue;
+    ApplyArgs a{};
+    a.t.psi = psi;
+    a.t.ntiles = g.ntiles;
+    a.t.T = g.T;
+    a.t.m = g.m;
+    a.t.nx = g.nx;
+    for (int e = 0; e < 6; ++e) a.t.xpos[e] = g.xpos[e];
+    a.mat = d_mat;
+    for (int j = 0; j < K; ++j) {
+        int p = phys[j];
+        int loc = p;
+        if (p >= g.m) {
+            int e = 0;
+            while (g.xpos[e] != p) ++e;
+            loc = g.m + e;
+        }
+        a.tl[j] = loc;
+        a.tls[j] = loc;
+    }
+    std::sort(a.tls, a.tls + K);
+    const int D = 1 << K;
+    const size_t smem = sizeof(float2) * (static_cast<size_t>(C::S) << g.T) + sizeof(float2) * D * D +
+                        sizeof(uint64_t) * 64 + sizeof(int) * 64;
+    auto kern = k_apply_fp32<K, C::R, C::S>;
+    static int max_set = 0;
+    if (static_cast<int>(smem) > max_set) {
+        size_t full = sizeof(float2) * (static_cast<size_t>(C::S) << C::T) + sizeof(float2) * D * D +
+                      sizeof(uint64_t) * 64 + sizeof(int) * 64;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(full));
+        if (e != cudaSuccess) return e;
+        max_set = static_cast<int>(full);
+    }
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    uint64_t grid = static_cast<uint64_t>(num_sms()) * occ;
+    if (grid > g.ntiles) grid = g.ntiles;
+    kern<<<static_cast<unsigned>(grid), kThreads, smem, st>>>(a);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Permute
+// ---------------------------------------------------------------------------
+struct PermArgs {
+    TileArgs t;
+    int npairs;
+    int la[6], lb[6];   // tile-local positions of each pair
+};
+
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_permute(PermArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tileAmps = 1 << a.t.T;
+    float2* stage = reinterpret_cast<float2*>(smem_raw);
+    uint64_t* runoff = reinterpret_cast<uint64_t*>(stage + S * tileAmps);
+    build_runoff(a.t, runoff);
+    __syncthreads();
+    const uint64_t stride = gridDim.x;
+#pragma unroll
+    for (int s = 0; s < S - 1; ++s) {
+        uint64_t t = blockIdx.x + s * stride;
+        if (t < a.t.ntiles) load_tile(a.t, runoff, t, stage + s * tileAmps);
+        cp_async_commit();
+    }
+    int it_stage = 0;
+    const uint32_t chunks = static_cast<uint32_t>(tileAmps) >> 1;
+    for (uint64_t t = blockIdx.x; t < a.t.ntiles; t += stride) {
+        uint64_t tn = t + (S - 1) * stride;
+        int ld_stage = it_stage + (S - 1);
+        if (ld_stage >= S) ld_stage -= S;
+        if (tn < a.t.ntiles) load_tile(a.t, runoff, tn, stage + ld_stage * tileAmps);
+        cp_async_commit();
+        cp_async_wait<S - 1>();
+        __syncthreads();
+        const float2* st = stage + it_stage * tileAmps;
+        const uint64_t base = tile_base(a.t, t);
+        for (uint32_t q = threadIdx.x; q < chunks; q += blockDim.x) {
+            uint32_t d0 = q << 1, d1 = d0 | 1u;
+            uint32_t s0 = d0, s1 = d1;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                if (i >= a.npairs) break;
+                uint32_t x0 = ((s0 >> a.la[i]) ^ (s0 >> a.lb[i])) & 1u;
+                s0 ^= (x0 << a.la[i]) | (x0 << a.lb[i]);
+                uint32_t x1 = ((s1 >> a.la[i]) ^ (s1 >> a.lb[i])) & 1u;
+                s1 ^= (x1 << a.la[i]) | (x1 << a.lb[i]);
+            }
+            float2 v0 = st[s0], v1 = st[s1];
+            float4* dst = reinterpret_cast<float4*>(a.t.psi + tile_global(a.t, runoff, base, d0));
+            __stcs(dst, make_float4(v0.x, v0.y, v1.x, v1.y));
+        }
+        __syncthreads();
+        if (++it_stage == S) it_stage = 0;
+    }
+    cp_async_wait<0>();
+}
+
+__global__ void k_set_one(float2* psi) { psi[0] = make_float2(1.f, 0.f); }
+
+}  // namespace
+
+int num_sms() {
+    static int cached = 0;
+    if (!cached) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
+        if (cached <= 0) cached = 1;
+    }
+    return cached;
+}
+
+bool make_geom(int n, const int* special, int ns, int T_want, TileGeom* g) {
+    g->n = n;
+    g->T = std::min(T_want, n);
+    int m = g->T;
+    for (;;) {
+        int cnt = 0;
+        for (int i = 0; i < ns; ++i)
+            if (special[i] >= m) ++cnt;
+        if (m + cnt <= g->T) break;
+        --m;
+    }
+    if (m < 1) return false;
+    g->m = m;
+    int nx = 0;
+    int tmp[16];
+    for (int i = 0; i < ns; ++i)
+        if (special[i] >= m) {
+            if (nx >= 6) return false;
+            tmp[nx++] = special[i];
+        }
+    std::sort(tmp, tmp + nx);
+    g->nx = nx;
+    for (int e = 0; e < 6; ++e) g->xpos[e] = e < nx ? tmp[e] : 0;
+    g->ntiles = 1ull << (n - g->T);
+    return true;
+}
+
+cudaError_t launch_init_zero(float2* psi, int n, cudaStream_t st, uint64_t* launches) {
+    cudaError_t e = cudaMemsetAsync(psi, 0, sizeof(float2) << n, st);
+    if (e != cudaSuccess) return e;
+    k_set_one<<<1, 1, 0, st>>>(psi);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_fp32(float2* psi, int n, const int* phys, int k, const float* d_mat, cudaStream_t st,
+                              uint64_t* launches) {
+    switch (k) {
+        case 1: return launch_apply_k<1>(psi, n, phys, d_mat, st, launches);
+        case 2: return launch_apply_k<2>(psi, n, phys, d_mat, st, launches);
+        case 3: return launch_apply_k<3>(psi, n, phys, d_mat, st, launches);
+        case 4: return launch_apply_k<4>(psi, n, phys, d_mat, st, launches);
+        case 5: return launch_apply_k<5>(psi, n, phys, d_mat, st, launches);
+        case 6: return launch_apply_k<6>(psi, n, phys, d_mat, st, launches);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_permute(float2* psi, int n, const int* pa, const int* pb, int npairs, cudaStream_t st,
+                           uint64_t* launches) {
+    constexpr int S = 3, T = 11;
+    int i0 = 0;
+    while (i0 < npairs) {
+        // grow the pass while its extra tile bits fit
+        int i1 = i0 + 1;
+        TileGeom g;
+        int spec[12];
+        for (;;) {
+            int ns = 0;
+            for (int i = i0; i < i1; ++i) { spec[ns++] = pa[i]; spec[ns++] = pb[i]; }
+            if (!make_geom(n, spec, ns, T, &g)) {
+                if (i1 == i0 + 1) return cudaErrorInvalidValue;
+                --i1;
+                ns = 0;
+                for (int i = i0; i < i1; ++i) { spec[ns++] = pa[i]; spec[ns++] = pb[i]; }
+                make_geom(n, spec, ns, T, &g);
+                break;
+            }
+            if (i1 == npairs || i1 - i0 == 6) break;
+            ++i1;
+        }
+        PermArgs a{};
+        a.t.psi = psi;
+        a.t.ntiles = g.ntiles;
+        a.t.T = g.T;
+        a.t.m = g.m;
+        a.t.nx = g.nx;
+        for (int e = 0; e < 6; ++e) a.t.xpos[e] = g.xpos[e];
+        a.npairs = i1 - i0;
+        auto local = [&](int p) {
+            if (p < g.m) return p;
+            int e = 0;
+            while (g.xpos[e] != p) ++e;
+            return g.m + e;
+        };
+        for (int i = i0; i < i1; ++i) {
+            a.la[i - i0] = local(pa[i]);
+            a.lb[i - i0] = local(pb[i]);
+        }
+        const size_t smem = sizeof(float2) * (static_cast<size_t>(S) << g.T) + sizeof(uint64_t) * 64;
+        auto kern = k_permute<S>;
+        static bool attr = false;
+        if (!attr) {
+            size_t full = sizeof(float2) * (static_cast<size_t>(S) << T) + sizeof(uint64_t) * 64;
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(full));
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        int occ = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) occ = 1;
+        uint64_t grid = static_cast<uint64_t>(num_sms()) * occ;
+        if (grid > g.ntiles) grid = g.ntiles;
+        kern<<<static_cast<unsigned>(grid), kThreads, smem, st>>>(a);
+        ++*launches;
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        i0 = i1;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace qsa

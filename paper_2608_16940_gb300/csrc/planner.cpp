@@ -1,0 +1,466 @@
+// Fusion planning (§IV-C) and circuit execution.
+//
+//   - per-gate:   one block per input op (the plain comparator path);
+//   - greedy:     extend the current block in circuit order while the union of
+//                 targets stays within kmax (the plain width-limit heuristic);
+//   - DP:         Eq. dp-recurrence over windows of W ops,
+//                 D_i = min_{j in J_i} D_j + Gamma(B(j,i)),
+//                 Gamma = 4^k (dense) / 1 (diagonal), ties to the smallest j,
+//                 then a greedy cross-window merge (merge neighbours when the
+//                 union fits the cap and Gamma(merged) <= Gamma(a) + Gamma(b)),
+//                 the whole pipeline repeated on the blocks at most `rounds`
+//                 times while the block count falls;
+//   - DP-MLP:     the same DP with Gamma(B) = the cost model's predicted
+//                 seconds for the block's width and physical target mask.
+// Block matrices are formed in FP64 in circuit order, later ops multiplied on
+// the left (§IV-C).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <unordered_map>
+#include <vector>
+
+#include "qsa.h"
+#include "qsa_internal.h"
+#include "qsa_runtime.h"
+#include "qsa_costmodel.h"
+
+namespace qsa {
+
+namespace {
+
+struct Unit {
+    uint64_t mask;   // logical target qubits
+    bool diag;
+    size_t s, e;     // range of input ops
+};
+
+using Scorer = double (*)(void* ctx, int width, bool diag, uint64_t mask);
+
+double gamma_score(void*, int width, bool diag, uint64_t) { return diag ? 1.0 : std::ldexp(1.0, 2 * width); }
+
+struct MlpCtx {
+    int n;
+    const int32_t* L;
+    std::unordered_map<uint64_t, double> cache;
+};
+
+double mlp_score(void* ctx, int width, bool, uint64_t mask) {
+    auto* c = static_cast<MlpCtx*>(ctx);
+    auto it = c->cache.find(mask);
+    if (it != c->cache.end()) return it->second;
+    uint64_t pm = 0;
+    for (int q = 0; q < c->n; ++q)
+        if ((mask >> q) & 1) pm |= 1ull << c->L[q];
+    double v = costmodel_predict_seconds(width, pm, c->n, 1);
+    c->cache[mask] = v;
+    return v;
+}
+
+int popc(uint64_t v) { return __builtin_popcountll(v); }
+
+std::vector<Unit> dp_window(const std::vector<Unit>& u, size_t b, size_t e, int kmax, int kmax_diag, Scorer sc,
+                            void* ctx) {
+    const size_t h = e - b;
+    std::vector<double> D(h + 1, 0.0);
+    std::vector<size_t> arg(h + 1, 0);
+    for (size_t i = 1; i <= h; ++i) {
+        double best = INFINITY;
+        size_t bj = i - 1;
+        uint64_t mask = 0;
+        bool diag = true;
+        // walk j downward so the union grows incrementally; keep the
+        // smallest j on ties by accepting equal scores as j decreases
+        std::vector<std::pair<size_t, double>> cand;
+        for (size_t jj = i; jj-- > 0;) {
+            mask |= u[b + jj].mask;
+            diag = diag && u[b + jj].diag;
+            const int w = popc(mask);
+            const int cap = diag ? kmax_diag : kmax;
+            if (w > cap && jj != i - 1) {
+                // widths only grow as j decreases, but a diagonal run can turn
+                // dense; the cap of a dense block is >= the diagonal cap, so
+                // once the dense cap is exceeded no smaller j is feasible
+                if (w > std::max(kmax, kmax_diag)) break;
+                continue;
+            }
+            const double val = D[jj] + sc(ctx, w, diag, mask);
+            if (val <= best) {
+                best = val;
+                bj = jj;
+            }
+        }
+        D[i] = best;
+        arg[i] = bj;
+    }
+    std::vector<Unit> out;
+    size_t i = h;
+    while (i > 0) {
+        size_t j = arg[i];
+        Unit m{0, true, u[b + j].s, u[b + i - 1].e};
+        for (size_t t = j; t < i; ++t) {
+            m.mask |= u[b + t].mask;
+            m.diag = m.diag && u[b + t].diag;
+        }
+        out.push_back(m);
+        i = j;
+    }
+    std::reverse(out.begin(), out.end());
+    return out;
+}
+
+std::vector<Unit> merge_pass(const std::vector<Unit>& blocks, int kmax, int kmax_diag, Scorer sc, void* ctx) {
+    std::vector<Unit> out;
+    if (blocks.empty()) return out;
+    Unit cur = blocks[0];
+    for (size_t i = 1; i < blocks.size(); ++i) {
+        const Unit& nx = blocks[i];
+        const uint64_t m = cur.mask | nx.mask;
+        const bool dg = cur.diag && nx.diag;
+        const int w = popc(m);
+        const int cap = dg ? kmax_diag : kmax;
+        if (w <= cap && sc(ctx, w, dg, m) <= sc(ctx, popc(cur.mask), cur.diag, cur.mask) +
+                                                   sc(ctx, popc(nx.mask), nx.diag, nx.mask)) {
+            cur = Unit{m, dg, cur.s, nx.e};
+        } else {
+            out.push_back(cur);
+            cur = nx;
+        }
+    }
+    out.push_back(cur);
+    return out;
+}
+
+std::vector<Unit> dp_pipeline(const std::vector<Unit>& gates, const qsa_plan_opts& o, Scorer sc, void* ctx) {
+    std::vector<Unit> units = gates;
+    for (int round = 0; round < o.rounds; ++round) {
+        std::vector<Unit> blocks;
+        for (size_t b = 0; b < units.size(); b += static_cast<size_t>(o.window)) {
+            size_t e = std::min(units.size(), b + static_cast<size_t>(o.window));
+            auto w = dp_window(units, b, e, o.kmax, o.kmax_diag, sc, ctx);
+            blocks.insert(blocks.end(), w.begin(), w.end());
+        }
+        blocks = merge_pass(blocks, o.kmax, o.kmax_diag, sc, ctx);
+        if (round > 0 && blocks.size() >= units.size()) break;
+        units.swap(blocks);
+    }
+    return units;
+}
+
+std::vector<Unit> greedy(const std::vector<Unit>& gates, int kmax) {
+    std::vector<Unit> out;
+    if (gates.empty()) return out;
+    Unit cur = gates[0];
+    for (size_t i = 1; i < gates.size(); ++i) {
+        uint64_t m = cur.mask | gates[i].mask;
+        if (popc(m) > kmax) {
+            out.push_back(cur);
+            cur = gates[i];
+        } else {
+            cur = Unit{m, cur.diag && gates[i].diag, cur.s, gates[i].e};
+        }
+    }
+    out.push_back(cur);
+    return out;
+}
+
+qsa_status validate_ops(const qsa_op* ops, size_t n_ops, int n_qubits) {
+    if (n_ops > 0 && !ops) return fail(QSA_E_ARG, "ops is NULL");
+    for (size_t i = 0; i < n_ops; ++i) {
+        qsa_status st = validate_targets(n_qubits, ops[i].targets, ops[i].k);
+        if (st != QSA_OK) return st;
+        if (!ops[i].matrix) return fail(QSA_E_ARG, "op matrix is NULL");
+    }
+    return QSA_OK;
+}
+
+qsa_status normalise_opts(const qsa_plan_opts* in, qsa_plan_opts* o) {
+    if (in) *o = *in; else qsa_plan_opts_default(o);
+    if (o->planner < 0 || o->planner > 3) return fail(QSA_E_ARG, "unknown planner");
+    if (o->kmax < 1 || o->kmax > QSA_MAX_K) return fail(QSA_E_ARG, "kmax must be in 1..6");
+    if (o->kmax_diag < 1 || o->kmax_diag > o->kmax) return fail(QSA_E_ARG, "kmax_diag must be in 1..kmax");
+    if (o->window < 1) return fail(QSA_E_ARG, "window must be >= 1");
+    if (o->rounds < 1 || o->rounds > 4) return fail(QSA_E_ARG, "rounds must be in 1..4");
+    if (o->precision < 0 || o->precision > 1) return fail(QSA_E_ARG, "unknown precision");
+    if (o->lowering < 0 || o->lowering > 2) return fail(QSA_E_ARG, "unknown lowering");
+    return QSA_OK;
+}
+
+std::vector<Unit> plan(const qsa_op* ops, size_t n_ops, int n_qubits, const qsa_plan_opts& o, const int32_t* L) {
+    std::vector<Unit> gates(n_ops);
+    for (size_t i = 0; i < n_ops; ++i) {
+        uint64_t m = 0;
+        for (int j = 0; j < ops[i].k; ++j) m |= 1ull << ops[i].targets[j];
+        gates[i] = Unit{m, (ops[i].flags & QSA_OP_DIAG) != 0, i, i + 1};
+    }
+    if (o.planner == QSA_PLAN_PER_GATE) return gates;
+    if (o.planner == QSA_PLAN_GREEDY) return greedy(gates, o.kmax);
+    if (o.planner == QSA_PLAN_DP_MLP) {
+        if (!costmodel_loaded()) return greedy(gates, o.kmax);
+        int32_t ident[QSA_MAX_QUBITS];
+        if (!L) {
+            for (int q = 0; q < n_qubits; ++q) ident[q] = q;
+            L = ident;
+        }
+        MlpCtx ctx{n_qubits, L, {}};
+        return dp_pipeline(gates, o, mlp_score, &ctx);
+    }
+    return dp_pipeline(gates, o, gamma_score, nullptr);
+}
+
+// M <- E(op) M for the D x D block matrix M (row-major), op on block positions pos[].
+void left_multiply(std::vector<std::complex<double>>& M, int u, const int* pos, int k, const double* g) {
+    const size_t D = size_t(1) << u, d = size_t(1) << k;
+    size_t opmask = 0;
+    for (int j = 0; j < k; ++j) opmask |= size_t(1) << pos[j];
+    std::vector<size_t> off(d);
+    for (size_t c = 0; c < d; ++c) {
+        size_t o = 0;
+        for (int j = 0; j < k; ++j)
+            if ((c >> j) & 1) o |= size_t(1) << pos[j];
+        off[c] = o;
+    }
+    std::vector<std::complex<double>> v(d);
+    for (size_t col = 0; col < D; ++col)
+        for (size_t x = 0; x < D; ++x) {
+            if (x & opmask) continue;
+            for (size_t c = 0; c < d; ++c) v[c] = M[(x | off[c]) * D + col];
+            for (size_t r = 0; r < d; ++r) {
+                std::complex<double> acc = 0;
+                for (size_t c = 0; c < d; ++c)
+                    acc += std::complex<double>(g[2 * (r * d + c)], g[2 * (r * d + c) + 1]) * v[c];
+                M[(x | off[r]) * D + col] = acc;
+            }
+        }
+}
+
+// Fused matrix of ops[s..e) on the ascending union of their targets.
+qsa_status fuse_range(const qsa_op* ops, size_t s, size_t e, int32_t* tgt, int* width, std::vector<double>* out) {
+    uint64_t m = 0;
+    for (size_t i = s; i < e; ++i)
+        for (int j = 0; j < ops[i].k; ++j) m |= 1ull << ops[i].targets[j];
+    const int u = popc(m);
+    if (u > QSA_MAX_K) return fail(QSA_E_ARG, "fused block wider than 6 qubits");
+    int t = 0;
+    for (int q = 0; q < 64; ++q)
+        if ((m >> q) & 1) tgt[t++] = q;
+    *width = u;
+    const size_t D = size_t(1) << u;
+    std::vector<std::complex<double>> M(D * D, 0.0);
+    for (size_t i = 0; i < D; ++i) M[i * D + i] = 1.0;
+    for (size_t i = s; i < e; ++i) {
+        int pos[QSA_MAX_K];
+        for (int j = 0; j < ops[i].k; ++j) pos[j] = static_cast<int>(std::find(tgt, tgt + u, ops[i].targets[j]) - tgt);
+        left_multiply(M, u, pos, ops[i].k, ops[i].matrix);
+    }
+    out->resize(2 * D * D);
+    for (size_t i = 0; i < D * D; ++i) {
+        (*out)[2 * i] = M[i].real();
+        (*out)[2 * i + 1] = M[i].imag();
+    }
+    return QSA_OK;
+}
+
+}  // namespace
+
+}  // namespace qsa
+
+using namespace qsa;
+
+extern "C" {
+
+void qsa_plan_opts_default(qsa_plan_opts* o) {
+    if (!o) return;
+    o->planner = QSA_PLAN_DP;
+    o->kmax = 4;
+    o->kmax_diag = 4;
+    o->window = 64;
+    o->rounds = 4;
+    o->precision = QSA_PREC_FP32;
+    o->lowering = QSA_LOWER_AUTO;
+    o->timing = 0;
+}
+
+qsa_status qsa_plan_circuit(const qsa_op* ops, size_t n_ops, int n_qubits, const qsa_plan_opts* opts,
+                            size_t* block_start, size_t* n_blocks) {
+    if (n_qubits < 1 || n_qubits > QSA_MAX_QUBITS) return fail(QSA_E_ARG, "n_qubits must be in 1..34");
+    if (!n_blocks || (n_ops > 0 && !block_start)) return fail(QSA_E_ARG, "NULL output");
+    qsa_plan_opts o;
+    qsa_status st = normalise_opts(opts, &o);
+    if (st != QSA_OK) return st;
+    st = validate_ops(ops, n_ops, n_qubits);
+    if (st != QSA_OK) return st;
+    auto blocks = plan(ops, n_ops, n_qubits, o, nullptr);
+    for (size_t i = 0; i < blocks.size(); ++i) block_start[i] = blocks[i].s;
+    *n_blocks = blocks.size();
+    return QSA_OK;
+}
+
+qsa_status qsa_fuse_ops(const qsa_op* ops, size_t n_ops, int32_t* block_targets_out, int* width_out,
+                        double* matrix_out) {
+    if (!ops || n_ops == 0 || !block_targets_out || !width_out || !matrix_out) return fail(QSA_E_ARG, "NULL argument");
+    for (size_t i = 0; i < n_ops; ++i) {
+        qsa_status st = validate_targets(QSA_MAX_QUBITS, ops[i].targets, ops[i].k);
+        if (st != QSA_OK) return st;
+        if (!ops[i].matrix) return fail(QSA_E_ARG, "op matrix is NULL");
+    }
+    std::vector<double> M;
+    qsa_status st = fuse_range(ops, 0, n_ops, block_targets_out, width_out, &M);
+    if (st != QSA_OK) return st;
+    std::memcpy(matrix_out, M.data(), sizeof(double) * M.size());
+    return QSA_OK;
+}
+
+qsa_status qsa_plan_create(const qsa_op* ops, size_t n_ops, int n_qubits, const qsa_plan_opts* opts,
+                           const int32_t* layout, qsa_plan* out) {
+    if (!out) return fail(QSA_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_qubits < 1 || n_qubits > QSA_MAX_QUBITS) return fail(QSA_E_ARG, "n_qubits must be in 1..34");
+    qsa_plan_opts o;
+    qsa_status st = normalise_opts(opts, &o);
+    if (st != QSA_OK) return st;
+    st = validate_ops(ops, n_ops, n_qubits);
+    if (st != QSA_OK) return st;
+    if (layout) {
+        uint64_t seen = 0;
+        for (int q = 0; q < n_qubits; ++q) {
+            if (layout[q] < 0 || layout[q] >= n_qubits || ((seen >> layout[q]) & 1))
+                return fail(QSA_E_ARG, "layout is not a bijection");
+            seen |= 1ull << layout[q];
+        }
+    }
+    auto* p = new qsa_plan_s();
+    p->n = n_qubits;
+    p->opts = o;
+    p->n_ops = n_ops;
+    auto blocks = plan(ops, n_ops, n_qubits, o, layout);
+    p->blocks.resize(blocks.size());
+    std::vector<double> M;
+    for (size_t i = 0; i < blocks.size(); ++i) {
+        const Unit& u = blocks[i];
+        PlanBlock& b = p->blocks[i];
+        b.off = p->host_mat.size();
+        b.first_op = u.s;
+        if (u.e - u.s == 1) {
+            const qsa_op& op = ops[u.s];
+            b.k = op.k;
+            for (int j = 0; j < op.k; ++j) b.t[j] = op.targets[j];
+            const size_t cnt = 2ull << (2 * op.k);
+            p->host_mat.resize(b.off + cnt);
+            to_float_matrix(op.matrix, op.k, p->host_mat.data() + b.off);
+        } else {
+            st = fuse_range(ops, u.s, u.e, b.t, &b.k, &M);
+            if (st != QSA_OK) {
+                delete p;
+                return st;
+            }
+            p->host_mat.resize(b.off + M.size());
+            for (size_t j = 0; j < M.size(); ++j) p->host_mat[b.off + j] = static_cast<float>(M[j]);
+        }
+        p->max_width = std::max(p->max_width, b.k);
+        while (p->host_mat.size() % 4) p->host_mat.push_back(0.f);  // 16-byte aligned matrices
+    }
+    *out = p;
+    return QSA_OK;
+}
+
+qsa_status qsa_plan_info(qsa_plan p, size_t* n_blocks, size_t* n_ops, int* max_width, size_t* matrix_bytes) {
+    if (!p) return fail(QSA_E_ARG, "plan is NULL");
+    if (n_blocks) *n_blocks = p->blocks.size();
+    if (n_ops) *n_ops = p->n_ops;
+    if (max_width) *max_width = p->max_width;
+    if (matrix_bytes) *matrix_bytes = p->host_mat.size() * sizeof(float);
+    return QSA_OK;
+}
+
+qsa_status qsa_plan_blocks(qsa_plan p, size_t* first_op, int32_t* widths, size_t capacity) {
+    if (!p) return fail(QSA_E_ARG, "plan is NULL");
+    if (capacity < p->blocks.size()) return fail(QSA_E_RANGE, "capacity smaller than the number of blocks");
+    for (size_t i = 0; i < p->blocks.size(); ++i) {
+        if (first_op) first_op[i] = p->blocks[i].first_op;
+        if (widths) widths[i] = p->blocks[i].k;
+    }
+    return QSA_OK;
+}
+
+qsa_status qsa_plan_destroy(qsa_plan p) {
+    if (!p) return fail(QSA_E_ARG, "plan is NULL");
+    if (p->d_mat) {
+        cudaDeviceSynchronize();
+        cudaFree(p->d_mat);
+    }
+    delete p;
+    return QSA_OK;
+}
+
+qsa_status qsa_plan_execute(qsa_state s, qsa_plan p, qsa_run_stats* stats) {
+    qsa_status st = check_state(s);
+    if (st != QSA_OK) return st;
+    if (!p) return fail(QSA_E_ARG, "plan is NULL");
+    if (p->n != s->n) return fail(QSA_E_ARG, "plan and state have different qubit counts");
+    qsa_run_stats local{};
+    qsa_run_stats* rs = stats ? stats : &local;
+    *rs = qsa_run_stats{};
+    if (p->blocks.empty()) return QSA_OK;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!p->d_mat || p->dev != dev) {
+        // first execution on this device: upload the fused matrices once
+        if (p->d_mat) cudaFree(p->d_mat);
+        p->d_mat = nullptr;
+        const size_t bytes = p->host_mat.size() * sizeof(float);
+        cudaError_t e = cudaMalloc(&p->d_mat, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p->d_mat = nullptr;
+            return fail(QSA_E_NOMEM, "cudaMalloc of plan matrices failed");
+        }
+        e = cudaMemcpyAsync(p->d_mat, p->host_mat.data(), bytes, cudaMemcpyHostToDevice, s->stream);
+        if (e != cudaSuccess) return cuda_fail(s, e, "plan matrix upload");
+        p->dev = dev;
+        rs->h2d_bytes = static_cast<double>(bytes);
+    }
+    const uint64_t l0 = s->launches;
+    s->timing = p->opts.timing != 0;
+    for (size_t i = 0; i < p->blocks.size(); ++i) {
+        const PlanBlock& b = p->blocks[i];
+        st = apply_logical(s, b.t, b.k, p->d_mat + b.off, p->opts.lowering, p->opts.precision, rs);
+        if (st != QSA_OK) {
+            s->timing = false;
+            return st;
+        }
+    }
+    s->timing = false;
+    if (p->opts.timing) collect_timers(s, &rs->seconds);
+    rs->launches = s->launches - l0;
+    return QSA_OK;
+}
+
+qsa_status qsa_apply_circuit(qsa_state s, const qsa_op* ops, size_t n_ops, const qsa_plan_opts* opts,
+                             qsa_run_stats* stats) {
+    qsa_status st = check_state(s);
+    if (st != QSA_OK) return st;
+    qsa_plan p = nullptr;
+    st = qsa_plan_create(ops, n_ops, s->n, opts, s->L, &p);
+    if (st != QSA_OK) return st;
+    st = qsa_plan_execute(s, p, stats);
+    if (p->d_mat) {
+        // free after the stream has consumed the matrices
+        cudaStreamSynchronize(s->stream);
+        cudaFree(p->d_mat);
+        p->d_mat = nullptr;
+    }
+    delete p;
+    return st;
+}
+
+qsa_status qsa_state_counters(qsa_state s, uint64_t* launches) {
+    if (!s || !launches) return fail(QSA_E_ARG, "NULL argument");
+    *launches = s->launches;
+    return QSA_OK;
+}
+
+}  // extern "C"

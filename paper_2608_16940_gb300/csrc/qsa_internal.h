@@ -1,0 +1,68 @@
+// Internal declarations shared by the runtime (.cpp) and the kernels (.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "qsa.h"
+
+namespace qsa {
+
+// Tile geometry of one full-state pass (§IV-B: the 2^k x 2^(N-k) view is
+// walked tile by tile).  A tile is every amplitude whose index agrees with the
+// tile's base on all "outer" bit positions; its T tile bits are the m lowest
+// positions (contiguous runs of 2^m amplitudes) plus nx extra positions
+// xpos[] >= m.  Tiles partition the state, so a pass can run in place.
+struct TileGeom {
+    int n;          // qubits
+    int T;          // tile bits
+    int m;          // run bits (positions 0..m-1)
+    int nx;         // extra tile bits
+    int xpos[6];    // extra positions, ascending
+    uint64_t ntiles;
+};
+
+// Chooses m so that every position in `special` is a tile bit and
+// m + #(special >= m) <= T (T = min(T_want, n)).  Returns false if more than
+// six special positions would be extra bits.
+bool make_geom(int n, const int* special, int ns, int T_want, TileGeom* g);
+
+// Number of SMs of the current device (cached).
+int num_sms();
+
+// ---- launchers (return the first CUDA error; *launches incremented) --------
+cudaError_t launch_init_zero(float2* psi, int n, cudaStream_t st, uint64_t* launches);
+
+// FP32 fused dense update: phys[j] = physical position of target j (V order),
+// d_mat = 2*4^k floats (row-major, interleaved) in device memory.
+cudaError_t launch_apply_fp32(float2* psi, int n, const int* phys, int k, const float* d_mat,
+                              cudaStream_t st, uint64_t* launches);
+
+// Split-TF32 tensor-core update for k = 5, 6.  d_mat as above.  d_err: one
+// int in device memory; the kernel writes a non-zero code when a bounded wait
+// gives up.  Returns cudaErrorNotSupported for other k.
+cudaError_t launch_apply_tc(float2* psi, int n, const int* phys, int k, const float* d_mat, int* d_err,
+                            cudaStream_t st, uint64_t* launches);
+
+// In-place swap of physical bit pairs (pa[i] <-> pb[i]), all positions distinct.
+cudaError_t launch_permute(float2* psi, int n, const int* pa, const int* pb, int npairs, cudaStream_t st,
+                           uint64_t* launches);
+
+// FP64 sum of (-1)^{popcount(y & physmask)} |psi_y|^2 into *d_out (device).
+// d_partials must hold reduce_partials() doubles.
+int reduce_partials();
+cudaError_t launch_reduce_z(const float2* psi, int n, uint64_t physmask, double* d_partials, double* d_out,
+                            cudaStream_t st, uint64_t* launches);
+
+// out[x] = |psi_{encode(x)}|^2 for logical x; d_layout = int32 L[0..n-1] on device.
+cudaError_t launch_probs_logical(const float2* psi, int n, const int32_t* d_layout, double* out,
+                                 cudaStream_t st, uint64_t* launches);
+
+// Sampler scratch sizes and launch (see qsa_sample_counts).
+size_t sample_scratch_bytes(int n, uint64_t shots);
+cudaError_t launch_sample(const float2* psi, int n, const int32_t* d_layout, uint64_t shots, uint64_t seed,
+                          uint64_t stream_id, void* d_scratch, uint64_t* d_out_keys, uint64_t* d_out_counts,
+                          uint64_t* d_n_distinct, cudaStream_t st, uint64_t* launches);
+
+}  // namespace qsa

@@ -1,0 +1,94 @@
+// Host-side state object and helpers shared by runtime.cpp and planner.cpp.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "qsa.h"
+
+struct qsa_state_s {
+    int n = 0;
+    float2* psi = nullptr;
+    bool owned = false;
+    cudaStream_t stream = nullptr;
+    int32_t L[QSA_MAX_QUBITS] = {};   // layout map: logical -> physical
+    bool known_zero = false;          // state is |0..0> (metadata-only relabel allowed)
+    bool failed = false;              // sticky after a CUDA error
+    uint64_t launches = 0;            // kernels issued on this state
+    bool timing = false;              // record CUDA events around launches
+    // device scratch (grown on demand)
+    float* d_mat = nullptr;
+    size_t mat_cap = 0;
+    double* d_red = nullptr;
+    size_t red_cap = 0;
+    void* d_samp = nullptr;
+    size_t samp_cap = 0;
+    float* d_mlp = nullptr;
+    size_t mlp_cap = 0;
+    int* d_err = nullptr;             // device error word written by bounded waits
+    // CUDA-event timers
+    struct Pending {
+        cudaEvent_t a, b;
+        double* acc;
+    };
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free;
+    std::vector<Pending> ev_pending;
+};
+
+struct PlanBlock {
+    int32_t t[QSA_MAX_K];   // ordered logical targets of the fused block
+    int k = 0;
+    size_t off = 0;         // float offset of its matrix in host_mat / d_mat
+    size_t first_op = 0;
+};
+
+struct qsa_plan_s {
+    int n = 0;
+    qsa_plan_opts opts{};
+    size_t n_ops = 0;
+    int max_width = 0;
+    std::vector<PlanBlock> blocks;
+    std::vector<float> host_mat;   // all fused matrices, FP32, 16-byte aligned
+    float* d_mat = nullptr;        // device copy (uploaded on first execution)
+    int dev = -1;
+};
+
+namespace qsa {
+
+// In-block bits: the low positions a tile of the FP32 kernels covers as one
+// contiguous run (2^11 amplitudes = 16 KiB).
+constexpr int kInBlockBits = 11;
+
+qsa_status fail(qsa_status st, const std::string& msg);
+qsa_status cuda_fail(qsa_state s, cudaError_t e, const char* where);
+qsa_status check_state(qsa_state s);
+qsa_status ensure_dev(qsa_state s, void** ptr, size_t* cap, size_t bytes);
+void to_float_matrix(const double* m, int k, float* out);
+qsa_status validate_targets(int n, const int32_t* targets, int k);
+qsa_status apply_logical(qsa_state s, const int32_t* targets, int k, const float* d_mat, int lowering,
+                         int precision, qsa_run_stats* rs);
+qsa_status apply_physical(qsa_state s, const int* phys, int k, const float* d_mat, int precision,
+                          qsa_run_stats* rs);
+qsa_status permute_positions(qsa_state s, const int* pa, const int* pb, int np, qsa_run_stats* rs);
+bool tc_available(qsa_state s, int k);
+
+// Records a pair of CUDA events around the launches issued during its
+// lifetime; the elapsed time is added to *acc by collect_timers().
+class Timer {
+  public:
+    Timer(qsa_state s, double* acc);
+    ~Timer();
+    void stop();
+
+  private:
+    qsa_state s_;
+    double* acc_;
+    cudaEvent_t ev_[2] = {nullptr, nullptr};
+    bool stopped_ = false;
+};
+void collect_timers(qsa_state s, double* total);
+
+}  // namespace qsa

@@ -1,0 +1,402 @@
+// Reductions and sampling on the complex64 state (sm_103a).
+//
+//   launch_reduce_z      <Z_mask> and the norm, FP64 accumulation (App. B:
+//                        block totals kept in FP64).
+//   launch_probs_logical p_x = fl64(re^2) + fl64(im^2) for every logical x,
+//                        decoded through the layout map (Theorem 1).
+//   launch_sample        hierarchical CDF sampler (§IV-E "Sampling": 2^10-entry
+//                        blocks, strict upper bound) with integer weights
+//                        P_y = floor(re^2 2^60) + floor(im^2 2^60) so that the
+//                        CDF is exact and independent of summation order, one
+//                        Philox4x64-10 draw per shot, decode through L (§IV-D),
+//                        then sort + run-length encode into (outcome, count).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "qsa_internal.h"
+
+namespace qsa {
+
+namespace {
+
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocksPerSM = 8;
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_reduce_z(const float4* __restrict__ psi2, uint64_t npairs,
+                                                           uint64_t physmask, double* __restrict__ partials) {
+    double acc = 0.0;
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < npairs; i += stride) {
+        const float4 a = __ldcs(psi2 + i);
+        const double p0 = __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y));
+        const double p1 = __dadd_rn(__dmul_rn(a.z, a.z), __dmul_rn(a.w, a.w));
+        const uint64_t y0 = i << 1;
+        acc += (__popcll(y0 & physmask) & 1) ? -p0 : p0;
+        acc += (__popcll((y0 | 1ull) & physmask) & 1) ? -p1 : p1;
+    }
+    __shared__ double ws[kRedThreads / 32];
+    acc = warp_sum_d(acc);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (kRedThreads / 32) ? ws[threadIdx.x] : 0.0;
+        v = warp_sum_d(v);
+        if (threadIdx.x == 0) partials[blockIdx.x] = v;
+    }
+}
+
+// Fixed-order sum of the partials (deterministic for a given grid).
+__global__ void k_finalize_sum(const double* __restrict__ partials, int n, double* __restrict__ out) {
+    __shared__ double sh[1024];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += partials[i];
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
+        if (static_cast<int>(threadIdx.x) < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+struct Layout {
+    int n;
+    int L[QSA_MAX_QUBITS];
+};
+
+__device__ __forceinline__ uint64_t encode_logical(uint64_t x, const Layout& lay) {
+    uint64_t y = 0;
+#pragma unroll
+    for (int q = 0; q < QSA_MAX_QUBITS; ++q)
+        if (q < lay.n) y |= ((x >> q) & 1ull) << lay.L[q];
+    return y;
+}
+
+__device__ __forceinline__ uint64_t decode_physical(uint64_t y, const Layout& lay) {
+    uint64_t x = 0;
+#pragma unroll
+    for (int q = 0; q < QSA_MAX_QUBITS; ++q)
+        if (q < lay.n) x |= ((y >> lay.L[q]) & 1ull) << q;
+    return x;
+}
+
+__global__ void k_probs_logical(const float2* __restrict__ psi, Layout lay, double* __restrict__ out) {
+    const uint64_t dim = 1ull << lay.n;
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    for (uint64_t x = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < dim; x += stride) {
+        const float2 a = psi[encode_logical(x, lay)];
+        out[x] = __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Sampler
+// ---------------------------------------------------------------------------
+
+// floor(v^2 * 2^60) exactly, in integers: v = M * 2^E with a 24-bit M, so
+// v^2 2^60 = M^2 2^(2E+60).  Valid for |v| < 2.
+__device__ __forceinline__ uint64_t sq_fixed60(float v) {
+    const uint32_t b = __float_as_uint(v) & 0x7fffffffu;
+    const uint32_t e8 = b >> 23;
+    const uint32_t M = (b & 0x7fffffu) | (e8 ? 0x800000u : 0u);
+    const int E = static_cast<int>(e8 ? e8 : 1u) - 150;
+    const uint64_t sq = static_cast<uint64_t>(M) * M;
+    const int s = 2 * E + 60;
+    if (s >= 0) return s < 16 ? (sq << s) : (1ull << 62);
+    return (-s) >= 64 ? 0ull : (sq >> (-s));
+}
+
+__device__ __forceinline__ uint64_t weight(float2 a) { return sq_fixed60(a.x) + sq_fixed60(a.y); }
+
+__device__ __forceinline__ uint64_t warp_incl_scan_u64(uint64_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint64_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One warp per block of `bsz` amplitudes: total integer weight.
+__global__ void k_block_weights(const float2* __restrict__ psi, uint64_t nblocks, int bsz,
+                                uint64_t* __restrict__ cum) {
+    const uint64_t w = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nblocks) return;
+    const float2* p = psi + w * bsz;
+    uint64_t s = 0;
+    for (int j = lane; j < bsz; j += 32) s += weight(p[j]);
+    s = warp_sum_u64(s);
+    if (lane == 0) cum[w] = s;
+}
+
+// In-place inclusive scan of cum[0..n-1] by one CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) k_scan_inclusive(uint64_t* __restrict__ cum, uint64_t n) {
+    __shared__ uint64_t wsum[32];
+    __shared__ uint64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (uint64_t base = 0; base < n; base += blockDim.x) {
+        const uint64_t i = base + threadIdx.x;
+        uint64_t v = i < n ? cum[i] : 0;
+        uint64_t inc = warp_incl_scan_u64(v);
+        if (lane == 31) wsum[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            uint64_t s = wsum[lane];
+            wsum[lane] = warp_incl_scan_u64(s);
+        }
+        __syncthreads();
+        const uint64_t off = carry + (wid ? wsum[wid - 1] : 0);
+        if (i < n) cum[i] = inc + off;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = inc + off;
+        __syncthreads();
+    }
+}
+
+// Philox4x64-10 (Salmon et al., SC'11), word 0 of the block at (ctr, key).
+__device__ __forceinline__ uint64_t philox4x64_10_w0(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                                     uint64_t k0, uint64_t k1) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+        const uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+        const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return c0;
+}
+
+// One warp per shot: draw u, find the block (first cum > u), then the amplitude.
+__global__ void k_draw(const float2* __restrict__ psi, const uint64_t* __restrict__ cum, uint64_t nblocks, int bsz,
+                       Layout lay, uint64_t shots, uint64_t seed, uint64_t stream_id, uint64_t* __restrict__ keys) {
+    const uint64_t s = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (s >= shots) return;
+    const uint64_t total = cum[nblocks - 1];
+    if (total == 0) {  // all-zero state: the host reports it; avoid the modulo by zero
+        if (lane == 0) keys[s] = 0;
+        return;
+    }
+    const uint64_t r = philox4x64_10_w0(s, stream_id, 0, 0, seed, 0);
+    const uint64_t u = r % total;
+    // first block b with cum[b] > u
+    uint64_t lo = 0, hi = nblocks - 1;
+    while (lo < hi) {
+        uint64_t mid = lo + ((hi - lo) >> 1);
+        if (cum[mid] > u) hi = mid; else lo = mid + 1;
+    }
+    const uint64_t b = lo;
+    const uint64_t ub = u - (b ? cum[b - 1] : 0);
+    // lane l covers amplitudes [l*per, (l+1)*per) of the block
+    const int per = (bsz + 31) >> 5;
+    const float2* p = psi + b * static_cast<uint64_t>(bsz);
+    uint64_t wl = 0;
+    for (int j = 0; j < per; ++j) {
+        int idx = lane * per + j;
+        if (idx < bsz) wl += weight(p[idx]);
+    }
+    const uint64_t incl = warp_incl_scan_u64(wl);
+    const uint64_t excl = incl - wl;
+    const unsigned hit = __ballot_sync(0xffffffffu, excl <= ub && ub < incl);
+    const int owner = __ffs(hit) - 1;   // exactly one lane: the weights sum to cum[b] - cum[b-1] > ub
+    if (lane == owner) {
+        uint64_t acc = excl;
+        int j = 0;
+        for (; j < per; ++j) {
+            int idx = lane * per + j;
+            if (idx >= bsz) break;
+            acc += weight(p[idx]);
+            if (acc > ub) break;
+        }
+        const uint64_t y = b * static_cast<uint64_t>(bsz) + static_cast<uint64_t>(lane * per + j);
+        keys[s] = decode_physical(y, lay);
+    }
+}
+
+__global__ void k_fill_u64(uint64_t* a, uint64_t from, uint64_t to, uint64_t v) {
+    uint64_t i = from + static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < to) a[i] = v;
+}
+
+// Bitonic sort of P = 2^p keys.  Small P: one CTA in shared memory.
+__global__ void __launch_bounds__(1024) k_bitonic_smem(uint64_t* keys, int P) {
+    extern __shared__ uint64_t sk[];
+    for (int i = threadIdx.x; i < P; i += blockDim.x) sk[i] = keys[i];
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                int l = i ^ j;
+                if (l > i) {
+                    bool up = (i & k) == 0;
+                    uint64_t a = sk[i], c = sk[l];
+                    if ((a > c) == up) {
+                        sk[i] = c;
+                        sk[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < P; i += blockDim.x) keys[i] = sk[i];
+}
+
+__global__ void k_bitonic_step(uint64_t* keys, uint64_t P, uint64_t j, uint64_t k) {
+    uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    uint64_t l = i ^ j;
+    if (l > i) {
+        bool up = (i & k) == 0;
+        uint64_t a = keys[i], c = keys[l];
+        if ((a > c) == up) {
+            keys[i] = c;
+            keys[l] = a;
+        }
+    }
+}
+
+// Run-length encode the sorted keys[0..n-1] with one CTA: distinct keys and
+// their counts, and the number of distinct keys.
+__global__ void __launch_bounds__(1024) k_rle(const uint64_t* __restrict__ keys, uint64_t n,
+                                              uint64_t* __restrict__ out_keys, uint64_t* __restrict__ starts,
+                                              uint64_t* __restrict__ out_counts, uint64_t* __restrict__ n_distinct) {
+    __shared__ uint64_t wsum[32];
+    __shared__ uint64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (uint64_t base = 0; base < n; base += blockDim.x) {
+        const uint64_t i = base + threadIdx.x;
+        const uint64_t head = (i < n && (i == 0 || keys[i] != keys[i - 1])) ? 1 : 0;
+        uint64_t inc = warp_incl_scan_u64(head);
+        if (lane == 31) wsum[wid] = inc;
+        __syncthreads();
+        if (wid == 0) wsum[lane] = warp_incl_scan_u64(wsum[lane]);
+        __syncthreads();
+        const uint64_t pos = carry + (wid ? wsum[wid - 1] : 0) + inc - head;
+        if (head) {
+            out_keys[pos] = keys[i];
+            starts[pos] = i;
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = pos + head;
+        __syncthreads();
+    }
+    const uint64_t nd = carry;
+    for (uint64_t d = threadIdx.x; d < nd; d += blockDim.x)
+        out_counts[d] = (d + 1 < nd ? starts[d + 1] : n) - starts[d];
+    if (threadIdx.x == 0) *n_distinct = nd;
+}
+
+inline uint64_t next_pow2(uint64_t v) {
+    uint64_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+int reduce_partials() { return num_sms() * kRedBlocksPerSM; }
+
+cudaError_t launch_reduce_z(const float2* psi, int n, uint64_t physmask, double* d_partials, double* d_out,
+                            cudaStream_t st, uint64_t* launches) {
+    const uint64_t npairs = (1ull << n) >> 1;
+    const int nb = reduce_partials();
+    if (npairs == 0) {
+        // n = 1 is still >= one pair; n >= 1 always holds here
+        return cudaErrorInvalidValue;
+    }
+    k_reduce_z<<<nb, kRedThreads, 0, st>>>(reinterpret_cast<const float4*>(psi), npairs, physmask, d_partials);
+    k_finalize_sum<<<1, 1024, 0, st>>>(d_partials, nb, d_out);
+    *launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_probs_logical(const float2* psi, int n, const int32_t* layout_host, double* out, cudaStream_t st,
+                                 uint64_t* launches) {
+    Layout lay{};
+    lay.n = n;
+    for (int q = 0; q < n; ++q) lay.L[q] = layout_host[q];
+    const uint64_t dim = 1ull << n;
+    uint64_t blocks = (dim + 255) / 256;
+    const uint64_t cap = static_cast<uint64_t>(num_sms()) * 16;
+    if (blocks > cap) blocks = cap;
+    k_probs_logical<<<static_cast<unsigned>(blocks), 256, 0, st>>>(psi, lay, out);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+size_t sample_scratch_bytes(int n, uint64_t shots) {
+    const int bsz = n >= 10 ? 1024 : (1 << n);
+    const uint64_t nblocks = (1ull << n) / bsz;
+    const uint64_t P = next_pow2(shots);
+    return sizeof(uint64_t) * (nblocks + P + shots) + 256;
+}
+
+cudaError_t launch_sample(const float2* psi, int n, const int32_t* layout_host, uint64_t shots, uint64_t seed,
+                          uint64_t stream_id, void* d_scratch, uint64_t* d_out_keys, uint64_t* d_out_counts,
+                          uint64_t* d_n_distinct, cudaStream_t st, uint64_t* launches) {
+    Layout lay{};
+    lay.n = n;
+    for (int q = 0; q < n; ++q) lay.L[q] = layout_host[q];
+    const int bsz = n >= 10 ? 1024 : (1 << n);
+    const uint64_t nblocks = (1ull << n) / bsz;
+    const uint64_t P = next_pow2(shots);
+    uint64_t* cum = reinterpret_cast<uint64_t*>(d_scratch);
+    uint64_t* keys = cum + nblocks;
+    uint64_t* starts = keys + P;
+
+    const unsigned wpb = 8;  // warps per CTA
+    k_block_weights<<<static_cast<unsigned>((nblocks + wpb - 1) / wpb), wpb * 32, 0, st>>>(psi, nblocks, bsz, cum);
+    k_scan_inclusive<<<1, 1024, 0, st>>>(cum, nblocks);
+    k_draw<<<static_cast<unsigned>((shots + wpb - 1) / wpb), wpb * 32, 0, st>>>(psi, cum, nblocks, bsz, lay, shots,
+                                                                                 seed, stream_id, keys);
+    *launches += 3;
+    if (P > shots) {
+        k_fill_u64<<<static_cast<unsigned>((P - shots + 255) / 256), 256, 0, st>>>(keys, shots, P, ~0ull);
+        ++*launches;
+    }
+    if (P <= 4096) {
+        k_bitonic_smem<<<1, 1024, sizeof(uint64_t) * P, st>>>(keys, static_cast<int>(P));
+        ++*launches;
+    } else {
+        const unsigned nb = static_cast<unsigned>((P + 255) / 256);
+        for (uint64_t k = 2; k <= P; k <<= 1)
+            for (uint64_t j = k >> 1; j > 0; j >>= 1) {
+                k_bitonic_step<<<nb, 256, 0, st>>>(keys, P, j, k);
+                ++*launches;
+            }
+    }
+    k_rle<<<1, 1024, 0, st>>>(keys, shots, d_out_keys, starts, d_out_counts, d_n_distinct);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+}  // namespace qsa

@@ -1,0 +1,499 @@
+// Host runtime behind the C ABI in include/qsa.h: state objects, the layout
+// map, lowering dispatch, circuit execution and output reductions.
+//
+// Layout map (§II, Theorem 1): L[q] = physical position of logical qubit q.
+// The stored amplitude at y equals the logical amplitude at x with
+// x_q = y_{L(q)}.  Every physical permutation composes L with the same
+// transpositions (Lemma "distributed promotion swap"), so consumers decode
+// through L instead of restoring canonical order (§IV-D).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "qsa.h"
+#include "qsa_internal.h"
+#include "qsa_runtime.h"
+
+namespace {
+thread_local std::string g_err;
+}
+
+namespace qsa {
+
+qsa_status fail(qsa_status st, const std::string& msg) {
+    g_err = msg;
+    return st;
+}
+
+qsa_status cuda_fail(qsa_state s, cudaError_t e, const char* where) {
+    if (s) s->failed = true;
+    return fail(QSA_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+qsa_status check_state(qsa_state s) {
+    if (!s) return fail(QSA_E_ARG, "state is NULL");
+    if (s->failed) return fail(QSA_E_STATE, "state is marked failed after a CUDA error");
+    return QSA_OK;
+}
+
+qsa_status ensure_dev(qsa_state s, void** ptr, size_t* cap, size_t bytes) {
+    if (*cap >= bytes && *ptr) return QSA_OK;
+    if (*ptr) {
+        cudaStreamSynchronize(s->stream);
+        cudaFree(*ptr);
+        *ptr = nullptr;
+        *cap = 0;
+    }
+    size_t want = std::max<size_t>(bytes, 4096);
+    cudaError_t e = cudaMalloc(ptr, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return fail(QSA_E_NOMEM, std::string("cudaMalloc of scratch failed: ") + cudaGetErrorString(e));
+    }
+    *cap = want;
+    return QSA_OK;
+}
+
+void to_float_matrix(const double* m, int k, float* out) {
+    const size_t cnt = 2ull << (2 * k);
+    for (size_t i = 0; i < cnt; ++i) out[i] = static_cast<float>(m[i]);
+}
+
+qsa_status validate_targets(int n, const int32_t* targets, int k) {
+    if (!targets) return fail(QSA_E_ARG, "targets is NULL");
+    if (k < 1 || k > QSA_MAX_K) return fail(QSA_E_ARG, "k must be in 1..6");
+    if (k > n) return fail(QSA_E_ARG, "k exceeds the number of qubits");
+    uint64_t seen = 0;
+    for (int j = 0; j < k; ++j) {
+        if (targets[j] < 0 || targets[j] >= n) return fail(QSA_E_ARG, "target out of range");
+        if (seen & (1ull << targets[j])) return fail(QSA_E_ARG, "repeated target");
+        seen |= 1ull << targets[j];
+    }
+    return QSA_OK;
+}
+
+// Swap physical positions pairs (pa[i], pb[i]) in data and layout.
+qsa_status permute_positions(qsa_state s, const int* pa, const int* pb, int np, qsa_run_stats* rs) {
+    if (np == 0) return QSA_OK;
+    Timer tm(s, rs ? &rs->permute_seconds : nullptr);
+    cudaError_t e = launch_permute(s->psi, s->n, pa, pb, np, s->stream, &s->launches);
+    tm.stop();
+    if (e != cudaSuccess) return cuda_fail(s, e, "permute kernel");
+    int inv[64];
+    for (int q = 0; q < s->n; ++q) inv[s->L[q]] = q;
+    for (int i = 0; i < np; ++i) {
+        int qa = inv[pa[i]], qb = inv[pb[i]];
+        s->L[qa] = pb[i];
+        s->L[qb] = pa[i];
+        inv[pa[i]] = qb;
+        inv[pb[i]] = qa;
+    }
+    if (rs) {
+        rs->permutes += 1;
+        rs->passes += 1;
+        rs->hbm_bytes += 16.0 * static_cast<double>(1ull << s->n);
+    }
+    return QSA_OK;
+}
+
+// Promote targets outside the in-block bits (positions >= inblock) to the
+// lowest free in-block positions (first-free victim choice, §IV-D), updating
+// phys[] to the new positions.
+qsa_status promote_targets(qsa_state s, int* phys, int k, int inblock, qsa_run_stats* rs) {
+    inblock = std::min(inblock, s->n);
+    int pa[6], pb[6], np = 0;
+    uint64_t pinned = 0;
+    for (int j = 0; j < k; ++j)
+        if (phys[j] < inblock) pinned |= 1ull << phys[j];
+    int next = 0;
+    for (int j = 0; j < k; ++j) {
+        if (phys[j] < inblock) continue;
+        while (next < inblock && ((pinned >> next) & 1)) ++next;
+        if (next >= inblock) return fail(QSA_E_ARG, "not enough free in-block positions");
+        pa[np] = phys[j];
+        pb[np] = next;
+        pinned |= 1ull << next;
+        phys[j] = next;
+        ++np;
+    }
+    return permute_positions(s, pa, pb, np, rs);
+}
+
+qsa_status apply_physical(qsa_state s, const int* phys, int k, const float* d_mat, int precision,
+                          qsa_run_stats* rs) {
+    cudaError_t e;
+    bool tc = precision == QSA_PREC_TF32X3 && (k == 5 || k == 6) && tc_available(s, k);
+    {
+        Timer tm(s, rs ? &rs->apply_seconds : nullptr);
+        if (tc)
+            e = launch_apply_tc(s->psi, s->n, phys, k, d_mat, s->d_err, s->stream, &s->launches);
+        else
+            e = launch_apply_fp32(s->psi, s->n, phys, k, d_mat, s->stream, &s->launches);
+        tm.stop();
+    }
+    if (e != cudaSuccess) return cuda_fail(s, e, tc ? "tensor-core apply kernel" : "apply kernel");
+    s->known_zero = false;
+    if (rs) {
+        rs->blocks += 1;
+        rs->passes += 1;
+        rs->tc_blocks += tc ? 1 : 0;
+        rs->hbm_bytes += 16.0 * static_cast<double>(1ull << s->n);
+    }
+    return QSA_OK;
+}
+
+qsa_status apply_logical(qsa_state s, const int32_t* targets, int k, const float* d_mat, int lowering,
+                         int precision, qsa_run_stats* rs) {
+    int phys[6];
+    for (int j = 0; j < k; ++j) phys[j] = s->L[targets[j]];
+    if (lowering == QSA_LOWER_PERMUTE) {
+        qsa_status st = promote_targets(s, phys, k, kInBlockBits, rs);
+        if (st != QSA_OK) return st;
+    }
+    return apply_physical(s, phys, k, d_mat, precision, rs);
+}
+
+// ---- timers ------------------------------------------------------------------
+Timer::Timer(qsa_state s, double* acc) : s_(s), acc_(s->timing ? acc : nullptr) {
+    if (!acc_) return;
+    if (s_->ev_free.empty()) {
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        ev_[0] = a;
+        ev_[1] = b;
+    } else {
+        auto p = s_->ev_free.back();
+        s_->ev_free.pop_back();
+        ev_[0] = p.first;
+        ev_[1] = p.second;
+    }
+    cudaEventRecord(ev_[0], s_->stream);
+}
+
+void Timer::stop() {
+    if (!acc_ || stopped_) return;
+    stopped_ = true;
+    cudaEventRecord(ev_[1], s_->stream);
+    s_->ev_pending.push_back({ev_[0], ev_[1], acc_});
+}
+
+Timer::~Timer() { stop(); }
+
+void collect_timers(qsa_state s, double* total) {
+    if (s->ev_pending.empty()) return;
+    cudaStreamSynchronize(s->stream);
+    for (auto& p : s->ev_pending) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        *p.acc += ms * 1e-3;
+        if (total) *total += ms * 1e-3;
+        s->ev_free.push_back({p.a, p.b});
+    }
+    s->ev_pending.clear();
+}
+
+}  // namespace qsa
+
+using namespace qsa;
+
+extern "C" {
+
+const char* qsa_last_error(void) { return g_err.c_str(); }
+
+qsa_status qsa_state_create_ex(int n_qubits, qsa_dtype dtype, void* dev_buf, size_t bytes, void* cuda_stream,
+                               int init_zero, qsa_state* out) {
+    if (!out) return fail(QSA_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (dtype == QSA_C128) return fail(QSA_E_UNSUPPORTED, "complex128 states are not implemented");
+    if (dtype != QSA_C64) return fail(QSA_E_ARG, "unknown dtype");
+    if (n_qubits < 1 || n_qubits > QSA_MAX_QUBITS) return fail(QSA_E_ARG, "n_qubits must be in 1..34");
+    const size_t need = sizeof(float2) << n_qubits;
+    auto* s = new qsa_state_s();
+    s->n = n_qubits;
+    s->stream = static_cast<cudaStream_t>(cuda_stream);
+    for (int q = 0; q < n_qubits; ++q) s->L[q] = q;
+    if (dev_buf) {
+        if (bytes < need) {
+            delete s;
+            return fail(QSA_E_ARG, "device buffer smaller than 8 * 2^N bytes");
+        }
+        if (reinterpret_cast<uintptr_t>(dev_buf) % 16) {
+            delete s;
+            return fail(QSA_E_ARG, "device buffer must be 16-byte aligned");
+        }
+        s->psi = static_cast<float2*>(dev_buf);
+        s->owned = false;
+    } else {
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            delete s;
+            return fail(QSA_E_NOMEM, std::string("cudaMalloc of the state failed: ") + cudaGetErrorString(e));
+        }
+        s->psi = static_cast<float2*>(p);
+        s->owned = true;
+        init_zero = 1;
+    }
+    cudaError_t e = cudaMalloc(&s->d_err, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, sizeof(int) * 4, s->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (s->owned) cudaFree(s->psi);
+        delete s;
+        return fail(QSA_E_NOMEM, "cudaMalloc of the error word failed");
+    }
+    if (init_zero) {
+        e = launch_init_zero(s->psi, s->n, s->stream, &s->launches);
+        if (e != cudaSuccess) {
+            qsa_status st = cuda_fail(s, e, "init");
+            if (s->owned) cudaFree(s->psi);
+            delete s;
+            return st;
+        }
+        s->known_zero = true;
+    }
+    *out = s;
+    return QSA_OK;
+}
+
+qsa_status qsa_state_create(int n_qubits, qsa_dtype dtype, qsa_state* out) {
+    return qsa_state_create_ex(n_qubits, dtype, nullptr, 0, nullptr, 1, out);
+}
+
+qsa_status qsa_state_destroy(qsa_state s) {
+    if (!s) return fail(QSA_E_ARG, "state is NULL");
+    cudaStreamSynchronize(s->stream);
+    cudaGetLastError();
+    if (s->owned && s->psi) cudaFree(s->psi);
+    if (s->d_mat) cudaFree(s->d_mat);
+    if (s->d_red) cudaFree(s->d_red);
+    if (s->d_samp) cudaFree(s->d_samp);
+    if (s->d_err) cudaFree(s->d_err);
+    if (s->d_mlp) cudaFree(s->d_mlp);
+    for (auto& p : s->ev_free) {
+        cudaEventDestroy(p.first);
+        cudaEventDestroy(p.second);
+    }
+    for (auto& p : s->ev_pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    delete s;
+    return QSA_OK;
+}
+
+qsa_status qsa_set_stream(qsa_state s, void* cuda_stream) {
+    if (!s) return fail(QSA_E_ARG, "state is NULL");
+    s->stream = static_cast<cudaStream_t>(cuda_stream);
+    return QSA_OK;
+}
+
+qsa_status qsa_state_reset(qsa_state s) {
+    if (!s) return fail(QSA_E_ARG, "state is NULL");
+    if (s->failed) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return fail(QSA_E_STATE, "device is not healthy");
+        s->failed = false;
+    }
+    for (int q = 0; q < s->n; ++q) s->L[q] = q;
+    cudaError_t e = launch_init_zero(s->psi, s->n, s->stream, &s->launches);
+    if (e != cudaSuccess) return cuda_fail(s, e, "reset");
+    s->known_zero = true;
+    return QSA_OK;
+}
+
+qsa_status qsa_state_info(qsa_state s, int* n_qubits, void** dev_amplitudes) {
+    if (!s) return fail(QSA_E_ARG, "state is NULL");
+    if (n_qubits) *n_qubits = s->n;
+    if (dev_amplitudes) *dev_amplitudes = s->psi;
+    return QSA_OK;
+}
+
+qsa_status qsa_get_layout(qsa_state s, int32_t* phys_of_logical) {
+    if (!s || !phys_of_logical) return fail(QSA_E_ARG, "NULL argument");
+    for (int q = 0; q < s->n; ++q) phys_of_logical[q] = s->L[q];
+    return QSA_OK;
+}
+
+qsa_status qsa_set_layout(qsa_state s, const int32_t* phys_of_logical, int materialise) {
+    qsa_status st = check_state(s);
+    if (st != QSA_OK) return st;
+    if (!phys_of_logical) return fail(QSA_E_ARG, "layout is NULL");
+    uint64_t seen = 0;
+    for (int q = 0; q < s->n; ++q) {
+        int p = phys_of_logical[q];
+        if (p < 0 || p >= s->n || ((seen >> p) & 1)) return fail(QSA_E_ARG, "layout is not a bijection on 0..N-1");
+        seen |= 1ull << p;
+    }
+    if (!materialise) {
+        if (!s->known_zero) return fail(QSA_E_STATE, "metadata-only relabel needs the state |0..0>");
+        for (int q = 0; q < s->n; ++q) s->L[q] = phys_of_logical[q];
+        return QSA_OK;
+    }
+    // Passes of disjoint transpositions; each swap puts one logical qubit in
+    // its final position.
+    for (int guard = 0; guard < 2 * QSA_MAX_QUBITS; ++guard) {
+        int pa[QSA_MAX_QUBITS], pb[QSA_MAX_QUBITS], np = 0;
+        uint64_t used = 0;
+        for (int q = 0; q < s->n; ++q) {
+            int a = s->L[q], b = phys_of_logical[q];
+            if (a == b || ((used >> a) & 1) || ((used >> b) & 1)) continue;
+            used |= (1ull << a) | (1ull << b);
+            pa[np] = a;
+            pb[np] = b;
+            ++np;
+        }
+        if (np == 0) break;
+        for (int i = 0; i < np; i += 6) {
+            st = permute_positions(s, pa + i, pb + i, std::min(6, np - i), nullptr);
+            if (st != QSA_OK) return st;
+        }
+    }
+    for (int q = 0; q < s->n; ++q)
+        if (s->L[q] != phys_of_logical[q]) return fail(QSA_E_STATE, "layout materialisation did not converge");
+    return QSA_OK;
+}
+
+qsa_status qsa_permute_bits(qsa_state s, const int32_t* phys_a, const int32_t* phys_b, int n_pairs) {
+    qsa_status st = check_state(s);
+    if (st != QSA_OK) return st;
+    if (n_pairs < 0 || (n_pairs > 0 && (!phys_a || !phys_b))) return fail(QSA_E_ARG, "bad pair list");
+    uint64_t seen = 0;
+    std::vector<int> a(n_pairs), b(n_pairs);
+    for (int i = 0; i < n_pairs; ++i) {
+        int x = phys_a[i], y = phys_b[i];
+        if (x < 0 || x >= s->n || y < 0 || y >= s->n || x == y) return fail(QSA_E_ARG, "bad position");
+        if (((seen >> x) & 1) || ((seen >> y) & 1)) return fail(QSA_E_ARG, "positions must be distinct");
+        seen |= (1ull << x) | (1ull << y);
+        a[i] = x;
+        b[i] = y;
+    }
+    for (int i = 0; i < n_pairs; i += 6) {
+        st = permute_positions(s, a.data() + i, b.data() + i, std::min(6, n_pairs - i), nullptr);
+        if (st != QSA_OK) return st;
+    }
+    return QSA_OK;
+}
+
+qsa_status qsa_apply_fused_ex(qsa_state s, const int32_t* targets, int k, const double* matrix, int lowering,
+                              int precision) {
+    qsa_status st = check_state(s);
+    if (st != QSA_OK) return st;
+    st = validate_targets(s->n, targets, k);
+    if (st != QSA_OK) return st;
+    if (!matrix) return fail(QSA_E_ARG, "matrix is NULL");
+    if (lowering < 0 || lowering > 2) return fail(QSA_E_ARG, "unknown lowering");
+    if (precision < 0 || precision > 1) return fail(QSA_E_ARG, "unknown precision");
+    const size_t cnt = 2ull << (2 * k);
+    std::vector<float> hm(cnt);
+    to_float_matrix(matrix, k, hm.data());
+    st = ensure_dev(s, reinterpret_cast<void**>(&s->d_mat), &s->mat_cap, cnt * sizeof(float));
+    if (st != QSA_OK) return st;
+    // pageable source: the copy is staged before the call returns
+    cudaError_t e = cudaMemcpyAsync(s->d_mat, hm.data(), cnt * sizeof(float), cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "matrix upload");
+    return apply_logical(s, targets, k, s->d_mat, lowering, precision, nullptr);
+}
+
+qsa_status qsa_apply_fused(qsa_state s, const int32_t* targets, int k, const double* matrix) {
+    return qsa_apply_fused_ex(s, targets, k, matrix, QSA_LOWER_AUTO, QSA_PREC_FP32);
+}
+
+qsa_status qsa_expectation_z(qsa_state s, uint64_t logical_mask, double* out) {
+    qsa_status st = check_state(s);
+    if (st != QSA_OK) return st;
+    if (!out) return fail(QSA_E_ARG, "out is NULL");
+    if (s->n < 64 && (logical_mask >> s->n)) return fail(QSA_E_ARG, "mask has bits beyond N");
+    uint64_t pm = 0;
+    for (int q = 0; q < s->n; ++q)
+        if ((logical_mask >> q) & 1) pm |= 1ull << s->L[q];
+    st = ensure_dev(s, reinterpret_cast<void**>(&s->d_red), &s->red_cap, sizeof(double) * (reduce_partials() + 8));
+    if (st != QSA_OK) return st;
+    double* d_out = s->d_red + reduce_partials();
+    cudaError_t e = launch_reduce_z(s->psi, s->n, pm, s->d_red, d_out, s->stream, &s->launches);
+    if (e != cudaSuccess) return cuda_fail(s, e, "reduction kernel");
+    e = cudaMemcpyAsync(out, d_out, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "reduction result");
+    return QSA_OK;
+}
+
+qsa_status qsa_probabilities_device(qsa_state s, double* out_dev, double* norm_out) {
+    qsa_status st = check_state(s);
+    if (st != QSA_OK) return st;
+    if (out_dev) {
+        cudaError_t e = launch_probs_logical(s->psi, s->n, s->L, out_dev, s->stream, &s->launches);
+        if (e != cudaSuccess) return cuda_fail(s, e, "probability kernel");
+    }
+    if (norm_out) return qsa_expectation_z(s, 0, norm_out);
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "probabilities");
+    return QSA_OK;
+}
+
+qsa_status qsa_probabilities(qsa_state s, double* out_host, double* norm_out) {
+    qsa_status st = check_state(s);
+    if (st != QSA_OK) return st;
+    if (out_host) {
+        const size_t bytes = sizeof(double) << s->n;
+        double* tmp = nullptr;
+        cudaError_t e = cudaMalloc(&tmp, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(QSA_E_NOMEM, "cudaMalloc of the probability buffer failed");
+        }
+        e = launch_probs_logical(s->psi, s->n, s->L, tmp, s->stream, &s->launches);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, tmp, bytes, cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        cudaFree(tmp);
+        if (e != cudaSuccess) return cuda_fail(s, e, "probabilities");
+    }
+    if (norm_out) return qsa_expectation_z(s, 0, norm_out);
+    return QSA_OK;
+}
+
+qsa_status qsa_sample_counts(qsa_state s, uint64_t shots, uint64_t seed, uint64_t* outcomes, uint64_t* counts,
+                             size_t capacity, size_t* n_distinct) {
+    qsa_status st = check_state(s);
+    if (st != QSA_OK) return st;
+    if (!n_distinct) return fail(QSA_E_ARG, "n_distinct is NULL");
+    if (shots < 1 || shots > (1ull << 26)) return fail(QSA_E_ARG, "shots must be in 1..2^26");
+    if (capacity > 0 && (!outcomes || !counts)) return fail(QSA_E_ARG, "output arrays are NULL");
+    const size_t scratch = sample_scratch_bytes(s->n, shots);
+    const size_t outb = sizeof(uint64_t) * (2 * shots + 4);
+    st = ensure_dev(s, &s->d_samp, &s->samp_cap, scratch + outb);
+    if (st != QSA_OK) return st;
+    uint64_t* d_keys = reinterpret_cast<uint64_t*>(static_cast<char*>(s->d_samp) + scratch);
+    uint64_t* d_cnts = d_keys + shots;
+    uint64_t* d_nd = d_cnts + shots;
+    cudaError_t e = launch_sample(s->psi, s->n, s->L, shots, seed, 0, s->d_samp, d_keys, d_cnts, d_nd, s->stream,
+                                  &s->launches);
+    if (e != cudaSuccess) return cuda_fail(s, e, "sampler kernels");
+    uint64_t hdr[2] = {0, 0};
+    const int bsz = s->n >= 10 ? 1024 : (1 << s->n);
+    const uint64_t nblocks = (1ull << s->n) / bsz;
+    e = cudaMemcpyAsync(&hdr[0], d_nd, sizeof(uint64_t), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&hdr[1], static_cast<uint64_t*>(s->d_samp) + (nblocks - 1), sizeof(uint64_t),
+                            cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "sampler result");
+    if (hdr[1] == 0) return fail(QSA_E_STATE, "every amplitude weight is zero");
+    *n_distinct = static_cast<size_t>(hdr[0]);
+    if (capacity < hdr[0]) return fail(QSA_E_RANGE, "capacity smaller than the number of distinct outcomes");
+    e = cudaMemcpyAsync(outcomes, d_keys, sizeof(uint64_t) * hdr[0], cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(counts, d_cnts, sizeof(uint64_t) * hdr[0], cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "sampler copy");
+    return QSA_OK;
+}
+
+}  // extern "C"

@@ -1,4 +1,7 @@
 """Pins for the oracle's counter-based generator and CDF sampler (no GPU)."""
+import math
+from fractions import Fraction
+
 import numpy as np
 import pytest
 from scipy import stats
@@ -24,16 +27,16 @@ def test_philox4x64_10_matches_numpy(key, ctr):
 
 
 def _brute_force_sample(psi_logical, L, shots, seed, stream):
-    """Same reading written with Python integers and numpy's Philox: weights
-    trunc(p * 2^62) in physical order, linear scan for the first cumulative
-    value above u."""
+    """Same reading written with exact rationals and numpy's Philox: weights
+    floor(re^2 2^60) + floor(im^2 2^60) in physical order, linear scan for the
+    first cumulative value above u."""
     n = int(psi_logical.size).bit_length() - 1
     w = []
     for y in range(1 << n):
         x = sum(((y >> L[q]) & 1) << q for q in range(n))
         a = psi_logical[x]
-        p = float(a.real) * float(a.real) + float(a.imag) * float(a.imag)
-        w.append(int(p * 2.0 ** 62))
+        w.append(math.floor(Fraction(float(a.real)) ** 2 * 2 ** 60) +
+                 math.floor(Fraction(float(a.imag)) ** 2 * 2 ** 60))
     total = sum(w)
     out = []
     for s in range(shots):
