@@ -258,6 +258,36 @@ qsa_status qsa_expectation_z(qsa_state s, uint64_t logical_mask, double* out);
 qsa_status qsa_sample_counts(qsa_state s, uint64_t shots, uint64_t seed, uint64_t* outcomes, uint64_t* counts,
                              size_t capacity, size_t* n_distinct);
 
+/* Sampling that allocates nothing on the device.  The paper has no
+ * counterpart: this exists for callers that cannot let the library call
+ * cudaMalloc, e.g. a framework whose caching allocator owns the device memory
+ * budget (at N = 33/34 the state fills most of HBM and a stray allocation can
+ * fail or fragment the pool) or a pipeline that must not stall (cudaFree
+ * synchronises the whole device).
+ *
+ * Same draws and results as qsa_sample_counts, but everything is caller-owned
+ * except the scratch, which is one fixed device array of
+ * QSA_NOALLOC_SCRATCH_WORDS 64-bit words (4 MiB) held by every GPU that loads
+ * the library until the process exits.  Requests needing more scratch,
+ * 2^max(N-10,0) + next_pow2(shots) + shots words (e.g. N <= 28 with 65536
+ * shots), are rejected with QSA_E_RANGE before any launch.
+ *   dev_amplitudes   device, 8*2^N bytes, 16-byte aligned, stored (physical) order;
+ *   phys_of_logical  host, N entries, the layout map (a bijection);
+ *   out_outcomes_dev, out_counts_dev  device, >= shots uint64 each: distinct
+ *                    logical outcomes ascending and their counts;
+ *   out_n_distinct_dev  device, one uint64.
+ * Asynchronous on cuda_stream; nothing is copied to the host.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  Every
+ * call shares the one array, so calls that overlap on the GPU (other streams,
+ * other threads) race; nothing in it needs clearing between calls.  An
+ * all-zero state gives unspecified counts.  Errors: QSA_E_ARG, QSA_E_RANGE,
+ * QSA_E_CUDA. */
+#define QSA_NOALLOC_SCRATCH_WORDS (1u << 19)
+qsa_status qsa_sample_counts_noalloc(const void* dev_amplitudes, int n_qubits, const int32_t* phys_of_logical,
+                                     uint64_t shots, uint64_t seed, uint64_t* out_outcomes_dev,
+                                     uint64_t* out_counts_dev, uint64_t* out_n_distinct_dev, void* cuda_stream);
+
 const char* qsa_last_error(void);
 
 #ifdef __cplusplus

@@ -60,6 +60,7 @@ cudaError_t launch_probs_logical(const float2* psi, int n, const int32_t* d_layo
                                  cudaStream_t st, uint64_t* launches);
 
 // Sampler scratch sizes and launch (see qsa_sample_counts).
+uint64_t next_pow2_u64(uint64_t v);
 size_t sample_scratch_bytes(int n, uint64_t shots);
 cudaError_t launch_sample(const float2* psi, int n, const int32_t* d_layout, uint64_t shots, uint64_t seed,
                           uint64_t stream_id, void* d_scratch, uint64_t* d_out_keys, uint64_t* d_out_counts,

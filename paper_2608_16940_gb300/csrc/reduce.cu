@@ -323,6 +323,8 @@ inline uint64_t next_pow2(uint64_t v) {
 
 }  // namespace
 
+uint64_t next_pow2_u64(uint64_t v) { return next_pow2(v); }
+
 int reduce_partials() { return num_sms() * kRedBlocksPerSM; }
 
 cudaError_t launch_reduce_z(const float2* psi, int n, uint64_t physmask, double* d_partials, double* d_out,
@@ -400,3 +402,80 @@ cudaError_t launch_sample(const float2* psi, int n, const int32_t* layout_host, 
 }
 
 }  // namespace qsa
+
+// ---------------------------------------------------------------------------
+// Sampling without any device allocation.
+//
+// Some callers cannot let the library call cudaMalloc: a framework whose
+// caching allocator owns the device memory budget (a stray cudaMalloc can fail
+// or fragment the pool when the state fills most of HBM, as at N = 33/34), or
+// a pipeline that must not stall, since cudaFree synchronises the whole
+// device.  For them the sampler's scratch (block cumulative weights, the sort
+// keys and the run starts) lives in one fixed, file-scope device array that
+// every GPU loading this library holds until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+#include <string>
+
+#include "qsa_runtime.h"
+
+namespace {
+constexpr uint64_t kNoAllocWords = QSA_NOALLOC_SCRATCH_WORDS;
+static __device__ __align__(256) uint64_t g_noalloc_scratch[kNoAllocWords];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[256] = {};
+
+// Device address of the array for the current device, looked up once per
+// device (host code only sees a host-side stand-in for the symbol).
+cudaError_t noalloc_scratch_ptr(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
+extern "C" qsa_status qsa_sample_counts_noalloc(const void* dev_amplitudes, int n_qubits,
+                                                const int32_t* phys_of_logical, uint64_t shots, uint64_t seed,
+                                                uint64_t* out_outcomes_dev, uint64_t* out_counts_dev,
+                                                uint64_t* out_n_distinct_dev, void* cuda_stream) {
+    using qsa::fail;
+    if (!dev_amplitudes || (reinterpret_cast<uintptr_t>(dev_amplitudes) % 16))
+        return fail(QSA_E_ARG, "amplitudes must be a non-NULL, 16-byte aligned device pointer");
+    if (n_qubits < 1 || n_qubits > QSA_MAX_QUBITS) return fail(QSA_E_ARG, "n_qubits must be in 1..34");
+    if (!phys_of_logical) return fail(QSA_E_ARG, "layout is NULL");
+    uint64_t seen = 0;
+    for (int q = 0; q < n_qubits; ++q) {
+        const int p = phys_of_logical[q];
+        if (p < 0 || p >= n_qubits || ((seen >> p) & 1)) return fail(QSA_E_ARG, "layout is not a bijection");
+        seen |= 1ull << p;
+    }
+    if (shots < 1 || shots > (1ull << 26)) return fail(QSA_E_ARG, "shots must be in 1..2^26");
+    if (!out_outcomes_dev || !out_counts_dev || !out_n_distinct_dev) return fail(QSA_E_ARG, "output is NULL");
+    const int bsz = n_qubits >= 10 ? 1024 : (1 << n_qubits);
+    const uint64_t nblocks = (1ull << n_qubits) / bsz;
+    const uint64_t need = nblocks + qsa::next_pow2_u64(shots) + shots;
+    if (need > kNoAllocWords)
+        return fail(QSA_E_RANGE, "request needs " + std::to_string(need) + " words of sampler scratch; the fixed "
+                                 "no-allocation buffer holds " + std::to_string(kNoAllocWords) +
+                                 " (2^(N-10) + next_pow2(shots) + shots must fit)");
+    void* scratch = nullptr;
+    cudaError_t e = noalloc_scratch_ptr(&scratch);
+    if (e != cudaSuccess) return fail(QSA_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    uint64_t launches = 0;
+    e = qsa::launch_sample(static_cast<const float2*>(dev_amplitudes), n_qubits, phys_of_logical, shots, seed, 0,
+                           scratch, out_outcomes_dev, out_counts_dev, out_n_distinct_dev,
+                           static_cast<cudaStream_t>(cuda_stream), &launches);
+    if (e != cudaSuccess) return fail(QSA_E_CUDA, std::string("sampler kernels: ") + cudaGetErrorString(e));
+    return QSA_OK;
+}
