@@ -232,6 +232,12 @@ qsa_status qsa_plan_destroy(qsa_plan p);
 /* Total kernels launched on this state since creation. */
 qsa_status qsa_state_counters(qsa_state s, uint64_t* launches);
 
+/* Wait for all work queued on the state's stream.  Returns QSA_E_TIMEOUT (and
+ * marks the state failed) if a kernel's bounded wait gave up since the last
+ * check, QSA_E_CUDA on a CUDA error.  Calls that return results to the host
+ * make the same check. */
+qsa_status qsa_state_sync(qsa_state s);
+
 /* ---- outputs (§IV-E "Sampling", App. B "Numerical configuration") ----------- */
 
 /* p_x = |psi_x|^2 in FP64 for every LOGICAL index x (decoded through L),
@@ -257,6 +263,59 @@ qsa_status qsa_expectation_z(qsa_state s, uint64_t logical_mask, double* out);
  * *n_distinct set and nothing written.  shots in 1..2^26.  Synchronises. */
 qsa_status qsa_sample_counts(qsa_state s, uint64_t shots, uint64_t seed, uint64_t* outcomes, uint64_t* counts,
                              size_t capacity, size_t* n_distinct);
+
+/* ---- cost model: 37 -> 64 -> 64 -> 1 ReLU network on log-seconds ------------
+ * Not in the paper (its planner score gamma "is not a runtime predictor",
+ * §IV-C); it replaces gamma in Eq. dp-recurrence with predicted seconds.
+ * Features x = [k/6, b_0..b_33 (physical target mask), N/34, log2(batch)/8].
+ * Parameters: 6657 floats, W1[64][37], b1[64], W2[64][64], b2[64], W3[1][64],
+ * b3[1], row-major.  All device pointers are caller-owned FP32 arrays. */
+#define QSA_MLP_PARAMS 6657
+#define QSA_MLP_FEATURES 37
+
+/* Feature vector of a k-qubit pass on physical positions phys_mask (host out37). */
+qsa_status qsa_costmodel_features(int k, uint64_t phys_mask, int n_qubits, int batch, float* out37);
+
+/* Install (params != NULL, host, copied) or remove (NULL) the process-wide
+ * model used by QSA_PLAN_DP_MLP. */
+qsa_status qsa_costmodel_set(const float* params);
+
+/* exp(f(x)) in seconds for n feature rows (host) with the installed model;
+ * QSA_E_STATE if none is installed. */
+qsa_status qsa_costmodel_predict(const float* features, size_t n, double* seconds_out);
+
+/* He-uniform initial parameters from a seed (host out). */
+qsa_status qsa_costmodel_init(uint64_t seed, float* params_host);
+
+/* Bytes of device workspace the MLP kernels need for n samples. */
+size_t qsa_mlp_workspace_bytes(size_t n);
+
+/* y_dev[s] = f(X_dev[s]) for s < n (X row-major n x 37).  Asynchronous. */
+qsa_status qsa_mlp_forward(const float* params_dev, const float* X_dev, size_t n, float* y_dev, float* workspace_dev,
+                           void* stream);
+
+/* Loss L = mean_s (f(X_s) - t_s)^2 into *loss_dev (nullable) and dL/dparams
+ * into grads_dev (6657 floats), by backpropagation.  Asynchronous. */
+qsa_status qsa_mlp_loss_grad(const float* params_dev, const float* X_dev, const float* t_dev, size_t n,
+                             float* grads_dev, float* loss_dev, float* workspace_dev, void* stream);
+
+/* One Adam step (Kingma & Ba 2015) on count parameters, step number >= 1. */
+qsa_status qsa_mlp_adam_step(float* params_dev, const float* grads_dev, float* m_dev, float* v_dev, size_t count,
+                             int step, float lr, float beta1, float beta2, float eps, void* stream);
+
+/* Time one pass of n_samples random (k in 1..min(6,N), uniformly drawn
+ * physical targets) fused operators on s (identity matrices: the amplitudes
+ * are unchanged), median of reps launches each, at the given precision.
+ * Fills X_host (n_samples x 37) and y_host (log seconds).  Synchronises. */
+qsa_status qsa_costmodel_collect(qsa_state s, size_t n_samples, int reps, int precision, uint64_t seed,
+                                 float* X_host, float* y_host);
+
+/* Train on (X_host, y_host) with the library's GPU kernels: epochs of
+ * shuffled minibatches, MSE loss, Adam(lr, 0.9, 0.999, 1e-8).  params_inout:
+ * initial parameters in, trained parameters out (host).  epoch_loss_host
+ * (nullable, epochs floats) receives the full-set loss after each epoch. */
+qsa_status qsa_costmodel_train(const float* X_host, const float* y_host, size_t n, int epochs, int batch, float lr,
+                               uint64_t seed, float* params_inout_host, float* epoch_loss_host);
 
 /* Sampling that allocates nothing on the device.  The paper has no
  * counterpart: this exists for callers that cannot let the library call

@@ -103,6 +103,7 @@ _f = {
     "qsa_plan_execute": _sig("qsa_plan_execute", [_vp, _vp, _c.POINTER(qsa_run_stats)]),
     "qsa_plan_destroy": _sig("qsa_plan_destroy", [_vp]),
     "qsa_state_counters": _sig("qsa_state_counters", [_vp, _u64p]),
+    "qsa_state_sync": _sig("qsa_state_sync", [_vp]),
     "qsa_probabilities": _sig("qsa_probabilities", [_vp, _dp, _dp]),
     "qsa_probabilities_device": _sig("qsa_probabilities_device", [_vp, _vp, _dp]),
     "qsa_expectation_z": _sig("qsa_expectation_z", [_vp, _c.c_uint64, _dp]),
@@ -298,6 +299,10 @@ def qsa_plan_destroy(p: int) -> None:
     _check(_f["qsa_plan_destroy"](_vp(p)))
 
 
+def qsa_state_sync(s: int) -> None:
+    _check(_f["qsa_state_sync"](_vp(s)))
+
+
 def qsa_state_counters(s: int) -> int:
     v = _c.c_uint64()
     _check(_f["qsa_state_counters"](_vp(s), _c.byref(v)))
@@ -358,6 +363,65 @@ def qsa_costmodel_predict(features: np.ndarray) -> np.ndarray:
     out = np.zeros(X.shape[0], dtype=np.float64)
     _check(_f["qsa_costmodel_predict"](X.ctypes.data_as(_fp), X.shape[0], out.ctypes.data_as(_dp)))
     return out
+
+
+_f["qsa_costmodel_init"] = _sig("qsa_costmodel_init", [_c.c_uint64, _fp])
+_f["qsa_mlp_workspace_bytes"] = _sig("qsa_mlp_workspace_bytes", [_c.c_size_t], _c.c_size_t)
+_f["qsa_mlp_forward"] = _sig("qsa_mlp_forward", [_vp, _vp, _c.c_size_t, _vp, _vp, _vp])
+_f["qsa_mlp_loss_grad"] = _sig("qsa_mlp_loss_grad", [_vp, _vp, _vp, _c.c_size_t, _vp, _vp, _vp, _vp])
+_f["qsa_mlp_adam_step"] = _sig("qsa_mlp_adam_step", [_vp, _vp, _vp, _vp, _c.c_size_t, _c.c_int, _c.c_float,
+                                                     _c.c_float, _c.c_float, _c.c_float, _vp])
+_f["qsa_costmodel_collect"] = _sig("qsa_costmodel_collect", [_vp, _c.c_size_t, _c.c_int, _c.c_int, _c.c_uint64,
+                                                             _fp, _fp])
+_f["qsa_costmodel_train"] = _sig("qsa_costmodel_train", [_fp, _fp, _c.c_size_t, _c.c_int, _c.c_int, _c.c_float,
+                                                         _c.c_uint64, _fp, _fp])
+
+
+def qsa_costmodel_init(seed: int) -> np.ndarray:
+    p = np.zeros(MLP_PARAMS, dtype=np.float32)
+    _check(_f["qsa_costmodel_init"](_c.c_uint64(seed), p.ctypes.data_as(_fp)))
+    return p
+
+
+def qsa_mlp_workspace_bytes(n: int) -> int:
+    return int(_f["qsa_mlp_workspace_bytes"](n))
+
+
+def qsa_mlp_forward(params_dev: int, X_dev: int, n: int, y_dev: int, ws_dev: int, stream: int = 0) -> None:
+    _check(_f["qsa_mlp_forward"](_vp(params_dev), _vp(X_dev), n, _vp(y_dev), _vp(ws_dev), _vp(stream)))
+
+
+def qsa_mlp_loss_grad(params_dev: int, X_dev: int, t_dev: int, n: int, grads_dev: int, loss_dev: int, ws_dev: int,
+                      stream: int = 0) -> None:
+    _check(_f["qsa_mlp_loss_grad"](_vp(params_dev), _vp(X_dev), _vp(t_dev), n, _vp(grads_dev), _vp(loss_dev),
+                                   _vp(ws_dev), _vp(stream)))
+
+
+def qsa_mlp_adam_step(params_dev: int, grads_dev: int, m_dev: int, v_dev: int, count: int, step: int,
+                      lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+                      stream: int = 0) -> None:
+    _check(_f["qsa_mlp_adam_step"](_vp(params_dev), _vp(grads_dev), _vp(m_dev), _vp(v_dev), count, step, lr, beta1,
+                                   beta2, eps, _vp(stream)))
+
+
+def qsa_costmodel_collect(s: int, n_samples: int, reps: int = 3, precision: int = QSA_PREC_FP32,
+                          seed: int = 0) -> Tuple[np.ndarray, np.ndarray]:
+    X = np.zeros((n_samples, MLP_IN), dtype=np.float32)
+    y = np.zeros(n_samples, dtype=np.float32)
+    _check(_f["qsa_costmodel_collect"](_vp(s), n_samples, reps, precision, _c.c_uint64(seed),
+                                       X.ctypes.data_as(_fp), y.ctypes.data_as(_fp)))
+    return X, y
+
+
+def qsa_costmodel_train(X: np.ndarray, y: np.ndarray, epochs: int = 200, batch: int = 64, lr: float = 1e-3,
+                        seed: int = 0, params: Optional[np.ndarray] = None) -> Tuple[np.ndarray, np.ndarray]:
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    p = qsa_costmodel_init(seed) if params is None else np.ascontiguousarray(params, dtype=np.float32).copy()
+    losses = np.zeros(epochs, dtype=np.float32)
+    _check(_f["qsa_costmodel_train"](X.ctypes.data_as(_fp), y.ctypes.data_as(_fp), X.shape[0], epochs, batch, lr,
+                                     _c.c_uint64(seed), p.ctypes.data_as(_fp), losses.ctypes.data_as(_fp)))
+    return p, losses
 
 
 def exported_symbols() -> List[str]:

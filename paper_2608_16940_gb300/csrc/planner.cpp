@@ -434,8 +434,11 @@ qsa_status qsa_plan_execute(qsa_state s, qsa_plan p, qsa_run_stats* stats) {
         }
     }
     s->timing = false;
-    if (p->opts.timing) collect_timers(s, &rs->seconds);
     rs->launches = s->launches - l0;
+    if (p->opts.timing) {
+        collect_timers(s, &rs->seconds);
+        return sync_and_check(s, "plan execution");
+    }
     return QSA_OK;
 }
 

@@ -65,6 +65,7 @@ constexpr int kInBlockBits = 11;
 qsa_status fail(qsa_status st, const std::string& msg);
 qsa_status cuda_fail(qsa_state s, cudaError_t e, const char* where);
 qsa_status check_state(qsa_state s);
+qsa_status sync_and_check(qsa_state s, const char* where);
 qsa_status ensure_dev(qsa_state s, void** ptr, size_t* cap, size_t bytes);
 void to_float_matrix(const double* m, int k, float* out);
 qsa_status validate_targets(int n, const int32_t* targets, int k);

@@ -34,6 +34,21 @@ qsa_status cuda_fail(qsa_state s, cudaError_t e, const char* where) {
     return fail(QSA_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// Synchronise the state's stream and report a device-side give-up recorded
+// in the error word by a bounded wait (QSA_E_TIMEOUT; the state is then failed).
+qsa_status sync_and_check(qsa_state s, const char* where) {
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, where);
+    if (h != 0) {
+        s->failed = true;
+        return fail(QSA_E_TIMEOUT, std::string(where) + ": a kernel gave up a bounded wait (code " +
+                                       std::to_string(h) + "); the amplitudes are invalid");
+    }
+    return QSA_OK;
+}
+
 qsa_status check_state(qsa_state s) {
     if (!s) return fail(QSA_E_ARG, "state is NULL");
     if (s->failed) return fail(QSA_E_STATE, "state is marked failed after a CUDA error");
@@ -420,9 +435,14 @@ qsa_status qsa_expectation_z(qsa_state s, uint64_t logical_mask, double* out) {
     cudaError_t e = launch_reduce_z(s->psi, s->n, pm, s->d_red, d_out, s->stream, &s->launches);
     if (e != cudaSuccess) return cuda_fail(s, e, "reduction kernel");
     e = cudaMemcpyAsync(out, d_out, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "reduction result");
-    return QSA_OK;
+    return sync_and_check(s, "reduction result");
+}
+
+qsa_status qsa_state_sync(qsa_state s) {
+    qsa_status st = check_state(s);
+    if (st != QSA_OK) return st;
+    return sync_and_check(s, "synchronise");
 }
 
 qsa_status qsa_probabilities_device(qsa_state s, double* out_dev, double* norm_out) {
@@ -451,9 +471,13 @@ qsa_status qsa_probabilities(qsa_state s, double* out_host, double* norm_out) {
         }
         e = launch_probs_logical(s->psi, s->n, s->L, tmp, s->stream, &s->launches);
         if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, tmp, bytes, cudaMemcpyDeviceToHost, s->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) {
+            cudaFree(tmp);
+            return cuda_fail(s, e, "probabilities");
+        }
+        st = sync_and_check(s, "probabilities");
         cudaFree(tmp);
-        if (e != cudaSuccess) return cuda_fail(s, e, "probabilities");
+        if (st != QSA_OK) return st;
     }
     if (norm_out) return qsa_expectation_z(s, 0, norm_out);
     return QSA_OK;
@@ -483,8 +507,9 @@ qsa_status qsa_sample_counts(qsa_state s, uint64_t shots, uint64_t seed, uint64_
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(&hdr[1], static_cast<uint64_t*>(s->d_samp) + (nblocks - 1), sizeof(uint64_t),
                             cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "sampler result");
+    st = sync_and_check(s, "sampler result");
+    if (st != QSA_OK) return st;
     if (hdr[1] == 0) return fail(QSA_E_STATE, "every amplitude weight is zero");
     *n_distinct = static_cast<size_t>(hdr[0]);
     if (capacity < hdr[0]) return fail(QSA_E_RANGE, "capacity smaller than the number of distinct outcomes");
