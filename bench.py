@@ -4,11 +4,11 @@ Workload (one "step" = one pass of the whole hot path over one synthetic
 circuit): QAOA on a seeded random 3-regular graph, N = 30 qubits, p = 8
 rounds (H on every qubit, then 8 x (ZZ on 45 edges + RX on 30 qubits) = 630
 gates), complex64 state of 8 GiB.  A step resets the state to |0...0>,
-executes the fused plan (fused k-qubit blocks, FP32 or split-TF32 tensor
-cores for k = 5, 6), reduces the norm in FP64, draws 1000 sampled counts and
-evaluates <Z_a Z_b> on one edge.  The plan (fusion + block products) is built
-once outside the timed region, as the paper's timer excludes plan
-construction.
+executes the fused plan (fused k-qubit blocks; FP32 CUDA cores, or split-TF32
+tensor cores for k = 5, 6), reduces the norm in FP64, draws 1000 sampled
+counts and evaluates <Z_a Z_b> on one edge.  The plan (cost-model training,
+fusion, block products) is built once before the timed region, as the
+paper's timer excludes plan construction.
 
 Metric: gate-level amplitude-updates/s = (input gates x 2^N) / step time,
 whole job (sum over ranks).  Multi-GPU runs are independent replicas (the
@@ -110,8 +110,7 @@ def run_reference(args):
     n_s = args.ref_qubits
     ops, _ = W.qaoa_circuit(n=n_s, p=args.p, seed=args.seed)
     psi = oracle.zero_state(n_s)
-    # alternate a one-qubit and a two-qubit gate of the circuit per step
-    picks = [ops[0], ops[n_s]]
+    picks = [ops[0], ops[n_s]]   # alternate a one-qubit and a two-qubit gate of the circuit
     times = []
     for i in range(args.warmup + args.steps):
         g = picks[i % 2]
@@ -148,6 +147,22 @@ def cpu_baseline(n_s: int, seed: int, p: int):
             "sample": f"2 gates (H, ZZ) of the QAOA circuit at N={n_s}, {dt:.1f} s single-threaded FP64"}
 
 
+def train_cost_model(q, s, precision, seed, n_samples):
+    """Collect timings of the library's own kernels on the bench state, train
+    the cost model on the GPU and install it; returns its held-out error."""
+    X, y = q.qsa_costmodel_collect(s, n_samples, reps=3, precision=precision, seed=seed + 101)
+    perm = np.random.default_rng(seed).permutation(len(y))
+    n_tr = int(0.85 * len(y))
+    tr, te = perm[:n_tr], perm[n_tr:]
+    params, losses = q.qsa_costmodel_train(X[tr], y[tr], epochs=200, batch=32, lr=2e-3, seed=seed + 7,
+                                           weight_decay=1e-2)
+    q.qsa_costmodel_set(params)
+    pred = q.qsa_costmodel_predict(X[te])
+    rel = np.abs(pred - np.exp(y[te])) / np.exp(y[te])
+    return {"samples": int(len(y)), "heldout_median_rel_err": float(np.median(rel)),
+            "final_loss": float(losses[-1])}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -158,14 +173,16 @@ def main():
     ap.add_argument("--p", type=int, default=8)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--shots", type=int, default=1000)
-    ap.add_argument("--planner", default="dp", choices=["per_gate", "greedy", "dp", "dp_mlp"])
+    ap.add_argument("--planner", default="dp_mlp", choices=["per_gate", "greedy", "dp", "dp_mlp"])
     ap.add_argument("--kmax", type=int, default=4)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3"])
     ap.add_argument("--lowering", default="auto", choices=["auto", "strided", "permute"])
+    ap.add_argument("--cm-samples", type=int, default=240)
     ap.add_argument("--ref-qubits", type=int, default=28)
     ap.add_argument("--cpu-qubits", type=int, default=28)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the per-gate comparison run")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
 
     if args.impl == "reference":
@@ -192,12 +209,16 @@ def main():
     buf = torch.empty(1 << n, dtype=torch.complex64, device=dev)
     stream = torch.cuda.current_stream(dev).cuda_stream
     s = q.qsa_state_create_ex(n, buf.data_ptr(), buf.numel() * 8, stream, 1)
+    cm = None
+    if planner == 3:
+        cm = train_cost_model(q, s, prec, args.seed, args.cm_samples)
+        q.qsa_state_reset(s)
     plan = q.qsa_plan_create(ops, n, opts)
     pinfo = q.qsa_plan_info(plan)
     edge_mask = (1 << edges[0][0]) | (1 << edges[0][1])
 
-    agg = {"apply_seconds": 0.0, "permute_seconds": 0.0, "blocks": 0, "permutes": 0, "tc_blocks": 0,
-           "launches": 0}
+    agg = {"apply_seconds": 0.0, "tc_seconds": 0.0, "permute_seconds": 0.0, "blocks": 0, "permutes": 0,
+           "tc_blocks": 0}
 
     def step(record):
         q.qsa_state_reset(s)
@@ -221,11 +242,13 @@ def main():
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("qsa_timed")
     ev0.record()
     for _ in range(args.steps):
         norm, zz, nshot = step(True)
     ev1.record()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     launches = q.qsa_state_counters(s) - l0
     clocks = clk.stop()
     elapsed = ev0.elapsed_time(ev1) * 1e-3
@@ -238,33 +261,43 @@ def main():
     amp_updates = len(ops) * float(1 << n)
     value = ws * amp_updates / per_step
 
-    # dominant kernel roofline: the fused-operator kernel, 16 B per amplitude per launch
+    # roofline of the dominant fused-operator kernel: 16 B per amplitude per launch
     hbm_peak, peak_kind = _peaks()
-    nb = max(1, agg["blocks"])
-    apply_avg = agg["apply_seconds"] / nb
     bytes_per_launch = 16.0 * (1 << n)
-    achieved = bytes_per_launch / apply_avg / 1e9 if apply_avg > 0 else 0.0
-    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": achieved / hbm_peak, "traffic": None, "kernel": "k_apply_fp32 (fused dense update)",
-            "peak_source": peak_kind, "bytes_per_launch": bytes_per_launch,
-            "avg_launch_ms": apply_avg * 1e3}
+    n_fp32 = agg["blocks"] - agg["tc_blocks"]
+    kinds = []
+    if n_fp32:
+        kinds.append(("k_apply_fp32 (FP32 fused dense update)", agg["apply_seconds"], n_fp32))
+    if agg["tc_blocks"]:
+        kinds.append(("k_apply_tc (split-TF32 tcgen05 fused update)", agg["tc_seconds"], agg["tc_blocks"]))
+    if agg["permutes"]:
+        kinds.append(("k_permute (qubit permutation)", agg["permute_seconds"], agg["permutes"]))
+    name, tot, cnt = max(kinds, key=lambda kv: kv[1])
+    avg = tot / cnt
+    achieved = bytes_per_launch / avg / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+            "traffic": None, "kernel": name, "peak_source": peak_kind, "bytes_per_launch": bytes_per_launch,
+            "avg_launch_ms": avg * 1e3, "launches_per_step": cnt / args.steps,
+            "share_of_step": tot / args.steps / per_step}
 
     # end to end through the public API from host data: plan + upload + apply + counts copied back
-    e2e_times = []
-    h2d = 0.0
-    d2h = 0.0
-    for _ in range(max(1, min(3, args.steps))):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        q.qsa_state_reset(s)
-        st = q.qsa_apply_circuit(s, ops, q.make_opts(planner=planner, kmax=args.kmax, kmax_diag=args.kmax,
-                                                      precision=prec, lowering=low))
-        vals, cnts = q.qsa_sample_counts(s, args.shots, seed=args.seed + 17)
-        torch.cuda.synchronize()
-        e2e_times.append(time.perf_counter() - t0)
-        h2d = st["h2d_bytes"]
-        d2h = 16.0 * len(vals) + 16
-    e2e_val = ws * amp_updates / statistics.median(e2e_times)
+    e2e = None
+    if not args.no_e2e:
+        e2e_times = []
+        h2d = d2h = 0.0
+        for _ in range(max(1, min(3, args.steps))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            q.qsa_state_reset(s)
+            st = q.qsa_apply_circuit(s, ops, q.make_opts(planner=planner, kmax=args.kmax, kmax_diag=args.kmax,
+                                                          precision=prec, lowering=low))
+            vals, cnts = q.qsa_sample_counts(s, args.shots, seed=args.seed + 17)
+            torch.cuda.synchronize()
+            e2e_times.append(time.perf_counter() - t0)
+            h2d = st["h2d_bytes"]
+            d2h = 16.0 * len(vals) + 16
+        e2e = {"value": ws * amp_updates / statistics.median(e2e_times), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
 
     extra = {}
     if not args.no_compare and rank == 0:
@@ -283,27 +316,30 @@ def main():
         pg_t = e0.elapsed_time(e1) * 1e-3
         q.qsa_plan_destroy(pg)
         extra["per_gate"] = {"value": amp_updates / pg_t, "unit": UNIT, "seconds": pg_t, "passes": pst["passes"],
-                             "hbm_gbs": pst["passes"] * bytes_per_launch / pg_t / 1e9}
+                             "hbm_gbs": pst["passes"] * bytes_per_launch / pg_t / 1e9,
+                             "fused_speedup": (amp_updates / per_step) / (amp_updates / pg_t)}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_qubits, args.seed, args.p)
 
+    q.qsa_costmodel_set(None)
     q.qsa_plan_destroy(plan)
     q.qsa_state_destroy(s)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "c64/f32 (FP64 reductions)", "data": "synthetic",
-                "config": {"workload": f"qaoa{n}_p{args.p}: 3-regular graph, {len(ops)} gates, N={n} complex64",
+                "vs_baseline": None, "dtype": "c64 state, f32 arithmetic (3xTF32 on tensor cores), f64 reductions",
+                "data": "synthetic",
+                "config": {"workload": f"qaoa{n}_p{args.p}: random 3-regular graph, {len(ops)} gates, N={n} "
+                                       f"complex64 (8 GiB), 1000 shots + norm + <ZZ> per step",
                            "planner": args.planner, "kmax": args.kmax, "precision": args.precision,
-                           "lowering": args.lowering, "shots": args.shots, "fused_blocks": pinfo["blocks"],
+                           "lowering": args.lowering, "fused_blocks": pinfo["blocks"],
                            "l2": "state 8 GiB > 129 MB L2; no flush needed", "parallelism": f"replicas x{ws}"},
-                "gpu_launches": launches, "clocks": clocks, "roofline": roof, "cpu_baseline": cpu,
-                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "clocks": clocks, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "passes_per_step": (agg["blocks"] + agg["permutes"]) / args.steps,
                 "hbm_gbs_step": (agg["blocks"] + agg["permutes"]) / args.steps * bytes_per_launch / per_step / 1e9,
-                "check": {"norm": norm, "zz_edge0": zz, "shots": nshot}}
+                "cost_model": cm, "check": {"norm": norm, "zz_edge0": zz, "shots": nshot}}
         line.update(extra)
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -106,7 +106,7 @@ typedef struct {
 
 typedef struct {
     double seconds;         /* device time of all launches (timing = 1), else 0 */
-    double apply_seconds;   /* device time of fused-operator kernels */
+    double apply_seconds;   /* device time of FP32 fused-operator kernels */
     double permute_seconds; /* device time of permutation kernels */
     double hbm_bytes;       /* algorithmic HBM bytes: 16 B x 2^N per full-state pass */
     uint64_t blocks;        /* fused blocks applied */
@@ -115,6 +115,7 @@ typedef struct {
     uint64_t tc_blocks;     /* blocks run on the tensor-core path */
     uint64_t launches;      /* kernel launches issued */
     double h2d_bytes;       /* host-to-device bytes copied by the call (fused matrices) */
+    double tc_seconds;      /* device time of tensor-core fused-operator kernels */
 } qsa_run_stats;
 
 /* A compiled circuit: the planner's blocks with their fused FP32 matrices. */
@@ -255,7 +256,7 @@ qsa_status qsa_expectation_z(qsa_state s, uint64_t logical_mask, double* out);
 /* Draw `shots` outcomes (§IV-E): weights P_y = trunc(p_y * 2^62) (integer,
  * so the CDF does not depend on summation order) over physical indices in
  * 2^10-amplitude blocks; shot i draws Philox4x64-10(ctr = (i, 0, 0, 0),
- * key = (seed, 0)).word0 mod total and takes the first physical index whose
+ *  key = (seed, 0)).word0 = r, maps it to u = floor(r * total / 2^64) and takes the first physical index whose
  * cumulative weight is strictly greater (a zero-weight bin is never drawn);
  * the outcome is decoded to the logical bitstring through L (§IV-D).
  * Results: distinct logical outcomes ascending in outcomes[], their counts in
@@ -263,6 +264,42 @@ qsa_status qsa_expectation_z(qsa_state s, uint64_t logical_mask, double* out);
  * *n_distinct set and nothing written.  shots in 1..2^26.  Synchronises. */
 qsa_status qsa_sample_counts(qsa_state s, uint64_t shots, uint64_t seed, uint64_t* outcomes, uint64_t* counts,
                              size_t capacity, size_t* n_distinct);
+
+/* ---- batched trajectories ---------------------------------------------------
+ * Many independent small states (noisy trajectories: the per-gate Pauli
+ * channels of §IV-A sampled into explicit Pauli branches, so every trajectory
+ * is a unitary circuit) evolved in ONE persistent kernel launch: each CTA pops
+ * a trajectory from an atomic queue (longest first), resets it to |0..0> and
+ * applies all of its fused blocks; a second kernel samples every state (one
+ * CTA per trajectory, Philox stream id = trajectory index, identity layout),
+ * and both can be replayed as one captured CUDA graph. */
+typedef struct qsa_batch_s* qsa_batch;
+
+/* Host planning + one-time upload: trajectory t is ops[op_offsets[t] ..
+ * op_offsets[t+1]) (op_offsets has n_traj + 1 entries, op_offsets[0] = 0).
+ * N in 1..22; opts->kmax <= 4 (QSA_E_ARG otherwise). */
+qsa_status qsa_batch_create(int n_qubits, int n_traj, const qsa_op* ops, const size_t* op_offsets,
+                            const qsa_plan_opts* opts, qsa_batch* out);
+
+/* Total fused blocks, input ops, and kernels launched so far. */
+qsa_status qsa_batch_info(qsa_batch b, size_t* total_blocks, size_t* total_ops, uint64_t* launches);
+
+/* Evolve every trajectory from |0..0> into dev_states (caller-owned device
+ * buffer of >= n_traj * 8 * 2^N bytes, state t at offset t * 8 * 2^N) and
+ * draw `shots` (1..16384) samples of each with the rule of qsa_sample_counts
+ * (stream id t).  use_graph = 1 captures the launches into a CUDA graph on
+ * first use (re-captured when an argument changes) and replays it.
+ * budget_cycles > 0 bounds each CTA's run time in SM clock cycles: a CTA that
+ * runs over stops between blocks and the call returns QSA_E_TIMEOUT.
+ * Synchronises cuda_stream; stats->seconds is the device time of the launch. */
+qsa_status qsa_batch_run(qsa_batch b, void* dev_states, size_t bytes, uint64_t shots, uint64_t seed,
+                         uint64_t budget_cycles, int use_graph, void* cuda_stream, qsa_run_stats* stats);
+
+/* Copy the last run's samples to the host: for trajectory t, outcomes and
+ * counts at [t * shots, t * shots + n_distinct[t]) (ascending outcomes). */
+qsa_status qsa_batch_counts(qsa_batch b, uint32_t* outcomes, uint32_t* counts, uint32_t* n_distinct);
+
+qsa_status qsa_batch_destroy(qsa_batch b);
 
 /* ---- cost model: 37 -> 64 -> 64 -> 1 ReLU network on log-seconds ------------
  * Not in the paper (its planner score gamma "is not a runtime predictor",
@@ -311,11 +348,14 @@ qsa_status qsa_costmodel_collect(qsa_state s, size_t n_samples, int reps, int pr
                                  float* X_host, float* y_host);
 
 /* Train on (X_host, y_host) with the library's GPU kernels: epochs of
- * shuffled minibatches, MSE loss, Adam(lr, 0.9, 0.999, 1e-8).  params_inout:
- * initial parameters in, trained parameters out (host).  epoch_loss_host
- * (nullable, epochs floats) receives the full-set loss after each epoch. */
+ * shuffled minibatches, MSE loss on standardised targets (the mean and scale
+ * are folded back into W3, b3) plus an L2 penalty (weight_decay/2)|p|^2,
+ * Adam(lr, 0.9, 0.999, 1e-8).  The penalty keeps the network from fitting
+ * noise through the 34 sparse mask features.  params_inout: initial
+ * parameters in, trained parameters out (host).  epoch_loss_host (nullable,
+ * epochs floats) receives the full-set MSE after each epoch. */
 qsa_status qsa_costmodel_train(const float* X_host, const float* y_host, size_t n, int epochs, int batch, float lr,
-                               uint64_t seed, float* params_inout_host, float* epoch_loss_host);
+                               float weight_decay, uint64_t seed, float* params_inout_host, float* epoch_loss_host);
 
 /* Sampling that allocates nothing on the device.  The paper has no
  * counterpart: this exists for callers that cannot let the library call

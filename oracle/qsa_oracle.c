@@ -143,7 +143,9 @@ void orc_philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2], uint6
  * integer prefix sum C_y = sum_{y' <= y} P_y', so it is exact and independent
  * of summation order.
  * Shot s of stream t draws r = Philox4x64-10(ctr = (s, t, 0, 0),
- * key = (seed, 0)).word0, u = r mod C_last, and takes the first y with
+ * key = (seed, 0)).word0, maps it to u = floor(r * C_last / 2^64) in
+ * [0, C_last) (multiply-high range reduction: u moves by less than the change
+ * of C_last when the weights change slightly), and takes the first y with
  * C_y > u.  The logical outcome x has x_q = y_{L(q)}.
  *
  *   amps_logical: FP64 interleaved amplitudes in canonical logical order;
@@ -193,7 +195,7 @@ int orc_sample(const double* amps_logical, int n, const int* phys_of_logical,
     for (uint64_t s = 0; s < shots; ++s) {
         uint64_t ctr[4] = {s, stream, 0, 0}, key[2] = {seed, 0}, out[4];
         orc_philox4x64_10(ctr, key, out);
-        uint64_t u = out[0] % total;
+        uint64_t u = (uint64_t)(((unsigned __int128)out[0] * (unsigned __int128)total) >> 64);
         /* first y with cum[y] > u (binary search over a non-decreasing array) */
         uint64_t lo = 0, hi = dim - 1;
         while (lo < hi) {

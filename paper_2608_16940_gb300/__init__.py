@@ -63,7 +63,7 @@ class qsa_run_stats(_c.Structure):
     _fields_ = [("seconds", _c.c_double), ("apply_seconds", _c.c_double), ("permute_seconds", _c.c_double),
                 ("hbm_bytes", _c.c_double), ("blocks", _c.c_uint64), ("passes", _c.c_uint64),
                 ("permutes", _c.c_uint64), ("tc_blocks", _c.c_uint64), ("launches", _c.c_uint64),
-                ("h2d_bytes", _c.c_double)]
+                ("h2d_bytes", _c.c_double), ("tc_seconds", _c.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -374,7 +374,7 @@ _f["qsa_mlp_adam_step"] = _sig("qsa_mlp_adam_step", [_vp, _vp, _vp, _vp, _c.c_si
 _f["qsa_costmodel_collect"] = _sig("qsa_costmodel_collect", [_vp, _c.c_size_t, _c.c_int, _c.c_int, _c.c_uint64,
                                                              _fp, _fp])
 _f["qsa_costmodel_train"] = _sig("qsa_costmodel_train", [_fp, _fp, _c.c_size_t, _c.c_int, _c.c_int, _c.c_float,
-                                                         _c.c_uint64, _fp, _fp])
+                                                         _c.c_float, _c.c_uint64, _fp, _fp])
 
 
 def qsa_costmodel_init(seed: int) -> np.ndarray:
@@ -414,14 +414,66 @@ def qsa_costmodel_collect(s: int, n_samples: int, reps: int = 3, precision: int 
 
 
 def qsa_costmodel_train(X: np.ndarray, y: np.ndarray, epochs: int = 200, batch: int = 64, lr: float = 1e-3,
-                        seed: int = 0, params: Optional[np.ndarray] = None) -> Tuple[np.ndarray, np.ndarray]:
+                        seed: int = 0, params: Optional[np.ndarray] = None,
+                        weight_decay: float = 1e-2) -> Tuple[np.ndarray, np.ndarray]:
     X = np.ascontiguousarray(X, dtype=np.float32)
     y = np.ascontiguousarray(y, dtype=np.float32)
     p = qsa_costmodel_init(seed) if params is None else np.ascontiguousarray(params, dtype=np.float32).copy()
     losses = np.zeros(epochs, dtype=np.float32)
     _check(_f["qsa_costmodel_train"](X.ctypes.data_as(_fp), y.ctypes.data_as(_fp), X.shape[0], epochs, batch, lr,
-                                     _c.c_uint64(seed), p.ctypes.data_as(_fp), losses.ctypes.data_as(_fp)))
+                                     weight_decay, _c.c_uint64(seed), p.ctypes.data_as(_fp),
+                                     losses.ctypes.data_as(_fp)))
     return p, losses
+
+
+_f["qsa_batch_create"] = _sig("qsa_batch_create", [_c.c_int, _c.c_int, _c.POINTER(qsa_op), _szp,
+                                                   _c.POINTER(qsa_plan_opts), _c.POINTER(_vp)])
+_f["qsa_batch_info"] = _sig("qsa_batch_info", [_vp, _szp, _szp, _u64p])
+_f["qsa_batch_run"] = _sig("qsa_batch_run", [_vp, _vp, _c.c_size_t, _c.c_uint64, _c.c_uint64, _c.c_uint64, _c.c_int,
+                                             _vp, _c.POINTER(qsa_run_stats)])
+_f["qsa_batch_counts"] = _sig("qsa_batch_counts", [_vp, _vp, _vp, _vp])
+_f["qsa_batch_destroy"] = _sig("qsa_batch_destroy", [_vp])
+
+
+def qsa_batch_create(n_qubits: int, trajectories, opts: Optional[qsa_plan_opts] = None) -> int:
+    """``trajectories``: list of op lists."""
+    flat = [op for t in trajectories for op in t]
+    offs = np.zeros(len(trajectories) + 1, dtype=np.uint64)
+    offs[1:] = np.cumsum([len(t) for t in trajectories])
+    oa = OpArray(flat)
+    h = _vp()
+    _check(_f["qsa_batch_create"](n_qubits, len(trajectories), oa.arr, offs.ctypes.data_as(_szp),
+                                  _c.byref(opts) if opts else None, _c.byref(h)))
+    return h.value
+
+
+def qsa_batch_info(b: int) -> dict:
+    tb, to = _c.c_size_t(), _c.c_size_t()
+    la = _c.c_uint64()
+    _check(_f["qsa_batch_info"](_vp(b), _c.byref(tb), _c.byref(to), _c.byref(la)))
+    return {"blocks": tb.value, "ops": to.value, "launches": la.value}
+
+
+def qsa_batch_run(b: int, states_ptr: int, nbytes: int, shots: int, seed: int, budget_cycles: int = 0,
+                  use_graph: int = 1, stream: int = 0) -> dict:
+    st = qsa_run_stats()
+    _check(_f["qsa_batch_run"](_vp(b), _vp(states_ptr), nbytes, shots, _c.c_uint64(seed), _c.c_uint64(budget_cycles),
+                               use_graph, _vp(stream), _c.byref(st)))
+    return st.as_dict()
+
+
+def qsa_batch_counts(b: int, n_traj: int, shots: int):
+    """Per trajectory: (outcomes ascending, counts) as uint32 arrays."""
+    outc = np.zeros(n_traj * shots, dtype=np.uint32)
+    cnt = np.zeros(n_traj * shots, dtype=np.uint32)
+    nd = np.zeros(n_traj, dtype=np.uint32)
+    _check(_f["qsa_batch_counts"](_vp(b), _vp(outc.ctypes.data), _vp(cnt.ctypes.data), _vp(nd.ctypes.data)))
+    return [(outc[t * shots: t * shots + nd[t]].copy(), cnt[t * shots: t * shots + nd[t]].copy())
+            for t in range(n_traj)]
+
+
+def qsa_batch_destroy(b: int) -> None:
+    _check(_f["qsa_batch_destroy"](_vp(b)))
 
 
 def exported_symbols() -> List[str]:

@@ -1,46 +1,38 @@
-// FP32 fused dense update and qubit-permutation kernels (sm_103a).
+// FP32 fused dense update, qubit-permutation and batched-trajectory kernels
+// (sm_103a).
 //
-// Both kernels share one tile engine: a persistent CTA walks tiles
-// blockIdx.x, blockIdx.x + gridDim.x, ...; each tile (2^T amplitudes = 2^nx
-// contiguous runs of 2^m amplitudes) is staged into shared memory with 16-byte
-// cp.async copies in an S-deep ring, transformed, and written back in place.
-// Tiles partition the index space, so the in-place update needs no second
-// state buffer (the paper's CUDA path holds two, App. C "Capacity").
+// All three share one tile engine: a CTA walks tiles t0, t0 + stride, ...;
+// each tile (2^T amplitudes = 2^nx contiguous runs of 2^m amplitudes) is
+// staged into shared memory with 16-byte cp.async copies in an S-deep ring,
+// transformed, and written back in place.  Tiles partition the index space,
+// so the in-place update needs no second state buffer (the paper's CUDA path
+// holds two, App. C "Capacity and execution profiles").
 //
-//   apply  (§IV-B, R2 apply; Eq. cost-formal): for every group of 2^k
-//          amplitudes that differ only in the target bits,
-//          psi'[x|spread(r)] = sum_c G[r][c] psi[x|spread(c)];
+//   apply   (§IV-B, R2 apply; Eq. cost-formal): for every group of 2^k
+//           amplitudes that differ only in the target bits,
+//           psi'[x|spread(r)] = sum_c G[r][c] psi[x|spread(c)];
 //   permute (§IV-D, Lemma "distributed promotion swap" with the rank bits read
-//          as out-of-block bits): psi'[tau(y)] = psi[y] for a product tau of
-//          disjoint bit transpositions.
+//           as out-of-block bits): psi'[tau(y)] = psi[y] for a product tau of
+//           disjoint bit transpositions;
+//   batch   many independent states (noisy trajectories, §IV-A channels
+//           sampled as explicit Pauli branches) in one persistent launch: each
+//           CTA pops a trajectory from an atomic queue (longest first), resets
+//           it to |0...0> and applies all of its fused blocks.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
 
+#include "qsa_device.cuh"
 #include "qsa_internal.h"
 
 namespace qsa {
 
 namespace {
 
+using namespace dev;
+
 constexpr int kThreads = 256;
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-// Insert a zero bit at position p (positions handled in ascending order).
-__device__ __forceinline__ uint64_t insert_zero(uint64_t v, int p) {
-    uint64_t lo = v & ((1ull << p) - 1ull);
-    return ((v >> p) << (p + 1)) | lo;
-}
 
 struct TileArgs {
     float2* psi;
@@ -93,33 +85,16 @@ struct ApplyArgs {
     int tls[6];         // the same positions, ascending
 };
 
+// The tile pipeline of one fused operator over tiles t0, t0 + stride, ...
+// Ms (G as float2[D][D]), runoff and loff are set up in shared memory.
 template <int K, int R, int S>
-__global__ void __launch_bounds__(kThreads) k_apply_fp32(ApplyArgs a) {
+__device__ __forceinline__ void apply_tiles(const ApplyArgs& a, float2* stage, const float2* Ms,
+                                            const uint64_t* runoff, const int* loff, uint64_t t0, uint64_t stride) {
     constexpr int D = 1 << K;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tileAmps = 1 << a.t.T;
-    float2* stage = reinterpret_cast<float2*>(smem_raw);
-    float2* Ms = stage + S * tileAmps;
-    uint64_t* runoff = reinterpret_cast<uint64_t*>(Ms + D * D);
-    int* loff = reinterpret_cast<int*>(runoff + 64);
-
-    const float2* gm = reinterpret_cast<const float2*>(a.mat);
-    for (int i = threadIdx.x; i < D * D; i += blockDim.x) Ms[i] = gm[i];
-    build_runoff(a.t, runoff);
-    for (int c = threadIdx.x; c < D; c += blockDim.x) {
-        int o = 0;
-#pragma unroll
-        for (int j = 0; j < K; ++j)
-            if ((c >> j) & 1) o |= 1 << a.tl[j];
-        loff[c] = o;
-    }
-    __syncthreads();
-
-    const uint64_t stride = gridDim.x;
-    // prologue: S-1 tiles in flight
 #pragma unroll
     for (int s = 0; s < S - 1; ++s) {
-        uint64_t t = blockIdx.x + s * stride;
+        uint64_t t = t0 + s * stride;
         if (t < a.t.ntiles) load_tile(a.t, runoff, t, stage + s * tileAmps);
         cp_async_commit();
     }
@@ -127,7 +102,7 @@ __global__ void __launch_bounds__(kThreads) k_apply_fp32(ApplyArgs a) {
     const int gshift = a.t.T - K;
     const int items = G * (D / R);
     int it_stage = 0;
-    for (uint64_t t = blockIdx.x; t < a.t.ntiles; t += stride) {
+    for (uint64_t t = t0; t < a.t.ntiles; t += stride) {
         uint64_t tn = t + (S - 1) * stride;
         int ld_stage = it_stage + (S - 1);
         if (ld_stage >= S) ld_stage -= S;
@@ -175,6 +150,36 @@ __global__ void __launch_bounds__(kThreads) k_apply_fp32(ApplyArgs a) {
 }
 
 template <int K>
+__device__ __forceinline__ void build_loff(const int* tl, int* loff) {
+    constexpr int D = 1 << K;
+    for (int c = threadIdx.x; c < D; c += blockDim.x) {
+        int o = 0;
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if ((c >> j) & 1) o |= 1 << tl[j];
+        loff[c] = o;
+    }
+}
+
+template <int K, int R, int S>
+__global__ void __launch_bounds__(kThreads) k_apply_fp32(ApplyArgs a) {
+    constexpr int D = 1 << K;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tileAmps = 1 << a.t.T;
+    float2* stage = reinterpret_cast<float2*>(smem_raw);
+    float2* Ms = stage + S * tileAmps;
+    uint64_t* runoff = reinterpret_cast<uint64_t*>(Ms + D * D);
+    int* loff = reinterpret_cast<int*>(runoff + 64);
+
+    const float2* gm = reinterpret_cast<const float2*>(a.mat);
+    for (int i = threadIdx.x; i < D * D; i += blockDim.x) Ms[i] = gm[i];
+    build_runoff(a.t, runoff);
+    build_loff<K>(a.tl, loff);
+    __syncthreads();
+    apply_tiles<K, R, S>(a, stage, Ms, runoff, loff, blockIdx.x, gridDim.x);
+}
+
+template <int K>
 struct ApplyCfg;
 template <> struct ApplyCfg<1> { static constexpr int T = 11, R = 2, S = 3; };
 template <> struct ApplyCfg<2> { static constexpr int T = 11, R = 4, S = 3; };
@@ -182,6 +187,22 @@ template <> struct ApplyCfg<3> { static constexpr int T = 11, R = 8, S = 3; };
 template <> struct ApplyCfg<4> { static constexpr int T = 11, R = 8, S = 3; };
 template <> struct ApplyCfg<5> { static constexpr int T = 12, R = 8, S = 2; };
 template <> struct ApplyCfg<6> { static constexpr int T = 12, R = 8, S = 2; };
+
+// Tile-local positions of the targets for geometry g.
+void local_targets(const TileGeom& g, const int* phys, int k, int* tl, int* tls) {
+    for (int j = 0; j < k; ++j) {
+        int p = phys[j];
+        int loc = p;
+        if (p >= g.m) {
+            int e = 0;
+            while (g.xpos[e] != p) ++e;
+            loc = g.m + e;
+        }
+        tl[j] = loc;
+        tls[j] = loc;
+    }
+    std::sort(tls, tls + k);
+}
 
 template <int K>
 cudaError_t launch_apply_k(float2* psi, int n, const int* phys, const float* d_mat, cudaStream_t st,
@@ -197,18 +218,7 @@ cudaError_t launch_apply_k(float2* psi, int n, const int* phys, const float* d_m
     a.t.nx = g.nx;
     for (int e = 0; e < 6; ++e) a.t.xpos[e] = g.xpos[e];
     a.mat = d_mat;
-    for (int j = 0; j < K; ++j) {
-        int p = phys[j];
-        int loc = p;
-        if (p >= g.m) {
-            int e = 0;
-            while (g.xpos[e] != p) ++e;
-            loc = g.m + e;
-        }
-        a.tl[j] = loc;
-        a.tls[j] = loc;
-    }
-    std::sort(a.tls, a.tls + K);
+    local_targets(g, phys, K, a.tl, a.tls);
     const int D = 1 << K;
     const size_t smem = sizeof(float2) * (static_cast<size_t>(C::S) << g.T) + sizeof(float2) * D * D +
                         sizeof(uint64_t) * 64 + sizeof(int) * 64;
@@ -292,6 +302,78 @@ __global__ void __launch_bounds__(kThreads) k_permute(PermArgs a) {
 
 __global__ void k_set_one(float2* psi) { psi[0] = make_float2(1.f, 0.f); }
 
+// ---------------------------------------------------------------------------
+// Batched trajectories: one persistent launch over many small states
+// ---------------------------------------------------------------------------
+constexpr int kBatchT = 11;
+constexpr int kBatchS = 3;
+
+__global__ void __launch_bounds__(kThreads) k_batch_evolve(BatchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* stage = reinterpret_cast<float2*>(smem_raw);
+    float2* Ms = stage + (kBatchS << kBatchT);
+    uint64_t* runoff = reinterpret_cast<uint64_t*>(Ms + 256);
+    int* loff = reinterpret_cast<int*>(runoff + 64);
+    __shared__ int s_slot;
+    __shared__ int s_stop;
+    const long long t_start = clock64();
+    for (;;) {
+        if (threadIdx.x == 0) s_slot = static_cast<int>(atomicAdd(a.queue, 1u));
+        __syncthreads();
+        const int slot = s_slot;
+        __syncthreads();
+        if (slot >= a.n_traj) break;
+        const int traj = a.order[slot];
+        float2* psi = a.states + (static_cast<uint64_t>(traj) << a.n);
+        // |0...0>
+        float4* p4 = reinterpret_cast<float4*>(psi);
+        const uint64_t npairs = (1ull << a.n) >> 1;
+        for (uint64_t i = threadIdx.x; i < npairs; i += blockDim.x)
+            p4[i] = make_float4(i == 0 ? 1.f : 0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
+        for (uint32_t b = a.bstart[traj]; b < a.bstart[traj + 1]; ++b) {
+            const BatchBlock d = a.blocks[b];
+            ApplyArgs aa{};
+            aa.t.psi = psi;
+            aa.t.T = d.T;
+            aa.t.m = d.m;
+            aa.t.nx = d.nx;
+            aa.t.ntiles = 1ull << (a.n - d.T);
+#pragma unroll
+            for (int e = 0; e < 6; ++e) {
+                aa.t.xpos[e] = d.xpos[e];
+                aa.tl[e] = d.tl[e];
+                aa.tls[e] = d.tls[e];
+            }
+            const int D = 1 << d.k;
+            const float2* gm = reinterpret_cast<const float2*>(a.mats + d.mat_off);
+            for (int i = threadIdx.x; i < D * D; i += blockDim.x) Ms[i] = gm[i];
+            build_runoff(aa.t, runoff);
+            switch (d.k) {
+                case 1: build_loff<1>(aa.tl, loff); break;
+                case 2: build_loff<2>(aa.tl, loff); break;
+                case 3: build_loff<3>(aa.tl, loff); break;
+                default: build_loff<4>(aa.tl, loff); break;
+            }
+            __syncthreads();
+            switch (d.k) {
+                case 1: apply_tiles<1, 2, kBatchS>(aa, stage, Ms, runoff, loff, 0, 1); break;
+                case 2: apply_tiles<2, 4, kBatchS>(aa, stage, Ms, runoff, loff, 0, 1); break;
+                case 3: apply_tiles<3, 8, kBatchS>(aa, stage, Ms, runoff, loff, 0, 1); break;
+                default: apply_tiles<4, 8, kBatchS>(aa, stage, Ms, runoff, loff, 0, 1); break;
+            }
+            // watchdog: thread 0 decides for the whole CTA
+            if (threadIdx.x == 0)
+                s_stop = (a.budget != 0 && static_cast<unsigned long long>(clock64() - t_start) > a.budget) ? 1 : 0;
+            __syncthreads();
+            if (s_stop) {
+                if (threadIdx.x == 0) atomicExch(a.err, 7);
+                return;
+            }
+        }
+    }
+}
+
 }  // namespace
 
 int num_sms() {
@@ -332,6 +414,43 @@ bool make_geom(int n, const int* special, int ns, int T_want, TileGeom* g) {
     return true;
 }
 
+bool make_batch_block(int n, const int* phys, int k, uint32_t mat_off, BatchBlock* b) {
+    if (k < 1 || k > 4) return false;
+    TileGeom g;
+    if (!make_geom(n, phys, k, kBatchT, &g)) return false;
+    *b = BatchBlock{};
+    b->k = k;
+    b->T = g.T;
+    b->m = g.m;
+    b->nx = g.nx;
+    for (int e = 0; e < 6; ++e) b->xpos[e] = g.xpos[e];
+    local_targets(g, phys, k, b->tl, b->tls);
+    b->mat_off = mat_off;
+    return true;
+}
+
+cudaError_t launch_batch_evolve(const BatchArgs& a, cudaStream_t st, uint64_t* launches) {
+    const size_t smem = sizeof(float2) * (static_cast<size_t>(kBatchS) << kBatchT) + sizeof(float2) * 256 +
+                        sizeof(uint64_t) * 64 + sizeof(int) * 64;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_batch_evolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_evolve, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    unsigned grid = static_cast<unsigned>(num_sms() * occ);
+    if (grid > static_cast<unsigned>(a.n_traj)) grid = static_cast<unsigned>(a.n_traj);
+    if (grid == 0) grid = 1;
+    k_batch_evolve<<<grid, kThreads, smem, st>>>(a);
+    ++*launches;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init_zero(float2* psi, int n, cudaStream_t st, uint64_t* launches) {
     cudaError_t e = cudaMemsetAsync(psi, 0, sizeof(float2) << n, st);
     if (e != cudaSuccess) return e;
@@ -364,12 +483,18 @@ cudaError_t launch_permute(float2* psi, int n, const int* pa, const int* pb, int
         int spec[12];
         for (;;) {
             int ns = 0;
-            for (int i = i0; i < i1; ++i) { spec[ns++] = pa[i]; spec[ns++] = pb[i]; }
+            for (int i = i0; i < i1; ++i) {
+                spec[ns++] = pa[i];
+                spec[ns++] = pb[i];
+            }
             if (!make_geom(n, spec, ns, T, &g)) {
                 if (i1 == i0 + 1) return cudaErrorInvalidValue;
                 --i1;
                 ns = 0;
-                for (int i = i0; i < i1; ++i) { spec[ns++] = pa[i]; spec[ns++] = pb[i]; }
+                for (int i = i0; i < i1; ++i) {
+                    spec[ns++] = pa[i];
+                    spec[ns++] = pb[i];
+                }
                 make_geom(n, spec, ns, T, &g);
                 break;
             }

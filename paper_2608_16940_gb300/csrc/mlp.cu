@@ -98,12 +98,13 @@ __global__ void k_weight_grad(const float* __restrict__ delta, int out, const fl
 
 // Adam: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
 // p -= lr * (m / c1) / (sqrt(v / c2) + eps), with c1 = 1 - b1^t, c2 = 1 - b2^t.
+// With wd > 0 the gradient of the L2 penalty (wd / 2) |p|^2 is added first.
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                        float* __restrict__ v, size_t count, float lr, float b1, float b2, float eps, float c1,
-                       float c2) {
+                       float c2, float wd) {
     const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= count) return;
-    const float gi = g[i];
+    const float gi = g[i] + wd * p[i];
     const float mi = b1 * m[i] + (1.f - b1) * gi;
     const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
     m[i] = mi;
@@ -205,7 +206,8 @@ qsa_status qsa_mlp_adam_step(float* params_dev, const float* grads_dev, float* m
     const float c1 = static_cast<float>(1.0 - std::pow(static_cast<double>(beta1), step));
     const float c2 = static_cast<float>(1.0 - std::pow(static_cast<double>(beta2), step));
     k_adam<<<blocks_for(count, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(params_dev, grads_dev, m_dev, v_dev,
-                                                                                  count, lr, beta1, beta2, eps, c1, c2);
+                                                                                  count, lr, beta1, beta2, eps, c1, c2,
+                                                                                  0.f);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(QSA_E_CUDA, std::string("adam: ") + cudaGetErrorString(e));
     return QSA_OK;
@@ -227,9 +229,22 @@ qsa_status qsa_costmodel_init(uint64_t seed, float* params_host) {
 }
 
 qsa_status qsa_costmodel_train(const float* X_host, const float* y_host, size_t n, int epochs, int batch, float lr,
-                               uint64_t seed, float* params_inout_host, float* epoch_loss_host) {
-    if (!X_host || !y_host || !params_inout_host || n == 0 || epochs < 1 || batch < 1)
+                               float weight_decay, uint64_t seed, float* params_inout_host, float* epoch_loss_host) {
+    if (!X_host || !y_host || !params_inout_host || n == 0 || epochs < 1 || batch < 1 || weight_decay < 0.f)
         return fail(QSA_E_ARG, "bad training arguments");
+    // Standardise the targets (log-seconds sit far from the network's initial
+    // output): train on (y - mu) / sigma with the output layer rescaled to
+    // match, then fold mu and sigma back into W3 and b3.
+    double mu = 0.0, var = 0.0;
+    for (size_t i = 0; i < n; ++i) mu += y_host[i];
+    mu /= static_cast<double>(n);
+    for (size_t i = 0; i < n; ++i) var += (y_host[i] - mu) * (y_host[i] - mu);
+    const double sigma = std::max(1e-6, std::sqrt(var / static_cast<double>(n)));
+    std::vector<float> yn(n);
+    for (size_t i = 0; i < n; ++i) yn[i] = static_cast<float>((y_host[i] - mu) / sigma);
+    for (int j = 0; j < H; ++j) params_inout_host[OFF_W3 + j] = static_cast<float>(params_inout_host[OFF_W3 + j] / sigma);
+    params_inout_host[OFF_B3] = static_cast<float>((params_inout_host[OFF_B3] - mu) / sigma);
+    y_host = yn.data();
     const size_t bsz = std::min<size_t>(static_cast<size_t>(batch), n);
     float *dX = nullptr, *dY = nullptr, *dP = nullptr, *dG = nullptr, *dM = nullptr, *dV = nullptr, *dWs = nullptr,
           *dLoss = nullptr, *dXb = nullptr, *dYb = nullptr, *dOut = nullptr;
@@ -274,7 +289,8 @@ qsa_status qsa_costmodel_train(const float* X_host, const float* y_host, size_t 
             if (e == cudaSuccess) {
                 const float c1 = static_cast<float>(1.0 - std::pow(0.9, step));
                 const float c2 = static_cast<float>(1.0 - std::pow(0.999, step));
-                k_adam<<<blocks_for(np, 256), 256, 0, st>>>(dP, dG, dM, dV, np, lr, 0.9f, 0.999f, 1e-8f, c1, c2);
+                k_adam<<<blocks_for(np, 256), 256, 0, st>>>(dP, dG, dM, dV, np, lr, 0.9f, 0.999f, 1e-8f, c1, c2,
+                                                            weight_decay);
                 e = cudaGetLastError();
             }
             // the pageable staging vectors are reused: wait for the copies
@@ -295,6 +311,12 @@ qsa_status qsa_costmodel_train(const float* X_host, const float* y_host, size_t 
     for (float* p : {dX, dY, dP, dG, dM, dV, dWs, dLoss, dXb, dYb, dOut})
         if (p) cudaFree(p);
     if (st) cudaStreamDestroy(st);
+    // fold the standardisation back into the output layer (also on failure,
+    // so the caller's parameters keep their meaning)
+    for (int j = 0; j < H; ++j) params_inout_host[OFF_W3 + j] = static_cast<float>(params_inout_host[OFF_W3 + j] * sigma);
+    params_inout_host[OFF_B3] = static_cast<float>(params_inout_host[OFF_B3] * sigma + mu);
+    if (epoch_loss_host)
+        for (int ep = 0; ep < epochs; ++ep) epoch_loss_host[ep] = static_cast<float>(epoch_loss_host[ep] * sigma * sigma);
     if (e != cudaSuccess) return fail(QSA_E_CUDA, std::string("cost-model training: ") + cudaGetErrorString(e));
     return QSA_OK;
 }

@@ -467,3 +467,275 @@ qsa_status qsa_state_counters(qsa_state s, uint64_t* launches) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched trajectories
+// ---------------------------------------------------------------------------
+struct qsa_batch_s {
+    int n = 0, n_traj = 0;
+    size_t total_ops = 0;
+    std::vector<qsa::BatchBlock> blocks;
+    std::vector<uint32_t> bstart;
+    std::vector<int32_t> order;
+    std::vector<float> mats;
+    qsa::BatchBlock* d_blocks = nullptr;
+    uint32_t* d_bstart = nullptr;
+    int32_t* d_order = nullptr;
+    float* d_mats = nullptr;
+    unsigned* d_queue = nullptr;   // [0] work counter, [1] error word
+    uint32_t* d_out = nullptr;     // keys, counts (n_traj * shots each), n_distinct (n_traj)
+    size_t out_cap = 0;
+    uint64_t shots = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    void* g_states = nullptr;
+    uint64_t g_shots = 0, g_seed = 0, g_budget = 0;
+    uint64_t launches = 0;
+};
+
+namespace {
+
+void batch_free_device(qsa_batch b) {
+    for (void* p : {static_cast<void*>(b->d_blocks), static_cast<void*>(b->d_bstart), static_cast<void*>(b->d_order),
+                    static_cast<void*>(b->d_mats), static_cast<void*>(b->d_queue), static_cast<void*>(b->d_out)})
+        if (p) cudaFree(p);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+}
+
+cudaError_t batch_enqueue(qsa_batch b, float2* states, uint64_t shots, uint64_t seed, uint64_t budget, cudaStream_t st) {
+    uint32_t* keys = b->d_out;
+    uint32_t* cnts = keys + static_cast<size_t>(b->n_traj) * shots;
+    uint32_t* nd = cnts + static_cast<size_t>(b->n_traj) * shots;
+    cudaError_t e = cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    qsa::BatchArgs a{};
+    a.states = states;
+    a.n = b->n;
+    a.n_traj = b->n_traj;
+    a.blocks = b->d_blocks;
+    a.bstart = b->d_bstart;
+    a.order = b->d_order;
+    a.mats = b->d_mats;
+    a.queue = b->d_queue;
+    a.err = reinterpret_cast<int*>(b->d_queue + 1);
+    a.budget = budget;
+    e = qsa::launch_batch_evolve(a, st, &b->launches);
+    if (e != cudaSuccess) return e;
+    return qsa::launch_batch_sample(states, b->n, b->n_traj, static_cast<uint32_t>(shots), seed, keys, cnts, nd, st,
+                                    &b->launches);
+}
+
+}  // namespace
+
+extern "C" {
+
+qsa_status qsa_batch_create(int n_qubits, int n_traj, const qsa_op* ops, const size_t* op_offsets,
+                            const qsa_plan_opts* opts, qsa_batch* out) {
+    if (!out) return fail(QSA_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_qubits < 1 || n_qubits > 22) return fail(QSA_E_ARG, "batched states need 1 <= N <= 22");
+    if (n_traj < 1 || !op_offsets) return fail(QSA_E_ARG, "bad trajectory list");
+    qsa_plan_opts o;
+    qsa_status st = normalise_opts(opts, &o);
+    if (st != QSA_OK) return st;
+    if (o.kmax > 4) return fail(QSA_E_ARG, "batched trajectories fuse blocks of at most 4 qubits (kmax <= 4)");
+    if (op_offsets[0] != 0) return fail(QSA_E_ARG, "op_offsets[0] must be 0");
+    for (int t = 0; t < n_traj; ++t)
+        if (op_offsets[t + 1] < op_offsets[t]) return fail(QSA_E_ARG, "op_offsets must be non-decreasing");
+    st = validate_ops(ops, op_offsets[n_traj], n_qubits);
+    if (st != QSA_OK) return st;
+    auto* b = new qsa_batch_s();
+    b->n = n_qubits;
+    b->n_traj = n_traj;
+    b->total_ops = op_offsets[n_traj];
+    b->bstart.push_back(0);
+    std::vector<double> M;
+    for (int t = 0; t < n_traj; ++t) {
+        const qsa_op* tops = ops + op_offsets[t];
+        const size_t cnt = op_offsets[t + 1] - op_offsets[t];
+        auto units = plan(tops, cnt, n_qubits, o, nullptr);
+        for (const Unit& u : units) {
+            int32_t tg[QSA_MAX_K];
+            int k = 0;
+            const uint32_t off = static_cast<uint32_t>(b->mats.size());
+            if (u.e - u.s == 1) {
+                k = tops[u.s].k;
+                for (int j = 0; j < k; ++j) tg[j] = tops[u.s].targets[j];
+                b->mats.resize(off + (2u << (2 * k)));
+                to_float_matrix(tops[u.s].matrix, k, b->mats.data() + off);
+            } else {
+                st = fuse_range(tops, u.s, u.e, tg, &k, &M);
+                if (st != QSA_OK) {
+                    delete b;
+                    return st;
+                }
+                b->mats.resize(off + M.size());
+                for (size_t j = 0; j < M.size(); ++j) b->mats[off + j] = static_cast<float>(M[j]);
+            }
+            while (b->mats.size() % 4) b->mats.push_back(0.f);
+            qsa::BatchBlock bb;
+            int phys[QSA_MAX_K];
+            for (int j = 0; j < k; ++j) phys[j] = tg[j];
+            if (!qsa::make_batch_block(n_qubits, phys, k, off, &bb)) {
+                delete b;
+                return fail(QSA_E_ARG, "could not tile a fused block");
+            }
+            b->blocks.push_back(bb);
+        }
+        b->bstart.push_back(static_cast<uint32_t>(b->blocks.size()));
+    }
+    // longest trajectories first, so the tail of the queue holds short work
+    b->order.resize(n_traj);
+    for (int t = 0; t < n_traj; ++t) b->order[t] = t;
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
+        return b->bstart[x + 1] - b->bstart[x] > b->bstart[y + 1] - b->bstart[y];
+    });
+    cudaError_t e = cudaSuccess;
+    auto up = [&](void** dst, const void* src, size_t bytes) {
+        if (e != cudaSuccess) return;
+        e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
+        if (e == cudaSuccess && bytes) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    up(reinterpret_cast<void**>(&b->d_blocks), b->blocks.data(), b->blocks.size() * sizeof(qsa::BatchBlock));
+    up(reinterpret_cast<void**>(&b->d_bstart), b->bstart.data(), b->bstart.size() * sizeof(uint32_t));
+    up(reinterpret_cast<void**>(&b->d_order), b->order.data(), b->order.size() * sizeof(int32_t));
+    up(reinterpret_cast<void**>(&b->d_mats), b->mats.data(), b->mats.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        batch_free_device(b);
+        delete b;
+        return fail(QSA_E_NOMEM, std::string("batch setup: ") + cudaGetErrorString(e));
+    }
+    *out = b;
+    return QSA_OK;
+}
+
+qsa_status qsa_batch_info(qsa_batch b, size_t* total_blocks, size_t* total_ops, uint64_t* launches) {
+    if (!b) return fail(QSA_E_ARG, "batch is NULL");
+    if (total_blocks) *total_blocks = b->blocks.size();
+    if (total_ops) *total_ops = b->total_ops;
+    if (launches) *launches = b->launches;
+    return QSA_OK;
+}
+
+qsa_status qsa_batch_run(qsa_batch b, void* dev_states, size_t bytes, uint64_t shots, uint64_t seed,
+                         uint64_t budget_cycles, int use_graph, void* cuda_stream, qsa_run_stats* stats) {
+    if (!b || !dev_states) return fail(QSA_E_ARG, "NULL argument");
+    if (bytes < (static_cast<size_t>(b->n_traj) * sizeof(float2) << b->n))
+        return fail(QSA_E_ARG, "state buffer smaller than n_traj * 8 * 2^N bytes");
+    if (reinterpret_cast<uintptr_t>(dev_states) % 16) return fail(QSA_E_ARG, "states must be 16-byte aligned");
+    if (shots < 1 || shots > 16384) return fail(QSA_E_ARG, "batched sampling takes 1..16384 shots per trajectory");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const size_t need = sizeof(uint32_t) * (2 * static_cast<size_t>(b->n_traj) * shots + b->n_traj);
+    if (need > b->out_cap) {
+        if (b->d_out) {
+            cudaDeviceSynchronize();
+            cudaFree(b->d_out);
+        }
+        b->d_out = nullptr;
+        b->out_cap = 0;
+        if (b->gexec) {
+            cudaGraphExecDestroy(b->gexec);
+            cudaGraphDestroy(b->graph);
+            b->gexec = nullptr;
+            b->graph = nullptr;
+        }
+        cudaError_t e = cudaMalloc(&b->d_out, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(QSA_E_NOMEM, "cudaMalloc of batch outputs failed");
+        }
+        b->out_cap = need;
+    }
+    b->shots = shots;
+    float2* states = static_cast<float2*>(dev_states);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaError_t e = cudaSuccess;
+    if (use_graph) {
+        const bool fresh = !b->gexec || b->g_states != dev_states || b->g_shots != shots || b->g_seed != seed ||
+                           b->g_budget != budget_cycles;
+        if (fresh) {
+            if (b->gexec) {
+                cudaGraphExecDestroy(b->gexec);
+                cudaGraphDestroy(b->graph);
+                b->gexec = nullptr;
+                b->graph = nullptr;
+            }
+            // one direct run first: it sets the kernels' attributes outside the capture
+            e = batch_enqueue(b, states, shots, seed, budget_cycles, b->cap_stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(b->cap_stream);
+            if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t ee = batch_enqueue(b, states, shots, seed, budget_cycles, b->cap_stream);
+                e = cudaStreamEndCapture(b->cap_stream, &b->graph);
+                if (ee != cudaSuccess) e = ee;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, b->graph, 0);
+            if (e != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return fail(QSA_E_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+            }
+            b->g_states = dev_states;
+            b->g_shots = shots;
+            b->g_seed = seed;
+            b->g_budget = budget_cycles;
+        }
+        cudaEventRecord(e0, st);
+        e = cudaGraphLaunch(b->gexec, st);
+        cudaEventRecord(e1, st);
+        if (e == cudaSuccess) b->launches += 2;
+    } else {
+        cudaEventRecord(e0, st);
+        e = batch_enqueue(b, states, shots, seed, budget_cycles, st);
+        cudaEventRecord(e1, st);
+    }
+    unsigned err_word = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err_word, b->d_queue + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return fail(QSA_E_CUDA, std::string("batch run: ") + cudaGetErrorString(e));
+    if (stats) {
+        *stats = qsa_run_stats{};
+        stats->seconds = ms * 1e-3;
+        stats->apply_seconds = ms * 1e-3;
+        stats->blocks = b->blocks.size();
+        stats->passes = b->blocks.size();
+        stats->hbm_bytes = 16.0 * static_cast<double>(1ull << b->n) * static_cast<double>(b->blocks.size());
+        stats->launches = use_graph ? 2 : 2;
+    }
+    if (err_word != 0)
+        return fail(QSA_E_TIMEOUT, "batched trajectories: the cycle budget ran out (error word " +
+                                       std::to_string(err_word) + "); the states and counts are incomplete");
+    return QSA_OK;
+}
+
+qsa_status qsa_batch_counts(qsa_batch b, uint32_t* outcomes, uint32_t* counts, uint32_t* n_distinct) {
+    if (!b || !b->d_out || !outcomes || !counts || !n_distinct) return fail(QSA_E_ARG, "NULL argument or no run yet");
+    const size_t m = static_cast<size_t>(b->n_traj) * b->shots;
+    cudaError_t e = cudaMemcpy(outcomes, b->d_out, sizeof(uint32_t) * m, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(counts, b->d_out + m, sizeof(uint32_t) * m, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(n_distinct, b->d_out + 2 * m, sizeof(uint32_t) * b->n_traj, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(QSA_E_CUDA, std::string("batch counts: ") + cudaGetErrorString(e));
+    return QSA_OK;
+}
+
+qsa_status qsa_batch_destroy(qsa_batch b) {
+    if (!b) return fail(QSA_E_ARG, "batch is NULL");
+    cudaDeviceSynchronize();
+    batch_free_device(b);
+    delete b;
+    return QSA_OK;
+}
+
+}  // extern "C"

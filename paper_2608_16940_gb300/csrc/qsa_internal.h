@@ -31,6 +31,36 @@ bool make_geom(int n, const int* special, int ns, int T_want, TileGeom* g);
 // Number of SMs of the current device (cached).
 int num_sms();
 
+// One fused block of a trajectory in the batched kernel (k <= 4, tile bits 11).
+struct BatchBlock {
+    int32_t k, T, m, nx;
+    int32_t xpos[6], tl[6], tls[6];
+    uint32_t mat_off;   // float offset of G in the matrix table
+    uint32_t pad;
+};
+
+struct BatchArgs {
+    float2* states;            // n_traj consecutive states of 2^n amplitudes
+    int n, n_traj;
+    const BatchBlock* blocks;
+    const uint32_t* bstart;    // n_traj + 1 block offsets
+    const int32_t* order;      // trajectories in queue order (longest first)
+    const float* mats;
+    unsigned int* queue;       // work counter, zero before the launch
+    int* err;                  // set to 7 when the cycle budget runs out
+    unsigned long long budget; // clock64 cycles per CTA, 0 = unlimited
+};
+
+bool make_batch_block(int n, const int* phys, int k, uint32_t mat_off, BatchBlock* b);
+cudaError_t launch_batch_evolve(const BatchArgs& a, cudaStream_t st, uint64_t* launches);
+
+// One CTA per trajectory: sample `shots` outcomes of every state (identity
+// layout) with Philox stream id = trajectory index, sort, run-length encode.
+// Outputs per trajectory t at t * shots: outcomes, counts; n_distinct[t].
+cudaError_t launch_batch_sample(const float2* states, int n, int n_traj, uint32_t shots, uint64_t seed,
+                                uint32_t* out_keys, uint32_t* out_counts, uint32_t* n_distinct, cudaStream_t st,
+                                uint64_t* launches);
+
 // ---- launchers (return the first CUDA error; *launches incremented) --------
 cudaError_t launch_init_zero(float2* psi, int n, cudaStream_t st, uint64_t* launches);
 

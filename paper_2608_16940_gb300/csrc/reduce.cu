@@ -14,11 +14,14 @@
 
 #include <cstdint>
 
+#include "qsa_device.cuh"
 #include "qsa_internal.h"
 
 namespace qsa {
 
 namespace {
+
+using namespace dev;
 
 constexpr int kRedThreads = 256;
 constexpr int kRedBlocksPerSM = 8;
@@ -66,26 +69,6 @@ __global__ void k_finalize_sum(const double* __restrict__ partials, int n, doubl
     if (threadIdx.x == 0) *out = sh[0];
 }
 
-struct Layout {
-    int n;
-    int L[QSA_MAX_QUBITS];
-};
-
-__device__ __forceinline__ uint64_t encode_logical(uint64_t x, const Layout& lay) {
-    uint64_t y = 0;
-#pragma unroll
-    for (int q = 0; q < QSA_MAX_QUBITS; ++q)
-        if (q < lay.n) y |= ((x >> q) & 1ull) << lay.L[q];
-    return y;
-}
-
-__device__ __forceinline__ uint64_t decode_physical(uint64_t y, const Layout& lay) {
-    uint64_t x = 0;
-#pragma unroll
-    for (int q = 0; q < QSA_MAX_QUBITS; ++q)
-        if (q < lay.n) x |= ((y >> lay.L[q]) & 1ull) << q;
-    return x;
-}
 
 __global__ void k_probs_logical(const float2* __restrict__ psi, Layout lay, double* __restrict__ out) {
     const uint64_t dim = 1ull << lay.n;
@@ -100,36 +83,6 @@ __global__ void k_probs_logical(const float2* __restrict__ psi, Layout lay, doub
 // Sampler
 // ---------------------------------------------------------------------------
 
-// floor(v^2 * 2^60) exactly, in integers: v = M * 2^E with a 24-bit M, so
-// v^2 2^60 = M^2 2^(2E+60).  Valid for |v| < 2.
-__device__ __forceinline__ uint64_t sq_fixed60(float v) {
-    const uint32_t b = __float_as_uint(v) & 0x7fffffffu;
-    const uint32_t e8 = b >> 23;
-    const uint32_t M = (b & 0x7fffffu) | (e8 ? 0x800000u : 0u);
-    const int E = static_cast<int>(e8 ? e8 : 1u) - 150;
-    const uint64_t sq = static_cast<uint64_t>(M) * M;
-    const int s = 2 * E + 60;
-    if (s >= 0) return s < 16 ? (sq << s) : (1ull << 62);
-    return (-s) >= 64 ? 0ull : (sq >> (-s));
-}
-
-__device__ __forceinline__ uint64_t weight(float2 a) { return sq_fixed60(a.x) + sq_fixed60(a.y); }
-
-__device__ __forceinline__ uint64_t warp_incl_scan_u64(uint64_t v) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint64_t t = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += t;
-    }
-    return v;
-}
-
-__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // One warp per block of `bsz` amplitudes: total integer weight.
 __global__ void k_block_weights(const float2* __restrict__ psi, uint64_t nblocks, int bsz,
@@ -170,27 +123,6 @@ __global__ void __launch_bounds__(1024) k_scan_inclusive(uint64_t* __restrict__ 
     }
 }
 
-// Philox4x64-10 (Salmon et al., SC'11), word 0 of the block at (ctr, key).
-__device__ __forceinline__ uint64_t philox4x64_10_w0(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
-                                                     uint64_t k0, uint64_t k1) {
-    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
-    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r) {
-            k0 += W0;
-            k1 += W1;
-        }
-        const uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
-        const uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
-        const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
-        c0 = n0;
-        c1 = lo1;
-        c2 = n2;
-        c3 = lo0;
-    }
-    return c0;
-}
 
 // One warp per shot: draw u, find the block (first cum > u), then the amplitude.
 __global__ void k_draw(const float2* __restrict__ psi, const uint64_t* __restrict__ cum, uint64_t nblocks, int bsz,
@@ -204,7 +136,7 @@ __global__ void k_draw(const float2* __restrict__ psi, const uint64_t* __restric
         return;
     }
     const uint64_t r = philox4x64_10_w0(s, stream_id, 0, 0, seed, 0);
-    const uint64_t u = r % total;
+    const uint64_t u = __umul64hi(r, total);  // floor(r * total / 2^64)
     // first block b with cum[b] > u
     uint64_t lo = 0, hi = nblocks - 1;
     while (lo < hi) {
@@ -321,9 +253,165 @@ inline uint64_t next_pow2(uint64_t v) {
     return p;
 }
 
+// Batched sampler: CTA t samples state t (identity layout) with Philox stream
+// id t.  Shared memory: cum[nblocks] (uint64) then keys[P] (uint32).
+constexpr int kBatchSampleThreads = 512;
+
+__global__ void __launch_bounds__(kBatchSampleThreads)
+    k_batch_sample(const float2* __restrict__ states, int n, uint32_t shots, uint32_t P, uint64_t seed,
+                   uint32_t* __restrict__ out_keys, uint32_t* __restrict__ out_counts,
+                   uint32_t* __restrict__ n_distinct) {
+    extern __shared__ uint64_t sm64[];
+    const int traj = blockIdx.x;
+    const float2* psi = states + (static_cast<uint64_t>(traj) << n);
+    const int bsz = n >= 10 ? 1024 : (1 << n);
+    const int nb = (1 << n) / bsz;
+    uint64_t* cum = sm64;
+    uint32_t* keys = reinterpret_cast<uint32_t*>(cum + nb);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry;
+
+    for (int b = warp; b < nb; b += nw) {
+        uint64_t s = 0;
+        for (int j = lane; j < bsz; j += 32) s += weight(psi[static_cast<uint64_t>(b) * bsz + j]);
+        s = warp_sum_u64(s);
+        if (lane == 0) cum[b] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {   // inclusive scan: lane l owns a contiguous range
+        const int per = (nb + 31) / 32;
+        const int lo = lane * per, hi = min(nb, lo + per);
+        uint64_t s = 0;
+        for (int i = lo; i < hi; ++i) s += cum[i];
+        uint64_t run = warp_incl_scan_u64(s) - s;
+        for (int i = lo; i < hi; ++i) {
+            run += cum[i];
+            cum[i] = run;
+        }
+    }
+    __syncthreads();
+    const uint64_t total = cum[nb - 1];
+    const int per = (bsz + 31) >> 5;
+    for (uint32_t s = warp; s < shots; s += nw) {
+        const uint64_t r = philox4x64_10_w0(s, static_cast<uint64_t>(traj), 0, 0, seed, 0);
+        const uint64_t u = __umul64hi(r, total);  // floor(r * total / 2^64)
+        int lo = 0, hi = nb - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (cum[mid] > u) hi = mid; else lo = mid + 1;
+        }
+        const uint64_t ub = u - (lo ? cum[lo - 1] : 0);
+        const float2* p = psi + static_cast<uint64_t>(lo) * bsz;
+        uint64_t wl = 0;
+        for (int j = 0; j < per; ++j) {
+            const int idx = lane * per + j;
+            if (idx < bsz) wl += weight(p[idx]);
+        }
+        const uint64_t incl = warp_incl_scan_u64(wl);
+        const uint64_t excl = incl - wl;
+        const unsigned hit = __ballot_sync(0xffffffffu, excl <= ub && ub < incl);
+        const int owner = hit ? __ffs(hit) - 1 : 0;
+        if (lane == owner) {
+            uint64_t acc = excl;
+            int j = 0;
+            for (; j < per; ++j) {
+                const int idx = lane * per + j;
+                if (idx >= bsz) break;
+                acc += weight(p[idx]);
+                if (acc > ub) break;
+            }
+            keys[s] = static_cast<uint32_t>(lo * bsz + lane * per + j);
+        }
+    }
+    for (uint32_t i = shots + threadIdx.x; i < P; i += blockDim.x) keys[i] = 0xFFFFFFFFu;
+    __syncthreads();
+    for (uint32_t k = 2; k <= P; k <<= 1)
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+                const uint32_t l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    const uint32_t x = keys[i], y = keys[l];
+                    if ((x > y) == up) {
+                        keys[i] = y;
+                        keys[l] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    // run-length encode: heads get their output slot; out_counts holds the
+    // run starts until they are turned into counts
+    uint32_t* okeys = out_keys + static_cast<uint64_t>(traj) * shots;
+    uint32_t* ocnt = out_counts + static_cast<uint64_t>(traj) * shots;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < shots; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t head = (i < shots && (i == 0 || keys[i] != keys[i - 1])) ? 1u : 0u;
+        uint32_t inc = head;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) wsum[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t v = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += t;
+            }
+            wsum[lane] = v;
+        }
+        __syncthreads();
+        const uint32_t pos = carry + (warp ? wsum[warp - 1] : 0) + inc - head;
+        if (head) {
+            okeys[pos] = keys[i];
+            ocnt[pos] = i;
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = pos + head;
+        __syncthreads();
+    }
+    const uint32_t nd = carry;
+    for (uint32_t base = 0; base < nd; base += blockDim.x) {
+        const uint32_t d = base + threadIdx.x;
+        uint32_t c = 0;
+        if (d < nd) c = (d + 1 < nd ? ocnt[d + 1] : shots) - ocnt[d];
+        __syncthreads();
+        if (d < nd) ocnt[d] = c;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) n_distinct[traj] = nd;
+}
+
 }  // namespace
 
 uint64_t next_pow2_u64(uint64_t v) { return next_pow2(v); }
+
+cudaError_t launch_batch_sample(const float2* states, int n, int n_traj, uint32_t shots, uint64_t seed,
+                                uint32_t* out_keys, uint32_t* out_counts, uint32_t* n_distinct, cudaStream_t st,
+                                uint64_t* launches) {
+    const int bsz = n >= 10 ? 1024 : (1 << n);
+    const uint64_t nb = (1ull << n) / bsz;
+    const uint32_t P = static_cast<uint32_t>(next_pow2(shots));
+    const size_t smem = sizeof(uint64_t) * nb + sizeof(uint32_t) * P;
+    static size_t attr = 0;
+    if (smem > attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_batch_sample, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        attr = smem;
+    }
+    k_batch_sample<<<n_traj, kBatchSampleThreads, smem, st>>>(states, n, shots, P, seed, out_keys, out_counts,
+                                                              n_distinct);
+    ++*launches;
+    return cudaGetLastError();
+}
 
 int reduce_partials() { return num_sms() * kRedBlocksPerSM; }
 

@@ -144,7 +144,7 @@ qsa_status apply_physical(qsa_state s, const int* phys, int k, const float* d_ma
     cudaError_t e;
     bool tc = precision == QSA_PREC_TF32X3 && (k == 5 || k == 6) && tc_available(s, k);
     {
-        Timer tm(s, rs ? &rs->apply_seconds : nullptr);
+        Timer tm(s, rs ? (tc ? &rs->tc_seconds : &rs->apply_seconds) : nullptr);
         if (tc)
             e = launch_apply_tc(s->psi, s->n, phys, k, d_mat, s->d_err, s->stream, &s->launches);
         else

@@ -120,10 +120,11 @@ def test_learned_planner_gain_over_heuristics(q, capsys):
     n = 26
     st = GState(q, torch, n)
     try:
-        X, y = q.qsa_costmodel_collect(st.h, 360, reps=5, precision=q.QSA_PREC_FP32, seed=11)
+        X, y = q.qsa_costmodel_collect(st.h, 600, reps=3, precision=q.QSA_PREC_FP32, seed=11)
         perm = np.random.default_rng(0).permutation(len(y))
-        tr, te = perm[:300], perm[300:]
-        params, losses = q.qsa_costmodel_train(X[tr], y[tr], epochs=400, batch=32, lr=2e-3, seed=1)
+        tr, te = perm[:500], perm[500:]
+        params, losses = q.qsa_costmodel_train(X[tr], y[tr], epochs=200, batch=32, lr=2e-3, seed=1,
+                                               weight_decay=1e-2)
         assert losses[-1] < losses[0]
         q.qsa_costmodel_set(params)
         pred = q.qsa_costmodel_predict(X[te])
@@ -141,7 +142,7 @@ def test_learned_planner_gain_over_heuristics(q, capsys):
                   f"blocks {blocks}; seconds {times}; "
                   f"gain vs greedy {times['greedy'] / times['dp_mlp']:.2f}x, vs 4^k DP "
                   f"{times['dp_4k'] / times['dp_mlp']:.2f}x")
-        assert np.median(rel) < 0.35
+        assert np.median(rel) < 0.10
         assert times["dp_mlp"] <= 1.05 * min(times["greedy"], times["dp_4k"])
     finally:
         q.qsa_costmodel_set(None)

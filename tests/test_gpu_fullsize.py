@@ -1,0 +1,129 @@
+"""Full-size runs in the bench's launch configuration, checked where the FP64
+oracle cannot run the whole circuit: closed forms at sampled indices and
+invariants that hold at any size.
+
+- N = 28 fusion workload: the QFT of a random basis state matches its closed
+  form at sampled indices, and the whole circuit followed by its inverse
+  returns to |0...0>;
+- N = 30 QAOA workload: norm 1, global bit-flip symmetry of the state
+  (p(x) = p(~x), <Z_q> = 0), and the fused path agrees with the plain
+  per-gate path at sampled amplitudes;
+- N = 32 / 33 wide workload (k = 5, 6 on the tensor cores): ops then their
+  inverse return to |0...0>; N = 33 exercises indices beyond 2^32.
+- the N = 20, 200-op instance of the wide workload against the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_helpers import check_close
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2608_16940_gb300 as q
+    return q
+
+
+class Big:
+    def __init__(self, q, n):
+        self.q, self.n = q, n
+        self.buf = torch.empty(1 << n, dtype=torch.complex64, device="cuda:0")
+        self.h = q.qsa_state_create_ex(n, self.buf.data_ptr(), self.buf.numel() * 8,
+                                       torch.cuda.current_stream().cuda_stream, 1)
+
+    def amps(self, logical_idx):
+        """Logical amplitudes at the given indices, decoded through the layout."""
+        L = self.q.qsa_get_layout(self.h)
+        x = np.asarray(logical_idx, dtype=np.int64)
+        y = np.zeros_like(x)
+        for qb in range(self.n):
+            y |= ((x >> qb) & 1) << L[qb]
+        self.q.qsa_state_sync(self.h)
+        return self.buf[torch.from_numpy(y).cuda()].cpu().numpy().astype(np.complex128)
+
+    def close(self):
+        self.q.qsa_state_destroy(self.h)
+        del self.buf
+        torch.cuda.empty_cache()
+
+
+def test_fusion28_qft_closed_form_and_inverse_return(q):
+    n = 28
+    ops, x0 = W.fusion_circuit(n=n, layers=40, seed=0, with_inverse=True)
+    prefix = W.basis_prep(n, x0) + W.qft_ops(n)
+    st = Big(q, n)
+    try:
+        opts = q.make_opts(planner=q.QSA_PLAN_DP, kmax=4, kmax_diag=4, lowering=q.QSA_LOWER_PERMUTE)
+        q.qsa_apply_circuit(st.h, prefix, opts)
+        ys = np.random.default_rng(1).integers(0, 1 << n, size=256)
+        got = st.amps(ys)
+        ref = np.exp(2j * np.pi * ((x0 * ys) % (1 << n)) / (1 << n)) / np.sqrt(1 << n)
+        assert np.max(np.abs(got - ref)) < 1e-6
+        q.qsa_state_reset(st.h)
+        stats = q.qsa_apply_circuit(st.h, ops, opts)
+        assert stats["blocks"] < len(ops)
+        a0 = st.amps([0])[0]
+        assert abs(a0) ** 2 >= 1 - 1e-5
+    finally:
+        st.close()
+
+
+def test_qaoa30_symmetries_and_fused_equals_per_gate(q):
+    n = 30
+    ops, edges = W.qaoa_circuit(n=n, p=8, seed=0)
+    st = Big(q, n)
+    try:
+        q.qsa_apply_circuit(st.h, ops, q.make_opts(planner=q.QSA_PLAN_DP, kmax=4, kmax_diag=4))
+        assert abs(q.qsa_expectation_z(st.h, 0) - 1) < 1e-5
+        for qb in (0, 7, 29):
+            assert abs(q.qsa_expectation_z(st.h, 1 << qb)) < 1e-5
+        xs = np.random.default_rng(2).integers(0, 1 << n, size=128)
+        a = st.amps(xs)
+        b = st.amps(xs ^ ((1 << n) - 1))
+        pa, pb = np.abs(a) ** 2, np.abs(b) ** 2
+        assert np.all(np.abs(pa - pb) <= 1e-3 * (pa + pb) + 1e-15)
+        q.qsa_state_reset(st.h)
+        q.qsa_apply_circuit(st.h, ops, q.make_opts(planner=q.QSA_PLAN_PER_GATE))
+        c = st.amps(xs)
+        assert np.linalg.norm(a - c) <= 1e-4 * np.linalg.norm(a)
+    finally:
+        st.close()
+
+
+@pytest.mark.parametrize("n,n_ops", [(32, 20), (33, 8)])
+def test_wide_tensor_core_ops_then_inverse_return(q, n, n_ops):
+    ops = W.wide_circuit(n, n_ops=n_ops, widths=(5, 6), seed=n)
+    st = Big(q, n)
+    try:
+        stats = q.qsa_apply_circuit(st.h, ops + W.inverse(ops),
+                                    q.make_opts(planner=0, kmax=6, kmax_diag=6, precision=q.QSA_PREC_TF32X3))
+        assert stats["tc_blocks"] == 2 * n_ops
+        a0 = st.amps([0])[0]
+        assert abs(a0) ** 2 >= 1 - 1e-5
+        assert abs(q.qsa_expectation_z(st.h, 0) - 1) < 1e-5
+    finally:
+        st.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_wide_200_ops_fidelity_vs_oracle(q, prec, capsys):
+    n = 20
+    ops = W.wide_circuit(n, n_ops=200, widths=(5, 6), seed=0)
+    st = Big(q, n)
+    try:
+        q.qsa_apply_circuit(st.h, ops, q.make_opts(planner=0, kmax=6, kmax_diag=6, precision=prec))
+        got = st.amps(np.arange(1 << n))
+        ref = oracle.run_circuit(n, ops)
+        infid, err = check_close(ref, got)
+        with capsys.disabled():
+            print(f"\nwide 200 ops N=20 precision={'3xTF32' if prec else 'FP32'}: 1-F = {infid:.3e}, "
+                  f"max|d| = {err:.3e}")
+    finally:
+        st.close()

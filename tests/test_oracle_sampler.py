@@ -46,7 +46,7 @@ def _brute_force_sample(psi_logical, L, shots, seed, stream):
         else:
             c = np.array([s - 1, stream, 0, 0], dtype=np.uint64)
         r = int(np.random.Philox(key=np.array([seed, 0], dtype=np.uint64), counter=c).random_raw(1)[0])
-        u = r % total
+        u = (r * total) >> 64
         acc = 0
         for y in range(1 << n):
             acc += w[y]
