@@ -119,28 +119,59 @@ __device__ __forceinline__ void apply_tiles(const ApplyArgs& a, float2* stage, c
             uint32_t lb = static_cast<uint32_t>(g);
 #pragma unroll
             for (int j = 0; j < K; ++j) lb = static_cast<uint32_t>(insert_zero(lb, a.tls[j]));
-            float2 v[D];
+            if constexpr (K <= 5) {
+                // Packed FP32 pairs: with x2_c = (Re v_c, Re v_c), y2_c = (Im v_c, Im v_c)
+                // and g = (Re G, Im G), p = sum x2_c * g and q = sum y2_c * g give
+                // Re = p.x - q.y and Im = p.y + q.x; one 16-byte load of two G entries
+                // feeds four f32x2 FMAs.
+                uint64_t x2[D], y2[D];
 #pragma unroll
-            for (int c = 0; c < D; ++c) v[c] = st[lb | loff[c]];
-#pragma unroll
-            for (int rr = 0; rr < R; ++rr) {
-                const int r = rb * R + rr;
-                const float4* mrow = reinterpret_cast<const float4*>(Ms + r * D);
-                float ar = 0.f, ai = 0.f;
-#pragma unroll
-                for (int c = 0; c < D; c += 2) {
-                    float4 m2 = mrow[c >> 1];  // G[r][c], G[r][c+1]
-                    ar = fmaf(m2.x, v[c].x, ar);
-                    ar = fmaf(-m2.y, v[c].y, ar);
-                    ai = fmaf(m2.x, v[c].y, ai);
-                    ai = fmaf(m2.y, v[c].x, ai);
-                    ar = fmaf(m2.z, v[c + 1].x, ar);
-                    ar = fmaf(-m2.w, v[c + 1].y, ar);
-                    ai = fmaf(m2.z, v[c + 1].y, ai);
-                    ai = fmaf(m2.w, v[c + 1].x, ai);
+                for (int c = 0; c < D; ++c) {
+                    const float2 f = st[lb | loff[c]];
+                    x2[c] = pack2(f.x, f.x);
+                    y2[c] = pack2(f.y, f.y);
                 }
-                const uint32_t lj = lb | loff[r];
-                __stcs(a.t.psi + tile_global(a.t, runoff, base, lj), make_float2(ar, ai));
+#pragma unroll
+                for (int rr = 0; rr < R; ++rr) {
+                    const int r = rb * R + rr;
+                    const ulonglong2* mrow = reinterpret_cast<const ulonglong2*>(Ms + r * D);
+                    uint64_t p = 0, qv = 0;
+#pragma unroll
+                    for (int c = 0; c < D; c += 2) {
+                        const ulonglong2 gg = mrow[c >> 1];  // G[r][c], G[r][c+1]
+                        p = fma2(x2[c], gg.x, p);
+                        qv = fma2(y2[c], gg.x, qv);
+                        p = fma2(x2[c + 1], gg.y, p);
+                        qv = fma2(y2[c + 1], gg.y, qv);
+                    }
+                    const float2 P = unpack2(p), Q = unpack2(qv);
+                    const uint32_t lj = lb | loff[r];
+                    __stcs(a.t.psi + tile_global(a.t, runoff, base, lj), make_float2(P.x - Q.y, P.y + Q.x));
+                }
+            } else {
+                float2 v[D];
+#pragma unroll
+                for (int c = 0; c < D; ++c) v[c] = st[lb | loff[c]];
+#pragma unroll
+                for (int rr = 0; rr < R; ++rr) {
+                    const int r = rb * R + rr;
+                    const float4* mrow = reinterpret_cast<const float4*>(Ms + r * D);
+                    float ar = 0.f, ai = 0.f;
+#pragma unroll
+                    for (int c = 0; c < D; c += 2) {
+                        float4 m2 = mrow[c >> 1];  // G[r][c], G[r][c+1]
+                        ar = fmaf(m2.x, v[c].x, ar);
+                        ar = fmaf(-m2.y, v[c].y, ar);
+                        ai = fmaf(m2.x, v[c].y, ai);
+                        ai = fmaf(m2.y, v[c].x, ai);
+                        ar = fmaf(m2.z, v[c + 1].x, ar);
+                        ar = fmaf(-m2.w, v[c + 1].y, ar);
+                        ai = fmaf(m2.z, v[c + 1].y, ai);
+                        ai = fmaf(m2.w, v[c + 1].x, ai);
+                    }
+                    const uint32_t lj = lb | loff[r];
+                    __stcs(a.t.psi + tile_global(a.t, runoff, base, lj), make_float2(ar, ai));
+                }
             }
         }
         __syncthreads();

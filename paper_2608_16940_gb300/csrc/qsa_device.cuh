@@ -27,6 +27,24 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Two FP32 values in one 64-bit register pair, and the paired FMA
+// (fma.rn.f32x2: both lanes rounded to nearest like fmaf).
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 unpack2(uint64_t v) {
+    float2 f;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(f.x), "=f"(f.y) : "l"(v));
+    return f;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 // floor(v^2 * 2^60) exactly, in integers: v = M * 2^E with a 24-bit M, so
 // v^2 2^60 = M^2 2^(2E+60).  Valid for |v| < 2.
 __device__ __forceinline__ uint64_t sq_fixed60(float v) {

@@ -1,7 +1,8 @@
 // Reductions and sampling on the complex64 state (sm_103a).
 //
-//   launch_reduce_z      <Z_mask> and the norm, FP64 accumulation (App. B:
-//                        block totals kept in FP64).
+//   launch_reduce_z      <Z_mask> and the norm: exact squares accumulated per
+//                        thread in double-float (about 48 bits), partials
+//                        combined in FP64 (App. B: totals kept in FP64).
 //   launch_probs_logical p_x = fl64(re^2) + fl64(im^2) for every logical x,
 //                        decoded through the layout map (Theorem 1).
 //   launch_sample        hierarchical CDF sampler (§IV-E "Sampling": 2^10-entry
@@ -32,18 +33,42 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
+// Per-thread accumulation as an unevaluated float pair s + c: every square is
+// split exactly into h + l (FMA two-product, h = fl(v^2), l = v^2 - h) and h
+// is added with Knuth's two-sum, whose rounding error goes to c with l.  The
+// pair carries about 48 significant bits, so the FP64 value (double)s +
+// (double)c of each thread's partial sum matches FP64 accumulation of the
+// exact squares, while costing FP32 instructions only (GB300's FP64 rate is a
+// small fraction of its FP32 rate).
+__device__ __forceinline__ void acc_square(float& s, float& c, float v, bool neg) {
+    float h = __fmul_rn(v, v);
+    float l = __fmaf_rn(v, v, -h);
+    if (neg) {
+        h = -h;
+        l = -l;
+    }
+    const float t = __fadd_rn(s, h);
+    const float bp = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(h, bp));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(e, l));
+}
+
 __global__ void __launch_bounds__(kRedThreads) k_reduce_z(const float4* __restrict__ psi2, uint64_t npairs,
                                                            uint64_t physmask, double* __restrict__ partials) {
-    double acc = 0.0;
+    float s = 0.f, c = 0.f;
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
     for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < npairs; i += stride) {
         const float4 a = __ldcs(psi2 + i);
-        const double p0 = __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y));
-        const double p1 = __dadd_rn(__dmul_rn(a.z, a.z), __dmul_rn(a.w, a.w));
         const uint64_t y0 = i << 1;
-        acc += (__popcll(y0 & physmask) & 1) ? -p0 : p0;
-        acc += (__popcll((y0 | 1ull) & physmask) & 1) ? -p1 : p1;
+        const bool n0 = __popcll(y0 & physmask) & 1;
+        const bool n1 = __popcll((y0 | 1ull) & physmask) & 1;
+        acc_square(s, c, a.x, n0);
+        acc_square(s, c, a.y, n0);
+        acc_square(s, c, a.z, n1);
+        acc_square(s, c, a.w, n1);
     }
+    double acc = static_cast<double>(s) + static_cast<double>(c);
     __shared__ double ws[kRedThreads / 32];
     acc = warp_sum_d(acc);
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
