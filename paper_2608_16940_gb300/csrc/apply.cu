@@ -339,7 +339,7 @@ __global__ void k_set_one(float2* psi) { psi[0] = make_float2(1.f, 0.f); }
 constexpr int kBatchT = 11;
 constexpr int kBatchS = 3;
 
-__global__ void __launch_bounds__(kThreads) k_batch_evolve(BatchArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) k_batch_evolve(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* stage = reinterpret_cast<float2*>(smem_raw);
     float2* Ms = stage + (kBatchS << kBatchT);
