@@ -38,6 +38,12 @@ import workloads as W  # noqa: E402
 METRIC = "amplitude-updates/s"
 UNIT = "amp-updates/s"
 
+# DRAM bytes (read + write) per amplitude of one launch, from single ncu captures
+# at N=28 (profiles/k_apply_tc6_n28.md: 4.241 GB; profiles/k_apply_fp32_k4_n28.md:
+# 4.234 GB; each / 2^28).  Traffic scales with the state size, so a launch at N
+# moves this many bytes times 2^N.
+DRAM_BYTES_PER_AMP = {"k_apply_tc": 4.241e9 / 2**28, "k_apply_fp32": 4.234e9 / 2**28}
+
 
 def _peaks():
     try:
@@ -174,8 +180,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--shots", type=int, default=1000)
     ap.add_argument("--planner", default="dp_mlp", choices=["per_gate", "greedy", "dp", "dp_mlp"])
-    ap.add_argument("--kmax", type=int, default=4)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3"])
+    ap.add_argument("--kmax", type=int, default=6)
+    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3"])
     ap.add_argument("--lowering", default="auto", choices=["auto", "strided", "permute"])
     ap.add_argument("--cm-samples", type=int, default=240)
     ap.add_argument("--ref-qubits", type=int, default=28)
@@ -275,8 +281,9 @@ def main():
     name, tot, cnt = max(kinds, key=lambda kv: kv[1])
     avg = tot / cnt
     achieved = bytes_per_launch / avg / 1e9
+    dram = DRAM_BYTES_PER_AMP.get(name.split(" ")[0])
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-            "traffic": None, "kernel": name, "peak_source": peak_kind, "bytes_per_launch": bytes_per_launch,
+            "traffic": dram * (1 << n) if dram else None, "kernel": name, "peak_source": peak_kind, "bytes_per_launch": bytes_per_launch,
             "avg_launch_ms": avg * 1e3, "launches_per_step": cnt / args.steps,
             "share_of_step": tot / args.steps / per_step}
 
@@ -329,10 +336,13 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "c64 state, f32 arithmetic (3xTF32 on tensor cores), f64 reductions",
+                "vs_baseline": None,
+                "dtype": ("c64 state, f32 arithmetic (k=5/6 products as 3xTF32 on tensor cores, f32 accumulation), "
+                          "f64 reductions") if prec else "c64 state, f32 arithmetic, f64 reductions",
                 "data": "synthetic",
                 "config": {"workload": f"qaoa{n}_p{args.p}: random 3-regular graph, {len(ops)} gates, N={n} "
-                                       f"complex64 (8 GiB), 1000 shots + norm + <ZZ> per step",
+                                       f"complex64 ({8 * (1 << n) / 2**30:g} GiB), {args.shots} shots + norm + <ZZ> "
+                                       f"per step",
                            "planner": args.planner, "kmax": args.kmax, "precision": args.precision,
                            "lowering": args.lowering, "fused_blocks": pinfo["blocks"],
                            "l2": "state 8 GiB > 129 MB L2; no flush needed", "parallelism": f"replicas x{ws}"},

@@ -5,7 +5,8 @@ invariants that hold at any size.
 - N = 28 fusion workload: the QFT of a random basis state matches its closed
   form at sampled indices, and the whole circuit followed by its inverse
   returns to |0...0>;
-- N = 30 QAOA workload: norm 1, global bit-flip symmetry of the state
+- N = 30 QAOA workload (kmax 4 FP32, and the bench's kmax 6 with split-TF32
+  for k = 5, 6): norm 1, global bit-flip symmetry of the state
   (p(x) = p(~x), <Z_q> = 0), and the fused path agrees with the plain
   per-gate path at sampled amplitudes;
 - N = 32 / 33 wide workload (k = 5, 6 on the tensor cores): ops then their
@@ -75,12 +76,15 @@ def test_fusion28_qft_closed_form_and_inverse_return(q):
         st.close()
 
 
-def test_qaoa30_symmetries_and_fused_equals_per_gate(q):
+@pytest.mark.parametrize("kmax,prec", [(4, 0), (6, 1)], ids=["kmax4-fp32", "kmax6-3xtf32"])
+def test_qaoa30_symmetries_and_fused_equals_per_gate(q, kmax, prec):
+    """The bench's workload and launch configuration (kmax 6 with the split-TF32
+    path for k = 5, 6) and the FP32-only configuration."""
     n = 30
     ops, edges = W.qaoa_circuit(n=n, p=8, seed=0)
     st = Big(q, n)
     try:
-        q.qsa_apply_circuit(st.h, ops, q.make_opts(planner=q.QSA_PLAN_DP, kmax=4, kmax_diag=4))
+        q.qsa_apply_circuit(st.h, ops, q.make_opts(planner=q.QSA_PLAN_DP, kmax=kmax, kmax_diag=kmax, precision=prec))
         assert abs(q.qsa_expectation_z(st.h, 0) - 1) < 1e-5
         for qb in (0, 7, 29):
             assert abs(q.qsa_expectation_z(st.h, 1 << qb)) < 1e-5
