@@ -10,6 +10,8 @@ Contents
   single-threaded FP64 state-vector update, probabilities, <Z>, Philox4x64-10
   and the fixed-point CDF sampler.
 * this module: ctypes wrappers plus plain numpy restatements of
+  - the diagonal branch of Alg. 2 (elementwise multiply by the entry the
+    target bits index) and the fused diagonal of a block of diagonal gates,
   - the Kronecker embedding and block product used by fusion (§IV-C: "within a
     block, matrices remain in circuit order, with later gates multiplied on
     the left"),
@@ -98,6 +100,43 @@ def apply(psi: np.ndarray, targets: Sequence[int], mat: np.ndarray) -> None:
     rc = lib().orc_apply(_dptr(psi.view(np.float64)), n, t, k, _dptr(m.view(np.float64)))
     if rc != 0:
         raise ValueError("oracle apply: invalid arguments")
+
+
+def diag_index(n: int, targets: Sequence[int]) -> np.ndarray:
+    """c(x) for every canonical index x: bit j of c is bit targets[j] of x."""
+    x = np.arange(1 << n, dtype=np.int64)
+    c = np.zeros_like(x)
+    for j, t in enumerate(targets):
+        c |= ((x >> int(t)) & 1) << j
+    return c
+
+
+def apply_diag(psi: np.ndarray, targets: Sequence[int], d: np.ndarray) -> None:
+    """In place: the diagonal branch of Alg. 2 (axis-shifted lowering), "multiply
+    each amplitude by the diagonal entry indexed by the target bits":
+    psi[x] <- d[c(x)], with bit j of c equal to bit targets[j] of x (§II
+    little-endian order); the layout is unchanged."""
+    n = int(psi.size).bit_length() - 1
+    d = np.asarray(d, dtype=np.complex128)
+    assert d.shape == (1 << len(targets),)
+    psi *= d[diag_index(n, targets)]
+
+
+def fuse_diag(gates: Sequence, block_targets: Sequence[int]) -> np.ndarray:
+    """Diagonal of the fused block of diagonal gates on ``block_targets``
+    (ascending union of the gates' targets): entry c is the product, in circuit
+    order, of each gate's diagonal entry at the bits of c that are its targets
+    (§IV-C block product restricted to the diagonal mode)."""
+    u = len(block_targets)
+    pos = {int(q): i for i, q in enumerate(block_targets)}
+    d = np.ones(1 << u, dtype=np.complex128)
+    cs = np.arange(1 << u, dtype=np.int64)
+    for g in gates:
+        gi = np.zeros_like(cs)
+        for j, t in enumerate(g.targets):
+            gi |= ((cs >> pos[int(t)]) & 1) << j
+        d = np.diag(np.asarray(g.matrix, dtype=np.complex128))[gi] * d
+    return d
 
 
 def run_circuit(n: int, ops: Iterable, psi: np.ndarray | None = None) -> np.ndarray:
