@@ -181,6 +181,7 @@ def main():
     ap.add_argument("--shots", type=int, default=1000)
     ap.add_argument("--planner", default="dp_mlp", choices=["per_gate", "greedy", "dp", "dp_mlp"])
     ap.add_argument("--kmax", type=int, default=6)
+    ap.add_argument("--kmax-diag", type=int, default=12, help="diagonal-block cap (1..12)")
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3"])
     ap.add_argument("--lowering", default="auto", choices=["auto", "strided", "permute"])
     ap.add_argument("--cm-samples", type=int, default=240)
@@ -210,7 +211,8 @@ def main():
     planner = {"per_gate": 0, "greedy": 1, "dp": 2, "dp_mlp": 3}[args.planner]
     prec = {"fp32": 0, "tf32x3": 1}[args.precision]
     low = {"auto": 0, "strided": 1, "permute": 2}[args.lowering]
-    opts = q.make_opts(planner=planner, kmax=args.kmax, kmax_diag=args.kmax, precision=prec, lowering=low, timing=1)
+    kdiag = args.kmax_diag
+    opts = q.make_opts(planner=planner, kmax=args.kmax, kmax_diag=kdiag, precision=prec, lowering=low, timing=1)
 
     buf = torch.empty(1 << n, dtype=torch.complex64, device=dev)
     stream = torch.cuda.current_stream(dev).cuda_stream
@@ -223,8 +225,8 @@ def main():
     pinfo = q.qsa_plan_info(plan)
     edge_mask = (1 << edges[0][0]) | (1 << edges[0][1])
 
-    agg = {"apply_seconds": 0.0, "tc_seconds": 0.0, "permute_seconds": 0.0, "blocks": 0, "permutes": 0,
-           "tc_blocks": 0}
+    agg = {"apply_seconds": 0.0, "tc_seconds": 0.0, "permute_seconds": 0.0, "diag_seconds": 0.0, "blocks": 0,
+           "permutes": 0, "tc_blocks": 0, "diag_blocks": 0}
 
     def step(record):
         q.qsa_state_reset(s)
@@ -270,12 +272,14 @@ def main():
     # roofline of the dominant fused-operator kernel: 16 B per amplitude per launch
     hbm_peak, peak_kind = _peaks()
     bytes_per_launch = 16.0 * (1 << n)
-    n_fp32 = agg["blocks"] - agg["tc_blocks"]
+    n_fp32 = agg["blocks"] - agg["tc_blocks"] - agg["diag_blocks"]
     kinds = []
     if n_fp32:
         kinds.append(("k_apply_fp32 (FP32 fused dense update)", agg["apply_seconds"], n_fp32))
     if agg["tc_blocks"]:
         kinds.append(("k_apply_tc (split-TF32 tcgen05 fused update)", agg["tc_seconds"], agg["tc_blocks"]))
+    if agg["diag_blocks"]:
+        kinds.append(("k_apply_diag (diagonal streaming update)", agg["diag_seconds"], agg["diag_blocks"]))
     if agg["permutes"]:
         kinds.append(("k_permute (qubit permutation)", agg["permute_seconds"], agg["permutes"]))
     name, tot, cnt = max(kinds, key=lambda kv: kv[1])
@@ -296,7 +300,7 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             q.qsa_state_reset(s)
-            st = q.qsa_apply_circuit(s, ops, q.make_opts(planner=planner, kmax=args.kmax, kmax_diag=args.kmax,
+            st = q.qsa_apply_circuit(s, ops, q.make_opts(planner=planner, kmax=args.kmax, kmax_diag=kdiag,
                                                           precision=prec, lowering=low))
             vals, cnts = q.qsa_sample_counts(s, args.shots, seed=args.seed + 17)
             torch.cuda.synchronize()
@@ -343,7 +347,8 @@ def main():
                 "config": {"workload": f"qaoa{n}_p{args.p}: random 3-regular graph, {len(ops)} gates, N={n} "
                                        f"complex64 ({8 * (1 << n) / 2**30:g} GiB), {args.shots} shots + norm + <ZZ> "
                                        f"per step",
-                           "planner": args.planner, "kmax": args.kmax, "precision": args.precision,
+                           "planner": args.planner, "kmax": args.kmax, "kmax_diag": kdiag,
+                           "precision": args.precision,
                            "lowering": args.lowering, "fused_blocks": pinfo["blocks"],
                            "l2": "state 8 GiB > 129 MB L2; no flush needed", "parallelism": f"replicas x{ws}"},
                 "gpu_launches": launches, "clocks": clocks, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,

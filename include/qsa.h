@@ -59,6 +59,11 @@ typedef struct qsa_state_s* qsa_state;
 
 #define QSA_MAX_QUBITS 34
 #define QSA_MAX_K 6
+/* Widest diagonal operator (qsa_apply_diag, diagonal plan blocks).  The
+ * paper caps marked-diagonal blocks at 6 on GPU (App. "Fusion
+ * configuration"); the streaming kernel keeps its 2^k-entry table in shared
+ * memory, so this build accepts up to 12. */
+#define QSA_MAX_DIAG 12
 
 /* Lowering of one fused dense operator (§III R4: the backend picks the
  * concrete kernel once the physical targets are known). */
@@ -96,7 +101,8 @@ typedef struct {
 typedef struct {
     int32_t planner;        /* qsa_planner */
     int32_t kmax;           /* dense fusion cap, 1..6 */
-    int32_t kmax_diag;      /* diagonal-block cap, 1..kmax */
+    int32_t kmax_diag;      /* diagonal-block cap, 1..QSA_MAX_DIAG (independent of kmax;
+                               the batch path needs kmax_diag <= kmax) */
     int32_t window;         /* DP window W (§IV-C uses 64) */
     int32_t rounds;         /* fuse pipeline repeats, 1..4 (§IV-C: at most four) */
     int32_t precision;      /* qsa_precision for k >= 5 blocks */
@@ -116,6 +122,8 @@ typedef struct {
     uint64_t launches;      /* kernel launches issued */
     double h2d_bytes;       /* host-to-device bytes copied by the call (fused matrices) */
     double tc_seconds;      /* device time of tensor-core fused-operator kernels */
+    uint64_t diag_blocks;   /* diagonal blocks run on the streaming kernel */
+    double diag_seconds;    /* device time of diagonal streaming kernels */
 } qsa_run_stats;
 
 /* A compiled circuit: the planner's blocks with their fused FP32 matrices. */
@@ -180,6 +188,15 @@ qsa_status qsa_apply_fused(qsa_state s, const int32_t* targets, int k, const dou
  * (qsa_precision).  QSA_LOWER_PERMUTE may change the layout (L' = tau o L). */
 qsa_status qsa_apply_fused_ex(qsa_state s, const int32_t* targets, int k, const double* matrix,
                               int lowering, int precision);
+
+/* Diagonal branch of Alg. 2 (Eq. cost-diag-formal: one streaming pass, no
+ * permutation): psi[y] <- diag[c] * psi[y], where bit j of c is bit L(q_j)
+ * of the physical index y; the layout is unchanged.  targets: k distinct
+ * logical qubits (host); diag: host, 2 * 2^k doubles, entry c as (Re, Im),
+ * rounded once to FP32.  Any complex entries are accepted (not only phases).
+ * Errors: QSA_E_ARG (k outside 1..QSA_MAX_DIAG or > N, bad / repeated
+ * target, NULL). */
+qsa_status qsa_apply_diag(qsa_state s, const int32_t* targets, int k, const double* diag);
 
 /* ---- circuits: fusion planning + execution (§IV-C) ------------------------- */
 

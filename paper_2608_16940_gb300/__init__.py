@@ -27,6 +27,7 @@ QSA_LOWER_AUTO, QSA_LOWER_STRIDED, QSA_LOWER_PERMUTE = 0, 1, 2
 QSA_PREC_FP32, QSA_PREC_TF32X3 = 0, 1
 QSA_PLAN_PER_GATE, QSA_PLAN_GREEDY, QSA_PLAN_DP, QSA_PLAN_DP_MLP = 0, 1, 2, 3
 QSA_OP_DIAG = 1
+QSA_MAX_K, QSA_MAX_DIAG = 6, 12
 MLP_PARAMS = 6657
 MLP_IN = 37
 
@@ -63,7 +64,8 @@ class qsa_run_stats(_c.Structure):
     _fields_ = [("seconds", _c.c_double), ("apply_seconds", _c.c_double), ("permute_seconds", _c.c_double),
                 ("hbm_bytes", _c.c_double), ("blocks", _c.c_uint64), ("passes", _c.c_uint64),
                 ("permutes", _c.c_uint64), ("tc_blocks", _c.c_uint64), ("launches", _c.c_uint64),
-                ("h2d_bytes", _c.c_double), ("tc_seconds", _c.c_double)]
+                ("h2d_bytes", _c.c_double), ("tc_seconds", _c.c_double), ("diag_blocks", _c.c_uint64),
+                ("diag_seconds", _c.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -90,6 +92,7 @@ _f = {
     "qsa_permute_bits": _sig("qsa_permute_bits", [_vp, _i32p, _i32p, _c.c_int]),
     "qsa_apply_fused": _sig("qsa_apply_fused", [_vp, _i32p, _c.c_int, _dp]),
     "qsa_apply_fused_ex": _sig("qsa_apply_fused_ex", [_vp, _i32p, _c.c_int, _dp, _c.c_int, _c.c_int]),
+    "qsa_apply_diag": _sig("qsa_apply_diag", [_vp, _i32p, _c.c_int, _dp]),
     "qsa_plan_opts_default": _sig("qsa_plan_opts_default", [_c.POINTER(qsa_plan_opts)], None),
     "qsa_plan_circuit": _sig("qsa_plan_circuit", [_c.POINTER(qsa_op), _c.c_size_t, _c.c_int,
                                                   _c.POINTER(qsa_plan_opts), _szp, _szp]),
@@ -203,6 +206,16 @@ def qsa_apply_fused_ex(s: int, targets: Sequence[int], matrix, lowering: int, pr
     m = _cmat(matrix)
     _check(_f["qsa_apply_fused_ex"](_vp(s), pt, len(t), m.view(np.float64).ctypes.data_as(_dp), lowering,
                                     precision))
+
+
+def qsa_apply_diag(s: int, targets: Sequence[int], diag) -> None:
+    """Diagonal operator on ``targets``: ``diag`` holds 2^k complex entries,
+    entry c for the target bits c (bit j = target j)."""
+    t, pt = _i32(targets)
+    d = np.ascontiguousarray(np.asarray(diag, dtype=np.complex128).reshape(-1))
+    if d.size != (1 << len(t)):
+        raise ValueError("diag must have 2^k entries")
+    _check(_f["qsa_apply_diag"](_vp(s), pt, len(t), d.view(np.float64).ctypes.data_as(_dp)))
 
 
 # ---- circuits ---------------------------------------------------------------

@@ -11,9 +11,12 @@
 //                 the whole pipeline repeated on the blocks at most `rounds`
 //                 times while the block count falls;
 //   - DP-MLP:     the same DP with Gamma(B) = the cost model's predicted
-//                 seconds for the block's width and physical target mask.
+//                 seconds for the block's width and physical target mask; a
+//                 diagonal block is one streaming pass, scored as a one-qubit
+//                 pass at its lowest physical target.
 // Block matrices are formed in FP64 in circuit order, later ops multiplied on
-// the left (§IV-C).
+// the left (§IV-C); a block of diagonal ops keeps only its diagonal (Alg. 2,
+// diagonal branch) and runs on the streaming kernel, up to QSA_MAX_DIAG wide.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -48,15 +51,17 @@ struct MlpCtx {
     std::unordered_map<uint64_t, double> cache;
 };
 
-double mlp_score(void* ctx, int width, bool, uint64_t mask) {
+double mlp_score(void* ctx, int width, bool diag, uint64_t mask) {
     auto* c = static_cast<MlpCtx*>(ctx);
-    auto it = c->cache.find(mask);
+    const uint64_t key = mask | (diag ? (1ull << 63) : 0ull);
+    auto it = c->cache.find(key);
     if (it != c->cache.end()) return it->second;
     uint64_t pm = 0;
     for (int q = 0; q < c->n; ++q)
         if ((mask >> q) & 1) pm |= 1ull << c->L[q];
-    double v = costmodel_predict_seconds(width, pm, c->n, 1);
-    c->cache[mask] = v;
+    const double v = diag ? costmodel_predict_seconds(1, pm & (~pm + 1), c->n, 1)
+                          : costmodel_predict_seconds(width, pm, c->n, 1);
+    c->cache[key] = v;
     return v;
 }
 
@@ -173,6 +178,13 @@ qsa_status validate_ops(const qsa_op* ops, size_t n_ops, int n_qubits) {
         qsa_status st = validate_targets(n_qubits, ops[i].targets, ops[i].k);
         if (st != QSA_OK) return st;
         if (!ops[i].matrix) return fail(QSA_E_ARG, "op matrix is NULL");
+        if (ops[i].flags & QSA_OP_DIAG) {
+            const size_t d = size_t(1) << ops[i].k;
+            for (size_t r = 0; r < d; ++r)
+                for (size_t c = 0; c < d; ++c)
+                    if (r != c && (ops[i].matrix[2 * (r * d + c)] != 0.0 || ops[i].matrix[2 * (r * d + c) + 1] != 0.0))
+                        return fail(QSA_E_ARG, "op flagged QSA_OP_DIAG has a nonzero off-diagonal entry");
+        }
     }
     return QSA_OK;
 }
@@ -181,7 +193,7 @@ qsa_status normalise_opts(const qsa_plan_opts* in, qsa_plan_opts* o) {
     if (in) *o = *in; else qsa_plan_opts_default(o);
     if (o->planner < 0 || o->planner > 3) return fail(QSA_E_ARG, "unknown planner");
     if (o->kmax < 1 || o->kmax > QSA_MAX_K) return fail(QSA_E_ARG, "kmax must be in 1..6");
-    if (o->kmax_diag < 1 || o->kmax_diag > o->kmax) return fail(QSA_E_ARG, "kmax_diag must be in 1..kmax");
+    if (o->kmax_diag < 1 || o->kmax_diag > QSA_MAX_DIAG) return fail(QSA_E_ARG, "kmax_diag must be in 1..12");
     if (o->window < 1) return fail(QSA_E_ARG, "window must be >= 1");
     if (o->rounds < 1 || o->rounds > 4) return fail(QSA_E_ARG, "rounds must be in 1..4");
     if (o->precision < 0 || o->precision > 1) return fail(QSA_E_ARG, "unknown precision");
@@ -260,6 +272,40 @@ qsa_status fuse_range(const qsa_op* ops, size_t s, size_t e, int32_t* tgt, int* 
     for (size_t i = 0; i < D * D; ++i) {
         (*out)[2 * i] = M[i].real();
         (*out)[2 * i + 1] = M[i].imag();
+    }
+    return QSA_OK;
+}
+
+// Diagonal of the fused block of diagonal ops ops[s..e) on the ascending union
+// of their targets: entry c is the product, in circuit order, of each op's
+// diagonal entry at the bits of c that are its targets.
+qsa_status fuse_diag_range(const qsa_op* ops, size_t s, size_t e, int32_t* tgt, int* width, std::vector<double>* out) {
+    uint64_t m = 0;
+    for (size_t i = s; i < e; ++i)
+        for (int j = 0; j < ops[i].k; ++j) m |= 1ull << ops[i].targets[j];
+    const int u = popc(m);
+    if (u > QSA_MAX_DIAG) return fail(QSA_E_ARG, "diagonal block wider than 12 qubits");
+    int t = 0;
+    for (int q = 0; q < 64; ++q)
+        if ((m >> q) & 1) tgt[t++] = q;
+    *width = u;
+    const size_t D = size_t(1) << u;
+    std::vector<std::complex<double>> d(D, 1.0);
+    for (size_t i = s; i < e; ++i) {
+        const qsa_op& op = ops[i];
+        int pos[QSA_MAX_K];
+        for (int j = 0; j < op.k; ++j) pos[j] = static_cast<int>(std::find(tgt, tgt + u, op.targets[j]) - tgt);
+        const size_t dk = size_t(1) << op.k;
+        for (size_t c = 0; c < D; ++c) {
+            size_t gi = 0;
+            for (int j = 0; j < op.k; ++j) gi |= ((c >> pos[j]) & 1) << j;
+            d[c] = std::complex<double>(op.matrix[2 * (gi * dk + gi)], op.matrix[2 * (gi * dk + gi) + 1]) * d[c];
+        }
+    }
+    out->resize(2 * D);
+    for (size_t c = 0; c < D; ++c) {
+        (*out)[2 * c] = d[c].real();
+        (*out)[2 * c + 1] = d[c].imag();
     }
     return QSA_OK;
 }
@@ -344,7 +390,16 @@ qsa_status qsa_plan_create(const qsa_op* ops, size_t n_ops, int n_qubits, const 
         PlanBlock& b = p->blocks[i];
         b.off = p->host_mat.size();
         b.first_op = u.s;
-        if (u.e - u.s == 1) {
+        if (u.diag) {
+            b.diag = true;
+            st = fuse_diag_range(ops, u.s, u.e, b.t, &b.k, &M);
+            if (st != QSA_OK) {
+                delete p;
+                return st;
+            }
+            p->host_mat.resize(b.off + M.size());
+            for (size_t j = 0; j < M.size(); ++j) p->host_mat[b.off + j] = static_cast<float>(M[j]);
+        } else if (u.e - u.s == 1) {
             const qsa_op& op = ops[u.s];
             b.k = op.k;
             for (int j = 0; j < op.k; ++j) b.t[j] = op.targets[j];
@@ -427,7 +482,8 @@ qsa_status qsa_plan_execute(qsa_state s, qsa_plan p, qsa_run_stats* stats) {
     s->timing = p->opts.timing != 0;
     for (size_t i = 0; i < p->blocks.size(); ++i) {
         const PlanBlock& b = p->blocks[i];
-        st = apply_logical(s, b.t, b.k, p->d_mat + b.off, p->opts.lowering, p->opts.precision, rs);
+        st = b.diag ? apply_diag_logical(s, b.t, b.k, p->d_mat + b.off, rs)
+                    : apply_logical(s, b.t, b.k, p->d_mat + b.off, p->opts.lowering, p->opts.precision, rs);
         if (st != QSA_OK) {
             s->timing = false;
             return st;
@@ -542,6 +598,7 @@ qsa_status qsa_batch_create(int n_qubits, int n_traj, const qsa_op* ops, const s
     qsa_status st = normalise_opts(opts, &o);
     if (st != QSA_OK) return st;
     if (o.kmax > 4) return fail(QSA_E_ARG, "batched trajectories fuse blocks of at most 4 qubits (kmax <= 4)");
+    if (o.kmax_diag > o.kmax) return fail(QSA_E_ARG, "batched trajectories need kmax_diag <= kmax");
     if (op_offsets[0] != 0) return fail(QSA_E_ARG, "op_offsets[0] must be 0");
     for (int t = 0; t < n_traj; ++t)
         if (op_offsets[t + 1] < op_offsets[t]) return fail(QSA_E_ARG, "op_offsets must be non-decreasing");

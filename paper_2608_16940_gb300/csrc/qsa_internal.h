@@ -74,6 +74,10 @@ cudaError_t launch_apply_fp32(float2* psi, int n, const int* phys, int k, const 
 // gives up.  Returns cudaErrorNotSupported for other k.
 cudaError_t launch_apply_tc(float2* psi, int n, const int* phys, int k, const float* d_mat, int* d_err,
                             cudaStream_t st, uint64_t* launches);
+// Diagonal streaming update (k <= QSA_MAX_DIAG): psi[y] *= d_tab[c(y)], bit j
+// of c = bit phys[j] of y; d_tab is 2^k interleaved FP32 complex numbers.
+cudaError_t launch_apply_diag(float2* psi, int n, const int* phys, int k, const float* d_tab, cudaStream_t st,
+                              uint64_t* launches);
 
 // In-place swap of physical bit pairs (pa[i] <-> pb[i]), all positions distinct.
 cudaError_t launch_permute(float2* psi, int n, const int* pa, const int* pb, int npairs, cudaStream_t st,

@@ -39,9 +39,10 @@ struct qsa_state_s {
 };
 
 struct PlanBlock {
-    int32_t t[QSA_MAX_K];   // ordered logical targets of the fused block
+    int32_t t[QSA_MAX_DIAG];   // ordered logical targets of the fused block
     int k = 0;
-    size_t off = 0;         // float offset of its matrix in host_mat / d_mat
+    bool diag = false;         // diagonal mode: 2^k entries, streaming kernel
+    size_t off = 0;            // float offset of its matrix / diagonal in host_mat / d_mat
     size_t first_op = 0;
 };
 
@@ -68,12 +69,14 @@ qsa_status check_state(qsa_state s);
 qsa_status sync_and_check(qsa_state s, const char* where);
 qsa_status ensure_dev(qsa_state s, void** ptr, size_t* cap, size_t bytes);
 void to_float_matrix(const double* m, int k, float* out);
-qsa_status validate_targets(int n, const int32_t* targets, int k);
+qsa_status validate_targets(int n, const int32_t* targets, int k, int kmax = QSA_MAX_K);
 qsa_status apply_logical(qsa_state s, const int32_t* targets, int k, const float* d_mat, int lowering,
                          int precision, qsa_run_stats* rs);
 qsa_status apply_physical(qsa_state s, const int* phys, int k, const float* d_mat, int precision,
                           qsa_run_stats* rs);
 qsa_status permute_positions(qsa_state s, const int* pa, const int* pb, int np, qsa_run_stats* rs);
+// Diagonal block on logical targets (the layout resolves them; it is not changed).
+qsa_status apply_diag_logical(qsa_state s, const int32_t* targets, int k, const float* d_tab, qsa_run_stats* rs);
 bool tc_available(qsa_state s, int k);
 
 // Records a pair of CUDA events around the launches issued during its

@@ -79,9 +79,9 @@ void to_float_matrix(const double* m, int k, float* out) {
     for (size_t i = 0; i < cnt; ++i) out[i] = static_cast<float>(m[i]);
 }
 
-qsa_status validate_targets(int n, const int32_t* targets, int k) {
+qsa_status validate_targets(int n, const int32_t* targets, int k, int kmax) {
     if (!targets) return fail(QSA_E_ARG, "targets is NULL");
-    if (k < 1 || k > QSA_MAX_K) return fail(QSA_E_ARG, "k must be in 1..6");
+    if (k < 1 || k > kmax) return fail(QSA_E_ARG, "k must be in 1.." + std::to_string(kmax));
     if (k > n) return fail(QSA_E_ARG, "k exceeds the number of qubits");
     uint64_t seen = 0;
     for (int j = 0; j < k; ++j) {
@@ -171,6 +171,26 @@ qsa_status apply_logical(qsa_state s, const int32_t* targets, int k, const float
         if (st != QSA_OK) return st;
     }
     return apply_physical(s, phys, k, d_mat, precision, rs);
+}
+
+qsa_status apply_diag_logical(qsa_state s, const int32_t* targets, int k, const float* d_tab, qsa_run_stats* rs) {
+    int phys[QSA_MAX_DIAG];
+    for (int j = 0; j < k; ++j) phys[j] = s->L[targets[j]];
+    cudaError_t e;
+    {
+        Timer tm(s, rs ? &rs->diag_seconds : nullptr);
+        e = launch_apply_diag(s->psi, s->n, phys, k, d_tab, s->stream, &s->launches);
+        tm.stop();
+    }
+    if (e != cudaSuccess) return cuda_fail(s, e, "diagonal kernel");
+    s->known_zero = false;
+    if (rs) {
+        rs->blocks += 1;
+        rs->passes += 1;
+        rs->diag_blocks += 1;
+        rs->hbm_bytes += 16.0 * static_cast<double>(1ull << s->n);
+    }
+    return QSA_OK;
 }
 
 // ---- timers ------------------------------------------------------------------
@@ -419,6 +439,23 @@ qsa_status qsa_apply_fused_ex(qsa_state s, const int32_t* targets, int k, const 
 
 qsa_status qsa_apply_fused(qsa_state s, const int32_t* targets, int k, const double* matrix) {
     return qsa_apply_fused_ex(s, targets, k, matrix, QSA_LOWER_AUTO, QSA_PREC_FP32);
+}
+
+qsa_status qsa_apply_diag(qsa_state s, const int32_t* targets, int k, const double* diag) {
+    qsa_status st = check_state(s);
+    if (st != QSA_OK) return st;
+    st = validate_targets(s->n, targets, k, QSA_MAX_DIAG);
+    if (st != QSA_OK) return st;
+    if (!diag) return fail(QSA_E_ARG, "diag is NULL");
+    const size_t cnt = 2ull << k;
+    std::vector<float> hd(cnt);
+    for (size_t i = 0; i < cnt; ++i) hd[i] = static_cast<float>(diag[i]);
+    st = ensure_dev(s, reinterpret_cast<void**>(&s->d_mat), &s->mat_cap, cnt * sizeof(float));
+    if (st != QSA_OK) return st;
+    // pageable source: the copy is staged before the call returns
+    cudaError_t e = cudaMemcpyAsync(s->d_mat, hd.data(), cnt * sizeof(float), cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "diagonal upload");
+    return apply_diag_logical(s, targets, k, s->d_mat, nullptr);
 }
 
 qsa_status qsa_expectation_z(qsa_state s, uint64_t logical_mask, double* out) {

@@ -63,6 +63,31 @@ def test_dp_planner_matches_oracle_pipeline(q, seed, n, n_ops, kmax, kdiag, wind
     assert got == ref
 
 
+@pytest.mark.parametrize("seed,n,n_ops,kmax,kdiag", [(10, 12, 300, 2, 8), (11, 14, 400, 4, 12), (12, 10, 250, 3, 6),
+                                                    (13, 16, 500, 6, 10)])
+def test_dp_planner_with_wide_diagonal_cap_matches_oracle(q, seed, n, n_ops, kmax, kdiag):
+    """Diagonal blocks wider than the dense cap (kmax_diag > kmax): the DP and
+    merge pipeline agree with the oracle's."""
+    rng = np.random.default_rng(seed)
+    ops = _random_circuit(rng, n, n_ops, kmax_in=min(3, kmax), diag_frac=0.6)
+    for o in ops:
+        if o.diag:
+            o.matrix = np.diag(np.exp(1j * rng.uniform(0, 6.3, size=1 << len(o.targets))))
+    got = q.qsa_plan_circuit(ops, n, q.make_opts(planner=q.QSA_PLAN_DP, kmax=kmax, kmax_diag=kdiag))
+    ref = oracle.fuse_pipeline(ops, kmax, kdiag, 64, 4)
+    assert got == ref
+
+
+def test_diagonal_options_and_flags_are_validated(q):
+    ops = [W.Op((0, 1), W.CZ.copy(), True)]
+    with pytest.raises(q.QsaError):
+        q.qsa_plan_circuit(ops, 4, q.make_opts(kmax=4, kmax_diag=13))
+    assert q.qsa_plan_circuit(ops, 4, q.make_opts(kmax=2, kmax_diag=12)) == [0]
+    bad = [W.Op((0, 1), W.CNOT.copy(), True)]   # flagged diagonal but not diagonal
+    with pytest.raises(q.QsaError):
+        q.qsa_plan_circuit(bad, 4, q.make_opts())
+
+
 @pytest.mark.parametrize("kmax", [1, 2, 3, 4, 6])
 def test_greedy_and_per_gate_planners_match_oracle(q, kmax):
     rng = np.random.default_rng(kmax)
