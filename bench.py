@@ -40,9 +40,10 @@ UNIT = "amp-updates/s"
 
 # DRAM bytes (read + write) per amplitude of one launch, from single ncu captures
 # at N=28 (profiles/k_apply_tc6_n28.md: 4.241 GB; profiles/k_apply_fp32_k4_n28.md:
-# 4.234 GB; each / 2^28).  Traffic scales with the state size, so a launch at N
+# 4.234 GB; profiles/k_apply_diag_n28.md: 4.234 GB; each / 2^28).  Traffic scales with the state size, so a launch at N
 # moves this many bytes times 2^N.
-DRAM_BYTES_PER_AMP = {"k_apply_tc": 4.241e9 / 2**28, "k_apply_fp32": 4.234e9 / 2**28}
+DRAM_BYTES_PER_AMP = {"k_apply_tc": 4.241e9 / 2**28, "k_apply_fp32": 4.234e9 / 2**28,
+                      "k_apply_diag": 4.234e9 / 2**28}
 
 
 def _peaks():

@@ -11,7 +11,9 @@ invariants that hold at any size.
   per-gate path at sampled amplitudes;
 - N = 32 / 33 wide workload (k = 5, 6 on the tensor cores): ops then their
   inverse return to |0...0>; N = 33 exercises indices beyond 2^32.
-- the N = 20, 200-op instance of the wide workload against the FP64 oracle.
+- the N = 20, 200-op instance of the wide workload against the FP64 oracle;
+- N = 33 diagonal streaming update across the 2^32 index boundary: closed
+  form at the populated amplitudes and return under the conjugate table.
 """
 import numpy as np
 import pytest
@@ -129,5 +131,31 @@ def test_wide_200_ops_fidelity_vs_oracle(q, prec, capsys):
         with capsys.disabled():
             print(f"\nwide 200 ops N=20 precision={'3xTF32' if prec else 'FP32'}: 1-F = {infid:.3e}, "
                   f"max|d| = {err:.3e}")
+    finally:
+        st.close()
+
+
+def test_diag33_beyond_2_32_closed_form_and_inverse(q):
+    """N = 33: H on qubits 0 and 32, then a 12-qubit diagonal that includes
+    qubit 32 (index bit beyond 2^32) and bits 0, 11, 12, 23, 24: the four
+    populated amplitudes are d[c] / 2 at their target bits; the conjugate
+    table returns the state."""
+    n = 33
+    st = Big(q, n)
+    rng = np.random.default_rng(33)
+    try:
+        for qb in (0, 32):
+            q.qsa_apply_fused(st.h, [qb], W.H)
+        t = [32, 0, 11, 12, 23, 24, 5, 17, 29, 30, 2, 8]
+        d = np.exp(1j * rng.uniform(0, 2 * np.pi, size=1 << len(t)))
+        q.qsa_apply_diag(st.h, t, d)
+        idx = np.array([0, 1, 1 << 32, (1 << 32) | 1], dtype=np.int64)
+        c = np.array([sum(((int(x) >> tq) & 1) << j for j, tq in enumerate(t)) for x in idx])
+        got = st.amps(idx)
+        assert np.max(np.abs(got - 0.5 * d[c])) < 1e-6
+        q.qsa_apply_diag(st.h, t, np.conj(d))
+        got = st.amps(idx)
+        assert np.max(np.abs(got - 0.5)) < 1e-6
+        assert abs(q.qsa_expectation_z(st.h, 0) - 1) < 1e-5
     finally:
         st.close()
