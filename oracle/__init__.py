@@ -17,6 +17,8 @@ Contents
     the left"),
   - the fusion partition dynamic program (§IV-C, Eq. dp-recurrence) and the
     plain width-limit greedy partition,
+  - the replay of on-demand promotions under first-free and farthest-next-use
+    victim choice (§IV-D, Corollary "ideal minimal demand-promotion count"),
   - the cost-model network (37 -> 64 -> 64 -> 1, ReLU, MSE on log-seconds)
     forward, backward and one Adam step (Kingma & Ba 2015, Algorithm 1),
   - fidelity metrics.
@@ -434,6 +436,57 @@ def lazy_ttgt(stored: np.ndarray, phys_of_logical: Sequence[int], targets: Seque
     Mp = np.asarray(mat, dtype=np.complex128) @ M
     Lp = [alpha[phys_of_logical[q]] for q in range(n)]
     return Lp, Mp.reshape(-1).copy()
+
+
+def promotion_replay(tuples: Sequence[Sequence[int]], n: int, frames: int, policy: str,
+                     layout: Sequence[int] | None = None, history: bool = False):
+    """Replay of on-demand promotions over a fused stream (§IV-D, Corollary
+    "ideal minimal demand-promotion count"): the ``frames`` lowest physical
+    positions are page frames, logical qubits are pages.  Before tuple i, each
+    of its targets (in tuple order) that is not in a frame is promoted by
+    swapping its position with a victim frame that holds no target of tuple i
+    (and was not filled for it already).  ``policy``: ``"first_free"`` takes
+    the lowest such frame (the CPU-MPI rule); ``"farthest"`` takes the frame
+    whose qubit is next targeted farthest in the future (never = infinity),
+    ties to the lowest frame (Belady).  Returns (promotions per tuple, final
+    layout phys_of_logical), plus the layout each tuple ran under when
+    ``history``."""
+    L = list(range(n)) if layout is None else [int(v) for v in layout]
+    inv = [0] * n
+    for q, p in enumerate(L):
+        inv[p] = q
+    counts, hist = [], []
+    for i, tup in enumerate(tuples):
+        pinned = {L[q] for q in tup if L[q] < frames}
+        c = 0
+        for q in tup:
+            if L[q] < frames:
+                continue
+            cand = [p for p in range(frames) if p not in pinned]
+            if not cand:
+                raise ValueError("tuple wider than the frames")
+            if policy == "first_free":
+                v = cand[0]
+            elif policy == "farthest":
+                def next_use(p):
+                    qq = inv[p]
+                    for j in range(i + 1, len(tuples)):
+                        if qq in tuples[j]:
+                            return j
+                    return float("inf")
+                best = max(next_use(p) for p in cand)
+                v = min(p for p in cand if next_use(p) == best)
+            else:
+                raise ValueError(policy)
+            hp, qv = L[q], inv[v]
+            L[q], L[qv] = v, hp
+            inv[v], inv[hp] = q, qv
+            pinned.add(v)
+            c += 1
+        counts.append(c)
+        if history:
+            hist.append(list(L))
+    return (counts, L, hist) if history else (counts, L)
 
 
 def merge_adjacent(blocks, kmax: int, kmax_diag: int, score=None):
