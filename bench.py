@@ -185,6 +185,8 @@ def main():
     ap.add_argument("--kmax-diag", type=int, default=12, help="diagonal-block cap (1..12)")
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3"])
     ap.add_argument("--lowering", default="auto", choices=["auto", "strided", "permute"])
+    ap.add_argument("--victim", default="first_free", choices=["first_free", "farthest"],
+                    help="eviction rule of --lowering permute promotions")
     ap.add_argument("--cm-samples", type=int, default=240)
     ap.add_argument("--ref-qubits", type=int, default=28)
     ap.add_argument("--cpu-qubits", type=int, default=28)
@@ -213,7 +215,9 @@ def main():
     prec = {"fp32": 0, "tf32x3": 1}[args.precision]
     low = {"auto": 0, "strided": 1, "permute": 2}[args.lowering]
     kdiag = args.kmax_diag
-    opts = q.make_opts(planner=planner, kmax=args.kmax, kmax_diag=kdiag, precision=prec, lowering=low, timing=1)
+    victim = {"first_free": 0, "farthest": 1}[args.victim]
+    opts = q.make_opts(planner=planner, kmax=args.kmax, kmax_diag=kdiag, precision=prec, lowering=low, timing=1,
+                       victim=victim)
 
     buf = torch.empty(1 << n, dtype=torch.complex64, device=dev)
     stream = torch.cuda.current_stream(dev).cuda_stream
@@ -302,7 +306,7 @@ def main():
             t0 = time.perf_counter()
             q.qsa_state_reset(s)
             st = q.qsa_apply_circuit(s, ops, q.make_opts(planner=planner, kmax=args.kmax, kmax_diag=kdiag,
-                                                          precision=prec, lowering=low))
+                                                          precision=prec, lowering=low, victim=victim))
             vals, cnts = q.qsa_sample_counts(s, args.shots, seed=args.seed + 17)
             torch.cuda.synchronize()
             e2e_times.append(time.perf_counter() - t0)
@@ -350,7 +354,7 @@ def main():
                                        f"per step",
                            "planner": args.planner, "kmax": args.kmax, "kmax_diag": kdiag,
                            "precision": args.precision,
-                           "lowering": args.lowering, "fused_blocks": pinfo["blocks"],
+                           "lowering": args.lowering, "victim": args.victim, "fused_blocks": pinfo["blocks"],
                            "l2": "state 8 GiB > 129 MB L2; no flush needed", "parallelism": f"replicas x{ws}"},
                 "gpu_launches": launches, "clocks": clocks, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "passes_per_step": (agg["blocks"] + agg["permutes"]) / args.steps,

@@ -98,6 +98,15 @@ typedef struct {
     uint32_t flags;         /* QSA_OP_DIAG or 0 */
 } qsa_op;
 
+/* Which in-block position a promotion evicts (§IV-D).  The frames are the
+ * min(11, N) lowest physical positions (the in-block bits of the tile). */
+typedef enum {
+    QSA_VICTIM_FIRST_FREE = 0,  /* lowest position not holding a target of the block (the CPU-MPI rule) */
+    QSA_VICTIM_FARTHEST = 1     /* position whose qubit a later dense block of the plan targets farthest
+                                   in the future (never = infinity), ties to the lowest; Corollary
+                                   "ideal minimal demand-promotion count" (Belady) */
+} qsa_victim;
+
 typedef struct {
     int32_t planner;        /* qsa_planner */
     int32_t kmax;           /* dense fusion cap, 1..6 */
@@ -108,6 +117,7 @@ typedef struct {
     int32_t precision;      /* qsa_precision for k >= 5 blocks */
     int32_t lowering;       /* qsa_lowering */
     int32_t timing;         /* 1: time every launch with CUDA events (fills *_seconds) */
+    int32_t victim;         /* qsa_victim: eviction rule of QSA_LOWER_PERMUTE promotions */
 } qsa_plan_opts;
 
 typedef struct {
@@ -238,6 +248,18 @@ qsa_status qsa_plan_info(qsa_plan p, size_t* n_blocks, size_t* n_ops, int* max_w
 
 /* First input op and width of every block (capacity >= n_blocks, else QSA_E_RANGE). */
 qsa_status qsa_plan_blocks(qsa_plan p, size_t* first_op, int32_t* widths, size_t capacity);
+
+/* Host-only replay of the promotions QSA_LOWER_PERMUTE makes for this plan
+ * (§IV-D demand model; no data moves): starting from layout_in (host,
+ * phys_of_logical, NULL = identity), each dense block's targets outside the
+ * frames are promoted in target order, evicting per `victim` (qsa_victim);
+ * diagonal blocks need no promotion.  *promotions = swapped position pairs,
+ * *passes = blocks that promoted (one permutation pass each); layout_out
+ * (host, N entries, nullable) receives the final layout.  Execution of the
+ * plan with QSA_LOWER_PERMUTE and the same victim rule makes exactly these
+ * promotions.  Errors: QSA_E_ARG (NULL plan, layout not a bijection, victim). */
+qsa_status qsa_plan_promotions(qsa_plan p, const int32_t* layout_in, int victim, uint64_t* promotions,
+                               uint64_t* passes, int32_t* layout_out);
 
 /* Apply the plan's blocks to s in order (asynchronous unless opts.timing).
  * The first execution on a device uploads the fused matrices once

@@ -28,6 +28,7 @@ QSA_PREC_FP32, QSA_PREC_TF32X3 = 0, 1
 QSA_PLAN_PER_GATE, QSA_PLAN_GREEDY, QSA_PLAN_DP, QSA_PLAN_DP_MLP = 0, 1, 2, 3
 QSA_OP_DIAG = 1
 QSA_MAX_K, QSA_MAX_DIAG = 6, 12
+QSA_VICTIM_FIRST_FREE, QSA_VICTIM_FARTHEST = 0, 1
 MLP_PARAMS = 6657
 MLP_IN = 37
 
@@ -57,7 +58,7 @@ class qsa_op(_c.Structure):
 class qsa_plan_opts(_c.Structure):
     _fields_ = [("planner", _c.c_int32), ("kmax", _c.c_int32), ("kmax_diag", _c.c_int32), ("window", _c.c_int32),
                 ("rounds", _c.c_int32), ("precision", _c.c_int32), ("lowering", _c.c_int32),
-                ("timing", _c.c_int32)]
+                ("timing", _c.c_int32), ("victim", _c.c_int32)]
 
 
 class qsa_run_stats(_c.Structure):
@@ -103,6 +104,8 @@ _f = {
                                                 _c.POINTER(qsa_plan_opts), _i32p, _c.POINTER(_vp)]),
     "qsa_plan_info": _sig("qsa_plan_info", [_vp, _szp, _szp, _c.POINTER(_c.c_int), _szp]),
     "qsa_plan_blocks": _sig("qsa_plan_blocks", [_vp, _szp, _i32p, _c.c_size_t]),
+    "qsa_plan_promotions": _sig("qsa_plan_promotions", [_vp, _i32p, _c.c_int, _c.POINTER(_c.c_uint64),
+                                                         _c.POINTER(_c.c_uint64), _i32p]),
     "qsa_plan_execute": _sig("qsa_plan_execute", [_vp, _vp, _c.POINTER(qsa_run_stats)]),
     "qsa_plan_destroy": _sig("qsa_plan_destroy", [_vp]),
     "qsa_state_counters": _sig("qsa_state_counters", [_vp, _u64p]),
@@ -300,6 +303,18 @@ def qsa_plan_blocks(p: int) -> Tuple[List[int], List[int]]:
     w = np.zeros(max(1, nb), dtype=np.int32)
     _check(_f["qsa_plan_blocks"](_vp(p), fo, w.ctypes.data_as(_i32p), nb))
     return [int(fo[i]) for i in range(nb)], [int(v) for v in w[:nb]]
+
+
+def qsa_plan_promotions(p: int, n_qubits: int, victim: int, layout=None) -> Tuple[int, int, List[int]]:
+    """Host replay of the plan's QSA_LOWER_PERMUTE promotions: (promoted
+    position pairs, permutation passes, final layout)."""
+    lay = None
+    if layout is not None:
+        la, lay = _i32(layout)
+    pr, ps = _c.c_uint64(), _c.c_uint64()
+    out = np.zeros(n_qubits, dtype=np.int32)
+    _check(_f["qsa_plan_promotions"](_vp(p), lay, victim, _c.byref(pr), _c.byref(ps), out.ctypes.data_as(_i32p)))
+    return int(pr.value), int(ps.value), [int(v) for v in out]
 
 
 def qsa_plan_execute(s: int, p: int) -> dict:

@@ -198,7 +198,23 @@ qsa_status normalise_opts(const qsa_plan_opts* in, qsa_plan_opts* o) {
     if (o->rounds < 1 || o->rounds > 4) return fail(QSA_E_ARG, "rounds must be in 1..4");
     if (o->precision < 0 || o->precision > 1) return fail(QSA_E_ARG, "unknown precision");
     if (o->lowering < 0 || o->lowering > 2) return fail(QSA_E_ARG, "unknown lowering");
+    if (o->victim < 0 || o->victim > 1) return fail(QSA_E_ARG, "unknown victim rule");
     return QSA_OK;
+}
+
+// next_use[i * n + q]: index of the first dense block after block i that
+// targets logical qubit q (INT32_MAX for none).
+void build_next_use(qsa_plan_s* p) {
+    const size_t B = p->blocks.size();
+    const int n = p->n;
+    p->next_use.assign(B * n, INT32_MAX);
+    std::vector<int32_t> cur(n, INT32_MAX);
+    for (size_t i = B; i-- > 0;) {
+        std::copy(cur.begin(), cur.end(), p->next_use.begin() + i * n);
+        const PlanBlock& b = p->blocks[i];
+        if (!b.diag)
+            for (int j = 0; j < b.k; ++j) cur[b.t[j]] = static_cast<int32_t>(i);
+    }
 }
 
 std::vector<Unit> plan(const qsa_op* ops, size_t n_ops, int n_qubits, const qsa_plan_opts& o, const int32_t* L) {
@@ -328,6 +344,7 @@ void qsa_plan_opts_default(qsa_plan_opts* o) {
     o->precision = QSA_PREC_FP32;
     o->lowering = QSA_LOWER_AUTO;
     o->timing = 0;
+    o->victim = QSA_VICTIM_FIRST_FREE;
 }
 
 qsa_status qsa_plan_circuit(const qsa_op* ops, size_t n_ops, int n_qubits, const qsa_plan_opts* opts,
@@ -418,7 +435,48 @@ qsa_status qsa_plan_create(const qsa_op* ops, size_t n_ops, int n_qubits, const 
         p->max_width = std::max(p->max_width, b.k);
         while (p->host_mat.size() % 4) p->host_mat.push_back(0.f);  // 16-byte aligned matrices
     }
+    build_next_use(p);
     *out = p;
+    return QSA_OK;
+}
+
+qsa_status qsa_plan_promotions(qsa_plan p, const int32_t* layout_in, int victim, uint64_t* promotions,
+                               uint64_t* passes, int32_t* layout_out) {
+    if (!p) return fail(QSA_E_ARG, "plan is NULL");
+    if (victim < 0 || victim > 1) return fail(QSA_E_ARG, "unknown victim rule");
+    const int n = p->n;
+    int32_t L[QSA_MAX_QUBITS];
+    uint64_t seen = 0;
+    for (int q = 0; q < n; ++q) {
+        L[q] = layout_in ? layout_in[q] : q;
+        if (L[q] < 0 || L[q] >= n || ((seen >> L[q]) & 1)) return fail(QSA_E_ARG, "layout is not a bijection");
+        seen |= 1ull << L[q];
+    }
+    const int frames = std::min(kInBlockBits, n);
+    uint64_t pr = 0, ps = 0;
+    for (size_t i = 0; i < p->blocks.size(); ++i) {
+        const PlanBlock& b = p->blocks[i];
+        if (b.diag) continue;
+        int phys[QSA_MAX_K], pa[QSA_MAX_K], pb[QSA_MAX_K];
+        for (int j = 0; j < b.k; ++j) phys[j] = L[b.t[j]];
+        const int np = choose_promotions(L, n, phys, b.k, frames, victim, p->next_use.data() + i * n, pa, pb);
+        if (np < 0) return fail(QSA_E_ARG, "block wider than the in-block frames");
+        // swap the logical qubits at each position pair, in order
+        for (int m = 0; m < np; ++m) {
+            int qa = -1, qb = -1;
+            for (int q = 0; q < n; ++q) {
+                if (L[q] == pa[m]) qa = q;
+                if (L[q] == pb[m]) qb = q;
+            }
+            L[qa] = pb[m];
+            L[qb] = pa[m];
+        }
+        pr += static_cast<uint64_t>(np);
+        ps += np > 0 ? 1 : 0;
+    }
+    if (promotions) *promotions = pr;
+    if (passes) *passes = ps;
+    if (layout_out) std::memcpy(layout_out, L, sizeof(int32_t) * n);
     return QSA_OK;
 }
 
@@ -482,8 +540,20 @@ qsa_status qsa_plan_execute(qsa_state s, qsa_plan p, qsa_run_stats* stats) {
     s->timing = p->opts.timing != 0;
     for (size_t i = 0; i < p->blocks.size(); ++i) {
         const PlanBlock& b = p->blocks[i];
-        st = b.diag ? apply_diag_logical(s, b.t, b.k, p->d_mat + b.off, rs)
-                    : apply_logical(s, b.t, b.k, p->d_mat + b.off, p->opts.lowering, p->opts.precision, rs);
+        if (b.diag) {
+            st = apply_diag_logical(s, b.t, b.k, p->d_mat + b.off, rs);
+        } else if (p->opts.lowering == QSA_LOWER_PERMUTE) {
+            // promote the targets into the in-block frames, victims per the plan's rule
+            int phys[QSA_MAX_K], pa[QSA_MAX_K], pb[QSA_MAX_K];
+            for (int j = 0; j < b.k; ++j) phys[j] = s->L[b.t[j]];
+            const int np = choose_promotions(s->L, s->n, phys, b.k, std::min(kInBlockBits, s->n), p->opts.victim,
+                                             p->next_use.data() + i * s->n, pa, pb);
+            st = np < 0 ? fail(QSA_E_ARG, "block wider than the in-block frames")
+                        : permute_positions(s, pa, pb, np, rs);
+            if (st == QSA_OK) st = apply_physical(s, phys, b.k, p->d_mat + b.off, p->opts.precision, rs);
+        } else {
+            st = apply_logical(s, b.t, b.k, p->d_mat + b.off, p->opts.lowering, p->opts.precision, rs);
+        }
         if (st != QSA_OK) {
             s->timing = false;
             return st;

@@ -54,6 +54,7 @@ struct qsa_plan_s {
     std::vector<PlanBlock> blocks;
     std::vector<float> host_mat;   // all fused matrices, FP32, 16-byte aligned
     float* d_mat = nullptr;        // device copy (uploaded on first execution)
+    std::vector<int32_t> next_use; // per block, per logical qubit: next dense block targeting it
     int dev = -1;
 };
 
@@ -75,6 +76,15 @@ qsa_status apply_logical(qsa_state s, const int32_t* targets, int k, const float
 qsa_status apply_physical(qsa_state s, const int* phys, int k, const float* d_mat, int precision,
                           qsa_run_stats* rs);
 qsa_status permute_positions(qsa_state s, const int* pa, const int* pb, int np, qsa_run_stats* rs);
+// Victims for the targets of one dense block under the demand model (§IV-D):
+// phys[j] (positions of the block's targets) are updated in place and the
+// position pairs to swap written to (pa[i], pb[i]); returns their count, or -1
+// if the frames (positions 0..frames-1) cannot hold the block.  next_use[q]
+// (per logical qubit; QSA_VICTIM_FARTHEST only) is the index of the next dense
+// block targeting q, INT32_MAX for never.  L is not modified.
+int choose_promotions(const int32_t* L, int n, int* phys, int k, int frames, int victim, const int32_t* next_use,
+                      int* pa, int* pb);
+qsa_status promote_targets(qsa_state s, int* phys, int k, int inblock, qsa_run_stats* rs);
 // Diagonal block on logical targets (the layout resolves them; it is not changed).
 qsa_status apply_diag_logical(qsa_state s, const int32_t* targets, int k, const float* d_tab, qsa_run_stats* rs);
 bool tc_available(qsa_state s, int k);

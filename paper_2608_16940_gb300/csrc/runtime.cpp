@@ -119,23 +119,48 @@ qsa_status permute_positions(qsa_state s, const int* pa, const int* pb, int np, 
 // Promote targets outside the in-block bits (positions >= inblock) to the
 // lowest free in-block positions (first-free victim choice, §IV-D), updating
 // phys[] to the new positions.
-qsa_status promote_targets(qsa_state s, int* phys, int k, int inblock, qsa_run_stats* rs) {
-    inblock = std::min(inblock, s->n);
-    int pa[6], pb[6], np = 0;
+int choose_promotions(const int32_t* L, int n, int* phys, int k, int frames, int victim, const int32_t* next_use,
+                      int* pa, int* pb) {
+    int inv[QSA_MAX_QUBITS];
+    for (int q = 0; q < n; ++q) inv[L[q]] = q;
     uint64_t pinned = 0;
     for (int j = 0; j < k; ++j)
-        if (phys[j] < inblock) pinned |= 1ull << phys[j];
-    int next = 0;
+        if (phys[j] < frames) pinned |= 1ull << phys[j];
+    int np = 0;
     for (int j = 0; j < k; ++j) {
-        if (phys[j] < inblock) continue;
-        while (next < inblock && ((pinned >> next) & 1)) ++next;
-        if (next >= inblock) return fail(QSA_E_ARG, "not enough free in-block positions");
-        pa[np] = phys[j];
-        pb[np] = next;
-        pinned |= 1ull << next;
-        phys[j] = next;
+        if (phys[j] < frames) continue;
+        int v = -1;
+        int64_t best = -1;
+        for (int f = 0; f < frames; ++f) {
+            if ((pinned >> f) & 1) continue;
+            if (victim != QSA_VICTIM_FARTHEST) {
+                v = f;
+                break;
+            }
+            const int64_t key = next_use[inv[f]];
+            if (key > best) {   // strict: ties keep the lowest frame
+                best = key;
+                v = f;
+            }
+        }
+        if (v < 0) return -1;
+        const int hp = phys[j], qv = inv[v], qt = inv[hp];
+        pa[np] = hp;
+        pb[np] = v;
         ++np;
+        inv[v] = qt;
+        inv[hp] = qv;
+        pinned |= 1ull << v;
+        phys[j] = v;
     }
+    return np;
+}
+
+qsa_status promote_targets(qsa_state s, int* phys, int k, int inblock, qsa_run_stats* rs) {
+    int pa[QSA_MAX_K], pb[QSA_MAX_K];
+    const int np = choose_promotions(s->L, s->n, phys, k, std::min(inblock, s->n), QSA_VICTIM_FIRST_FREE, nullptr,
+                                     pa, pb);
+    if (np < 0) return fail(QSA_E_ARG, "not enough free in-block positions");
     return permute_positions(s, pa, pb, np, rs);
 }
 

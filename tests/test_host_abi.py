@@ -88,6 +88,41 @@ def test_diagonal_options_and_flags_are_validated(q):
         q.qsa_plan_circuit(bad, 4, q.make_opts())
 
 
+def _dense_tuples(q, plan, ops):
+    """The plan's dense blocks as target tuples in the order the library
+    promotes them: a single op keeps its own order, a fused block its
+    ascending union; all-diagonal blocks need no promotion."""
+    first, _ = q.qsa_plan_blocks(plan)
+    bounds = first + [len(ops)]
+    out = []
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        blk = ops[a:b]
+        if all(o.diag for o in blk):
+            continue
+        out.append(list(blk[0].targets) if len(blk) == 1 else sorted({t for o in blk for t in o.targets}))
+    return out
+
+
+@pytest.mark.parametrize("seed,n,kmax,kdiag", [(0, 14, 3, 3), (1, 16, 4, 10), (2, 20, 6, 6), (3, 12, 2, 12)])
+def test_promotion_replay_matches_oracle(q, seed, n, kmax, kdiag):
+    """qsa_plan_promotions (host) equals the oracle's replay of the demand
+    model for both victim rules, from a random initial layout."""
+    rng = np.random.default_rng(seed)
+    ops = _random_circuit(rng, n, 400, kmax_in=min(3, kmax), diag_frac=0.3)
+    plan = q.qsa_plan_create(ops, n, q.make_opts(planner=q.QSA_PLAN_DP, kmax=kmax, kmax_diag=kdiag))
+    try:
+        tuples = _dense_tuples(q, plan, ops)
+        lay = [int(v) for v in rng.permutation(n)]
+        for rule, name in ((q.QSA_VICTIM_FIRST_FREE, "first_free"), (q.QSA_VICTIM_FARTHEST, "farthest")):
+            pr, ps, out = q.qsa_plan_promotions(plan, n, rule, lay)
+            counts, ref = oracle.promotion_replay(tuples, n, min(11, n), name, lay)
+            assert pr == sum(counts) and ps == sum(c > 0 for c in counts) and out == ref, name
+        with pytest.raises(q.QsaError):
+            q.qsa_plan_promotions(plan, n, 2)
+    finally:
+        q.qsa_plan_destroy(plan)
+
+
 @pytest.mark.parametrize("kmax", [1, 2, 3, 4, 6])
 def test_greedy_and_per_gate_planners_match_oracle(q, kmax):
     rng = np.random.default_rng(kmax)
