@@ -12,6 +12,8 @@ Contents
 * this module: ctypes wrappers plus plain numpy restatements of
   - the diagonal branch of Alg. 2 (elementwise multiply by the entry the
     target bits index) and the fused diagonal of a block of diagonal gates,
+  - the product lowering of a block of one-qubit factors on distinct qubits
+    and the grouping of a circuit into product units,
   - the Kronecker embedding and block product used by fusion (§IV-C: "within a
     block, matrices remain in circuit order, with later gates multiplied on
     the left"),
@@ -139,6 +141,50 @@ def fuse_diag(gates: Sequence, block_targets: Sequence[int]) -> np.ndarray:
             gi |= ((cs >> pos[int(t)]) & 1) << j
         d = np.diag(np.asarray(g.matrix, dtype=np.complex128))[gi] * d
     return d
+
+
+def apply_product(psi: np.ndarray, targets: Sequence[int], factors: Sequence[np.ndarray]) -> None:
+    """In place: the product operator U_{k-1} (x) ... (x) U_0 with the 2x2
+    factor U_j on qubit targets[j] (distinct), i.e. each factor applied as its
+    own one-qubit gate (they act on different qubits, so order is free).  A
+    structured fused block (§IV-D: such blocks may use cheaper lowerings)."""
+    assert len(set(int(t) for t in targets)) == len(targets)
+    for t, u in zip(targets, factors):
+        apply(psi, (int(t),), np.asarray(u, dtype=np.complex128))
+
+
+def fuse_product(ops: Sequence) -> Tuple[List[int], List[np.ndarray]]:
+    """Factors of a product unit: for each qubit (ascending), the product of
+    its one-qubit ops in circuit order, later ops on the left (§IV-C)."""
+    f = {}
+    for o in ops:
+        q = int(o.targets[0])
+        f[q] = np.asarray(o.matrix, dtype=np.complex128) @ f.get(q, np.eye(2, dtype=np.complex128))
+    t = sorted(f)
+    return t, [f[q] for q in t]
+
+
+def product_units(ops: Sequence, kmax_prod: int) -> List[Tuple[int, int]]:
+    """Product units of a circuit: maximal runs of consecutive non-diagonal
+    one-qubit ops touching at most ``kmax_prod`` distinct qubits (a run of
+    width 1 is an ordinary op); every other op is a unit of its own.  Returns
+    half-open op ranges in order."""
+    units, i, n_ops = [], 0, len(ops)
+    while i < n_ops:
+        o = ops[i]
+        if kmax_prod >= 2 and len(o.targets) == 1 and not o.diag:
+            qs, j = {o.targets[0]}, i + 1
+            while j < n_ops and len(ops[j].targets) == 1 and not ops[j].diag:
+                if ops[j].targets[0] not in qs and len(qs) == kmax_prod:
+                    break
+                qs.add(ops[j].targets[0])
+                j += 1
+            units.append((i, j))
+            i = j
+        else:
+            units.append((i, i + 1))
+            i += 1
+    return units
 
 
 def run_circuit(n: int, ops: Iterable, psi: np.ndarray | None = None) -> np.ndarray:
