@@ -40,10 +40,11 @@ UNIT = "amp-updates/s"
 
 # DRAM bytes (read + write) per amplitude of one launch, from single ncu captures
 # at N=28 (profiles/k_apply_tc6_n28.md: 4.241 GB; profiles/k_apply_fp32_k4_n28.md:
-# 4.234 GB; profiles/k_apply_diag_n28.md: 4.234 GB; each / 2^28).  Traffic scales with the state size, so a launch at N
+# 4.234 GB; profiles/k_apply_diag_n28.md: 4.234 GB; profiles/k_apply_prod_n28.md:
+# 4.260 GB; each / 2^28).  Traffic scales with the state size, so a launch at N
 # moves this many bytes times 2^N.
 DRAM_BYTES_PER_AMP = {"k_apply_tc": 4.241e9 / 2**28, "k_apply_fp32": 4.234e9 / 2**28,
-                      "k_apply_diag": 4.234e9 / 2**28}
+                      "k_apply_diag": 4.234e9 / 2**28, "k_apply_prod": 4.260e9 / 2**28}
 
 
 def _peaks():
@@ -183,6 +184,7 @@ def main():
     ap.add_argument("--planner", default="dp_mlp", choices=["per_gate", "greedy", "dp", "dp_mlp"])
     ap.add_argument("--kmax", type=int, default=6)
     ap.add_argument("--kmax-diag", type=int, default=12, help="diagonal-block cap (1..12)")
+    ap.add_argument("--kmax-prod", type=int, default=6, help="product-unit cap (0: off, 2..11)")
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3"])
     ap.add_argument("--lowering", default="auto", choices=["auto", "strided", "permute"])
     ap.add_argument("--victim", default="first_free", choices=["first_free", "farthest"],
@@ -217,7 +219,7 @@ def main():
     kdiag = args.kmax_diag
     victim = {"first_free": 0, "farthest": 1}[args.victim]
     opts = q.make_opts(planner=planner, kmax=args.kmax, kmax_diag=kdiag, precision=prec, lowering=low, timing=1,
-                       victim=victim)
+                       victim=victim, kmax_prod=args.kmax_prod)
 
     buf = torch.empty(1 << n, dtype=torch.complex64, device=dev)
     stream = torch.cuda.current_stream(dev).cuda_stream
@@ -230,8 +232,8 @@ def main():
     pinfo = q.qsa_plan_info(plan)
     edge_mask = (1 << edges[0][0]) | (1 << edges[0][1])
 
-    agg = {"apply_seconds": 0.0, "tc_seconds": 0.0, "permute_seconds": 0.0, "diag_seconds": 0.0, "blocks": 0,
-           "permutes": 0, "tc_blocks": 0, "diag_blocks": 0}
+    agg = {"apply_seconds": 0.0, "tc_seconds": 0.0, "permute_seconds": 0.0, "diag_seconds": 0.0,
+           "prod_seconds": 0.0, "blocks": 0, "permutes": 0, "tc_blocks": 0, "diag_blocks": 0, "prod_blocks": 0}
 
     def step(record):
         q.qsa_state_reset(s)
@@ -277,7 +279,7 @@ def main():
     # roofline of the dominant fused-operator kernel: 16 B per amplitude per launch
     hbm_peak, peak_kind = _peaks()
     bytes_per_launch = 16.0 * (1 << n)
-    n_fp32 = agg["blocks"] - agg["tc_blocks"] - agg["diag_blocks"]
+    n_fp32 = agg["blocks"] - agg["tc_blocks"] - agg["diag_blocks"] - agg["prod_blocks"]
     kinds = []
     if n_fp32:
         kinds.append(("k_apply_fp32 (FP32 fused dense update)", agg["apply_seconds"], n_fp32))
@@ -285,6 +287,8 @@ def main():
         kinds.append(("k_apply_tc (split-TF32 tcgen05 fused update)", agg["tc_seconds"], agg["tc_blocks"]))
     if agg["diag_blocks"]:
         kinds.append(("k_apply_diag (diagonal streaming update)", agg["diag_seconds"], agg["diag_blocks"]))
+    if agg["prod_blocks"]:
+        kinds.append(("k_apply_prod (product of one-qubit factors)", agg["prod_seconds"], agg["prod_blocks"]))
     if agg["permutes"]:
         kinds.append(("k_permute (qubit permutation)", agg["permute_seconds"], agg["permutes"]))
     name, tot, cnt = max(kinds, key=lambda kv: kv[1])
@@ -306,7 +310,8 @@ def main():
             t0 = time.perf_counter()
             q.qsa_state_reset(s)
             st = q.qsa_apply_circuit(s, ops, q.make_opts(planner=planner, kmax=args.kmax, kmax_diag=kdiag,
-                                                          precision=prec, lowering=low, victim=victim))
+                                                          precision=prec, lowering=low, victim=victim,
+                                                          kmax_prod=args.kmax_prod))
             vals, cnts = q.qsa_sample_counts(s, args.shots, seed=args.seed + 17)
             torch.cuda.synchronize()
             e2e_times.append(time.perf_counter() - t0)
@@ -353,6 +358,7 @@ def main():
                                        f"complex64 ({8 * (1 << n) / 2**30:g} GiB), {args.shots} shots + norm + <ZZ> "
                                        f"per step",
                            "planner": args.planner, "kmax": args.kmax, "kmax_diag": kdiag,
+                           "kmax_prod": args.kmax_prod,
                            "precision": args.precision,
                            "lowering": args.lowering, "victim": args.victim, "fused_blocks": pinfo["blocks"],
                            "l2": "state 8 GiB > 129 MB L2; no flush needed", "parallelism": f"replicas x{ws}"},

@@ -64,6 +64,11 @@ typedef struct qsa_state_s* qsa_state;
  * configuration"); the streaming kernel keeps its 2^k-entry table in shared
  * memory, so this build accepts up to 12. */
 #define QSA_MAX_DIAG 12
+/* Widest product block (qsa_apply_product, product plan blocks): one-qubit
+ * factors on distinct qubits, applied in one pass of the FP32 tile engine
+ * (2^11-amplitude tiles) when at most 6 of them lie above the tile's
+ * contiguous low bits, else in several passes. */
+#define QSA_MAX_PROD 11
 
 /* Lowering of one fused dense operator (§III R4: the backend picks the
  * concrete kernel once the physical targets are known). */
@@ -118,6 +123,10 @@ typedef struct {
     int32_t lowering;       /* qsa_lowering */
     int32_t timing;         /* 1: time every launch with CUDA events (fills *_seconds) */
     int32_t victim;         /* qsa_victim: eviction rule of QSA_LOWER_PERMUTE promotions */
+    int32_t kmax_prod;      /* 0 or 1: off; 2..QSA_MAX_PROD: maximal runs of non-diagonal one-qubit ops
+                               on at most this many qubits become product units, applied as one product
+                               block (one pass) while they stay blocks of their own (§IV-D structured
+                               blocks); not used by per-gate plans or batches */
 } qsa_plan_opts;
 
 typedef struct {
@@ -134,6 +143,8 @@ typedef struct {
     double tc_seconds;      /* device time of tensor-core fused-operator kernels */
     uint64_t diag_blocks;   /* diagonal blocks run on the streaming kernel */
     double diag_seconds;    /* device time of diagonal streaming kernels */
+    uint64_t prod_blocks;   /* product blocks (one-qubit factors) applied */
+    double prod_seconds;    /* device time of product kernels */
 } qsa_run_stats;
 
 /* A compiled circuit: the planner's blocks with their fused FP32 matrices. */
@@ -207,6 +218,17 @@ qsa_status qsa_apply_fused_ex(qsa_state s, const int32_t* targets, int k, const 
  * Errors: QSA_E_ARG (k outside 1..QSA_MAX_DIAG or > N, bad / repeated
  * target, NULL). */
 qsa_status qsa_apply_diag(qsa_state s, const int32_t* targets, int k, const double* diag);
+
+/* Product operator U_{k-1} (x) ... (x) U_0 with the 2x2 factor U_j on logical
+ * qubit targets[j]: a structured fused block (§IV-D: structured blocks may use
+ * cheaper lowerings), applied in one pass of the tile engine with 2k complex
+ * multiply-adds per amplitude instead of 2^k (several passes when more than 6
+ * targets lie above the tile's contiguous low bits).  targets: k distinct
+ * logical qubits (host); factors: host, 8 doubles per factor (row-major 2x2,
+ * interleaved Re, Im), rounded once to FP32.  The layout is unchanged.
+ * Errors: QSA_E_ARG (k outside 1..QSA_MAX_PROD or > N, bad / repeated target,
+ * NULL). */
+qsa_status qsa_apply_product(qsa_state s, const int32_t* targets, int k, const double* factors);
 
 /* ---- circuits: fusion planning + execution (§IV-C) ------------------------- */
 

@@ -298,9 +298,10 @@ def block_product(gates: Sequence, block_targets: Sequence[int]) -> np.ndarray:
     return M
 
 
-def gamma_score(width: int, diag: bool) -> float:
-    """gamma(k, dense) = 4^k, gamma(k, diag) = 1 (§IV-C)."""
-    return 1.0 if diag else float(4 ** width)
+def gamma_score(width: int, diag: bool, prod: bool = False) -> float:
+    """gamma(k, dense) = 4^k, gamma(k, diag) = 1 (§IV-C); a product block (one
+    streaming pass, like a diagonal one) also scores 1."""
+    return 1.0 if (diag or prod) else float(4 ** width)
 
 
 def _block_width(gates, j, i):
@@ -327,10 +328,11 @@ def dp_window(gates: Sequence, kmax: int, kmax_diag: int, score=None) -> List[Tu
             blk = gates[j:i]
             w = _block_width(gates, j, i)
             diag = all(g.diag for g in blk)
+            prod = i - j == 1 and getattr(blk[0], "prod", False)
             cap = kmax_diag if diag else kmax
             if w > cap and j != i - 1:
                 continue
-            sc = gamma_score(w, diag) if score is None else score(w, diag, blk)
+            sc = gamma_score(w, diag, prod) if score is None else score(w, diag, blk)
             val = D[j] + sc
             if val < best:  # strict: keeps the smallest j on ties
                 best, bj = val, j
@@ -540,7 +542,11 @@ def merge_adjacent(blocks, kmax: int, kmax_diag: int, score=None):
     width(a ∪ b) fits the cap of the merged mode and
     Gamma(a ∪ b) <= Gamma(a) + Gamma(b)).  ``blocks`` are dicts with keys
     targets (set), diag, s, e (input op range)."""
-    sc = score if score is not None else (lambda w, d, t: gamma_score(w, d))
+    def sc(blk):
+        if score is None:
+            return gamma_score(len(blk["targets"]), blk["diag"], blk.get("prod", False))
+        return score(len(blk["targets"]), blk["diag"], blk["targets"])
+
     out = []
     cur = None
     for b in blocks:
@@ -550,9 +556,9 @@ def merge_adjacent(blocks, kmax: int, kmax_diag: int, score=None):
         t = cur["targets"] | b["targets"]
         d = cur["diag"] and b["diag"]
         cap = kmax_diag if d else kmax
-        if len(t) <= cap and sc(len(t), d, t) <= sc(len(cur["targets"]), cur["diag"], cur["targets"]) + \
-                sc(len(b["targets"]), b["diag"], b["targets"]):
-            cur = {"targets": t, "diag": d, "s": cur["s"], "e": b["e"]}
+        merged = {"targets": t, "diag": d, "s": cur["s"], "e": b["e"], "prod": False}
+        if len(t) <= cap and sc(merged) <= sc(cur) + sc(b):
+            cur = merged
         else:
             out.append(cur)
             cur = dict(b)
@@ -568,10 +574,11 @@ def fuse_pipeline(gates, kmax: int, kmax_diag: int, window: int = 64, rounds: in
     (§IV-C).  Returns the first input-op index of every block."""
 
     class U:
-        def __init__(self, targets, diag, s, e):
+        def __init__(self, targets, diag, s, e, prod=False):
             self.targets, self.diag, self.s, self.e = tuple(sorted(targets)), diag, s, e
+            self.prod = prod
 
-    units = [U(g.targets, bool(g.diag), i, i + 1) for i, g in enumerate(gates)]
+    units = [U(g.targets, bool(g.diag), i, i + 1, bool(getattr(g, "prod", False))) for i, g in enumerate(gates)]
     wscore = None if score is None else (lambda w, d, blk: score(w, d, set().union(*[set(b.targets) for b in blk])))
     for rnd in range(rounds):
         blocks = []
@@ -582,9 +589,31 @@ def fuse_pipeline(gates, kmax: int, kmax_diag: int, window: int = 64, rounds: in
                 for u in win[j:i]:
                     t |= set(u.targets)
                 blocks.append({"targets": t, "diag": all(u.diag for u in win[j:i]), "s": win[j].s,
-                               "e": win[i - 1].e})
+                               "e": win[i - 1].e, "prod": i - j == 1 and win[j].prod})
         blocks = merge_adjacent(blocks, kmax, kmax_diag, score)
         if rnd > 0 and len(blocks) >= len(units):
             break
-        units = [U(b["targets"], b["diag"], b["s"], b["e"]) for b in blocks]
+        units = [U(b["targets"], b["diag"], b["s"], b["e"], b.get("prod", False)) for b in blocks]
     return [u.s for u in units]
+
+
+def fuse_pipeline_products(ops, kmax: int, kmax_diag: int, kmax_prod: int, window: int = 64, rounds: int = 4):
+    """The fusion pipeline over product units (:func:`product_units`): a unit
+    of two or more qubits is a product unit, scored as one pass while it
+    stays a block of its own; merged with other units it becomes dense.
+    Returns the first op index of every block."""
+
+    class G:
+        def __init__(self, targets, prod):
+            self.targets, self.diag, self.prod = tuple(sorted(targets)), False, prod
+
+    units = product_units(ops, kmax_prod)
+    gates = []
+    for a, b in units:
+        t = sorted({int(q) for o in ops[a:b] for q in o.targets})
+        if b - a == 1:
+            gates.append(ops[a])
+        else:
+            gates.append(G(t, len(t) >= 2))
+    starts = fuse_pipeline(gates, kmax, kmax_diag, window, rounds)
+    return [units[i][0] for i in starts]

@@ -27,7 +27,7 @@ QSA_LOWER_AUTO, QSA_LOWER_STRIDED, QSA_LOWER_PERMUTE = 0, 1, 2
 QSA_PREC_FP32, QSA_PREC_TF32X3 = 0, 1
 QSA_PLAN_PER_GATE, QSA_PLAN_GREEDY, QSA_PLAN_DP, QSA_PLAN_DP_MLP = 0, 1, 2, 3
 QSA_OP_DIAG = 1
-QSA_MAX_K, QSA_MAX_DIAG = 6, 12
+QSA_MAX_K, QSA_MAX_DIAG, QSA_MAX_PROD = 6, 12, 11
 QSA_VICTIM_FIRST_FREE, QSA_VICTIM_FARTHEST = 0, 1
 MLP_PARAMS = 6657
 MLP_IN = 37
@@ -58,7 +58,7 @@ class qsa_op(_c.Structure):
 class qsa_plan_opts(_c.Structure):
     _fields_ = [("planner", _c.c_int32), ("kmax", _c.c_int32), ("kmax_diag", _c.c_int32), ("window", _c.c_int32),
                 ("rounds", _c.c_int32), ("precision", _c.c_int32), ("lowering", _c.c_int32),
-                ("timing", _c.c_int32), ("victim", _c.c_int32)]
+                ("timing", _c.c_int32), ("victim", _c.c_int32), ("kmax_prod", _c.c_int32)]
 
 
 class qsa_run_stats(_c.Structure):
@@ -66,7 +66,7 @@ class qsa_run_stats(_c.Structure):
                 ("hbm_bytes", _c.c_double), ("blocks", _c.c_uint64), ("passes", _c.c_uint64),
                 ("permutes", _c.c_uint64), ("tc_blocks", _c.c_uint64), ("launches", _c.c_uint64),
                 ("h2d_bytes", _c.c_double), ("tc_seconds", _c.c_double), ("diag_blocks", _c.c_uint64),
-                ("diag_seconds", _c.c_double)]
+                ("diag_seconds", _c.c_double), ("prod_blocks", _c.c_uint64), ("prod_seconds", _c.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -94,6 +94,7 @@ _f = {
     "qsa_apply_fused": _sig("qsa_apply_fused", [_vp, _i32p, _c.c_int, _dp]),
     "qsa_apply_fused_ex": _sig("qsa_apply_fused_ex", [_vp, _i32p, _c.c_int, _dp, _c.c_int, _c.c_int]),
     "qsa_apply_diag": _sig("qsa_apply_diag", [_vp, _i32p, _c.c_int, _dp]),
+    "qsa_apply_product": _sig("qsa_apply_product", [_vp, _i32p, _c.c_int, _dp]),
     "qsa_plan_opts_default": _sig("qsa_plan_opts_default", [_c.POINTER(qsa_plan_opts)], None),
     "qsa_plan_circuit": _sig("qsa_plan_circuit", [_c.POINTER(qsa_op), _c.c_size_t, _c.c_int,
                                                   _c.POINTER(qsa_plan_opts), _szp, _szp]),
@@ -209,6 +210,13 @@ def qsa_apply_fused_ex(s: int, targets: Sequence[int], matrix, lowering: int, pr
     m = _cmat(matrix)
     _check(_f["qsa_apply_fused_ex"](_vp(s), pt, len(t), m.view(np.float64).ctypes.data_as(_dp), lowering,
                                     precision))
+
+
+def qsa_apply_product(s: int, targets: Sequence[int], factors) -> None:
+    """Product of 2x2 factors, factor j on targets[j]."""
+    t, pt = _i32(targets)
+    f = np.ascontiguousarray(np.asarray(factors, dtype=np.complex128).reshape(len(t), 2, 2))
+    _check(_f["qsa_apply_product"](_vp(s), pt, len(t), f.view(np.float64).ctypes.data_as(_dp)))
 
 
 def qsa_apply_diag(s: int, targets: Sequence[int], diag) -> None:

@@ -275,6 +275,156 @@ cudaError_t launch_apply_k(float2* psi, int n, const int* phys, const float* d_m
 }
 
 // ---------------------------------------------------------------------------
+// Product of one-qubit factors (a structured fused block, §IV-D)
+// ---------------------------------------------------------------------------
+constexpr int kProdT = 11, kProdS = 3, kProdHigh = 3;
+
+struct ProdArgs {
+    TileArgs t;
+    const float* fac;          // 8 floats per factor: 2x2 complex, row-major
+    int k;
+    int tl[QSA_MAX_PROD];      // tile-local position of factor j
+};
+
+// a x + b y for complex a, b, x, y.
+__device__ __forceinline__ float2 cfma2(float2 a, float2 x, float2 b, float2 y) {
+    return make_float2(a.x * x.x - a.y * x.y + b.x * y.x - b.y * y.y, a.x * x.y + a.y * x.x + b.x * y.y + b.y * y.x);
+}
+
+// One round over the staged tile.  A warp covers 32 x 2^H amplitudes: its
+// lanes are tile-local bits 0..4 (so every shared-memory access of the warp
+// touches 32 consecutive amplitudes), and each lane holds the 2^H
+// combinations of the round's H high targets (positions >= 5, ascending
+// hpos[]).  High factors are butterflies in registers, low factors (targets
+// below 5) butterflies across lanes with shuffles.  The last round stores
+// straight to HBM (32 consecutive amplitudes per warp store).
+template <int H>
+__device__ __forceinline__ void prod_round(const ProdArgs& a, float2* st, const float2* F, const int* hpos,
+                                           const int* hfi, int nlow, const int* lpos, const int* lfi, bool last,
+                                           const uint64_t* runoff, uint64_t base) {
+    constexpr int G = 1 << H;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int units = (1 << a.t.T) >> (5 + H);
+    for (int u = warp; u < units; u += nw) {
+        uint32_t ub = static_cast<uint32_t>(u) << 5;
+#pragma unroll
+        for (int j = 0; j < H; ++j) ub = static_cast<uint32_t>(insert_zero(ub, hpos[j]));
+        ub |= static_cast<uint32_t>(lane);
+        uint32_t off[G];
+        float2 v[G];
+#pragma unroll
+        for (int c = 0; c < G; ++c) {
+            uint32_t o = ub;
+#pragma unroll
+            for (int j = 0; j < H; ++j)
+                if ((c >> j) & 1) o |= 1u << hpos[j];
+            off[c] = o;
+            v[c] = st[o];
+        }
+#pragma unroll
+        for (int j = 0; j < H; ++j) {
+            const float2* U = F + 4 * hfi[j];
+#pragma unroll
+            for (int c = 0; c < G; ++c) {
+                if ((c >> j) & 1) continue;
+                const float2 x = v[c], y = v[c | (1 << j)];
+                v[c] = cfma2(U[0], x, U[1], y);
+                v[c | (1 << j)] = cfma2(U[3], y, U[2], x);
+            }
+        }
+        for (int l = 0; l < nlow; ++l) {
+            const int m = 1 << lpos[l];
+            const float2* U = F + 4 * lfi[l];
+            // bit clear: u00 x + u01 y; bit set: u11 x + u10 y (x own, y partner)
+            const bool one = (lane & m) != 0;
+            const float2 ua = one ? U[3] : U[0], ub2 = one ? U[2] : U[1];
+#pragma unroll
+            for (int c = 0; c < G; ++c) {
+                float2 y;
+                y.x = __shfl_xor_sync(0xffffffffu, v[c].x, m);
+                y.y = __shfl_xor_sync(0xffffffffu, v[c].y, m);
+                v[c] = cfma2(ua, v[c], ub2, y);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < G; ++c) {
+            if (last)
+                __stcs(a.t.psi + tile_global(a.t, runoff, base, off[c]), v[c]);
+            else
+                st[off[c]] = v[c];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_apply_prod(ProdArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tileAmps = 1 << a.t.T;
+    float2* stage = reinterpret_cast<float2*>(smem_raw);
+    float2* F = stage + kProdS * tileAmps;
+    uint64_t* runoff = reinterpret_cast<uint64_t*>(F + 4 * QSA_MAX_PROD);
+    const float2* gf = reinterpret_cast<const float2*>(a.fac);
+    for (int i = threadIdx.x; i < 4 * a.k; i += blockDim.x) F[i] = gf[i];
+    build_runoff(a.t, runoff);
+    // factors on tile-local bits 0..4 act across lanes (all in round 0); the
+    // others, ascending by position, go kProdHigh per round
+    int hpos[QSA_MAX_PROD], hfi[QSA_MAX_PROD], lpos[5], lfi[5];
+    int nh = 0, nl = 0;
+    for (int j = 0; j < a.k; ++j) {
+        if (a.tl[j] < 5) {
+            lpos[nl] = a.tl[j];
+            lfi[nl++] = j;
+        } else {
+            int x = nh++;
+            while (x > 0 && hpos[x - 1] > a.tl[j]) {
+                hpos[x] = hpos[x - 1];
+                hfi[x] = hfi[x - 1];
+                --x;
+            }
+            hpos[x] = a.tl[j];
+            hfi[x] = j;
+        }
+    }
+    const int rounds = nh > 0 ? (nh + kProdHigh - 1) / kProdHigh : 1;
+    __syncthreads();
+
+    const uint64_t t0 = blockIdx.x, stride = gridDim.x;
+#pragma unroll
+    for (int s = 0; s < kProdS - 1; ++s) {
+        const uint64_t t = t0 + s * stride;
+        if (t < a.t.ntiles) load_tile(a.t, runoff, t, stage + s * tileAmps);
+        cp_async_commit();
+    }
+    int it_stage = 0;
+    for (uint64_t t = t0; t < a.t.ntiles; t += stride) {
+        const uint64_t tn = t + (kProdS - 1) * stride;
+        int ld_stage = it_stage + (kProdS - 1);
+        if (ld_stage >= kProdS) ld_stage -= kProdS;
+        if (tn < a.t.ntiles) load_tile(a.t, runoff, tn, stage + ld_stage * tileAmps);
+        cp_async_commit();
+        cp_async_wait<kProdS - 1>();
+        __syncthreads();
+        float2* st = stage + it_stage * tileAmps;
+        const uint64_t base = tile_base(a.t, t);
+        for (int r = 0; r < rounds; ++r) {
+            const int h0 = r * kProdHigh, hb = min(kProdHigh, nh - h0);
+            const int nlr = r == 0 ? nl : 0;
+            const bool last = r == rounds - 1;
+            if (hb >= 3)
+                prod_round<3>(a, st, F, hpos + h0, hfi + h0, nlr, lpos, lfi, last, runoff, base);
+            else if (hb == 2)
+                prod_round<2>(a, st, F, hpos + h0, hfi + h0, nlr, lpos, lfi, last, runoff, base);
+            else if (hb == 1)
+                prod_round<1>(a, st, F, hpos + h0, hfi + h0, nlr, lpos, lfi, last, runoff, base);
+            else
+                prod_round<0>(a, st, F, hpos + h0, hfi + h0, nlr, lpos, lfi, last, runoff, base);
+            __syncthreads();
+        }
+        if (++it_stage == kProdS) it_stage = 0;
+    }
+    cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
 // Permute
 // ---------------------------------------------------------------------------
 struct PermArgs {
@@ -501,6 +651,63 @@ cudaError_t launch_apply_fp32(float2* psi, int n, const int* phys, int k, const 
         case 6: return launch_apply_k<6>(psi, n, phys, d_mat, st, launches);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_apply_prod(float2* psi, int n, const int* phys, int k, const float* d_fac, cudaStream_t st,
+                              uint64_t* launches) {
+    if (n < 5) {
+        // the product round maps warp lanes to 5 tile bits: tiny states apply
+        // each factor as its own one-qubit update
+        for (int j = 0; j < k; ++j) {
+            cudaError_t e = launch_apply_k<1>(psi, n, phys + j, d_fac + 8 * j, st, launches);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    // a tile holds at most 6 high target bits: larger sets go in several passes
+    int j0 = 0;
+    while (j0 < k) {
+        int j1 = k;
+        TileGeom g;
+        while (!make_geom(n, phys + j0, j1 - j0, kProdT, &g)) {
+            if (j1 - j0 == 1) return cudaErrorInvalidValue;
+            --j1;
+        }
+        ProdArgs a{};
+        a.t.psi = psi;
+        a.t.ntiles = g.ntiles;
+        a.t.T = g.T;
+        a.t.m = g.m;
+        a.t.nx = g.nx;
+        for (int e = 0; e < 6; ++e) a.t.xpos[e] = g.xpos[e];
+        a.fac = d_fac + 8 * j0;
+        a.k = j1 - j0;
+        int tls[QSA_MAX_PROD];
+        local_targets(g, phys + j0, a.k, a.tl, tls);
+        const size_t smem = sizeof(float2) * (static_cast<size_t>(kProdS) << g.T) + sizeof(float2) * 4 * QSA_MAX_PROD +
+                            sizeof(uint64_t) * 64;
+        static bool attr = false;
+        if (!attr) {
+            const size_t full = sizeof(float2) * (static_cast<size_t>(kProdS) << kProdT) +
+                                sizeof(float2) * 4 * QSA_MAX_PROD + sizeof(uint64_t) * 64;
+            cudaError_t e = cudaFuncSetAttribute(k_apply_prod, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(full));
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        int occ = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_apply_prod, kThreads, smem);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) occ = 1;
+        uint64_t grid = static_cast<uint64_t>(num_sms()) * occ;
+        if (grid > g.ntiles) grid = g.ntiles;
+        k_apply_prod<<<static_cast<unsigned>(grid), kThreads, smem, st>>>(a);
+        ++*launches;
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        j0 = j1;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_permute(float2* psi, int n, const int* pa, const int* pb, int npairs, cudaStream_t st,

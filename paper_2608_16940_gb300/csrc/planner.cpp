@@ -36,14 +36,18 @@ namespace qsa {
 namespace {
 
 struct Unit {
-    uint64_t mask;   // logical target qubits
+    uint64_t mask;       // logical target qubits
     bool diag;
-    size_t s, e;     // range of input ops
+    size_t s, e;         // range of input ops
+    bool prod = false;   // product unit (one-qubit ops on >= 2 qubits), while a block of its own
 };
 
-using Scorer = double (*)(void* ctx, int width, bool diag, uint64_t mask);
+using Scorer = double (*)(void* ctx, int width, bool diag, bool prod, uint64_t mask);
 
-double gamma_score(void*, int width, bool diag, uint64_t) { return diag ? 1.0 : std::ldexp(1.0, 2 * width); }
+// A diagonal or a product block is one streaming pass.
+double gamma_score(void*, int width, bool diag, bool prod, uint64_t) {
+    return (diag || prod) ? 1.0 : std::ldexp(1.0, 2 * width);
+}
 
 struct MlpCtx {
     int n;
@@ -51,8 +55,9 @@ struct MlpCtx {
     std::unordered_map<uint64_t, double> cache;
 };
 
-double mlp_score(void* ctx, int width, bool diag, uint64_t mask) {
+double mlp_score(void* ctx, int width, bool diag, bool prod, uint64_t mask) {
     auto* c = static_cast<MlpCtx*>(ctx);
+    diag = diag || prod;   // both run as one streaming pass
     const uint64_t key = mask | (diag ? (1ull << 63) : 0ull);
     auto it = c->cache.find(key);
     if (it != c->cache.end()) return it->second;
@@ -92,7 +97,7 @@ std::vector<Unit> dp_window(const std::vector<Unit>& u, size_t b, size_t e, int 
                 if (w > std::max(kmax, kmax_diag)) break;
                 continue;
             }
-            const double val = D[jj] + sc(ctx, w, diag, mask);
+            const double val = D[jj] + sc(ctx, w, diag, jj == i - 1 && u[b + jj].prod, mask);
             if (val <= best) {
                 best = val;
                 bj = jj;
@@ -110,6 +115,7 @@ std::vector<Unit> dp_window(const std::vector<Unit>& u, size_t b, size_t e, int 
             m.mask |= u[b + t].mask;
             m.diag = m.diag && u[b + t].diag;
         }
+        m.prod = i - j == 1 && u[b + j].prod;
         out.push_back(m);
         i = j;
     }
@@ -127,8 +133,8 @@ std::vector<Unit> merge_pass(const std::vector<Unit>& blocks, int kmax, int kmax
         const bool dg = cur.diag && nx.diag;
         const int w = popc(m);
         const int cap = dg ? kmax_diag : kmax;
-        if (w <= cap && sc(ctx, w, dg, m) <= sc(ctx, popc(cur.mask), cur.diag, cur.mask) +
-                                                   sc(ctx, popc(nx.mask), nx.diag, nx.mask)) {
+        if (w <= cap && sc(ctx, w, dg, false, m) <= sc(ctx, popc(cur.mask), cur.diag, cur.prod, cur.mask) +
+                                                          sc(ctx, popc(nx.mask), nx.diag, nx.prod, nx.mask)) {
             cur = Unit{m, dg, cur.s, nx.e};
         } else {
             out.push_back(cur);
@@ -199,6 +205,7 @@ qsa_status normalise_opts(const qsa_plan_opts* in, qsa_plan_opts* o) {
     if (o->precision < 0 || o->precision > 1) return fail(QSA_E_ARG, "unknown precision");
     if (o->lowering < 0 || o->lowering > 2) return fail(QSA_E_ARG, "unknown lowering");
     if (o->victim < 0 || o->victim > 1) return fail(QSA_E_ARG, "unknown victim rule");
+    if (o->kmax_prod < 0 || o->kmax_prod > QSA_MAX_PROD) return fail(QSA_E_ARG, "kmax_prod must be in 0..11");
     return QSA_OK;
 }
 
@@ -212,17 +219,36 @@ void build_next_use(qsa_plan_s* p) {
     for (size_t i = B; i-- > 0;) {
         std::copy(cur.begin(), cur.end(), p->next_use.begin() + i * n);
         const PlanBlock& b = p->blocks[i];
-        if (!b.diag)
+        if (!b.diag && !b.prod)
             for (int j = 0; j < b.k; ++j) cur[b.t[j]] = static_cast<int32_t>(i);
     }
 }
 
 std::vector<Unit> plan(const qsa_op* ops, size_t n_ops, int n_qubits, const qsa_plan_opts& o, const int32_t* L) {
-    std::vector<Unit> gates(n_ops);
-    for (size_t i = 0; i < n_ops; ++i) {
+    std::vector<Unit> gates;
+    gates.reserve(n_ops);
+    for (size_t i = 0; i < n_ops;) {
+        auto one_qubit = [&](size_t x) { return ops[x].k == 1 && !(ops[x].flags & QSA_OP_DIAG); };
+        if (o.kmax_prod >= 2 && o.planner != QSA_PLAN_PER_GATE && one_qubit(i)) {
+            // product unit: a maximal run of non-diagonal one-qubit ops on at most kmax_prod qubits
+            uint64_t m = 1ull << ops[i].targets[0];
+            size_t j = i + 1;
+            while (j < n_ops && one_qubit(j)) {
+                const uint64_t nm = m | (1ull << ops[j].targets[0]);
+                if (nm != m && popc(m) == o.kmax_prod) break;
+                m = nm;
+                ++j;
+            }
+            Unit u{m, false, i, j};
+            u.prod = popc(m) >= 2;
+            gates.push_back(u);
+            i = j;
+            continue;
+        }
         uint64_t m = 0;
         for (int j = 0; j < ops[i].k; ++j) m |= 1ull << ops[i].targets[j];
-        gates[i] = Unit{m, (ops[i].flags & QSA_OP_DIAG) != 0, i, i + 1};
+        gates.push_back(Unit{m, (ops[i].flags & QSA_OP_DIAG) != 0, i, i + 1});
+        ++i;
     }
     if (o.planner == QSA_PLAN_PER_GATE) return gates;
     if (o.planner == QSA_PLAN_GREEDY) return greedy(gates, o.kmax);
@@ -345,6 +371,7 @@ void qsa_plan_opts_default(qsa_plan_opts* o) {
     o->lowering = QSA_LOWER_AUTO;
     o->timing = 0;
     o->victim = QSA_VICTIM_FIRST_FREE;
+    o->kmax_prod = 0;
 }
 
 qsa_status qsa_plan_circuit(const qsa_op* ops, size_t n_ops, int n_qubits, const qsa_plan_opts* opts,
@@ -407,7 +434,38 @@ qsa_status qsa_plan_create(const qsa_op* ops, size_t n_ops, int n_qubits, const 
         PlanBlock& b = p->blocks[i];
         b.off = p->host_mat.size();
         b.first_op = u.s;
-        if (u.diag) {
+        if (u.prod) {
+            // per-qubit factors (ascending qubits), each the product of its ops in
+            // circuit order, later ops on the left
+            b.prod = true;
+            int t = 0;
+            for (int q = 0; q < 64; ++q)
+                if ((u.mask >> q) & 1) b.t[t++] = q;
+            b.k = t;
+            std::vector<std::complex<double>> F(4 * t);
+            for (int j = 0; j < t; ++j) {
+                F[4 * j] = 1.0;
+                F[4 * j + 3] = 1.0;
+            }
+            for (size_t x = u.s; x < u.e; ++x) {
+                const int j = static_cast<int>(std::find(b.t, b.t + t, ops[x].targets[0]) - b.t);
+                const double* g = ops[x].matrix;
+                std::complex<double> f[4], h[4];
+                for (int c = 0; c < 4; ++c) {
+                    f[c] = F[4 * j + c];
+                    h[c] = std::complex<double>(g[2 * c], g[2 * c + 1]);
+                }
+                F[4 * j] = h[0] * f[0] + h[1] * f[2];
+                F[4 * j + 1] = h[0] * f[1] + h[1] * f[3];
+                F[4 * j + 2] = h[2] * f[0] + h[3] * f[2];
+                F[4 * j + 3] = h[2] * f[1] + h[3] * f[3];
+            }
+            p->host_mat.resize(b.off + 8 * t);
+            for (int c = 0; c < 4 * t; ++c) {
+                p->host_mat[b.off + 2 * c] = static_cast<float>(F[c].real());
+                p->host_mat[b.off + 2 * c + 1] = static_cast<float>(F[c].imag());
+            }
+        } else if (u.diag) {
             b.diag = true;
             st = fuse_diag_range(ops, u.s, u.e, b.t, &b.k, &M);
             if (st != QSA_OK) {
@@ -456,7 +514,7 @@ qsa_status qsa_plan_promotions(qsa_plan p, const int32_t* layout_in, int victim,
     uint64_t pr = 0, ps = 0;
     for (size_t i = 0; i < p->blocks.size(); ++i) {
         const PlanBlock& b = p->blocks[i];
-        if (b.diag) continue;
+        if (b.diag || b.prod) continue;
         int phys[QSA_MAX_K], pa[QSA_MAX_K], pb[QSA_MAX_K];
         for (int j = 0; j < b.k; ++j) phys[j] = L[b.t[j]];
         const int np = choose_promotions(L, n, phys, b.k, frames, victim, p->next_use.data() + i * n, pa, pb);
@@ -540,7 +598,9 @@ qsa_status qsa_plan_execute(qsa_state s, qsa_plan p, qsa_run_stats* stats) {
     s->timing = p->opts.timing != 0;
     for (size_t i = 0; i < p->blocks.size(); ++i) {
         const PlanBlock& b = p->blocks[i];
-        if (b.diag) {
+        if (b.prod) {
+            st = apply_prod_logical(s, b.t, b.k, p->d_mat + b.off, rs);
+        } else if (b.diag) {
             st = apply_diag_logical(s, b.t, b.k, p->d_mat + b.off, rs);
         } else if (p->opts.lowering == QSA_LOWER_PERMUTE) {
             // promote the targets into the in-block frames, victims per the plan's rule
@@ -669,6 +729,7 @@ qsa_status qsa_batch_create(int n_qubits, int n_traj, const qsa_op* ops, const s
     if (st != QSA_OK) return st;
     if (o.kmax > 4) return fail(QSA_E_ARG, "batched trajectories fuse blocks of at most 4 qubits (kmax <= 4)");
     if (o.kmax_diag > o.kmax) return fail(QSA_E_ARG, "batched trajectories need kmax_diag <= kmax");
+    if (o.kmax_prod >= 2) return fail(QSA_E_ARG, "batched trajectories do not use product blocks (kmax_prod <= 1)");
     if (op_offsets[0] != 0) return fail(QSA_E_ARG, "op_offsets[0] must be 0");
     for (int t = 0; t < n_traj; ++t)
         if (op_offsets[t + 1] < op_offsets[t]) return fail(QSA_E_ARG, "op_offsets must be non-decreasing");

@@ -78,6 +78,10 @@ cudaError_t launch_apply_tc(float2* psi, int n, const int* phys, int k, const fl
 // of c = bit phys[j] of y; d_tab is 2^k interleaved FP32 complex numbers.
 cudaError_t launch_apply_diag(float2* psi, int n, const int* phys, int k, const float* d_tab, cudaStream_t st,
                               uint64_t* launches);
+// Product of one-qubit factors (k <= QSA_MAX_PROD): factor j (2x2 complex,
+// row-major, 8 floats at d_fac + 8 j) on physical position phys[j].
+cudaError_t launch_apply_prod(float2* psi, int n, const int* phys, int k, const float* d_fac, cudaStream_t st,
+                              uint64_t* launches);
 
 // In-place swap of physical bit pairs (pa[i] <-> pb[i]), all positions distinct.
 cudaError_t launch_permute(float2* psi, int n, const int* pa, const int* pb, int npairs, cudaStream_t st,

@@ -39,9 +39,10 @@ struct qsa_state_s {
 };
 
 struct PlanBlock {
-    int32_t t[QSA_MAX_DIAG];   // ordered logical targets of the fused block
+    int32_t t[QSA_MAX_DIAG];   // ordered logical targets of the fused block (QSA_MAX_DIAG >= QSA_MAX_PROD)
     int k = 0;
     bool diag = false;         // diagonal mode: 2^k entries, streaming kernel
+    bool prod = false;         // product of one-qubit factors: 8 floats per factor, product kernel
     size_t off = 0;            // float offset of its matrix / diagonal in host_mat / d_mat
     size_t first_op = 0;
 };
@@ -87,6 +88,8 @@ int choose_promotions(const int32_t* L, int n, int* phys, int k, int frames, int
 qsa_status promote_targets(qsa_state s, int* phys, int k, int inblock, qsa_run_stats* rs);
 // Diagonal block on logical targets (the layout resolves them; it is not changed).
 qsa_status apply_diag_logical(qsa_state s, const int32_t* targets, int k, const float* d_tab, qsa_run_stats* rs);
+// Product block on logical targets (factor j on targets[j]; layout unchanged).
+qsa_status apply_prod_logical(qsa_state s, const int32_t* targets, int k, const float* d_fac, qsa_run_stats* rs);
 bool tc_available(qsa_state s, int k);
 
 // Records a pair of CUDA events around the launches issued during its

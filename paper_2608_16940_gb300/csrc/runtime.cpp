@@ -218,6 +218,28 @@ qsa_status apply_diag_logical(qsa_state s, const int32_t* targets, int k, const 
     return QSA_OK;
 }
 
+qsa_status apply_prod_logical(qsa_state s, const int32_t* targets, int k, const float* d_fac, qsa_run_stats* rs) {
+    int phys[QSA_MAX_PROD];
+    for (int j = 0; j < k; ++j) phys[j] = s->L[targets[j]];
+    const uint64_t l0 = s->launches;
+    cudaError_t e;
+    {
+        Timer tm(s, rs ? &rs->prod_seconds : nullptr);
+        e = launch_apply_prod(s->psi, s->n, phys, k, d_fac, s->stream, &s->launches);
+        tm.stop();
+    }
+    if (e != cudaSuccess) return cuda_fail(s, e, "product kernel");
+    s->known_zero = false;
+    if (rs) {
+        const uint64_t passes = s->launches - l0;
+        rs->blocks += 1;
+        rs->passes += passes;
+        rs->prod_blocks += 1;
+        rs->hbm_bytes += 16.0 * static_cast<double>(1ull << s->n) * static_cast<double>(passes);
+    }
+    return QSA_OK;
+}
+
 // ---- timers ------------------------------------------------------------------
 Timer::Timer(qsa_state s, double* acc) : s_(s), acc_(s->timing ? acc : nullptr) {
     if (!acc_) return;
@@ -464,6 +486,23 @@ qsa_status qsa_apply_fused_ex(qsa_state s, const int32_t* targets, int k, const 
 
 qsa_status qsa_apply_fused(qsa_state s, const int32_t* targets, int k, const double* matrix) {
     return qsa_apply_fused_ex(s, targets, k, matrix, QSA_LOWER_AUTO, QSA_PREC_FP32);
+}
+
+qsa_status qsa_apply_product(qsa_state s, const int32_t* targets, int k, const double* factors) {
+    qsa_status st = check_state(s);
+    if (st != QSA_OK) return st;
+    st = validate_targets(s->n, targets, k, QSA_MAX_PROD);
+    if (st != QSA_OK) return st;
+    if (!factors) return fail(QSA_E_ARG, "factors is NULL");
+    const size_t cnt = 8ull * k;
+    std::vector<float> hf(cnt);
+    for (size_t i = 0; i < cnt; ++i) hf[i] = static_cast<float>(factors[i]);
+    st = ensure_dev(s, reinterpret_cast<void**>(&s->d_mat), &s->mat_cap, cnt * sizeof(float));
+    if (st != QSA_OK) return st;
+    // pageable source: the copy is staged before the call returns
+    cudaError_t e = cudaMemcpyAsync(s->d_mat, hf.data(), cnt * sizeof(float), cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "factor upload");
+    return apply_prod_logical(s, targets, k, s->d_mat, nullptr);
 }
 
 qsa_status qsa_apply_diag(qsa_state s, const int32_t* targets, int k, const double* diag) {

@@ -78,15 +78,18 @@ def test_fusion28_qft_closed_form_and_inverse_return(q):
         st.close()
 
 
-@pytest.mark.parametrize("kmax,prec", [(4, 0), (6, 1)], ids=["kmax4-fp32", "kmax6-3xtf32"])
-def test_qaoa30_symmetries_and_fused_equals_per_gate(q, kmax, prec):
-    """The bench's workload and launch configuration (kmax 6 with the split-TF32
-    path for k = 5, 6) and the FP32-only configuration."""
+@pytest.mark.parametrize("kmax,kdiag,kprod,prec", [(4, 4, 0, 0), (6, 6, 0, 1), (6, 12, 6, 1)],
+                         ids=["kmax4-fp32", "kmax6-3xtf32", "bench-kdiag12-kprod6-3xtf32"])
+def test_qaoa30_symmetries_and_fused_equals_per_gate(q, kmax, kdiag, kprod, prec):
+    """The bench's workload and launch configuration (kmax 6, diagonal blocks up
+    to 12 qubits, product units up to 6, split-TF32 for k = 5, 6), and two
+    dense-only configurations."""
     n = 30
     ops, edges = W.qaoa_circuit(n=n, p=8, seed=0)
     st = Big(q, n)
     try:
-        q.qsa_apply_circuit(st.h, ops, q.make_opts(planner=q.QSA_PLAN_DP, kmax=kmax, kmax_diag=kmax, precision=prec))
+        q.qsa_apply_circuit(st.h, ops, q.make_opts(planner=q.QSA_PLAN_DP, kmax=kmax, kmax_diag=kdiag,
+                                                   kmax_prod=kprod, precision=prec))
         assert abs(q.qsa_expectation_z(st.h, 0) - 1) < 1e-5
         for qb in (0, 7, 29):
             assert abs(q.qsa_expectation_z(st.h, 1 << qb)) < 1e-5

@@ -78,6 +78,30 @@ def test_dp_planner_with_wide_diagonal_cap_matches_oracle(q, seed, n, n_ops, kma
     assert got == ref
 
 
+@pytest.mark.parametrize("seed,n,kmax,kdiag,kprod", [(20, 14, 4, 4, 6), (21, 20, 6, 12, 11), (22, 10, 3, 8, 2),
+                                                      (23, 16, 2, 2, 11)])
+def test_dp_planner_with_product_units_matches_oracle(q, seed, n, kmax, kdiag, kprod):
+    """Runs of one-qubit ops become product units: the DP pipeline over them
+    agrees with the oracle's (fuse_pipeline_products)."""
+    rng = np.random.default_rng(seed)
+    ops = []
+    for _ in range(500):
+        r = rng.random()
+        if r < 0.55:
+            ops.append(W.Op((int(rng.integers(0, n)),), W.haar_unitary(2, rng), False))
+        elif r < 0.8:
+            t = tuple(int(v) for v in rng.choice(n, size=2, replace=False))
+            ops.append(W.Op(t, W.zz(float(rng.uniform(0, 6))), True))
+        else:
+            t = tuple(int(v) for v in rng.choice(n, size=int(rng.integers(2, 4)), replace=False))
+            ops.append(W.Op(t, np.eye(1 << len(t), dtype=np.complex128), False))
+    for planner in (q.QSA_PLAN_DP,):
+        got = q.qsa_plan_circuit(ops, n, q.make_opts(planner=planner, kmax=kmax, kmax_diag=kdiag, kmax_prod=kprod))
+        assert got == oracle.fuse_pipeline_products(ops, kmax, kdiag, kprod)
+    with pytest.raises(q.QsaError):
+        q.qsa_plan_circuit(ops, n, q.make_opts(kmax_prod=12))
+
+
 def test_diagonal_options_and_flags_are_validated(q):
     ops = [W.Op((0, 1), W.CZ.copy(), True)]
     with pytest.raises(q.QsaError):
