@@ -305,20 +305,27 @@ __device__ __forceinline__ void prod_round(const ProdArgs& a, float2* st, const 
     constexpr int G = 1 << H;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int units = (1 << a.t.T) >> (5 + H);
+    // per round: each high target's tile-local bit and the global offset of
+    // that bit (tile indexing is bitwise linear, so offsets add)
+    uint32_t hm[H > 0 ? H : 1];
+    uint64_t gb[H > 0 ? H : 1];
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+        hm[j] = 1u << hpos[j];
+        gb[j] = tile_global(a.t, runoff, 0, hm[j]);
+    }
     for (int u = warp; u < units; u += nw) {
         uint32_t ub = static_cast<uint32_t>(u) << 5;
 #pragma unroll
         for (int j = 0; j < H; ++j) ub = static_cast<uint32_t>(insert_zero(ub, hpos[j]));
         ub |= static_cast<uint32_t>(lane);
-        uint32_t off[G];
         float2 v[G];
 #pragma unroll
         for (int c = 0; c < G; ++c) {
             uint32_t o = ub;
 #pragma unroll
             for (int j = 0; j < H; ++j)
-                if ((c >> j) & 1) o |= 1u << hpos[j];
-            off[c] = o;
+                if ((c >> j) & 1) o |= hm[j];
             v[c] = st[o];
         }
 #pragma unroll
@@ -346,12 +353,25 @@ __device__ __forceinline__ void prod_round(const ProdArgs& a, float2* st, const 
                 v[c] = cfma2(ua, v[c], ub2, y);
             }
         }
+        if (last) {
+            float2* g0 = a.t.psi + tile_global(a.t, runoff, base, ub);
 #pragma unroll
-        for (int c = 0; c < G; ++c) {
-            if (last)
-                __stcs(a.t.psi + tile_global(a.t, runoff, base, off[c]), v[c]);
-            else
-                st[off[c]] = v[c];
+            for (int c = 0; c < G; ++c) {
+                uint64_t go = 0;
+#pragma unroll
+                for (int j = 0; j < H; ++j)
+                    if ((c >> j) & 1) go += gb[j];
+                __stcs(g0 + go, v[c]);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < G; ++c) {
+                uint32_t o = ub;
+#pragma unroll
+                for (int j = 0; j < H; ++j)
+                    if ((c >> j) & 1) o |= hm[j];
+                st[o] = v[c];
+            }
         }
     }
 }
