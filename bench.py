@@ -109,6 +109,25 @@ def _dist():
     return ws, rank, local
 
 
+def job_seconds(elapsed: float, ws: int, device=None) -> float:
+    """Whole-job time of a replica run: the slowest rank's timed region (max
+    over ranks, then a barrier); the replicas share no data, so this is the
+    only collective."""
+    if ws <= 1:
+        return elapsed
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([elapsed], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, ws: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the job time."""
+    return ws * units_per_rank / seconds
+
+
 def run_reference(args):
     """The FP64 CPU oracle, unmodified, on a bounded sample of the workload."""
     ws, rank, _ = _dist()
@@ -266,15 +285,10 @@ def main():
     torch.cuda.nvtx.range_pop()
     launches = q.qsa_state_counters(s) - l0
     clocks = clk.stop()
-    elapsed = ev0.elapsed_time(ev1) * 1e-3
-    if ws > 1:
-        t = torch.tensor([elapsed], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(t.item())
-        torch.distributed.barrier()
+    elapsed = job_seconds(ev0.elapsed_time(ev1) * 1e-3, ws, dev)
     per_step = elapsed / args.steps
     amp_updates = len(ops) * float(1 << n)
-    value = ws * amp_updates / per_step
+    value = job_value(amp_updates, ws, per_step)
 
     # roofline of the dominant fused-operator kernel: 16 B per amplitude per launch
     hbm_peak, peak_kind = _peaks()
