@@ -14,6 +14,8 @@ Contents
     target bits index) and the fused diagonal of a block of diagonal gates,
   - the product lowering of a block of one-qubit factors on distinct qubits
     and the grouping of a circuit into product units,
+  - density-matrix evolution by Kraus operators, its column-major
+    vectorisation and the superoperator of a channel,
   - the Kronecker embedding and block product used by fusion (§IV-C: "within a
     block, matrices remain in circuit order, with later gates multiplied on
     the left"),
@@ -185,6 +187,44 @@ def product_units(ops: Sequence, kmax_prod: int) -> List[Tuple[int, int]]:
             units.append((i, i + 1))
             i += 1
     return units
+
+
+def dm_zero(n: int) -> np.ndarray:
+    """|0...0><0...0| as a 2^n x 2^n matrix."""
+    rho = np.zeros((1 << n, 1 << n), dtype=np.complex128)
+    rho[0, 0] = 1.0
+    return rho
+
+
+def dm_apply_channel(rho: np.ndarray, targets: Sequence[int], kraus: Sequence[np.ndarray]) -> np.ndarray:
+    """rho' = sum_i E_i rho E_i^dagger with each Kraus operator E_i (2^k x 2^k)
+    acting on ``targets`` (§IV-B density-matrix wrapper; a unitary is the
+    single-operator channel).  Plain matrix products with the embedded
+    operators (full_operator), small n only."""
+    n = int(rho.shape[0]).bit_length() - 1
+    out = np.zeros_like(rho)
+    for E in kraus:
+        M = full_operator(n, targets, np.asarray(E, dtype=np.complex128))
+        out += M @ rho @ M.conj().T
+    return out
+
+
+def dm_vec(rho: np.ndarray) -> np.ndarray:
+    """Column-major vectorisation: index row + 2^n * column (the lower n bits
+    select the row, the upper n bits the column)."""
+    return np.ascontiguousarray(rho.T).reshape(-1)
+
+
+def dm_unvec(v: np.ndarray) -> np.ndarray:
+    d = int(round(np.sqrt(v.size)))
+    return v.reshape(d, d).T.copy()
+
+
+def dm_superoperator(kraus: Sequence[np.ndarray]) -> np.ndarray:
+    """sum_i conj(E_i) (x) E_i: the channel on the 2k axes of vec(rho), with the
+    original factor on the lower (row) bits and the conjugate on the upper
+    (column) bits."""
+    return sum(np.kron(np.conj(E), E) for E in kraus)
 
 
 def run_circuit(n: int, ops: Iterable, psi: np.ndarray | None = None) -> np.ndarray:
