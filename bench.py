@@ -16,6 +16,13 @@ path is not sharded): weak scaling, no collective on the data path.
 
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
 workload (one gate of the circuit per step at N = 28) on the host cores.
+
+``--workload dm_ghz`` measures the density-matrix path instead: noisy GHZ on
+n = 15 qubits (H, then CNOT(0 -> q) for q = 1..14, depolarising noise p = 0.01
+after every gate: 30 channels), held as vec(rho) on 2n = 30 qubits; each
+channel is lowered to its 2k-axis superoperator and the lowered circuit is
+fused and executed like any other (one step: reset, execute, trace and
+Tr(rho Z_0 Z_14)).  Its metric counts 4^n amplitude updates per channel.
 """
 from __future__ import annotations
 
@@ -135,9 +142,15 @@ def run_reference(args):
         return
     import oracle
     n_s = args.ref_qubits
-    ops, _ = W.qaoa_circuit(n=n_s, p=args.p, seed=args.seed)
+    if args.workload == "dm_ghz":
+        picks, _, what = _dm_oracle_picks(n_s // 2, args.dm_p)
+        n_s = 2 * (n_s // 2)
+        wl = f"dm_ghz{args.dm_n}"
+    else:
+        ops, _ = W.qaoa_circuit(n=n_s, p=args.p, seed=args.seed)
+        picks = [ops[0], ops[n_s]]   # alternate a one-qubit and a two-qubit gate of the circuit
+        wl, what = f"qaoa{args.n}_p{args.p}", "H / ZZ gate of the QAOA circuit"
     psi = oracle.zero_state(n_s)
-    picks = [ops[0], ops[n_s]]   # alternate a one-qubit and a two-qubit gate of the circuit
     times = []
     for i in range(args.warmup + args.steps):
         g = picks[i % 2]
@@ -151,27 +164,47 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_gate * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"qaoa{args.n}_p{args.p}", "sample": f"one gate per step at N={n_s}"},
+            "config": {"workload": wl, "sample": f"one gate per step at N={n_s}"},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"alternating H / ZZ gate of the QAOA circuit at N={n_s}, "
-                                       f"{args.steps} timed gates"},
+                             "sample": f"alternating {what} at N={n_s}, {args.steps} timed gates"},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(n_s: int, seed: int, p: int):
+class _LoweredOp:
+    def __init__(self, targets, matrix):
+        self.targets, self.matrix = tuple(targets), matrix
+
+
+def _dm_oracle_picks(n_dm: int, p_dep: float):
+    """Two channels of the noisy GHZ circuit (the first CNOT and its
+    depolarising noise) lowered by the oracle to superoperators on vec(rho)
+    of 2 n_dm qubits."""
+    import oracle
+    chans = W.noisy_ghz_channels(n_dm, p_dep)[2:4]
+    picks = [_LoweredOp(tuple(c.targets) + tuple(t + n_dm for t in c.targets), oracle.dm_superoperator(c.kraus))
+             for c in chans]
+    return picks, f"dm_ghz{n_dm}", "CNOT / two-qubit depolarising superoperator of noisy GHZ"
+
+
+def cpu_baseline(n_s: int, seed: int, p: int, workload: str = "qaoa", p_dep: float = 1e-2):
     """Oracle timed on the host (1 thread) on two gates at N = n_s."""
     import oracle
-    ops, _ = W.qaoa_circuit(n=n_s, p=p, seed=seed)
+    if workload == "dm_ghz":
+        picks, _, what = _dm_oracle_picks(n_s // 2, p_dep)
+        n_s = 2 * (n_s // 2)
+    else:
+        ops, _ = W.qaoa_circuit(n=n_s, p=p, seed=seed)
+        picks = [ops[0], ops[n_s]]
+        what = "2 gates (H, ZZ) of the QAOA circuit"
     psi = oracle.zero_state(n_s)
-    picks = [ops[0], ops[n_s]]
     t0 = time.perf_counter()
     for g in picks:
         oracle.apply(psi, g.targets, g.matrix)
     dt = time.perf_counter() - t0
     rate = len(picks) * (1 << n_s) / dt
     return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"2 gates (H, ZZ) of the QAOA circuit at N={n_s}, {dt:.1f} s single-threaded FP64"}
+            "sample": f"{what} at N={n_s}, {dt:.1f} s single-threaded FP64"}
 
 
 def train_cost_model(q, s, precision, seed, n_samples):
@@ -196,6 +229,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="qaoa", choices=["qaoa", "dm_ghz"])
+    ap.add_argument("--dm-n", type=int, default=15, help="density-matrix qubits of --workload dm_ghz (2..17)")
+    ap.add_argument("--dm-p", type=float, default=1e-2, help="depolarising rate of --workload dm_ghz")
     ap.add_argument("--n", type=int, default=30)
     ap.add_argument("--p", type=int, default=8)
     ap.add_argument("--seed", type=int, default=0)
@@ -230,8 +266,16 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device(f"cuda:{local}")
 
-    n = args.n
-    ops, edges = W.qaoa_circuit(n=n, p=args.p, seed=args.seed + rank)
+    dm = args.workload == "dm_ghz"
+    if dm:
+        n_dm = args.dm_n
+        n = 2 * n_dm
+        chans = W.noisy_ghz_channels(n_dm, args.dm_p)
+        ops = [q.qsa_dm_superoperator(n_dm, c.targets, c.kraus) for c in chans]
+        edges = [(0, n_dm - 1)]
+    else:
+        n = args.n
+        ops, edges = W.qaoa_circuit(n=n, p=args.p, seed=args.seed + rank)
     planner = {"per_gate": 0, "greedy": 1, "dp": 2, "dp_mlp": 3}[args.planner]
     prec = {"fp32": 0, "tf32x3": 1}[args.precision]
     low = {"auto": 0, "strided": 1, "permute": 2}[args.lowering]
@@ -257,13 +301,19 @@ def main():
     def step(record):
         q.qsa_state_reset(s)
         st = q.qsa_plan_execute(s, plan)
-        norm = q.qsa_expectation_z(s, 0)
-        vals, cnts = q.qsa_sample_counts(s, args.shots, seed=args.seed + 17)
-        zz = q.qsa_expectation_z(s, edge_mask)
+        if dm:
+            norm = q.qsa_dm_probabilities(s, n_dm, want_probs=False)[1]
+            zz = q.qsa_dm_expectation_z(s, n_dm, edge_mask)
+            nshot = 0
+        else:
+            norm = q.qsa_expectation_z(s, 0)
+            vals, cnts = q.qsa_sample_counts(s, args.shots, seed=args.seed + 17)
+            zz = q.qsa_expectation_z(s, edge_mask)
+            nshot = int(cnts.sum())
         if record:
             for k in agg:
                 agg[k] += st[k]
-        return norm, zz, int(cnts.sum())
+        return norm, zz, nshot
 
     for _ in range(args.warmup):
         step(False)
@@ -326,11 +376,15 @@ def main():
             st = q.qsa_apply_circuit(s, ops, q.make_opts(planner=planner, kmax=args.kmax, kmax_diag=kdiag,
                                                           precision=prec, lowering=low, victim=victim,
                                                           kmax_prod=args.kmax_prod))
-            vals, cnts = q.qsa_sample_counts(s, args.shots, seed=args.seed + 17)
+            if dm:
+                q.qsa_dm_probabilities(s, n_dm, want_probs=False)
+                d2h = 8.0
+            else:
+                vals, cnts = q.qsa_sample_counts(s, args.shots, seed=args.seed + 17)
+                d2h = 16.0 * len(vals) + 16
             torch.cuda.synchronize()
             e2e_times.append(time.perf_counter() - t0)
             h2d = st["h2d_bytes"]
-            d2h = 16.0 * len(vals) + 16
         e2e = {"value": ws * amp_updates / statistics.median(e2e_times), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
@@ -356,7 +410,7 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.cpu_qubits, args.seed, args.p)
+        cpu = cpu_baseline(args.cpu_qubits, args.seed, args.p, args.workload, args.dm_p)
 
     q.qsa_costmodel_set(None)
     q.qsa_plan_destroy(plan)
@@ -368,9 +422,13 @@ def main():
                 "dtype": ("c64 state, f32 arithmetic (k=5/6 products as 3xTF32 on tensor cores, f32 accumulation), "
                           "f64 reductions") if prec else "c64 state, f32 arithmetic, f64 reductions",
                 "data": "synthetic",
-                "config": {"workload": f"qaoa{n}_p{args.p}: random 3-regular graph, {len(ops)} gates, N={n} "
-                                       f"complex64 ({8 * (1 << n) / 2**30:g} GiB), {args.shots} shots + norm + <ZZ> "
-                                       f"per step",
+                "config": {"workload": (f"dm_ghz{n_dm}: noisy GHZ density matrix, {len(ops)} channels "
+                                        f"(depolarising p={args.dm_p:g} after each gate) lowered to superoperators, "
+                                        f"vec(rho) on 2n={n} qubits complex64 ({8 * (1 << n) / 2**30:g} GiB), "
+                                        f"trace + Tr(rho Z0 Z{n_dm - 1}) per step") if dm else
+                                       (f"qaoa{n}_p{args.p}: random 3-regular graph, {len(ops)} gates, N={n} "
+                                        f"complex64 ({8 * (1 << n) / 2**30:g} GiB), {args.shots} shots + norm + "
+                                        f"<ZZ> per step"),
                            "planner": args.planner, "kmax": args.kmax, "kmax_diag": kdiag,
                            "kmax_prod": args.kmax_prod,
                            "precision": args.precision,

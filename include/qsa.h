@@ -230,6 +230,48 @@ qsa_status qsa_apply_diag(qsa_state s, const int32_t* targets, int k, const doub
  * NULL). */
 qsa_status qsa_apply_product(qsa_state s, const int32_t* targets, int k, const double* factors);
 
+/* ---- density matrices (§IV-B density-matrix wrapper) ----------------------- */
+
+/* An n-qubit density matrix (2 <= n <= 17) is held as a 2n-qubit state
+ * (qsa_state_create(2n, ...)): vec(rho) stacked column-major, index
+ * row + 2^n * column, so the lower n qubits are row bits and qubit q + n is
+ * the column copy of qubit q; the state's |0..0> is |0..0><0..0|.  The state
+ * keeps its own layout map; the calls below resolve through it. */
+
+/* Host only: lower a k-qubit channel {E_i} of an n-qubit density matrix to
+ * one 2k-qubit operator of the vectorised state, so that channels and gates
+ * enter qsa_plan_create / qsa_apply_circuit as ordinary fused operators:
+ * targets_out (2k entries) = (targets, targets + n) -- row copies first, then
+ * column copies, target order kept in each group; matrix_out (2 * 16^k
+ * doubles, the qsa_op layout) = sum_i conj(E_i) (x) E_i with E_i on the row
+ * bits (index bits 0..k-1) and conj(E_i) on the column bits, summed in FP64.
+ * kraus: n_kraus x 2 * 4^k doubles (each E_i row-major, interleaved Re, Im).
+ * Errors: QSA_E_ARG (n outside 2..17, k outside 1..3, targets, n_kraus < 1,
+ * NULL). */
+qsa_status qsa_dm_superoperator(int n, const int32_t* targets, int k, const double* kraus, int n_kraus,
+                                int32_t* targets_out, double* matrix_out);
+
+/* rho <- sum_i E_i rho E_i^dagger: the superoperator sum_i conj(E_i) (x) E_i
+ * (formed once in FP64 on the host) applied as one fused 2k-qubit operator at
+ * (targets, targets + n) -- row copies first, original factor on the row
+ * bits -- through the dense path (precision: qsa_precision for 2k = 6).  A
+ * unitary is the one-operator channel.  targets: k distinct qubits of the
+ * density matrix (host), k in 1..3; kraus: host, n_kraus x 2 * 4^k doubles
+ * (each E_i row-major, interleaved Re, Im).  Trace preservation is the
+ * caller's (it is not checked).  Errors: QSA_E_ARG (state not 2n qubits,
+ * n outside 2..17, k, targets, n_kraus < 1, NULL). */
+qsa_status qsa_dm_apply_channel(qsa_state s, int n, const int32_t* targets, int k, const double* kraus,
+                                int n_kraus, int precision);
+
+/* Diagonal of rho: out_host (host, 2^n doubles, nullable) receives rho_xx in
+ * logical order (real parts, FP32 data summed in FP64); *trace_out (nullable)
+ * the sum.  Synchronises the stream.  Errors: QSA_E_ARG, QSA_E_NOMEM. */
+qsa_status qsa_dm_probabilities(qsa_state s, int n, double* out_host, double* trace_out);
+
+/* Tr(rho Z_mask) = sum_x rho_xx (-1)^popc(x & mask) over the density matrix's
+ * qubits (mask < 2^n), reduced in FP64 on the GPU.  Synchronises the stream. */
+qsa_status qsa_dm_expectation_z(qsa_state s, int n, uint64_t mask, double* out);
+
 /* ---- circuits: fusion planning + execution (§IV-C) ------------------------- */
 
 /* Fill *opts with the defaults: DP planner, kmax 4, kmax_diag 4, window 64,

@@ -114,6 +114,11 @@ _f = {
     "qsa_probabilities": _sig("qsa_probabilities", [_vp, _dp, _dp]),
     "qsa_probabilities_device": _sig("qsa_probabilities_device", [_vp, _vp, _dp]),
     "qsa_expectation_z": _sig("qsa_expectation_z", [_vp, _c.c_uint64, _dp]),
+    "qsa_dm_apply_channel": _sig("qsa_dm_apply_channel", [_vp, _c.c_int, _i32p, _c.c_int, _dp, _c.c_int,
+                                                           _c.c_int]),
+    "qsa_dm_superoperator": _sig("qsa_dm_superoperator", [_c.c_int, _i32p, _c.c_int, _dp, _c.c_int, _i32p, _dp]),
+    "qsa_dm_probabilities": _sig("qsa_dm_probabilities", [_vp, _c.c_int, _dp, _dp]),
+    "qsa_dm_expectation_z": _sig("qsa_dm_expectation_z", [_vp, _c.c_int, _c.c_uint64, _dp]),
     "qsa_sample_counts": _sig("qsa_sample_counts", [_vp, _c.c_uint64, _c.c_uint64, _u64p, _u64p, _c.c_size_t,
                                                     _szp]),
     "qsa_last_error": _sig("qsa_last_error", [], _c.c_char_p),
@@ -364,6 +369,55 @@ def qsa_probabilities_device(s: int, out_dev_ptr: int) -> float:
 def qsa_expectation_z(s: int, logical_mask: int) -> float:
     out = _c.c_double()
     _check(_f["qsa_expectation_z"](_vp(s), _c.c_uint64(logical_mask), _c.byref(out)))
+    return out.value
+
+
+# ---- density matrices ---------------------------------------------------------
+
+def qsa_dm_apply_channel(s: int, n: int, targets: Sequence[int], kraus, precision: int = 0) -> None:
+    """rho <- sum_i E_i rho E_i^dagger on the n-qubit density matrix held by
+    the 2n-qubit state ``s``; ``kraus`` is one 2^k x 2^k matrix or a stack."""
+    t, pt = _i32(targets)
+    d = 1 << len(t)
+    e = np.ascontiguousarray(np.asarray(kraus, dtype=np.complex128).reshape(-1, d, d))
+    _check(_f["qsa_dm_apply_channel"](_vp(s), n, pt, len(t), e.view(np.float64).ctypes.data_as(_dp), e.shape[0],
+                                      precision))
+
+
+class DensityOp:
+    """A channel lowered to one 2k-qubit operator of vec(rho) (the op shape the
+    planner takes: ``targets``, ``matrix``)."""
+
+    def __init__(self, targets, matrix):
+        self.targets = tuple(int(t) for t in targets)
+        self.matrix = matrix
+        self.diag = False
+
+
+def qsa_dm_superoperator(n: int, targets: Sequence[int], kraus) -> DensityOp:
+    """sum_i conj(E_i) (x) E_i on (targets, targets + n), built by the library."""
+    t, pt = _i32(targets)
+    k = len(t)
+    d = 1 << k
+    e = np.ascontiguousarray(np.asarray(kraus, dtype=np.complex128).reshape(-1, d, d))
+    to = np.zeros(2 * k, dtype=np.int32)
+    m = np.zeros((d * d, d * d), dtype=np.complex128)
+    _check(_f["qsa_dm_superoperator"](n, pt, k, e.view(np.float64).ctypes.data_as(_dp), e.shape[0],
+                                      to.ctypes.data_as(_i32p), m.view(np.float64).ctypes.data_as(_dp)))
+    return DensityOp(to, m)
+
+
+def qsa_dm_probabilities(s: int, n: int, want_probs: bool = True) -> Tuple[Optional[np.ndarray], float]:
+    """Diagonal of rho in logical order and its trace."""
+    tr = _c.c_double()
+    out = np.empty(1 << n, dtype=np.float64) if want_probs else None
+    _check(_f["qsa_dm_probabilities"](_vp(s), n, out.ctypes.data_as(_dp) if want_probs else None, _c.byref(tr)))
+    return out, tr.value
+
+
+def qsa_dm_expectation_z(s: int, n: int, mask: int) -> float:
+    out = _c.c_double()
+    _check(_f["qsa_dm_expectation_z"](_vp(s), n, _c.c_uint64(mask), _c.byref(out)))
     return out.value
 
 

@@ -82,6 +82,12 @@ cudaError_t launch_apply_diag(float2* psi, int n, const int* phys, int k, const 
 // row-major, 8 floats at d_fac + 8 j) on physical position phys[j].
 cudaError_t launch_apply_prod(float2* psi, int n, const int* phys, int k, const float* d_fac, cudaStream_t st,
                               uint64_t* launches);
+// Diagonal of a vectorised n-qubit density matrix held as a 2n-qubit state:
+// rho_xx to d_out (device, 2^n doubles, nullable) and
+// sum_x rho_xx (-1)^popc(x & mask) to *d_sum (device), via d_partials
+// (reduce_partials() doubles).
+cudaError_t launch_dm_diag(const float2* psi, int n, const int32_t* layout_host, uint64_t mask, double* d_out,
+                           double* d_partials, double* d_sum, cudaStream_t st, uint64_t* launches);
 
 // In-place swap of physical bit pairs (pa[i] <-> pb[i]), all positions distinct.
 cudaError_t launch_permute(float2* psi, int n, const int* pa, const int* pb, int npairs, cudaStream_t st,

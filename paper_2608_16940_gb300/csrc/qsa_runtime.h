@@ -28,6 +28,8 @@ struct qsa_state_s {
     size_t samp_cap = 0;
     float* d_mlp = nullptr;
     size_t mlp_cap = 0;
+    double* d_dm = nullptr;           // density-matrix diagonal readout
+    size_t dm_cap = 0;
     int* d_err = nullptr;             // device error word written by bounded waits
     // CUDA-event timers
     struct Pending {

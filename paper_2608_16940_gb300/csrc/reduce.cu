@@ -438,6 +438,32 @@ cudaError_t launch_batch_sample(const float2* states, int n, int n_traj, uint32_
     return cudaGetLastError();
 }
 
+// Diagonal of a vectorised density matrix (2n-qubit state, vec index
+// x + 2^n x): optional copy of rho_xx (real part) to out[], and per-block
+// FP64 partial sums of rho_xx (-1)^popc(x & mask) for the final reduction.
+__global__ void __launch_bounds__(kRedThreads) k_dm_diag(const float2* __restrict__ psi, Layout lay, int n,
+                                                          uint64_t mask, double* __restrict__ out,
+                                                          double* __restrict__ partials) {
+    const uint64_t dim = 1ull << n;
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    double acc = 0.0;
+    for (uint64_t x = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < dim; x += stride) {
+        const double p = psi[encode_logical(x | (x << n), lay)].x;
+        if (out) out[x] = p;
+        acc += (__popcll(x & mask) & 1) ? -p : p;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ double sh[kRedThreads / 32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kRedThreads / 32; ++w) t += sh[w];
+        partials[blockIdx.x] = t;
+    }
+}
+
 int reduce_partials() { return num_sms() * kRedBlocksPerSM; }
 
 cudaError_t launch_reduce_z(const float2* psi, int n, uint64_t physmask, double* d_partials, double* d_out,
@@ -450,6 +476,18 @@ cudaError_t launch_reduce_z(const float2* psi, int n, uint64_t physmask, double*
     }
     k_reduce_z<<<nb, kRedThreads, 0, st>>>(reinterpret_cast<const float4*>(psi), npairs, physmask, d_partials);
     k_finalize_sum<<<1, 1024, 0, st>>>(d_partials, nb, d_out);
+    *launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dm_diag(const float2* psi, int n, const int32_t* layout_host, uint64_t mask, double* d_out,
+                           double* d_partials, double* d_sum, cudaStream_t st, uint64_t* launches) {
+    Layout lay{};
+    lay.n = 2 * n;
+    for (int q = 0; q < 2 * n; ++q) lay.L[q] = layout_host[q];
+    const int nb = reduce_partials();
+    k_dm_diag<<<nb, kRedThreads, 0, st>>>(psi, lay, n, mask, d_out, d_partials);
+    k_finalize_sum<<<1, 1024, 0, st>>>(d_partials, nb, d_sum);
     *launches += 2;
     return cudaGetLastError();
 }

@@ -10,11 +10,7 @@ import workloads as W
 
 
 def _random_channel(k, r, rng):
-    """r Kraus operators of a random CPTP map: blocks of a random isometry."""
-    d = 1 << k
-    z = rng.standard_normal((r * d, d)) + 1j * rng.standard_normal((r * d, d))
-    q, _ = np.linalg.qr(z)
-    return [q[i * d:(i + 1) * d, :] for i in range(r)]
+    return W.random_kraus(k, r, rng)
 
 
 def test_pure_state_evolution_matches_state_vector_oracle():

@@ -261,6 +261,71 @@ def trajectory_batch(n_traj: int = 256, n: int = 20, dmin: int = 10, dmax: int =
     return trajs, depths
 
 
+# ---------------------------------------------------------------------------
+# Channels (Kraus lists) for the density-matrix path
+# ---------------------------------------------------------------------------
+@dataclass
+class Channel:
+    targets: Tuple[int, ...]
+    kraus: List[np.ndarray]       # each complex128, 2^k x 2^k, bit j <-> targets[j]
+    name: str = ""
+
+
+def pauli_string(s: int, k: int) -> np.ndarray:
+    """Tensor product of PAULIS[(s >> 2j) & 3] with factor j on tuple bit j."""
+    m = np.ones((1, 1), dtype=np.complex128)
+    for j in range(k):
+        m = np.kron(PAULIS[(s >> (2 * j)) & 3], m)
+    return m
+
+
+def depolarising_kraus(k: int, p: float) -> List[np.ndarray]:
+    """k-qubit depolarising noise, uniform over the 4^k - 1 non-identity Pauli
+    strings: sqrt(1-p) I and sqrt(p / (4^k - 1)) P."""
+    w = np.sqrt(p / (4 ** k - 1))
+    return [np.sqrt(1 - p) * np.eye(1 << k, dtype=np.complex128)] + [w * pauli_string(s, k)
+                                                                     for s in range(1, 4 ** k)]
+
+
+def amplitude_damping_kraus(gamma: float) -> List[np.ndarray]:
+    return [np.array([[1, 0], [0, np.sqrt(1 - gamma)]], dtype=np.complex128),
+            np.array([[0, np.sqrt(gamma)], [0, 0]], dtype=np.complex128)]
+
+
+def random_kraus(k: int, r: int, rng: np.random.Generator) -> List[np.ndarray]:
+    """r Kraus operators of a random trace-preserving map: the 2^k-row blocks
+    of a random (r 2^k) x 2^k isometry (QR of a complex Gaussian matrix)."""
+    d = 1 << k
+    z = rng.standard_normal((r * d, d)) + 1j * rng.standard_normal((r * d, d))
+    qm, _ = np.linalg.qr(z)
+    return [np.ascontiguousarray(qm[i * d:(i + 1) * d, :]) for i in range(r)]
+
+
+def noisy_ghz_channels(n: int, p: float = 1e-2) -> List[Channel]:
+    """GHZ preparation with depolarising noise p after the H and after each
+    CNOT (two-qubit depolarising on the CNOT's pair), the noisy-GHZ shape of
+    §V (routing benchmark); every gate is a one-operator channel."""
+    out: List[Channel] = []
+    for op in ghz_ops(n):
+        out.append(Channel(op.targets, [op.matrix], op.name))
+        out.append(Channel(op.targets, depolarising_kraus(op.k, p), f"dep{op.k}"))
+    return out
+
+
+def random_channel_circuit(n: int, n_ch: int, rng: np.random.Generator, kmax: int = 3) -> List[Channel]:
+    """A mix of Haar unitaries (one Kraus operator) and random channels of
+    1..kmax qubits with 1..4 Kraus operators on random target tuples."""
+    out: List[Channel] = []
+    for _ in range(n_ch):
+        k = int(rng.integers(1, kmax + 1))
+        t = tuple(int(v) for v in rng.choice(n, size=k, replace=False))
+        if rng.random() < 0.5:
+            out.append(Channel(t, [haar_unitary(1 << k, rng)], "u"))
+        else:
+            out.append(Channel(t, random_kraus(k, int(rng.integers(1, 5)), rng), "kraus"))
+    return out
+
+
 def random_state(n: int, seed: int = 0, zero_frac: float = 0.0) -> np.ndarray:
     """A normalised complex128 random state; a fraction of entries can be set
     exactly to zero (for sampler edge cases)."""
