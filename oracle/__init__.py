@@ -14,6 +14,9 @@ Contents
     target bits index) and the fused diagonal of a block of diagonal gates,
   - the product lowering of a block of one-qubit factors on distinct qubits
     and the grouping of a circuit into product units,
+  - layer blocks (one-qubit factors preceded by one- and two-qubit diagonal
+    gates on any qubits, one tile pass) and the commutation-aware grouping of
+    a circuit into them,
   - density-matrix evolution by Kraus operators, its column-major
     vectorisation and the superoperator of a channel,
   - the Kronecker embedding and block product used by fusion (§IV-C: "within a
@@ -187,6 +190,107 @@ def product_units(ops: Sequence, kmax_prod: int) -> List[Tuple[int, int]]:
             units.append((i, i + 1))
             i += 1
     return units
+
+
+# ---------------------------------------------------------------------------
+# Layer blocks: diagonal gates then a layer of one-qubit factors
+# ---------------------------------------------------------------------------
+LAYER_TILE_BITS = 12   # a tile of 2^12 amplitudes
+LAYER_LOW_BITS = 3     # its lowest 3 bits are the state's lowest 3 positions
+
+
+def layer_fits(positions: Iterable[int], n: int) -> bool:
+    """The factor positions fit one tile: a tile of T = min(12, n) bits keeps
+    the lowest min(3, T) positions, so at most T - min(3, T) factor positions
+    may lie above them."""
+    T = min(LAYER_TILE_BITS, n)
+    low = min(LAYER_LOW_BITS, T)
+    return sum(1 for p in positions if p >= low) <= T - low
+
+
+def apply_layer(psi: np.ndarray, diag_ops: Sequence, targets: Sequence[int], factors: Sequence[np.ndarray]) -> None:
+    """The layer block's definition (a structured fused block, §IV-D): every
+    diagonal gate, then the one-qubit factor j on targets[j] (distinct
+    qubits).  Applied gate by gate with ``apply``."""
+    for g in diag_ops:
+        apply(psi, g.targets, g.matrix)
+    for t, f in zip(targets, factors):
+        apply(psi, (t,), f)
+
+
+def layer_units(ops: Sequence, n: int, layout: Sequence[int] | None = None, lookahead: int = 256):
+    """Commutation-aware grouping into layer blocks.
+
+    Ops are taken from the front of the pending stream.  A stream whose first
+    op is neither one-qubit nor a diagonal gate on at most two qubits emits
+    that op as a plain unit.  Otherwise a block is grown by scanning the
+    pending ops in circuit order:
+
+    * a diagonal gate on k <= 2 qubits joins the diagonal part when none of
+      its qubits has a factor in the block yet and no skipped non-diagonal op
+      touches them (it then moves ahead of the skipped ops, which it commutes
+      with, and ahead of the block's factors, which act on other qubits);
+    * a one-qubit op joins the factor of its qubit (later ops on the left) when
+      no skipped op touches that qubit and the factor qubits' physical
+      positions still fit a tile (``layer_fits``);
+    * any other op is skipped and blocks its qubits: for everything, if it is
+      not diagonal; for non-diagonal ops only, if it is diagonal.
+
+    After more than ``lookahead`` skips the scan stops.  The block is the
+    diagonal part then the factors (each in circuit order); skipped ops stay
+    pending in order.  Returns (order, units): ``order`` lists the input op
+    indices in execution order and each unit is (start, end, is_layer, n_diag)
+    over ``order``, the first n_diag ops of a layer unit being its diagonal
+    part."""
+    L = list(range(n)) if layout is None else list(layout)
+    pending = list(range(len(ops)))
+    order: List[int] = []
+    units = []
+    while pending:
+        first = ops[pending[0]]
+        if not (len(first.targets) == 1 or (first.diag and len(first.targets) <= 2)):
+            units.append((len(order), len(order) + 1, False, 0))
+            order.append(pending.pop(0))
+            continue
+        diag_part, factor_part = [], []
+        fq = set()
+        blocked_nondiag, blocked_all = set(), set()
+        skips = 0
+        for idx in pending:
+            op = ops[idx]
+            Q = set(op.targets)
+            if op.diag and len(Q) <= 2 and not (Q & fq) and not (Q & blocked_nondiag):
+                diag_part.append(idx)
+            elif len(Q) == 1 and not (Q & blocked_all) and layer_fits([L[q] for q in fq | Q], n):
+                factor_part.append(idx)
+                fq |= Q
+            else:
+                blocked_all |= Q
+                if not op.diag:
+                    blocked_nondiag |= Q
+                skips += 1
+                if skips > lookahead:
+                    break
+        taken = set(diag_part) | set(factor_part)
+        start = len(order)
+        order += diag_part + factor_part
+        units.append((start, len(order), True, len(diag_part)))
+        pending = [x for x in pending if x not in taken]
+    return order, units
+
+
+def layer_block(ops: Sequence, idx: Sequence[int], n_diag: int):
+    """Split one layer unit (op indices in execution order, the first n_diag
+    of them diagonal gates) into its diagonal gates and its per-qubit factors
+    (qubits ascending, each the product of its ops in order, later ops on the
+    left)."""
+    diag_ops = [ops[i] for i in idx[:n_diag]]
+    fac = {}
+    for i in idx[n_diag:]:
+        q = ops[i].targets[0]
+        fac[q] = np.asarray(ops[i].matrix, dtype=np.complex128) @ fac.get(q, np.eye(2, dtype=np.complex128))
+    qs = sorted(fac)
+    return diag_ops, qs, [fac[q] for q in qs]
 
 
 def dm_zero(n: int) -> np.ndarray:
