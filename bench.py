@@ -239,7 +239,9 @@ def main():
     ap.add_argument("--planner", default="dp_mlp", choices=["per_gate", "greedy", "dp", "dp_mlp"])
     ap.add_argument("--kmax", type=int, default=6)
     ap.add_argument("--kmax-diag", type=int, default=12, help="diagonal-block cap (1..12)")
-    ap.add_argument("--kmax-prod", type=int, default=6, help="product-unit cap (0: off, 2..11)")
+    ap.add_argument("--kmax-prod", type=int, default=0, help="product-unit cap (0: off, 2..11)")
+    ap.add_argument("--layer", type=int, default=1, choices=[0, 1],
+                    help="1: layer units (diagonal gates + one-qubit factors in one tile pass)")
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3"])
     ap.add_argument("--lowering", default="auto", choices=["auto", "strided", "permute"])
     ap.add_argument("--victim", default="first_free", choices=["first_free", "farthest"],
@@ -282,7 +284,7 @@ def main():
     kdiag = args.kmax_diag
     victim = {"first_free": 0, "farthest": 1}[args.victim]
     opts = q.make_opts(planner=planner, kmax=args.kmax, kmax_diag=kdiag, precision=prec, lowering=low, timing=1,
-                       victim=victim, kmax_prod=args.kmax_prod)
+                       victim=victim, kmax_prod=args.kmax_prod, layer=args.layer)
 
     buf = torch.empty(1 << n, dtype=torch.complex64, device=dev)
     stream = torch.cuda.current_stream(dev).cuda_stream
@@ -296,7 +298,8 @@ def main():
     edge_mask = (1 << edges[0][0]) | (1 << edges[0][1])
 
     agg = {"apply_seconds": 0.0, "tc_seconds": 0.0, "permute_seconds": 0.0, "diag_seconds": 0.0,
-           "prod_seconds": 0.0, "blocks": 0, "permutes": 0, "tc_blocks": 0, "diag_blocks": 0, "prod_blocks": 0}
+           "prod_seconds": 0.0, "layer_seconds": 0.0, "blocks": 0, "passes": 0, "permutes": 0, "tc_blocks": 0,
+           "diag_blocks": 0, "prod_blocks": 0, "layer_blocks": 0}
 
     def step(record):
         q.qsa_state_reset(s)
@@ -343,7 +346,7 @@ def main():
     # roofline of the dominant fused-operator kernel: 16 B per amplitude per launch
     hbm_peak, peak_kind = _peaks()
     bytes_per_launch = 16.0 * (1 << n)
-    n_fp32 = agg["blocks"] - agg["tc_blocks"] - agg["diag_blocks"] - agg["prod_blocks"]
+    n_fp32 = agg["blocks"] - agg["tc_blocks"] - agg["diag_blocks"] - agg["prod_blocks"] - agg["layer_blocks"]
     kinds = []
     if n_fp32:
         kinds.append(("k_apply_fp32 (FP32 fused dense update)", agg["apply_seconds"], n_fp32))
@@ -353,6 +356,11 @@ def main():
         kinds.append(("k_apply_diag (diagonal streaming update)", agg["diag_seconds"], agg["diag_blocks"]))
     if agg["prod_blocks"]:
         kinds.append(("k_apply_prod (product of one-qubit factors)", agg["prod_seconds"], agg["prod_blocks"]))
+    if agg["layer_blocks"]:
+        # one pass per layer block unless its factors need more than one tile
+        n_layer_pass = agg["passes"] - agg["permutes"] - (agg["blocks"] - agg["layer_blocks"])
+        kinds.append(("k_apply_layer (diagonal gates + one-qubit factors, one tile pass)", agg["layer_seconds"],
+                      n_layer_pass))
     if agg["permutes"]:
         kinds.append(("k_permute (qubit permutation)", agg["permute_seconds"], agg["permutes"]))
     name, tot, cnt = max(kinds, key=lambda kv: kv[1])
@@ -375,7 +383,7 @@ def main():
             q.qsa_state_reset(s)
             st = q.qsa_apply_circuit(s, ops, q.make_opts(planner=planner, kmax=args.kmax, kmax_diag=kdiag,
                                                           precision=prec, lowering=low, victim=victim,
-                                                          kmax_prod=args.kmax_prod))
+                                                          kmax_prod=args.kmax_prod, layer=args.layer))
             if dm:
                 q.qsa_dm_probabilities(s, n_dm, want_probs=False)
                 d2h = 8.0
@@ -430,13 +438,13 @@ def main():
                                         f"complex64 ({8 * (1 << n) / 2**30:g} GiB), {args.shots} shots + norm + "
                                         f"<ZZ> per step"),
                            "planner": args.planner, "kmax": args.kmax, "kmax_diag": kdiag,
-                           "kmax_prod": args.kmax_prod,
+                           "kmax_prod": args.kmax_prod, "layer": args.layer,
                            "precision": args.precision,
                            "lowering": args.lowering, "victim": args.victim, "fused_blocks": pinfo["blocks"],
                            "l2": "state 8 GiB > 129 MB L2; no flush needed", "parallelism": f"replicas x{ws}"},
                 "gpu_launches": launches, "clocks": clocks, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "passes_per_step": (agg["blocks"] + agg["permutes"]) / args.steps,
-                "hbm_gbs_step": (agg["blocks"] + agg["permutes"]) / args.steps * bytes_per_launch / per_step / 1e9,
+                "passes_per_step": agg["passes"] / args.steps,
+                "hbm_gbs_step": agg["passes"] / args.steps * bytes_per_launch / per_step / 1e9,
                 "cost_model": cm, "check": {"norm": norm, "zz_edge0": zz, "shots": nshot}}
         line.update(extra)
         print(json.dumps(line), flush=True)

@@ -69,6 +69,12 @@ typedef struct qsa_state_s* qsa_state;
  * (2^11-amplitude tiles) when at most 6 of them lie above the tile's
  * contiguous low bits, else in several passes. */
 #define QSA_MAX_PROD 11
+/* Layer blocks (qsa_apply_layer, layer plan blocks): tiles of 2^12
+ * amplitudes whose 3 lowest bits are the state's 3 lowest positions, so at
+ * most 9 factor positions may lie at 3 or above; up to 12 factors. */
+#define QSA_LAYER_TILE_BITS 12
+#define QSA_LAYER_LOW_BITS 3
+#define QSA_MAX_LAYER 12
 
 /* Lowering of one fused dense operator (§III R4: the backend picks the
  * concrete kernel once the physical targets are known). */
@@ -127,6 +133,11 @@ typedef struct {
                                on at most this many qubits become product units, applied as one product
                                block (one pass) while they stay blocks of their own (§IV-D structured
                                blocks); not used by per-gate plans or batches */
+    int32_t layer;          /* 1: group the circuit into layer units first (qsa_apply_layer: one- and
+                               two-qubit QSA_OP_DIAG ops, then one-qubit ops on qubits whose positions
+                               fit a tile), moving ops only across ops they commute with (lookahead 256
+                               skipped ops); a layer unit runs as one layer block while it stays a block
+                               of its own.  Replaces kmax_prod.  0: off.  Not used by batches */
 } qsa_plan_opts;
 
 typedef struct {
@@ -145,6 +156,8 @@ typedef struct {
     double diag_seconds;    /* device time of diagonal streaming kernels */
     uint64_t prod_blocks;   /* product blocks (one-qubit factors) applied */
     double prod_seconds;    /* device time of product kernels */
+    uint64_t layer_blocks;  /* layer blocks applied */
+    double layer_seconds;   /* device time of layer kernels */
 } qsa_run_stats;
 
 /* A compiled circuit: the planner's blocks with their fused FP32 matrices. */
@@ -230,6 +243,26 @@ qsa_status qsa_apply_diag(qsa_state s, const int32_t* targets, int k, const doub
  * NULL). */
 qsa_status qsa_apply_product(qsa_state s, const int32_t* targets, int k, const double* factors);
 
+/* Layer block: every diagonal op diag_ops[0..n_diag) (k = 1 or 2, diagonal
+ * matrix; off-diagonal entries must be zero), then the product of the 2x2
+ * factor j on logical qubit targets[j] (distinct qubits; a diagonal op may
+ * share qubits with factors, it acts first) -- a structured fused block
+ * (§IV-D), in one pass when N >= 12 and at most QSA_LAYER_TILE_BITS -
+ * QSA_LAYER_LOW_BITS factor positions lie at QSA_LAYER_LOW_BITS or above
+ * (else the factors are split over several passes, the diagonal ops in the
+ * first).  Per tile of 2^12 amplitudes the diagonal ops become a 2^12-entry
+ * table over the tile's bits (ops with every qubit in the tile), one-qubit
+ * phases folded into the factors (ops with one qubit in the tile) and a scalar
+ * (ops with none), so any number of them costs one pass.  Matrices and
+ * factors are rounded once to FP32 (tables formed in FP64).  factors: host,
+ * 8 doubles per factor (row-major 2x2, interleaved Re, Im); k = 0 applies the
+ * diagonal ops only.  N < 12 runs the ops on the diagonal and product kernels.
+ * The layout is unchanged.  Errors: QSA_E_ARG (k outside 0..QSA_MAX_LAYER or
+ * > N, bad / repeated target, a diagonal op that is not k = 1, 2 or not
+ * diagonal, NULL). */
+qsa_status qsa_apply_layer(qsa_state s, const qsa_op* diag_ops, size_t n_diag, const int32_t* targets, int k,
+                           const double* factors);
+
 /* ---- density matrices (§IV-B density-matrix wrapper) ----------------------- */
 
 /* An n-qubit density matrix (2 <= n <= 17) is held as a 2n-qubit state
@@ -312,6 +345,17 @@ qsa_status qsa_plan_info(qsa_plan p, size_t* n_blocks, size_t* n_ops, int* max_w
 
 /* First input op and width of every block (capacity >= n_blocks, else QSA_E_RANGE). */
 qsa_status qsa_plan_blocks(qsa_plan p, size_t* first_op, int32_t* widths, size_t capacity);
+
+/* Execution order of the input ops (order[i] = input index of the i-th op
+ * executed; the identity unless opts.layer moved ops); first_op of
+ * qsa_plan_blocks indexes this order.  capacity >= n_ops, else QSA_E_RANGE. */
+qsa_status qsa_plan_order(qsa_plan p, size_t* order, size_t capacity);
+
+/* Kind of every block (0 dense, 1 diagonal, 2 product, 3 layer) and, for
+ * layer blocks, how many of its ops (the first ones in execution order) are
+ * its diagonal part (0 for other kinds).  Nullable outputs; capacity >=
+ * n_blocks, else QSA_E_RANGE. */
+qsa_status qsa_plan_block_kinds(qsa_plan p, int32_t* kinds, int32_t* n_diag, size_t capacity);
 
 /* Host-only replay of the promotions QSA_LOWER_PERMUTE makes for this plan
  * (§IV-D demand model; no data moves): starting from layout_in (host,

@@ -27,7 +27,7 @@ QSA_LOWER_AUTO, QSA_LOWER_STRIDED, QSA_LOWER_PERMUTE = 0, 1, 2
 QSA_PREC_FP32, QSA_PREC_TF32X3 = 0, 1
 QSA_PLAN_PER_GATE, QSA_PLAN_GREEDY, QSA_PLAN_DP, QSA_PLAN_DP_MLP = 0, 1, 2, 3
 QSA_OP_DIAG = 1
-QSA_MAX_K, QSA_MAX_DIAG, QSA_MAX_PROD = 6, 12, 11
+QSA_MAX_K, QSA_MAX_DIAG, QSA_MAX_PROD, QSA_MAX_LAYER = 6, 12, 11, 12
 QSA_VICTIM_FIRST_FREE, QSA_VICTIM_FARTHEST = 0, 1
 MLP_PARAMS = 6657
 MLP_IN = 37
@@ -58,7 +58,7 @@ class qsa_op(_c.Structure):
 class qsa_plan_opts(_c.Structure):
     _fields_ = [("planner", _c.c_int32), ("kmax", _c.c_int32), ("kmax_diag", _c.c_int32), ("window", _c.c_int32),
                 ("rounds", _c.c_int32), ("precision", _c.c_int32), ("lowering", _c.c_int32),
-                ("timing", _c.c_int32), ("victim", _c.c_int32), ("kmax_prod", _c.c_int32)]
+                ("timing", _c.c_int32), ("victim", _c.c_int32), ("kmax_prod", _c.c_int32), ("layer", _c.c_int32)]
 
 
 class qsa_run_stats(_c.Structure):
@@ -66,7 +66,8 @@ class qsa_run_stats(_c.Structure):
                 ("hbm_bytes", _c.c_double), ("blocks", _c.c_uint64), ("passes", _c.c_uint64),
                 ("permutes", _c.c_uint64), ("tc_blocks", _c.c_uint64), ("launches", _c.c_uint64),
                 ("h2d_bytes", _c.c_double), ("tc_seconds", _c.c_double), ("diag_blocks", _c.c_uint64),
-                ("diag_seconds", _c.c_double), ("prod_blocks", _c.c_uint64), ("prod_seconds", _c.c_double)]
+                ("diag_seconds", _c.c_double), ("prod_blocks", _c.c_uint64), ("prod_seconds", _c.c_double),
+                ("layer_blocks", _c.c_uint64), ("layer_seconds", _c.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -95,6 +96,9 @@ _f = {
     "qsa_apply_fused_ex": _sig("qsa_apply_fused_ex", [_vp, _i32p, _c.c_int, _dp, _c.c_int, _c.c_int]),
     "qsa_apply_diag": _sig("qsa_apply_diag", [_vp, _i32p, _c.c_int, _dp]),
     "qsa_apply_product": _sig("qsa_apply_product", [_vp, _i32p, _c.c_int, _dp]),
+    "qsa_apply_layer": _sig("qsa_apply_layer", [_vp, _vp, _c.c_size_t, _i32p, _c.c_int, _dp]),
+    "qsa_plan_order": _sig("qsa_plan_order", [_vp, _vp, _c.c_size_t]),
+    "qsa_plan_block_kinds": _sig("qsa_plan_block_kinds", [_vp, _i32p, _i32p, _c.c_size_t]),
     "qsa_plan_opts_default": _sig("qsa_plan_opts_default", [_c.POINTER(qsa_plan_opts)], None),
     "qsa_plan_circuit": _sig("qsa_plan_circuit", [_c.POINTER(qsa_op), _c.c_size_t, _c.c_int,
                                                   _c.POINTER(qsa_plan_opts), _szp, _szp]),
@@ -224,6 +228,18 @@ def qsa_apply_product(s: int, targets: Sequence[int], factors) -> None:
     _check(_f["qsa_apply_product"](_vp(s), pt, len(t), f.view(np.float64).ctypes.data_as(_dp)))
 
 
+def qsa_apply_layer(s: int, diag_ops, targets: Sequence[int], factors) -> None:
+    """Diagonal ops (objects with ``targets`` and a diagonal ``matrix``, k = 1
+    or 2), then the 2x2 factor j on targets[j], in one layer block."""
+    oa = diag_ops if isinstance(diag_ops, OpArray) else OpArray(list(diag_ops))
+    t = np.ascontiguousarray(np.asarray(list(targets), dtype=np.int32))
+    f = np.ascontiguousarray(np.asarray(factors, dtype=np.complex128).reshape(len(t), 2, 2)) if len(t) else \
+        np.zeros((1, 2, 2), dtype=np.complex128)
+    _check(_f["qsa_apply_layer"](_vp(s), _c.cast(oa.arr, _vp) if oa.n else None, oa.n,
+                                 t.ctypes.data_as(_i32p) if len(t) else None, len(t),
+                                 f.view(np.float64).ctypes.data_as(_dp)))
+
+
 def qsa_apply_diag(s: int, targets: Sequence[int], diag) -> None:
     """Diagonal operator on ``targets``: ``diag`` holds 2^k complex entries,
     entry c for the target bits c (bit j = target j)."""
@@ -316,6 +332,24 @@ def qsa_plan_blocks(p: int) -> Tuple[List[int], List[int]]:
     w = np.zeros(max(1, nb), dtype=np.int32)
     _check(_f["qsa_plan_blocks"](_vp(p), fo, w.ctypes.data_as(_i32p), nb))
     return [int(fo[i]) for i in range(nb)], [int(v) for v in w[:nb]]
+
+
+def qsa_plan_order(p: int) -> List[int]:
+    """Execution order of the input ops (moved by layer grouping)."""
+    n = qsa_plan_info(p)["ops"]
+    o = (_c.c_size_t * max(1, n))()
+    _check(_f["qsa_plan_order"](_vp(p), _c.cast(o, _vp), n))
+    return [int(o[i]) for i in range(n)]
+
+
+def qsa_plan_block_kinds(p: int) -> Tuple[List[int], List[int]]:
+    """Per block: kind (0 dense, 1 diagonal, 2 product, 3 layer) and the size
+    of a layer block's diagonal part."""
+    nb = qsa_plan_info(p)["blocks"]
+    k = np.zeros(max(1, nb), dtype=np.int32)
+    d = np.zeros(max(1, nb), dtype=np.int32)
+    _check(_f["qsa_plan_block_kinds"](_vp(p), k.ctypes.data_as(_i32p), d.ctypes.data_as(_i32p), nb))
+    return [int(v) for v in k[:nb]], [int(v) for v in d[:nb]]
 
 
 def qsa_plan_promotions(p: int, n_qubits: int, victim: int, layout=None) -> Tuple[int, int, List[int]]:

@@ -1,0 +1,291 @@
+// Layer blocks (a structured fused block, §IV-D "structured blocks may use
+// cheaper lowerings"): one- and two-qubit diagonal gates on any qubits, then a
+// layer of one-qubit factors, in one pass over the state.
+//
+// A tile is 2^12 amplitudes: the m lowest positions (m >= 3, one run of 2^m
+// contiguous amplitudes) and nx = 12 - m higher positions holding the
+// factors' remaining qubits.  Relative to a tile, every diagonal gate falls
+// into one of three classes, precomputed on the host:
+//   all-in  (its qubits are tile bits): multiplied into one 2^12-entry table
+//           over the tile-local index, applied elementwise;
+//   cross   (one qubit in the tile, one outside): with the outside bit fixed
+//           by the tile, a one-qubit phase on its tile bit, folded into that
+//           bit's factor (F' = F diag(d0, d1));
+//   out     (no qubit in the tile): a scalar per tile, folded into one factor.
+// Per tile: 16-byte cp.async copies into a 2-stage ring (XOR-swizzled 16-byte
+// chunks), then three register rounds over tile bits 0-3, 4-7 and 8-11 (each
+// thread holds the 16 amplitudes that differ in the round's bits and applies
+// the round's factors as butterflies); the last active round stores to HBM.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "qsa_device.cuh"
+#include "qsa_internal.h"
+
+namespace qsa {
+
+namespace {
+
+using namespace dev;
+
+constexpr int kLT = 12;                 // tile bits
+constexpr int kLAmps = 1 << kLT;        // amplitudes per tile
+constexpr int kLThreads = 256;
+constexpr int kLStages = 2;
+
+struct LayerArgs {
+    float2* psi;
+    uint64_t ntiles;
+    int m, nx;
+    int xpos[kLT];            // positions of tile bits m..11, ascending
+    uint32_t active;          // tile bits with a factor or a per-tile phase
+    int first_active;         // the bit whose factor absorbs the per-tile scalar
+    int ncross, nout;
+    int cstart[kLT + 1];      // cross gates of tile bit b: [cstart[b], cstart[b + 1])
+    const float2* fac;        // kLT x 4 complex (2x2 row-major), identity where no factor
+    const LayerGate* cross;   // a = tile bit, b = outside position, d[2 * o + v]
+    const LayerGate* outg;    // a, b = positions (b < 0: one qubit), d[v_a + 2 v_b]
+    const float2* din;        // 2^12 entries over tile-local bits, or nullptr
+};
+
+// Slot of tile-local amplitude j: 16-byte chunk c = j / 2 is stored at
+// c ^ ((c >> 3) & 7), which spreads each round's warp accesses over all banks.
+__device__ __forceinline__ int lsw(int j) {
+    const int c = j >> 1;
+    return ((c ^ ((c >> 3) & 7)) << 1) | (j & 1);
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+__device__ __forceinline__ uint64_t layer_base(const LayerArgs& a, uint64_t t) {
+    uint64_t b = t << a.m;
+#pragma unroll
+    for (int e = 0; e < kLT; ++e)
+        if (e < a.nx) b = insert_zero(b, a.xpos[e]);
+    return b;
+}
+
+__device__ __forceinline__ uint64_t layer_global(const LayerArgs& a, const uint64_t* runoff, uint64_t base, int j) {
+    return base | static_cast<uint64_t>(j & ((1 << a.m) - 1)) | runoff[j >> a.m];
+}
+
+// v[i], v[i | 2^LB] <- F (v[i], v[i | 2^LB]) for the 8 pairs.
+template <int LB>
+__device__ __forceinline__ void butterfly(float2 (&v)[16], const float2* F) {
+    const float2 f00 = F[0], f01 = F[1], f10 = F[2], f11 = F[3];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        if ((i >> LB) & 1) continue;
+        const float2 x0 = v[i], x1 = v[i | (1 << LB)];
+        v[i] = make_float2(f00.x * x0.x - f00.y * x0.y + f01.x * x1.x - f01.y * x1.y,
+                           f00.x * x0.y + f00.y * x0.x + f01.x * x1.y + f01.y * x1.x);
+        v[i | (1 << LB)] = make_float2(f10.x * x0.x - f10.y * x0.y + f11.x * x1.x - f11.y * x1.y,
+                                       f10.x * x0.y + f10.y * x0.x + f11.x * x1.y + f11.y * x1.x);
+    }
+}
+
+// One round over tile bits 4R..4R+3: read the stage, apply the diagonal table
+// (R = 0) and the round's factors, write back to the stage or (last round) to
+// HBM.
+template <int R>
+__device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, const float2* din_s,
+                                            const float2* tf, const uint64_t* runoff, uint64_t base, bool last) {
+    const int t = threadIdx.x;
+    const int jb = (t & ((1 << (4 * R)) - 1)) | ((t >> (4 * R)) << (4 * R + 4));
+    float2 v[16];
+    if constexpr (R == 0) {
+#pragma unroll
+        for (int i = 0; i < 16; i += 2) {
+            const float4 p = *reinterpret_cast<const float4*>(stage + lsw(jb | i));
+            v[i] = make_float2(p.x, p.y);
+            v[i + 1] = make_float2(p.z, p.w);
+        }
+        if (din_s) {
+#pragma unroll
+            for (int i = 0; i < 16; i += 2) {
+                const float4 d = *reinterpret_cast<const float4*>(din_s + lsw(jb | i));
+                v[i] = cmulf(v[i], make_float2(d.x, d.y));
+                v[i + 1] = cmulf(v[i + 1], make_float2(d.z, d.w));
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = stage[lsw(jb | (i << (4 * R)))];
+    }
+    const uint32_t act = (a.active >> (4 * R)) & 15u;
+    if (act & 1u) butterfly<0>(v, tf + 4 * (4 * R + 0));
+    if (act & 2u) butterfly<1>(v, tf + 4 * (4 * R + 1));
+    if (act & 4u) butterfly<2>(v, tf + 4 * (4 * R + 2));
+    if (act & 8u) butterfly<3>(v, tf + 4 * (4 * R + 3));
+    if (last) {
+        if constexpr (R == 0) {
+            // m >= 3: amplitudes jb | i and jb | (i + 1) are adjacent in HBM
+#pragma unroll
+            for (int i = 0; i < 16; i += 2)
+                __stcs(reinterpret_cast<float4*>(a.psi + layer_global(a, runoff, base, jb | i)),
+                       make_float4(v[i].x, v[i].y, v[i + 1].x, v[i + 1].y));
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                __stcs(a.psi + layer_global(a, runoff, base, jb | (i << (4 * R))), v[i]);
+        }
+    } else {
+        if constexpr (R == 0) {
+#pragma unroll
+            for (int i = 0; i < 16; i += 2)
+                *reinterpret_cast<float4*>(stage + lsw(jb | i)) = make_float4(v[i].x, v[i].y, v[i + 1].x, v[i + 1].y);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) stage[lsw(jb | (i << (4 * R)))] = v[i];
+        }
+    }
+}
+
+// Per-tile factors: the block factor of each active bit times the phases of
+// its cross gates (outside bit read from the tile's base index), the first
+// active bit also times the product of the out gates.  Run by warp 0.
+__device__ __forceinline__ void tile_factors(const LayerArgs& a, uint64_t base, float2* tf) {
+    const int lane = threadIdx.x & 31;
+    float2 sc = make_float2(1.f, 0.f);
+    for (int g = lane; g < a.nout; g += 32) {
+        const LayerGate& G = a.outg[g];
+        int v = static_cast<int>((base >> G.a) & 1ull);
+        if (G.b >= 0) v |= static_cast<int>((base >> G.b) & 1ull) << 1;
+        sc = cmulf(sc, G.d[v]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float2 other;
+        other.x = __shfl_xor_sync(0xffffffffu, sc.x, o);
+        other.y = __shfl_xor_sync(0xffffffffu, sc.y, o);
+        sc = cmulf(sc, other);
+    }
+    if (lane < kLT && ((a.active >> lane) & 1u)) {
+        float2 d0 = make_float2(1.f, 0.f), d1 = make_float2(1.f, 0.f);
+        for (int g = a.cstart[lane]; g < a.cstart[lane + 1]; ++g) {
+            const LayerGate& G = a.cross[g];
+            const int o = static_cast<int>((base >> G.b) & 1ull);
+            d0 = cmulf(d0, G.d[2 * o]);
+            d1 = cmulf(d1, G.d[2 * o + 1]);
+        }
+        if (lane == a.first_active) {
+            d0 = cmulf(d0, sc);
+            d1 = cmulf(d1, sc);
+        }
+        const float2* F = a.fac + 4 * lane;
+        tf[4 * lane + 0] = cmulf(F[0], d0);
+        tf[4 * lane + 1] = cmulf(F[1], d1);
+        tf[4 * lane + 2] = cmulf(F[2], d0);
+        tf[4 * lane + 3] = cmulf(F[3], d1);
+    }
+}
+
+__global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* stage = reinterpret_cast<float2*>(smem_raw);                  // kLStages x 4096
+    uint64_t* runoff = reinterpret_cast<uint64_t*>(stage + kLStages * kLAmps);  // 512
+    float2* tf = reinterpret_cast<float2*>(runoff + 512);                  // 12 x 4
+    float2* din_s = a.din ? tf + 4 * kLT : nullptr;                        // 4096 (swizzled)
+
+    for (int r = threadIdx.x; r < (1 << a.nx); r += blockDim.x) {
+        uint64_t off = 0;
+        for (int e = 0; e < a.nx; ++e)
+            if ((r >> e) & 1) off |= 1ull << a.xpos[e];
+        runoff[r] = off;
+    }
+    const bool dynamic = a.ncross > 0 || a.nout > 0;
+    if (!dynamic)
+        for (int i = threadIdx.x; i < 4 * kLT; i += blockDim.x) tf[i] = a.fac[i];
+    if (din_s)
+        for (int j = threadIdx.x; j < kLAmps; j += blockDim.x) din_s[lsw(j)] = a.din[j];
+    __syncthreads();
+
+    // rounds that do work; the last of them writes to HBM
+    int first = -1, last = -1;
+    for (int r = 0; r < 3; ++r)
+        if (((a.active >> (4 * r)) & 15u) || (r == 0 && din_s)) {
+            if (first < 0) first = r;
+            last = r;
+        }
+
+    const uint64_t stride = gridDim.x;
+    auto load = [&](uint64_t t, float2* st) {
+        const uint64_t base = layer_base(a, t);
+        for (int c = threadIdx.x; c < kLAmps / 2; c += blockDim.x)
+            cp_async16(st + lsw(2 * c), a.psi + layer_global(a, runoff, base, 2 * c));
+    };
+    if (blockIdx.x < a.ntiles) load(blockIdx.x, stage);
+    cp_async_commit();
+    int cur = 0;
+    for (uint64_t t = blockIdx.x; t < a.ntiles; t += stride) {
+        const uint64_t tn = t + stride;
+        if (tn < a.ntiles) load(tn, stage + (cur ^ 1) * kLAmps);
+        cp_async_commit();
+        const uint64_t base = layer_base(a, t);
+        if (dynamic && threadIdx.x < 32) tile_factors(a, base, tf);
+        cp_async_wait<1>();
+        __syncthreads();
+        float2* st = stage + cur * kLAmps;
+        if (first == 0) {
+            layer_round<0>(a, st, din_s, tf, runoff, base, last == 0);
+            if (last > 0) __syncthreads();
+        }
+        if (first <= 1 && last >= 1 && ((a.active >> 4) & 15u)) {
+            layer_round<1>(a, st, din_s, tf, runoff, base, last == 1);
+            if (last > 1) __syncthreads();
+        }
+        if (last == 2) layer_round<2>(a, st, din_s, tf, runoff, base, true);
+        __syncthreads();
+        cur ^= 1;
+    }
+    cp_async_wait<0>();
+}
+
+}  // namespace
+
+size_t layer_smem_bytes(bool with_din) {
+    return sizeof(float2) * kLStages * kLAmps + sizeof(uint64_t) * 512 + sizeof(float2) * 4 * kLT +
+           (with_din ? sizeof(float2) * kLAmps : 0);
+}
+
+cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const unsigned char* d_payload,
+                               const LayerPayload& p, cudaStream_t st, uint64_t* launches) {
+    if (n < kLT || g.m + g.nx != kLT || g.m < 3) return cudaErrorInvalidValue;
+    LayerArgs a{};
+    a.psi = psi;
+    a.ntiles = 1ull << (n - kLT);
+    a.m = g.m;
+    a.nx = g.nx;
+    for (int e = 0; e < kLT; ++e) a.xpos[e] = e < g.nx ? g.xpos[e] : 0;
+    a.active = p.active;
+    a.first_active = p.first_active;
+    a.ncross = p.ncross;
+    a.nout = p.nout;
+    for (int b = 0; b <= kLT; ++b) a.cstart[b] = p.cstart[b];
+    a.fac = reinterpret_cast<const float2*>(d_payload + p.off_fac);
+    a.cross = reinterpret_cast<const LayerGate*>(d_payload + p.off_cross);
+    a.outg = reinterpret_cast<const LayerGate*>(d_payload + p.off_out);
+    a.din = p.has_din ? reinterpret_cast<const float2*>(d_payload + p.off_din) : nullptr;
+    const size_t smem = layer_smem_bytes(p.has_din);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_apply_layer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(layer_smem_bytes(true)));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_apply_layer, kLThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    uint64_t grid = static_cast<uint64_t>(num_sms()) * occ;
+    if (grid > a.ntiles) grid = a.ntiles;
+    k_apply_layer<<<static_cast<unsigned>(grid), kLThreads, smem, st>>>(a);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+}  // namespace qsa

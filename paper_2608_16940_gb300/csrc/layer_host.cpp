@@ -1,0 +1,296 @@
+// Host side of layer blocks (§IV-D structured fused blocks): tile geometry
+// for a set of factor positions, classification of the diagonal ops relative
+// to the tile (all-in / cross / out), the 2^12-entry table of the all-in ops
+// (formed in FP64), the device payload of each pass, and qsa_apply_layer.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "qsa.h"
+#include "qsa_internal.h"
+#include "qsa_runtime.h"
+
+namespace qsa {
+
+namespace {
+
+constexpr int kTile = QSA_LAYER_TILE_BITS;
+constexpr int kLow = QSA_LAYER_LOW_BITS;
+
+// Largest m in [kLow, kTile] with m + #{pos >= m} <= kTile; the tile's extra
+// bits are those positions.  For N >= 12 the chosen m gives exactly kTile
+// tile bits.
+bool layer_geom(const std::vector<int>& pos, LayerGeom* g) {
+    for (int m = kTile; m >= kLow; --m) {
+        std::vector<int> hi;
+        for (int p : pos)
+            if (p >= m) hi.push_back(p);
+        if (m + static_cast<int>(hi.size()) <= kTile) {
+            std::sort(hi.begin(), hi.end());
+            g->m = m;
+            g->nx = static_cast<int>(hi.size());
+            for (int e = 0; e < kTile; ++e) g->xpos[e] = e < g->nx ? hi[e] : 0;
+            return g->m + g->nx == kTile;
+        }
+    }
+    return false;
+}
+
+int tile_bit(const LayerGeom& g, int p) {
+    if (p < g.m) return p;
+    for (int e = 0; e < g.nx; ++e)
+        if (g.xpos[e] == p) return g.m + e;
+    return -1;
+}
+
+void align16(std::vector<unsigned char>* b) {
+    while (b->size() % 16) b->push_back(0);
+}
+
+template <typename T>
+size_t append(std::vector<unsigned char>* b, const T* data, size_t count) {
+    align16(b);
+    const size_t off = b->size();
+    b->resize(off + sizeof(T) * count);
+    if (count) std::memcpy(b->data() + off, data, sizeof(T) * count);
+    return off;
+}
+
+float2 f2(std::complex<double> z) { return make_float2(static_cast<float>(z.real()), static_cast<float>(z.imag())); }
+
+// One pass: factors fsel (indices into spec.f), the diagonal ops if with_diag.
+// Returns false when there is nothing to apply.
+bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vector<int>& fsel, bool with_diag,
+                  std::vector<unsigned char>* bytes, LayerLaunch* out) {
+    std::vector<int> pos;
+    for (int j : fsel) pos.push_back(L[spec.t[j]]);
+    LayerGeom g;
+    if (!layer_geom(pos, &g)) return false;
+    (void)n;
+    LayerPayload p;
+    std::vector<std::array<std::complex<double>, 4>> fac(kTile, {1.0, 0.0, 0.0, 1.0});
+    for (size_t i = 0; i < fsel.size(); ++i) {
+        const int b = tile_bit(g, pos[i]);
+        fac[b] = spec.f[fsel[i]];
+        p.active |= 1u << b;
+    }
+    std::vector<LayerGate> cross, outg;
+    std::vector<std::complex<double>> din;
+    if (with_diag) {
+        for (const LayerDiagOp& op : spec.diag) {
+            const int p0 = L[op.q[0]], b0 = tile_bit(g, p0);
+            const int p1 = op.k == 2 ? L[op.q[1]] : -1, b1 = op.k == 2 ? tile_bit(g, p1) : -1;
+            if (b0 >= 0 && (op.k == 1 || b1 >= 0)) {
+                if (din.empty()) din.assign(1u << kTile, 1.0);
+                for (uint32_t j = 0; j < (1u << kTile); ++j) {
+                    int c = static_cast<int>((j >> b0) & 1u);
+                    if (op.k == 2) c |= static_cast<int>((j >> b1) & 1u) << 1;
+                    din[j] *= op.d[c];
+                }
+            } else if (op.k == 2 && (b0 >= 0) != (b1 >= 0)) {
+                // one qubit in the tile (v), one outside (o): d[2 o + v]
+                LayerGate G{};
+                const bool first_in = b0 >= 0;
+                G.a = first_in ? b0 : b1;
+                G.b = first_in ? p1 : p0;
+                for (int o = 0; o < 2; ++o)
+                    for (int v = 0; v < 2; ++v) G.d[2 * o + v] = f2(op.d[first_in ? (v | (o << 1)) : (o | (v << 1))]);
+                cross.push_back(G);
+                p.active |= 1u << G.a;
+            } else {
+                LayerGate G{};
+                G.a = p0;
+                G.b = p1;
+                for (int c = 0; c < (1 << op.k); ++c) G.d[c] = f2(op.d[c]);
+                outg.push_back(G);
+            }
+        }
+    }
+    if (!outg.empty() && p.active == 0) p.active = 1u;   // the scalar needs a factor to ride on
+    if (p.active == 0 && din.empty()) return false;
+    std::stable_sort(cross.begin(), cross.end(), [](const LayerGate& x, const LayerGate& y) { return x.a < y.a; });
+    p.ncross = static_cast<int>(cross.size());
+    p.nout = static_cast<int>(outg.size());
+    for (int b = 0, c = 0; b <= kTile; ++b) {
+        while (c < p.ncross && cross[c].a < b) ++c;
+        p.cstart[b] = c;
+    }
+    p.first_active = 0;   // the lowest active bit (none: only the table)
+    while (p.first_active < kTile && !((p.active >> p.first_active) & 1u)) ++p.first_active;
+    if (p.first_active == kTile) p.first_active = 0;
+    align16(bytes);
+    const size_t base = bytes->size();
+    std::vector<float2> facf(4 * kTile);
+    for (int b = 0; b < kTile; ++b)
+        for (int c = 0; c < 4; ++c) facf[4 * b + c] = f2(fac[b][c]);
+    p.off_fac = append(bytes, facf.data(), facf.size()) - base;
+    p.off_cross = append(bytes, cross.data(), cross.size()) - base;
+    p.off_out = append(bytes, outg.data(), outg.size()) - base;
+    if (!din.empty()) {
+        std::vector<float2> df(din.size());
+        for (size_t j = 0; j < din.size(); ++j) df[j] = f2(din[j]);
+        p.off_din = append(bytes, df.data(), df.size()) - base;
+        p.has_din = true;
+    }
+    align16(bytes);
+    p.bytes = bytes->size() - base;
+    out->g = g;
+    out->p = p;
+    out->dev_off = base;
+    return true;
+}
+
+}  // namespace
+
+bool layer_fits(int n, const int* pos, int k) {
+    const int T = std::min(kTile, n);
+    const int low = std::min(kLow, T);
+    int hi = 0;
+    for (int j = 0; j < k; ++j) hi += pos[j] >= low ? 1 : 0;
+    return hi <= T - low;
+}
+
+std::vector<LayerLaunch> prepare_layer(int n, const int32_t* L, const LayerSpec& spec,
+                                       std::vector<unsigned char>* bytes) {
+    std::vector<LayerLaunch> out;
+    if (n < kTile) return out;
+    // factor groups that fit a tile, in target order
+    std::vector<std::vector<int>> groups(1);
+    int hi = 0;
+    for (size_t j = 0; j < spec.t.size(); ++j) {
+        const bool high = L[spec.t[j]] >= kLow;
+        if (high && hi == kTile - kLow) {
+            groups.emplace_back();
+            hi = 0;
+        }
+        groups.back().push_back(static_cast<int>(j));
+        hi += high ? 1 : 0;
+    }
+    for (size_t i = 0; i < groups.size(); ++i) {
+        LayerLaunch ll;
+        if (prepare_pass(n, L, spec, groups[i], i == 0, bytes, &ll)) out.push_back(ll);
+    }
+    return out;
+}
+
+qsa_status run_layer_launches(qsa_state s, const std::vector<LayerLaunch>& ls, const unsigned char* d_base,
+                              qsa_run_stats* rs) {
+    for (const LayerLaunch& ll : ls) {
+        cudaError_t e;
+        {
+            Timer tm(s, rs ? &rs->layer_seconds : nullptr);
+            e = launch_apply_layer(s->psi, s->n, ll.g, d_base + ll.dev_off, ll.p, s->stream, &s->launches);
+            tm.stop();
+        }
+        if (e != cudaSuccess) return cuda_fail(s, e, "layer kernel");
+        s->known_zero = false;
+        if (rs) {
+            rs->passes += 1;
+            rs->hbm_bytes += 16.0 * static_cast<double>(1ull << s->n);
+        }
+    }
+    if (rs) {
+        rs->blocks += 1;
+        rs->layer_blocks += 1;
+    }
+    return QSA_OK;
+}
+
+qsa_status apply_layer_logical(qsa_state s, const LayerSpec& spec, qsa_run_stats* rs) {
+    if (s->n >= kTile) {
+        std::vector<unsigned char> bytes;
+        const auto ls = prepare_layer(s->n, s->L, spec, &bytes);
+        if (ls.empty()) return QSA_OK;
+        qsa_status st = ensure_dev(s, reinterpret_cast<void**>(&s->d_mat), &s->mat_cap, bytes.size());
+        if (st != QSA_OK) return st;
+        // pageable source: the copy is staged before the call returns
+        cudaError_t e = cudaMemcpyAsync(s->d_mat, bytes.data(), bytes.size(), cudaMemcpyHostToDevice, s->stream);
+        if (e != cudaSuccess) return cuda_fail(s, e, "layer payload upload");
+        return run_layer_launches(s, ls, reinterpret_cast<const unsigned char*>(s->d_mat), rs);
+    }
+    // small states: the ops one by one on the diagonal and product kernels
+    std::vector<float> tab;
+    std::vector<size_t> off;
+    for (const LayerDiagOp& op : spec.diag) {
+        off.push_back(tab.size());
+        for (int c = 0; c < (1 << op.k); ++c) {
+            tab.push_back(static_cast<float>(op.d[c].real()));
+            tab.push_back(static_cast<float>(op.d[c].imag()));
+        }
+        while (tab.size() % 4) tab.push_back(0.f);
+    }
+    const size_t foff = tab.size();
+    for (const auto& f : spec.f)
+        for (int c = 0; c < 4; ++c) {
+            tab.push_back(static_cast<float>(f[c].real()));
+            tab.push_back(static_cast<float>(f[c].imag()));
+        }
+    if (tab.empty()) return QSA_OK;
+    qsa_status st = ensure_dev(s, reinterpret_cast<void**>(&s->d_mat), &s->mat_cap, tab.size() * sizeof(float));
+    if (st != QSA_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(s->d_mat, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice,
+                                    s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "layer table upload");
+    for (size_t i = 0; i < spec.diag.size(); ++i) {
+        st = apply_diag_logical(s, spec.diag[i].q, spec.diag[i].k, s->d_mat + off[i], rs);
+        if (st != QSA_OK) return st;
+    }
+    if (!spec.t.empty()) return apply_prod_logical(s, spec.t.data(), static_cast<int>(spec.t.size()), s->d_mat + foff, rs);
+    return QSA_OK;
+}
+
+qsa_status layer_diag_from_op(const qsa_op& op, LayerDiagOp* out) {
+    if (op.k < 1 || op.k > 2) return fail(QSA_E_ARG, "layer diagonal ops act on 1 or 2 qubits");
+    if (!op.matrix) return fail(QSA_E_ARG, "op matrix is NULL");
+    const int D = 1 << op.k;
+    out->k = op.k;
+    for (int j = 0; j < op.k; ++j) out->q[j] = op.targets[j];
+    for (int r = 0; r < D; ++r)
+        for (int c = 0; c < D; ++c) {
+            const double re = op.matrix[2 * (r * D + c)], im = op.matrix[2 * (r * D + c) + 1];
+            if (r == c)
+                out->d[r] = std::complex<double>(re, im);
+            else if (re != 0.0 || im != 0.0)
+                return fail(QSA_E_ARG, "layer diagonal op has a nonzero off-diagonal entry");
+        }
+    return QSA_OK;
+}
+
+}  // namespace qsa
+
+using namespace qsa;
+
+extern "C" {
+
+qsa_status qsa_apply_layer(qsa_state s, const qsa_op* diag_ops, size_t n_diag, const int32_t* targets, int k,
+                           const double* factors) {
+    qsa_status st = check_state(s);
+    if (st != QSA_OK) return st;
+    if (k < 0 || k > QSA_MAX_LAYER) return fail(QSA_E_ARG, "k must be in 0..12");
+    if (k > 0) {
+        st = validate_targets(s->n, targets, k, QSA_MAX_LAYER);
+        if (st != QSA_OK) return st;
+        if (!factors) return fail(QSA_E_ARG, "factors is NULL");
+    }
+    if (n_diag > 0 && !diag_ops) return fail(QSA_E_ARG, "diag_ops is NULL");
+    LayerSpec spec;
+    for (size_t i = 0; i < n_diag; ++i) {
+        st = validate_targets(s->n, diag_ops[i].targets, diag_ops[i].k, 2);
+        if (st != QSA_OK) return st;
+        LayerDiagOp d;
+        st = layer_diag_from_op(diag_ops[i], &d);
+        if (st != QSA_OK) return st;
+        spec.diag.push_back(d);
+    }
+    for (int j = 0; j < k; ++j) {
+        spec.t.push_back(targets[j]);
+        std::array<std::complex<double>, 4> f;
+        for (int c = 0; c < 4; ++c) f[c] = std::complex<double>(factors[8 * j + 2 * c], factors[8 * j + 2 * c + 1]);
+        spec.f.push_back(f);
+    }
+    return apply_layer_logical(s, spec, nullptr);
+}
+
+}  // extern "C"

@@ -17,12 +17,18 @@
 // Block matrices are formed in FP64 in circuit order, later ops multiplied on
 // the left (§IV-C); a block of diagonal ops keeps only its diagonal (Alg. 2,
 // diagonal branch) and runs on the streaming kernel, up to QSA_MAX_DIAG wide.
+// With opts.layer, a pre-pass first groups the circuit into layer units
+// (diagonal gates on at most two qubits, then one-qubit ops whose qubits fit
+// one tile), moving an op ahead only of ops it commutes with; the planners
+// then run on the reordered stream, a layer unit counting as one pass.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <map>
+#include <numeric>
 #include <unordered_map>
 #include <vector>
 
@@ -38,8 +44,10 @@ namespace {
 struct Unit {
     uint64_t mask;       // logical target qubits
     bool diag;
-    size_t s, e;         // range of input ops
+    size_t s, e;         // range of ops (execution order)
     bool prod = false;   // product unit (one-qubit ops on >= 2 qubits), while a block of its own
+    bool layer = false;  // layer unit, while a block of its own
+    int nd = 0;          // layer unit: its first nd ops are the diagonal part
 };
 
 using Scorer = double (*)(void* ctx, int width, bool diag, bool prod, uint64_t mask);
@@ -97,7 +105,7 @@ std::vector<Unit> dp_window(const std::vector<Unit>& u, size_t b, size_t e, int 
                 if (w > std::max(kmax, kmax_diag)) break;
                 continue;
             }
-            const double val = D[jj] + sc(ctx, w, diag, jj == i - 1 && u[b + jj].prod, mask);
+            const double val = D[jj] + sc(ctx, w, diag, jj == i - 1 && (u[b + jj].prod || u[b + jj].layer), mask);
             if (val <= best) {
                 best = val;
                 bj = jj;
@@ -116,6 +124,8 @@ std::vector<Unit> dp_window(const std::vector<Unit>& u, size_t b, size_t e, int 
             m.diag = m.diag && u[b + t].diag;
         }
         m.prod = i - j == 1 && u[b + j].prod;
+        m.layer = i - j == 1 && u[b + j].layer;
+        m.nd = m.layer ? u[b + j].nd : 0;
         out.push_back(m);
         i = j;
     }
@@ -133,8 +143,9 @@ std::vector<Unit> merge_pass(const std::vector<Unit>& blocks, int kmax, int kmax
         const bool dg = cur.diag && nx.diag;
         const int w = popc(m);
         const int cap = dg ? kmax_diag : kmax;
-        if (w <= cap && sc(ctx, w, dg, false, m) <= sc(ctx, popc(cur.mask), cur.diag, cur.prod, cur.mask) +
-                                                          sc(ctx, popc(nx.mask), nx.diag, nx.prod, nx.mask)) {
+        if (w <= cap && sc(ctx, w, dg, false, m) <=
+                            sc(ctx, popc(cur.mask), cur.diag, cur.prod || cur.layer, cur.mask) +
+                                sc(ctx, popc(nx.mask), nx.diag, nx.prod || nx.layer, nx.mask)) {
             cur = Unit{m, dg, cur.s, nx.e};
         } else {
             out.push_back(cur);
@@ -206,6 +217,7 @@ qsa_status normalise_opts(const qsa_plan_opts* in, qsa_plan_opts* o) {
     if (o->lowering < 0 || o->lowering > 2) return fail(QSA_E_ARG, "unknown lowering");
     if (o->victim < 0 || o->victim > 1) return fail(QSA_E_ARG, "unknown victim rule");
     if (o->kmax_prod < 0 || o->kmax_prod > QSA_MAX_PROD) return fail(QSA_E_ARG, "kmax_prod must be in 0..11");
+    if (o->layer < 0 || o->layer > 1) return fail(QSA_E_ARG, "layer must be 0 or 1");
     return QSA_OK;
 }
 
@@ -219,15 +231,110 @@ void build_next_use(qsa_plan_s* p) {
     for (size_t i = B; i-- > 0;) {
         std::copy(cur.begin(), cur.end(), p->next_use.begin() + i * n);
         const PlanBlock& b = p->blocks[i];
-        if (!b.diag && !b.prod)
+        if (!b.diag && !b.prod && b.layer < 0)
             for (int j = 0; j < b.k; ++j) cur[b.t[j]] = static_cast<int32_t>(i);
     }
 }
 
-std::vector<Unit> plan(const qsa_op* ops, size_t n_ops, int n_qubits, const qsa_plan_opts& o, const int32_t* L) {
+uint64_t op_mask(const qsa_op& op) {
+    uint64_t m = 0;
+    for (int j = 0; j < op.k; ++j) m |= 1ull << op.targets[j];
+    return m;
+}
+
+// Layer pre-pass.  From the front of the pending stream: an op that is neither
+// one-qubit nor a diagonal gate on <= 2 qubits is a plain unit; otherwise a
+// layer unit is grown over the pending ops in circuit order -- a diagonal
+// gate on <= 2 qubits joins the diagonal part if no factor of the unit and no
+// skipped non-diagonal op touches its qubits; a one-qubit op joins its
+// qubit's factor if no skipped op touches the qubit and the factor qubits'
+// positions (layout L) still fit a tile; anything else is skipped and blocks
+// its qubits (all ops if it is non-diagonal, non-diagonal ops if diagonal).
+// The scan ends after more than 256 skips.  The unit executes its diagonal
+// part, then its factor ops (each in circuit order); skipped ops stay pending.
+void layer_prepass(const qsa_op* ops, size_t n_ops, int n, const int32_t* L, std::vector<size_t>* order,
+                   std::vector<Unit>* units) {
+    constexpr int kLookahead = 256;
+    std::vector<size_t> pending(n_ops);
+    std::iota(pending.begin(), pending.end(), size_t(0));
+    std::vector<char> taken(n_ops, 0);
+    while (!pending.empty()) {
+        const qsa_op& first = ops[pending[0]];
+        const bool first_diag = (first.flags & QSA_OP_DIAG) != 0;
+        if (!(first.k == 1 || (first_diag && first.k <= 2))) {
+            units->push_back(Unit{op_mask(first), first_diag, order->size(), order->size() + 1});
+            order->push_back(pending[0]);
+            pending.erase(pending.begin());
+            continue;
+        }
+        std::vector<size_t> dpart, fpart;
+        uint64_t fq = 0, blocked_nondiag = 0, blocked_all = 0, all = 0;
+        std::vector<int> fpos;
+        int skips = 0;
+        for (size_t idx : pending) {
+            const qsa_op& op = ops[idx];
+            const uint64_t Q = op_mask(op);
+            const bool dg = (op.flags & QSA_OP_DIAG) != 0;
+            if (dg && op.k <= 2 && !(Q & fq) && !(Q & blocked_nondiag)) {
+                dpart.push_back(idx);
+                all |= Q;
+                continue;
+            }
+            if (op.k == 1 && !(Q & blocked_all)) {
+                bool fits = (Q & fq) != 0;
+                if (!fits) {
+                    fpos.push_back(L[op.targets[0]]);
+                    fits = layer_fits(n, fpos.data(), static_cast<int>(fpos.size()));
+                    fpos.pop_back();
+                }
+                if (fits) {
+                    if (!(Q & fq)) fpos.push_back(L[op.targets[0]]);
+                    fpart.push_back(idx);
+                    fq |= Q;
+                    all |= Q;
+                    continue;
+                }
+            }
+            blocked_all |= Q;
+            if (!dg) blocked_nondiag |= Q;
+            if (++skips > kLookahead) break;
+        }
+        Unit u{all, false, order->size(), order->size() + dpart.size() + fpart.size()};
+        u.layer = true;
+        u.nd = static_cast<int>(dpart.size());
+        units->push_back(u);
+        for (size_t x : dpart) {
+            order->push_back(x);
+            taken[x] = 1;
+        }
+        for (size_t x : fpart) {
+            order->push_back(x);
+            taken[x] = 1;
+        }
+        std::vector<size_t> rest;
+        rest.reserve(pending.size());
+        for (size_t x : pending)
+            if (!taken[x]) rest.push_back(x);
+        pending.swap(rest);
+    }
+}
+
+// Units over the execution order *order (the identity unless the layer
+// pre-pass moved ops), then the planner.
+std::vector<Unit> plan(const qsa_op* ops, size_t n_ops, int n_qubits, const qsa_plan_opts& o, const int32_t* L,
+                       std::vector<size_t>* order) {
+    int32_t ident[QSA_MAX_QUBITS];
+    for (int q = 0; q < n_qubits; ++q) ident[q] = q;
+    order->clear();
     std::vector<Unit> gates;
+    if (o.layer && o.planner != QSA_PLAN_PER_GATE) {
+        layer_prepass(ops, n_ops, n_qubits, L ? L : ident, order, &gates);
+    } else {
+        order->resize(n_ops);
+        std::iota(order->begin(), order->end(), size_t(0));
+    }
     gates.reserve(n_ops);
-    for (size_t i = 0; i < n_ops;) {
+    for (size_t i = 0; i < n_ops && !(o.layer && o.planner != QSA_PLAN_PER_GATE);) {
         auto one_qubit = [&](size_t x) { return ops[x].k == 1 && !(ops[x].flags & QSA_OP_DIAG); };
         if (o.kmax_prod >= 2 && o.planner != QSA_PLAN_PER_GATE && one_qubit(i)) {
             // product unit: a maximal run of non-diagonal one-qubit ops on at most kmax_prod qubits
@@ -254,11 +361,7 @@ std::vector<Unit> plan(const qsa_op* ops, size_t n_ops, int n_qubits, const qsa_
     if (o.planner == QSA_PLAN_GREEDY) return greedy(gates, o.kmax);
     if (o.planner == QSA_PLAN_DP_MLP) {
         if (!costmodel_loaded()) return greedy(gates, o.kmax);
-        int32_t ident[QSA_MAX_QUBITS];
-        if (!L) {
-            for (int q = 0; q < n_qubits; ++q) ident[q] = q;
-            L = ident;
-        }
+        if (!L) L = ident;
         MlpCtx ctx{n_qubits, L, {}};
         return dp_pipeline(gates, o, mlp_score, &ctx);
     }
@@ -372,6 +475,7 @@ void qsa_plan_opts_default(qsa_plan_opts* o) {
     o->timing = 0;
     o->victim = QSA_VICTIM_FIRST_FREE;
     o->kmax_prod = 0;
+    o->layer = 0;
 }
 
 qsa_status qsa_plan_circuit(const qsa_op* ops, size_t n_ops, int n_qubits, const qsa_plan_opts* opts,
@@ -383,7 +487,8 @@ qsa_status qsa_plan_circuit(const qsa_op* ops, size_t n_ops, int n_qubits, const
     if (st != QSA_OK) return st;
     st = validate_ops(ops, n_ops, n_qubits);
     if (st != QSA_OK) return st;
-    auto blocks = plan(ops, n_ops, n_qubits, o, nullptr);
+    std::vector<size_t> order;
+    auto blocks = plan(ops, n_ops, n_qubits, o, nullptr, &order);
     for (size_t i = 0; i < blocks.size(); ++i) block_start[i] = blocks[i].s;
     *n_blocks = blocks.size();
     return QSA_OK;
@@ -426,7 +531,13 @@ qsa_status qsa_plan_create(const qsa_op* ops, size_t n_ops, int n_qubits, const 
     p->n = n_qubits;
     p->opts = o;
     p->n_ops = n_ops;
-    auto blocks = plan(ops, n_ops, n_qubits, o, layout);
+    p->L0.resize(n_qubits);
+    for (int q = 0; q < n_qubits; ++q) p->L0[q] = layout ? layout[q] : q;
+    auto blocks = plan(ops, n_ops, n_qubits, o, layout, &p->order);
+    // the ops in execution order
+    std::vector<qsa_op> perm(n_ops);
+    for (size_t i = 0; i < n_ops; ++i) perm[i] = ops[p->order[i]];
+    ops = perm.data();
     p->blocks.resize(blocks.size());
     std::vector<double> M;
     for (size_t i = 0; i < blocks.size(); ++i) {
@@ -434,6 +545,43 @@ qsa_status qsa_plan_create(const qsa_op* ops, size_t n_ops, int n_qubits, const 
         PlanBlock& b = p->blocks[i];
         b.off = p->host_mat.size();
         b.first_op = u.s;
+        if (u.layer) {
+            // diagonal part, then per-qubit factor products (qubits ascending,
+            // later ops on the left)
+            PlanLayer pl;
+            for (size_t x = u.s; x < u.s + static_cast<size_t>(u.nd); ++x) {
+                LayerDiagOp d;
+                st = layer_diag_from_op(ops[x], &d);
+                if (st != QSA_OK) {
+                    delete p;
+                    return st;
+                }
+                pl.spec.diag.push_back(d);
+            }
+            std::map<int, std::array<std::complex<double>, 4>> fac;
+            for (size_t x = u.s + static_cast<size_t>(u.nd); x < u.e; ++x) {
+                const int q = ops[x].targets[0];
+                auto it = fac.find(q);
+                std::array<std::complex<double>, 4> f =
+                    it == fac.end() ? std::array<std::complex<double>, 4>{1.0, 0.0, 0.0, 1.0} : it->second;
+                const double* g = ops[x].matrix;
+                std::complex<double> h[4];
+                for (int c = 0; c < 4; ++c) h[c] = std::complex<double>(g[2 * c], g[2 * c + 1]);
+                fac[q] = {h[0] * f[0] + h[1] * f[2], h[0] * f[1] + h[1] * f[3], h[2] * f[0] + h[3] * f[2],
+                          h[2] * f[1] + h[3] * f[3]};
+            }
+            for (const auto& kv : fac) {
+                pl.spec.t.push_back(kv.first);
+                pl.spec.f.push_back(kv.second);
+            }
+            pl.launches = prepare_layer(n_qubits, p->L0.data(), pl.spec, &p->host_layer);
+            b.layer = static_cast<int>(p->layers.size());
+            b.n_diag = u.nd;
+            b.k = static_cast<int>(pl.spec.t.size());
+            for (int j = 0; j < b.k; ++j) b.t[j] = pl.spec.t[j];
+            p->layers.push_back(std::move(pl));
+            continue;
+        }
         if (u.prod) {
             // per-qubit factors (ascending qubits), each the product of its ops in
             // circuit order, later ops on the left
@@ -514,7 +662,7 @@ qsa_status qsa_plan_promotions(qsa_plan p, const int32_t* layout_in, int victim,
     uint64_t pr = 0, ps = 0;
     for (size_t i = 0; i < p->blocks.size(); ++i) {
         const PlanBlock& b = p->blocks[i];
-        if (b.diag || b.prod) continue;
+        if (b.diag || b.prod || b.layer >= 0) continue;
         int phys[QSA_MAX_K], pa[QSA_MAX_K], pb[QSA_MAX_K];
         for (int j = 0; j < b.k; ++j) phys[j] = L[b.t[j]];
         const int np = choose_promotions(L, n, phys, b.k, frames, victim, p->next_use.data() + i * n, pa, pb);
@@ -557,12 +705,29 @@ qsa_status qsa_plan_blocks(qsa_plan p, size_t* first_op, int32_t* widths, size_t
     return QSA_OK;
 }
 
+qsa_status qsa_plan_order(qsa_plan p, size_t* order, size_t capacity) {
+    if (!p || !order) return fail(QSA_E_ARG, "NULL argument");
+    if (capacity < p->n_ops) return fail(QSA_E_RANGE, "capacity smaller than the number of ops");
+    for (size_t i = 0; i < p->n_ops; ++i) order[i] = i < p->order.size() ? p->order[i] : i;
+    return QSA_OK;
+}
+
+qsa_status qsa_plan_block_kinds(qsa_plan p, int32_t* kinds, int32_t* n_diag, size_t capacity) {
+    if (!p) return fail(QSA_E_ARG, "plan is NULL");
+    if (capacity < p->blocks.size()) return fail(QSA_E_RANGE, "capacity smaller than the number of blocks");
+    for (size_t i = 0; i < p->blocks.size(); ++i) {
+        const PlanBlock& b = p->blocks[i];
+        if (kinds) kinds[i] = b.layer >= 0 ? 3 : b.prod ? 2 : b.diag ? 1 : 0;
+        if (n_diag) n_diag[i] = b.layer >= 0 ? b.n_diag : 0;
+    }
+    return QSA_OK;
+}
+
 qsa_status qsa_plan_destroy(qsa_plan p) {
     if (!p) return fail(QSA_E_ARG, "plan is NULL");
-    if (p->d_mat) {
-        cudaDeviceSynchronize();
-        cudaFree(p->d_mat);
-    }
+    if (p->d_mat || p->d_layer) cudaDeviceSynchronize();
+    if (p->d_mat) cudaFree(p->d_mat);
+    if (p->d_layer) cudaFree(p->d_layer);
     delete p;
     return QSA_OK;
 }
@@ -578,27 +743,47 @@ qsa_status qsa_plan_execute(qsa_state s, qsa_plan p, qsa_run_stats* stats) {
     if (p->blocks.empty()) return QSA_OK;
     int dev = 0;
     cudaGetDevice(&dev);
-    if (!p->d_mat || p->dev != dev) {
-        // first execution on this device: upload the fused matrices once
+    if (p->dev != dev) {
+        // first execution on this device: upload the fused matrices and the
+        // layer payloads once
+        if (p->d_mat || p->d_layer) cudaStreamSynchronize(s->stream);
         if (p->d_mat) cudaFree(p->d_mat);
+        if (p->d_layer) cudaFree(p->d_layer);
         p->d_mat = nullptr;
+        p->d_layer = nullptr;
         const size_t bytes = p->host_mat.size() * sizeof(float);
-        cudaError_t e = cudaMalloc(&p->d_mat, bytes);
+        const size_t lbytes = p->host_layer.size();
+        cudaError_t e = bytes ? cudaMalloc(&p->d_mat, bytes) : cudaSuccess;
+        if (e == cudaSuccess && lbytes) e = cudaMalloc(&p->d_layer, lbytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
+            if (p->d_mat) cudaFree(p->d_mat);
             p->d_mat = nullptr;
+            p->d_layer = nullptr;
             return fail(QSA_E_NOMEM, "cudaMalloc of plan matrices failed");
         }
-        e = cudaMemcpyAsync(p->d_mat, p->host_mat.data(), bytes, cudaMemcpyHostToDevice, s->stream);
-        if (e != cudaSuccess) return cuda_fail(s, e, "plan matrix upload");
+        if (bytes) {
+            e = cudaMemcpyAsync(p->d_mat, p->host_mat.data(), bytes, cudaMemcpyHostToDevice, s->stream);
+            if (e != cudaSuccess) return cuda_fail(s, e, "plan matrix upload");
+        }
+        if (lbytes) {
+            e = cudaMemcpyAsync(p->d_layer, p->host_layer.data(), lbytes, cudaMemcpyHostToDevice, s->stream);
+            if (e != cudaSuccess) return cuda_fail(s, e, "plan layer upload");
+        }
         p->dev = dev;
-        rs->h2d_bytes = static_cast<double>(bytes);
+        rs->h2d_bytes = static_cast<double>(bytes + lbytes);
     }
     const uint64_t l0 = s->launches;
     s->timing = p->opts.timing != 0;
     for (size_t i = 0; i < p->blocks.size(); ++i) {
         const PlanBlock& b = p->blocks[i];
-        if (b.prod) {
+        if (b.layer >= 0) {
+            const PlanLayer& pl = p->layers[b.layer];
+            if (s->n >= QSA_LAYER_TILE_BITS && std::equal(p->L0.begin(), p->L0.end(), s->L))
+                st = run_layer_launches(s, pl.launches, p->d_layer, rs);
+            else
+                st = apply_layer_logical(s, pl.spec, rs);   // another layout: prepare again
+        } else if (b.prod) {
             st = apply_prod_logical(s, b.t, b.k, p->d_mat + b.off, rs);
         } else if (b.diag) {
             st = apply_diag_logical(s, b.t, b.k, p->d_mat + b.off, rs);
@@ -636,11 +821,13 @@ qsa_status qsa_apply_circuit(qsa_state s, const qsa_op* ops, size_t n_ops, const
     st = qsa_plan_create(ops, n_ops, s->n, opts, s->L, &p);
     if (st != QSA_OK) return st;
     st = qsa_plan_execute(s, p, stats);
-    if (p->d_mat) {
+    if (p->d_mat || p->d_layer) {
         // free after the stream has consumed the matrices
         cudaStreamSynchronize(s->stream);
-        cudaFree(p->d_mat);
+        if (p->d_mat) cudaFree(p->d_mat);
+        if (p->d_layer) cudaFree(p->d_layer);
         p->d_mat = nullptr;
+        p->d_layer = nullptr;
     }
     delete p;
     return st;
@@ -729,6 +916,7 @@ qsa_status qsa_batch_create(int n_qubits, int n_traj, const qsa_op* ops, const s
     if (st != QSA_OK) return st;
     if (o.kmax > 4) return fail(QSA_E_ARG, "batched trajectories fuse blocks of at most 4 qubits (kmax <= 4)");
     if (o.kmax_diag > o.kmax) return fail(QSA_E_ARG, "batched trajectories need kmax_diag <= kmax");
+    if (o.layer) return fail(QSA_E_ARG, "batched trajectories take no layer units");
     if (o.kmax_prod >= 2) return fail(QSA_E_ARG, "batched trajectories do not use product blocks (kmax_prod <= 1)");
     if (op_offsets[0] != 0) return fail(QSA_E_ARG, "op_offsets[0] must be 0");
     for (int t = 0; t < n_traj; ++t)
@@ -744,7 +932,8 @@ qsa_status qsa_batch_create(int n_qubits, int n_traj, const qsa_op* ops, const s
     for (int t = 0; t < n_traj; ++t) {
         const qsa_op* tops = ops + op_offsets[t];
         const size_t cnt = op_offsets[t + 1] - op_offsets[t];
-        auto units = plan(tops, cnt, n_qubits, o, nullptr);
+        std::vector<size_t> order;   // the identity: batches take no layer units
+        auto units = plan(tops, cnt, n_qubits, o, nullptr, &order);
         for (const Unit& u : units) {
             int32_t tg[QSA_MAX_K];
             int k = 0;

@@ -89,6 +89,32 @@ cudaError_t launch_apply_prod(float2* psi, int n, const int* phys, int k, const 
 cudaError_t launch_dm_diag(const float2* psi, int n, const int32_t* layout_host, uint64_t mask, double* d_out,
                            double* d_partials, double* d_sum, cudaStream_t st, uint64_t* launches);
 
+// Layer block launch (one pass; see layer.cu).  Tile of 12 bits: positions
+// 0..m-1 plus xpos[0..nx-1] (ascending, >= m), m + nx = 12, m >= 3.
+struct LayerGeom {
+    int m = 12, nx = 0;
+    int xpos[12] = {};
+};
+// A diagonal gate relative to a tile: cross (a = tile bit, b = outside
+// position, d[2 * o + v] for outside bit o and tile bit v) or out (a, b =
+// positions, b < 0 for one qubit, d[v_a + 2 v_b]).
+struct LayerGate {
+    int32_t a, b;
+    float2 d[4];
+};
+// Byte offsets of one launch's data in its device payload.
+struct LayerPayload {
+    uint32_t active = 0;      // tile bits with a factor or a per-tile phase
+    int first_active = 0;
+    int ncross = 0, nout = 0;
+    int cstart[13] = {};
+    bool has_din = false;     // 2^12-entry table of the gates with all qubits in the tile
+    size_t off_fac = 0, off_cross = 0, off_out = 0, off_din = 0, bytes = 0;
+};
+size_t layer_smem_bytes(bool with_din);
+cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const unsigned char* d_payload,
+                               const LayerPayload& p, cudaStream_t st, uint64_t* launches);
+
 // In-place swap of physical bit pairs (pa[i] <-> pb[i]), all positions distinct.
 cudaError_t launch_permute(float2* psi, int n, const int* pa, const int* pb, int npairs, cudaStream_t st,
                            uint64_t* launches);

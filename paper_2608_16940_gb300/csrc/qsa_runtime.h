@@ -3,11 +3,14 @@
 
 #include <cuda_runtime.h>
 
+#include <array>
+#include <complex>
 #include <string>
 #include <utility>
 #include <vector>
 
 #include "qsa.h"
+#include "qsa_internal.h"
 
 struct qsa_state_s {
     int n = 0;
@@ -40,13 +43,40 @@ struct qsa_state_s {
     std::vector<Pending> ev_pending;
 };
 
+// A layer block on logical qubits: diagonal ops (k = 1, 2; entries d[c], bit
+// j of c <-> q[j]) applied first, then one-qubit factors on distinct qubits.
+struct LayerDiagOp {
+    int k = 1;
+    int32_t q[2] = {0, 0};
+    std::complex<double> d[4];
+};
+struct LayerSpec {
+    std::vector<LayerDiagOp> diag;
+    std::vector<int32_t> t;                                 // factor qubits
+    std::vector<std::array<std::complex<double>, 4>> f;     // factor j on t[j], row-major
+};
+// One prepared pass: geometry, offsets relative to the payload at dev_off.
+struct LayerLaunch {
+    qsa::LayerGeom g;
+    qsa::LayerPayload p;
+    size_t dev_off = 0;
+};
+
 struct PlanBlock {
-    int32_t t[QSA_MAX_DIAG];   // ordered logical targets of the fused block (QSA_MAX_DIAG >= QSA_MAX_PROD)
+    int32_t t[QSA_MAX_DIAG];   // ordered logical targets of the fused block (QSA_MAX_DIAG >= QSA_MAX_LAYER);
+                               // a layer block lists its factor qubits
     int k = 0;
     bool diag = false;         // diagonal mode: 2^k entries, streaming kernel
     bool prod = false;         // product of one-qubit factors: 8 floats per factor, product kernel
+    int layer = -1;            // layer block: index into qsa_plan_s::layers
+    int n_diag = 0;            // layer block: ops of its diagonal part
     size_t off = 0;            // float offset of its matrix / diagonal in host_mat / d_mat
-    size_t first_op = 0;
+    size_t first_op = 0;       // in execution order
+};
+
+struct PlanLayer {
+    LayerSpec spec;
+    std::vector<LayerLaunch> launches;   // for the plan's layout (empty when N < 12)
 };
 
 struct qsa_plan_s {
@@ -59,6 +89,11 @@ struct qsa_plan_s {
     float* d_mat = nullptr;        // device copy (uploaded on first execution)
     std::vector<int32_t> next_use; // per block, per logical qubit: next dense block targeting it
     int dev = -1;
+    std::vector<size_t> order;     // execution order of the input ops
+    std::vector<int32_t> L0;       // the layout the plan was built for
+    std::vector<PlanLayer> layers;
+    std::vector<unsigned char> host_layer;   // layer payloads (16-byte aligned)
+    unsigned char* d_layer = nullptr;
 };
 
 namespace qsa {
@@ -93,6 +128,22 @@ qsa_status apply_diag_logical(qsa_state s, const int32_t* targets, int k, const 
 // Product block on logical targets (factor j on targets[j]; layout unchanged).
 qsa_status apply_prod_logical(qsa_state s, const int32_t* targets, int k, const float* d_fac, qsa_run_stats* rs);
 bool tc_available(qsa_state s, int k);
+
+// Layer blocks (layer.cu kernel; host preparation in layer_host.cpp).
+// True if factor positions pos[0..k) fit one tile (at most 9 at 3 or above).
+bool layer_fits(int n, const int* pos, int k);
+// The passes of a layer block for layout L (N >= 12): factors split into
+// groups that fit a tile (in target order), the diagonal ops in the first;
+// payloads appended to *bytes (16-byte aligned), dev_off relative to its start.
+std::vector<LayerLaunch> prepare_layer(int n, const int32_t* L, const LayerSpec& spec,
+                                       std::vector<unsigned char>* bytes);
+qsa_status run_layer_launches(qsa_state s, const std::vector<LayerLaunch>& ls, const unsigned char* d_base,
+                              qsa_run_stats* rs);
+// Prepare for the state's current layout, upload to scratch and run (N < 12:
+// the diagonal and product kernels, op by op).
+qsa_status apply_layer_logical(qsa_state s, const LayerSpec& spec, qsa_run_stats* rs);
+// Diagonal entries of a k = 1, 2 op (QSA_E_ARG if an off-diagonal entry is non-zero).
+qsa_status layer_diag_from_op(const qsa_op& op, LayerDiagOp* out);
 
 // Records a pair of CUDA events around the launches issued during its
 // lifetime; the elapsed time is added to *acc by collect_timers().

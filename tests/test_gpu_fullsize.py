@@ -5,8 +5,8 @@ invariants that hold at any size.
 - N = 28 fusion workload: the QFT of a random basis state matches its closed
   form at sampled indices, and the whole circuit followed by its inverse
   returns to |0...0>;
-- N = 30 QAOA workload (kmax 4 FP32, and the bench's kmax 6 with split-TF32
-  for k = 5, 6): norm 1, global bit-flip symmetry of the state
+- N = 30 QAOA workload (kmax 4 FP32, kmax 6 with split-TF32 for k = 5, 6,
+  product units, and the bench's layer units): norm 1, global bit-flip symmetry of the state
   (p(x) = p(~x), <Z_q> = 0), and the fused path agrees with the plain
   per-gate path at sampled amplitudes;
 - N = 32 / 33 wide workload (k = 5, 6 on the tensor cores): ops then their
@@ -78,18 +78,21 @@ def test_fusion28_qft_closed_form_and_inverse_return(q):
         st.close()
 
 
-@pytest.mark.parametrize("kmax,kdiag,kprod,prec", [(4, 4, 0, 0), (6, 6, 0, 1), (6, 12, 6, 1)],
-                         ids=["kmax4-fp32", "kmax6-3xtf32", "bench-kdiag12-kprod6-3xtf32"])
-def test_qaoa30_symmetries_and_fused_equals_per_gate(q, kmax, kdiag, kprod, prec):
-    """The bench's workload and launch configuration (kmax 6, diagonal blocks up
-    to 12 qubits, product units up to 6, split-TF32 for k = 5, 6), and two
-    dense-only configurations."""
+@pytest.mark.parametrize("kmax,kdiag,kprod,prec,layer", [(4, 4, 0, 0, 0), (6, 6, 0, 1, 0), (6, 12, 6, 1, 0),
+                                                       (6, 12, 0, 1, 1)],
+                         ids=["kmax4-fp32", "kmax6-3xtf32", "kdiag12-kprod6-3xtf32", "bench-layer-kdiag12-3xtf32"])
+def test_qaoa30_symmetries_and_fused_equals_per_gate(q, kmax, kdiag, kprod, prec, layer):
+    """The bench's workload and launch configuration (layer units, kmax 6,
+    diagonal blocks up to 12 qubits, split-TF32 for k = 5, 6), the product-unit
+    configuration and two dense-only ones."""
     n = 30
     ops, edges = W.qaoa_circuit(n=n, p=8, seed=0)
     st = Big(q, n)
     try:
-        q.qsa_apply_circuit(st.h, ops, q.make_opts(planner=q.QSA_PLAN_DP, kmax=kmax, kmax_diag=kdiag,
-                                                   kmax_prod=kprod, precision=prec))
+        stats = q.qsa_apply_circuit(st.h, ops, q.make_opts(planner=q.QSA_PLAN_DP, kmax=kmax, kmax_diag=kdiag,
+                                                           kmax_prod=kprod, precision=prec, layer=layer))
+        if layer:
+            assert stats["layer_blocks"] == 27 and stats["passes"] == 27
         assert abs(q.qsa_expectation_z(st.h, 0) - 1) < 1e-5
         for qb in (0, 7, 29):
             assert abs(q.qsa_expectation_z(st.h, 1 << qb)) < 1e-5

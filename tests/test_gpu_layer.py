@@ -1,0 +1,165 @@
+"""GPU parity of layer blocks (diagonal gates on one or two qubits anywhere,
+then one-qubit factors, one tile pass) against the FP64 oracle: every class
+of diagonal gate relative to a tile (all qubits in it, one in it, none),
+factors only, diagonal gates only, more factor positions than one tile holds
+(several passes), small states (other kernels), permuted layouts; plans with
+layer units (QAOA, brickwork, mixed circuits), a plan run under a layout
+other than its own, and the statistics."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_helpers import GState, check_close  # noqa: F401
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2608_16940_gb300 as q
+    return q
+
+
+def _diag_ops(n, count, rng, unit=True):
+    out = []
+    for _ in range(count):
+        k = 1 if rng.random() < 0.3 else 2
+        t = tuple(int(v) for v in rng.choice(n, size=k, replace=False))
+        d = np.exp(1j * rng.uniform(0, 2 * np.pi, 1 << k))
+        if not unit:
+            d = d * rng.uniform(0.8, 1.2, 1 << k)
+        out.append(W.Op(t, np.diag(d), True))
+    return out
+
+
+def _run(q, n, diag, targets, factors, layout=None, seed=0):
+    psi = W.random_state(n, seed=seed)
+    st = GState(q, torch, n, init=psi)
+    try:
+        if layout is not None:
+            q.qsa_set_layout(st.h, layout, 1)
+        q.qsa_apply_layer(st.h, diag, targets, factors)
+        ref = psi.copy()
+        oracle.apply_layer(ref, diag, targets, factors)
+        got = st.logical()
+        # non-unit diagonal entries leave the state unnormalised: compare in norm
+        assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+        assert oracle.max_abs_diff(ref, got) <= 1e-5
+    finally:
+        st.close()
+
+
+@pytest.mark.parametrize("n,k,n_diag,seed,permuted", [(12, 6, 20, 0, False), (13, 8, 30, 1, True),
+                                                      (16, 9, 40, 2, False), (16, 12, 60, 3, True),
+                                                      (20, 7, 80, 4, False), (22, 10, 100, 5, True)])
+def test_layer_matches_oracle(q, n, k, n_diag, seed, permuted):
+    rng = np.random.default_rng(seed)
+    layout = [int(v) for v in rng.permutation(n)] if permuted else list(range(n))
+    # factor qubits that fit one tile: at most 9 at positions >= 3
+    low = [qb for qb in range(n) if layout[qb] < 3]
+    high = [qb for qb in range(n) if layout[qb] >= 3]
+    nl = min(len(low), int(rng.integers(0, 4)), k)
+    t = [int(v) for v in rng.choice(low, size=nl, replace=False)] + \
+        [int(v) for v in rng.choice(high, size=min(9, k - nl), replace=False)]
+    fac = [W.haar_unitary(2, rng) for _ in t]
+    _run(q, n, _diag_ops(n, n_diag, rng, unit=seed % 2 == 0), t, fac, layout if permuted else None, seed)
+
+
+def test_layer_diagonal_only_and_factors_only(q):
+    rng = np.random.default_rng(10)
+    _run(q, 14, _diag_ops(14, 50, rng), [], [])
+    _run(q, 14, [], [0, 1, 2, 3], [W.haar_unitary(2, rng) for _ in range(4)])
+    _run(q, 14, [], [13, 12, 5], [W.haar_unitary(2, rng) for _ in range(3)])
+    _run(q, 16, [], [15], [W.H])
+
+
+def test_layer_gate_classes(q):
+    """n = 18, factors on qubits 0..2 and 10..18: ZZ inside the tile, across
+    its boundary (either qubit order) and outside it, one-qubit phases in and
+    out."""
+    n = 18
+    rng = np.random.default_rng(11)
+    t = [0, 1, 2] + list(range(9, 18))
+    fac = [W.haar_unitary(2, rng) for _ in t]
+    diag = [W.Op((0, 12), np.diag(np.exp(1j * rng.uniform(0, 6, 4))), True),
+            W.Op((5, 12), np.diag(np.exp(1j * rng.uniform(0, 6, 4))), True),
+            W.Op((12, 6), np.diag(np.exp(1j * rng.uniform(0, 6, 4))), True),
+            W.Op((4, 7), np.diag(np.exp(1j * rng.uniform(0, 6, 4))), True),
+            W.Op((8,), np.diag(np.exp(1j * rng.uniform(0, 6, 2))), True),
+            W.Op((17,), np.diag(np.exp(1j * rng.uniform(0, 6, 2))), True)]
+    _run(q, n, diag, t, fac)
+
+
+def test_layer_more_factors_than_a_tile_holds(q):
+    """Twelve factors all at positions >= 3: two passes (diagonal ops in the first)."""
+    n = 20
+    rng = np.random.default_rng(12)
+    t = list(range(5, 17))
+    _run(q, n, _diag_ops(n, 30, rng), t, [W.haar_unitary(2, rng) for _ in t])
+
+
+@pytest.mark.parametrize("n", [3, 8, 11])
+def test_layer_small_states(q, n):
+    rng = np.random.default_rng(13 + n)
+    t = [int(v) for v in rng.choice(n, size=min(n, 5), replace=False)]
+    _run(q, n, _diag_ops(n, 10, rng), t, [W.haar_unitary(2, rng) for _ in t])
+
+
+@pytest.mark.parametrize("kind,n,planner,kmax,prec", [("qaoa", 16, 2, 6, 1), ("qaoa", 20, 3, 6, 1),
+                                                     ("brick", 14, 2, 4, 0), ("mixed", 14, 2, 4, 0),
+                                                     ("mixed", 13, 1, 4, 0)])
+def test_plans_with_layer_units_match_oracle(q, kind, n, planner, kmax, prec):
+    rng = np.random.default_rng(n + planner)
+    if kind == "qaoa":
+        ops, _ = W.qaoa_circuit(n, 3, seed=1)
+    elif kind == "brick":
+        ops = W.brick_circuit(n, 8, seed=2)
+        ops = [W.Op(o.targets, o.matrix, o.name == "cz" or o.diag, o.name) for o in ops]
+    else:
+        from test_oracle_layer import _mixed_circuit
+        ops = _mixed_circuit(n, 200, rng)
+    st = GState(q, torch, n)
+    try:
+        stats = q.qsa_apply_circuit(st.h, ops, q.make_opts(planner=planner, kmax=kmax, kmax_diag=kmax, layer=1,
+                                                           precision=prec))
+        assert stats["layer_blocks"] > 0
+        check_close(oracle.run_circuit(n, ops), st.logical())
+    finally:
+        st.close()
+
+
+def test_plan_under_another_layout(q):
+    """A plan built for the identity layout, executed on a state whose layout
+    was permuted: layer blocks are prepared again for that layout."""
+    n = 16
+    ops, _ = W.qaoa_circuit(n, 2, seed=3)
+    p = q.qsa_plan_create(ops, n, q.make_opts(planner=2, kmax=6, kmax_diag=6, layer=1, timing=1))
+    st = GState(q, torch, n)
+    try:
+        q.qsa_set_layout(st.h, [int(v) for v in np.random.default_rng(4).permutation(n)], 1)
+        stats = q.qsa_plan_execute(st.h, p)
+        assert stats["layer_blocks"] > 0 and stats["layer_seconds"] > 0
+        check_close(oracle.run_circuit(n, ops), st.logical())
+    finally:
+        st.close()
+        q.qsa_plan_destroy(p)
+
+
+def test_layer_argument_errors(q):
+    st = GState(q, torch, 12)
+    try:
+        bad = [([W.Op((0, 1, 2), np.eye(8), True)], [], []),          # three-qubit diagonal op
+               ([W.Op((0, 1), W.CNOT, True)], [], []),                 # not diagonal
+               ([], [0, 0], [np.eye(2), np.eye(2)]),                   # repeated factor qubit
+               ([], [12], [np.eye(2)]),                                # qubit out of range
+               ([], list(range(12)) + [0], [np.eye(2)] * 13)]          # more than 12 factors
+        for dg, t, f in bad:
+            with pytest.raises(q.QsaError) as e:
+                q.qsa_apply_layer(st.h, dg, t, f)
+            assert e.value.code == q.QSA_E_ARG
+    finally:
+        st.close()
