@@ -10,12 +10,19 @@
 //           over the tile-local index, applied elementwise;
 //   cross   (one qubit in the tile, one outside): with the outside bit fixed
 //           by the tile, a one-qubit phase on its tile bit, folded into that
-//           bit's factor (F' = F diag(d0, d1));
-//   out     (no qubit in the tile): a scalar per tile, folded into one factor.
+//           bit's factor (F' = F diag(d0, d1)), or multiplied in where the bit
+//           has no factor;
+//   out     (no qubit in the tile): a scalar per tile, multiplied in.
+// Unitary factors run in rotation mode: each factor is split on the host as
+// F = diag(p) R diag(q) with R = [[c, -s], [s, c]] real, all q folded into
+// the entry table, all p into an exit table, so a factor costs a real
+// rotation (4 multiply-adds per amplitude instead of 8); the cross phases of
+// every bit are then multiplied in (they precede the rotation).  Other
+// factors run in general mode (complex 2x2 butterflies, cross phases folded).
 // Per tile: 16-byte cp.async copies into a 2-stage ring (XOR-swizzled 16-byte
-// chunks), then three register rounds over tile bits 0-3, 4-7 and 8-11 (each
-// thread holds the 16 amplitudes that differ in the round's bits and applies
-// the round's factors as butterflies); the last active round stores to HBM.
+// chunks); warp 0 forms the tile's phases; then three register rounds over
+// tile bits 0-3, 4-7 and 8-11 (each thread holds the 16 amplitudes that
+// differ in the round's bits); the last active round stores to HBM.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -39,14 +46,23 @@ struct LayerArgs {
     uint64_t ntiles;
     int m, nx;
     int xpos[kLT];            // positions of tile bits m..11, ascending
-    uint32_t active;          // tile bits with a factor or a per-tile phase
-    int first_active;         // the bit whose factor absorbs the per-tile scalar
+    uint32_t fmask;           // tile bits with a factor
+    uint32_t pmask;           // tile bits with a per-tile phase applied as a multiply
     int ncross, nout;
     int cstart[kLT + 1];      // cross gates of tile bit b: [cstart[b], cstart[b + 1])
-    const float2* fac;        // kLT x 4 complex (2x2 row-major), identity where no factor
+    const float2* fac;        // general mode: kLT x 4 complex (2x2 row-major); rotation mode:
+                              // (cos, sin) of each factor's rotation
     const LayerGate* cross;   // a = tile bit, b = outside position, d[2 * o + v]
     const LayerGate* outg;    // a, b = positions (b < 0: one qubit), d[v_a + 2 v_b]
-    const float2* din;        // 2^12 entries over tile-local bits, or nullptr
+    const float2* din;        // entry table, 2^12 entries over tile-local bits stored as
+                              // din[i * 256 + t] = entry(16 t + i) (round 0's access), or nullptr
+    const float2* dout;       // rotation mode: exit table, 2^12 entries in tile-local order, or nullptr
+};
+
+struct LayerShared {
+    float2 tf[kLT][4];        // general mode: this tile's factors (cross phases folded in)
+    float2 ph[kLT][2];        // per-tile phases of pmask bits
+    float2 pl[16];            // per-tile phases of round 0's 16 local amplitudes times the scalar
 };
 
 // Slot of tile-local amplitude j: 16-byte chunk c = j / 2 is stored at
@@ -72,7 +88,7 @@ __device__ __forceinline__ uint64_t layer_global(const LayerArgs& a, const uint6
     return base | static_cast<uint64_t>(j & ((1 << a.m) - 1)) | runoff[j >> a.m];
 }
 
-// v[i], v[i | 2^LB] <- F (v[i], v[i | 2^LB]) for the 8 pairs.
+// General factor: v[i], v[i | 2^LB] <- F (v[i], v[i | 2^LB]) for the 8 pairs.
 template <int LB>
 __device__ __forceinline__ void butterfly(float2 (&v)[16], const float2* F) {
     const float2 f00 = F[0], f01 = F[1], f10 = F[2], f11 = F[3];
@@ -87,12 +103,27 @@ __device__ __forceinline__ void butterfly(float2 (&v)[16], const float2* F) {
     }
 }
 
-// One round over tile bits 4R..4R+3: read the stage, apply the diagonal table
-// (R = 0) and the round's factors, write back to the stage or (last round) to
-// HBM.
-template <int R>
-__device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, const float2* din_s,
-                                            const float2* tf, const uint64_t* runoff, uint64_t base, bool last) {
+// Real rotation [[c, -s], [s, c]] on local bit LB.
+template <int LB>
+__device__ __forceinline__ void rotation(float2 (&v)[16], float2 cs) {
+    const float c = cs.x, s = cs.y;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        if ((i >> LB) & 1) continue;
+        const float2 x0 = v[i], x1 = v[i | (1 << LB)];
+        v[i] = make_float2(fmaf(c, x0.x, -s * x1.x), fmaf(c, x0.y, -s * x1.y));
+        v[i | (1 << LB)] = make_float2(fmaf(s, x0.x, c * x1.x), fmaf(s, x0.y, c * x1.y));
+    }
+}
+
+// One round over tile bits 4R..4R+3: read the stage; (R = 0) multiply by the
+// entry table and the per-tile phases; apply the round's factors; (last
+// round, rotation mode) multiply by the exit table; write back to the stage
+// or (last round) to HBM.
+template <bool ROT, int R>
+__device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, const float2* dout_s,
+                                            const LayerShared& sh, const float2* rot, const uint64_t* runoff,
+                                            uint64_t base, bool last, bool phase) {
     const int t = threadIdx.x;
     const int jb = (t & ((1 << (4 * R)) - 1)) | ((t >> (4 * R)) << (4 * R + 4));
     float2 v[16];
@@ -103,23 +134,49 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
             v[i] = make_float2(p.x, p.y);
             v[i + 1] = make_float2(p.z, p.w);
         }
-        if (din_s) {
+        if (a.din) {
+            const float2* dt = a.din + t;
 #pragma unroll
-            for (int i = 0; i < 16; i += 2) {
-                const float4 d = *reinterpret_cast<const float4*>(din_s + lsw(jb | i));
-                v[i] = cmulf(v[i], make_float2(d.x, d.y));
-                v[i + 1] = cmulf(v[i + 1], make_float2(d.z, d.w));
-            }
+            for (int i = 0; i < 16; ++i) v[i] = cmulf(v[i], __ldg(dt + i * (kLThreads)));
+        }
+        if (phase) {
+            // phases of pmask bits 4..11 (fixed for this thread) times those of the 16 local amplitudes
+            float2 ph = make_float2(1.f, 0.f);
+#pragma unroll
+            for (int b = 4; b < kLT; ++b)
+                if ((a.pmask >> b) & 1u) ph = cmulf(ph, sh.ph[b][(jb >> b) & 1]);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = cmulf(v[i], cmulf(ph, sh.pl[i]));
         }
     } else {
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = stage[lsw(jb | (i << (4 * R)))];
     }
-    const uint32_t act = (a.active >> (4 * R)) & 15u;
-    if (act & 1u) butterfly<0>(v, tf + 4 * (4 * R + 0));
-    if (act & 2u) butterfly<1>(v, tf + 4 * (4 * R + 1));
-    if (act & 4u) butterfly<2>(v, tf + 4 * (4 * R + 2));
-    if (act & 8u) butterfly<3>(v, tf + 4 * (4 * R + 3));
+    const uint32_t act = (a.fmask >> (4 * R)) & 15u;
+    if constexpr (ROT) {
+        if (act & 1u) rotation<0>(v, rot[4 * R + 0]);
+        if (act & 2u) rotation<1>(v, rot[4 * R + 1]);
+        if (act & 4u) rotation<2>(v, rot[4 * R + 2]);
+        if (act & 8u) rotation<3>(v, rot[4 * R + 3]);
+        if (last && dout_s) {
+            if constexpr (R == 0) {
+#pragma unroll
+                for (int i = 0; i < 16; i += 2) {
+                    const float4 d = *reinterpret_cast<const float4*>(dout_s + lsw(jb | i));
+                    v[i] = cmulf(v[i], make_float2(d.x, d.y));
+                    v[i + 1] = cmulf(v[i + 1], make_float2(d.z, d.w));
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = cmulf(v[i], dout_s[lsw(jb | (i << (4 * R)))]);
+            }
+        }
+    } else {
+        if (act & 1u) butterfly<0>(v, sh.tf[4 * R + 0]);
+        if (act & 2u) butterfly<1>(v, sh.tf[4 * R + 1]);
+        if (act & 4u) butterfly<2>(v, sh.tf[4 * R + 2]);
+        if (act & 8u) butterfly<3>(v, sh.tf[4 * R + 3]);
+    }
     if (last) {
         if constexpr (R == 0) {
             // m >= 3: amplitudes jb | i and jb | (i + 1) are adjacent in HBM
@@ -144,10 +201,12 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
     }
 }
 
-// Per-tile factors: the block factor of each active bit times the phases of
-// its cross gates (outside bit read from the tile's base index), the first
-// active bit also times the product of the out gates.  Run by warp 0.
-__device__ __forceinline__ void tile_factors(const LayerArgs& a, uint64_t base, float2* tf) {
+// The tile's factors and phases (warp 0): the scalar of the out gates (lanes
+// over gates, product across lanes); each tile bit's cross phases (lane b),
+// folded into the bit's factor (general mode, factor bits) or kept as a
+// phase; then the phases of round 0's 16 local amplitudes times the scalar.
+template <bool ROT>
+__device__ __forceinline__ void tile_phases(const LayerArgs& a, uint64_t base, LayerShared& sh) {
     const int lane = threadIdx.x & 31;
     float2 sc = make_float2(1.f, 0.f);
     for (int g = lane; g < a.nout; g += 32) {
@@ -163,7 +222,8 @@ __device__ __forceinline__ void tile_factors(const LayerArgs& a, uint64_t base, 
         other.y = __shfl_xor_sync(0xffffffffu, sc.y, o);
         sc = cmulf(sc, other);
     }
-    if (lane < kLT && ((a.active >> lane) & 1u)) {
+    const bool fold = !ROT && ((a.fmask >> lane) & 1u);
+    if (lane < kLT && (fold || ((a.pmask >> lane) & 1u))) {
         float2 d0 = make_float2(1.f, 0.f), d1 = make_float2(1.f, 0.f);
         for (int g = a.cstart[lane]; g < a.cstart[lane + 1]; ++g) {
             const LayerGate& G = a.cross[g];
@@ -171,24 +231,35 @@ __device__ __forceinline__ void tile_factors(const LayerArgs& a, uint64_t base, 
             d0 = cmulf(d0, G.d[2 * o]);
             d1 = cmulf(d1, G.d[2 * o + 1]);
         }
-        if (lane == a.first_active) {
-            d0 = cmulf(d0, sc);
-            d1 = cmulf(d1, sc);
+        if (fold) {
+            const float2* F = a.fac + 4 * lane;
+            sh.tf[lane][0] = cmulf(F[0], d0);
+            sh.tf[lane][1] = cmulf(F[1], d1);
+            sh.tf[lane][2] = cmulf(F[2], d0);
+            sh.tf[lane][3] = cmulf(F[3], d1);
+        } else {
+            sh.ph[lane][0] = d0;
+            sh.ph[lane][1] = d1;
         }
-        const float2* F = a.fac + 4 * lane;
-        tf[4 * lane + 0] = cmulf(F[0], d0);
-        tf[4 * lane + 1] = cmulf(F[1], d1);
-        tf[4 * lane + 2] = cmulf(F[2], d0);
-        tf[4 * lane + 3] = cmulf(F[3], d1);
+    }
+    __syncwarp();
+    if (lane < 16) {
+        float2 p = sc;
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+            if ((a.pmask >> b) & 1u) p = cmulf(p, sh.ph[b][(lane >> b) & 1]);
+        sh.pl[lane] = p;
     }
 }
 
+template <bool ROT>
 __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* stage = reinterpret_cast<float2*>(smem_raw);                  // kLStages x 4096
+    float2* stage = reinterpret_cast<float2*>(smem_raw);                        // kLStages x 4096
     uint64_t* runoff = reinterpret_cast<uint64_t*>(stage + kLStages * kLAmps);  // 512
-    float2* tf = reinterpret_cast<float2*>(runoff + 512);                  // 12 x 4
-    float2* din_s = a.din ? tf + 4 * kLT : nullptr;                        // 4096 (swizzled)
+    LayerShared& sh = *reinterpret_cast<LayerShared*>(runoff + 512);
+    float2* rot = reinterpret_cast<float2*>(&sh + 1);                           // kLT
+    float2* dout_s = a.dout ? rot + kLT : nullptr;                              // 4096, swizzled
 
     for (int r = threadIdx.x; r < (1 << a.nx); r += blockDim.x) {
         uint64_t off = 0;
@@ -197,16 +268,20 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
         runoff[r] = off;
     }
     const bool dynamic = a.ncross > 0 || a.nout > 0;
-    if (!dynamic)
-        for (int i = threadIdx.x; i < 4 * kLT; i += blockDim.x) tf[i] = a.fac[i];
-    if (din_s)
-        for (int j = threadIdx.x; j < kLAmps; j += blockDim.x) din_s[lsw(j)] = a.din[j];
+    const bool phase = a.pmask != 0 || a.nout > 0;
+    if (ROT) {
+        if (threadIdx.x < kLT) rot[threadIdx.x] = a.fac[threadIdx.x];
+    } else if (!dynamic) {
+        for (int i = threadIdx.x; i < 4 * kLT; i += blockDim.x) sh.tf[i >> 2][i & 3] = a.fac[i];
+    }
+    if (dout_s)
+        for (int j = threadIdx.x; j < kLAmps; j += blockDim.x) dout_s[lsw(j)] = a.dout[j];
     __syncthreads();
 
     // rounds that do work; the last of them writes to HBM
     int first = -1, last = -1;
     for (int r = 0; r < 3; ++r)
-        if (((a.active >> (4 * r)) & 15u) || (r == 0 && din_s)) {
+        if (((a.fmask >> (4 * r)) & 15u) || (r == 0 && (a.din || phase))) {
             if (first < 0) first = r;
             last = r;
         }
@@ -225,19 +300,19 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
         if (tn < a.ntiles) load(tn, stage + (cur ^ 1) * kLAmps);
         cp_async_commit();
         const uint64_t base = layer_base(a, t);
-        if (dynamic && threadIdx.x < 32) tile_factors(a, base, tf);
+        if (dynamic && threadIdx.x < 32) tile_phases<ROT>(a, base, sh);
         cp_async_wait<1>();
         __syncthreads();
         float2* st = stage + cur * kLAmps;
         if (first == 0) {
-            layer_round<0>(a, st, din_s, tf, runoff, base, last == 0);
+            layer_round<ROT, 0>(a, st, dout_s, sh, rot, runoff, base, last == 0, phase);
             if (last > 0) __syncthreads();
         }
-        if (first <= 1 && last >= 1 && ((a.active >> 4) & 15u)) {
-            layer_round<1>(a, st, din_s, tf, runoff, base, last == 1);
+        if (first <= 1 && last >= 1 && ((a.fmask >> 4) & 15u)) {
+            layer_round<ROT, 1>(a, st, dout_s, sh, rot, runoff, base, last == 1, phase);
             if (last > 1) __syncthreads();
         }
-        if (last == 2) layer_round<2>(a, st, din_s, tf, runoff, base, true);
+        if (last == 2) layer_round<ROT, 2>(a, st, dout_s, sh, rot, runoff, base, true, phase);
         __syncthreads();
         cur ^= 1;
     }
@@ -246,9 +321,9 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
 
 }  // namespace
 
-size_t layer_smem_bytes(bool with_din) {
-    return sizeof(float2) * kLStages * kLAmps + sizeof(uint64_t) * 512 + sizeof(float2) * 4 * kLT +
-           (with_din ? sizeof(float2) * kLAmps : 0);
+size_t layer_smem_bytes(bool with_dout) {
+    return sizeof(float2) * kLStages * kLAmps + sizeof(uint64_t) * 512 + sizeof(LayerShared) +
+           sizeof(float2) * kLT + (with_dout ? sizeof(float2) * kLAmps : 0);
 }
 
 cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const unsigned char* d_payload,
@@ -260,8 +335,8 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
     a.m = g.m;
     a.nx = g.nx;
     for (int e = 0; e < kLT; ++e) a.xpos[e] = e < g.nx ? g.xpos[e] : 0;
-    a.active = p.active;
-    a.first_active = p.first_active;
+    a.fmask = p.active;
+    a.pmask = p.pmask;
     a.ncross = p.ncross;
     a.nout = p.nout;
     for (int b = 0; b <= kLT; ++b) a.cstart[b] = p.cstart[b];
@@ -269,21 +344,25 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
     a.cross = reinterpret_cast<const LayerGate*>(d_payload + p.off_cross);
     a.outg = reinterpret_cast<const LayerGate*>(d_payload + p.off_out);
     a.din = p.has_din ? reinterpret_cast<const float2*>(d_payload + p.off_din) : nullptr;
-    const size_t smem = layer_smem_bytes(p.has_din);
+    a.dout = p.has_dout ? reinterpret_cast<const float2*>(d_payload + p.off_dout) : nullptr;
+    const size_t smem = layer_smem_bytes(p.has_dout);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_apply_layer, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(layer_smem_bytes(true)));
-        if (e != cudaSuccess) return e;
+        for (auto kern : {k_apply_layer<true>, k_apply_layer<false>}) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(layer_smem_bytes(true)));
+            if (e != cudaSuccess) return e;
+        }
         attr_set = true;
     }
+    auto kern = p.rotation ? k_apply_layer<true> : k_apply_layer<false>;
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_apply_layer, kLThreads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kLThreads, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
     uint64_t grid = static_cast<uint64_t>(num_sms()) * occ;
     if (grid > a.ntiles) grid = a.ntiles;
-    k_apply_layer<<<static_cast<unsigned>(grid), kLThreads, smem, st>>>(a);
+    kern<<<static_cast<unsigned>(grid), kLThreads, smem, st>>>(a);
     ++*launches;
     return cudaGetLastError();
 }

@@ -60,6 +60,35 @@ size_t append(std::vector<unsigned char>* b, const T* data, size_t count) {
 
 float2 f2(std::complex<double> z) { return make_float2(static_cast<float>(z.real()), static_cast<float>(z.imag())); }
 
+// F = diag(p) [[c, -s], [s, c]] diag(q) with q[0] = 1, c = |F00|, s = |F01|;
+// false unless the product reproduces F to 1e-10 (a unitary F does).
+bool split_rotation(const std::array<std::complex<double>, 4>& F, double* c, double* s, std::complex<double>* p,
+                    std::complex<double>* q) {
+    const std::complex<double> a = F[0], b = F[1], cc = F[2], d = F[3];
+    const double ca = std::abs(a), sb = std::abs(b);
+    if (ca == 0.0 && sb == 0.0) return false;
+    *c = ca;
+    *s = sb;
+    q[0] = 1.0;
+    if (ca > 0.0 && sb > 0.0) {
+        p[0] = a / ca;
+        q[1] = -b / (p[0] * sb);
+        p[1] = cc / sb;
+    } else if (sb == 0.0) {
+        p[0] = a / ca;
+        q[1] = 1.0;
+        p[1] = d / ca;
+    } else {
+        q[1] = 1.0;
+        p[0] = -b / sb;
+        p[1] = cc / sb;
+    }
+    const std::complex<double> rec[4] = {p[0] * ca * q[0], -p[0] * sb * q[1], p[1] * sb * q[0], p[1] * ca * q[1]};
+    for (int i = 0; i < 4; ++i)
+        if (std::abs(rec[i] - F[i]) > 1e-10) return false;
+    return true;
+}
+
 // One pass: factors fsel (indices into spec.f), the diagonal ops if with_diag.
 // Returns false when there is nothing to apply.
 bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vector<int>& fsel, bool with_diag,
@@ -76,7 +105,14 @@ bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vec
         fac[b] = spec.f[fsel[i]];
         p.active |= 1u << b;
     }
+    // rotation mode when every factor splits as diag(p) R diag(q)
+    std::vector<double> rc(kTile, 1.0), rs(kTile, 0.0);
+    std::vector<std::array<std::complex<double>, 2>> rp(kTile, {1.0, 1.0}), rq(kTile, {1.0, 1.0});
+    p.rotation = true;
+    for (int b = 0; b < kTile && p.rotation; ++b)
+        if ((p.active >> b) & 1u) p.rotation = split_rotation(fac[b], &rc[b], &rs[b], rp[b].data(), rq[b].data());
     std::vector<LayerGate> cross, outg;
+    uint32_t cross_bits = 0;
     std::vector<std::complex<double>> din;
     if (with_diag) {
         for (const LayerDiagOp& op : spec.diag) {
@@ -98,7 +134,7 @@ bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vec
                 for (int o = 0; o < 2; ++o)
                     for (int v = 0; v < 2; ++v) G.d[2 * o + v] = f2(op.d[first_in ? (v | (o << 1)) : (o | (v << 1))]);
                 cross.push_back(G);
-                p.active |= 1u << G.a;
+                cross_bits |= 1u << G.a;
             } else {
                 LayerGate G{};
                 G.a = p0;
@@ -108,8 +144,20 @@ bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vec
             }
         }
     }
-    if (!outg.empty() && p.active == 0) p.active = 1u;   // the scalar needs a factor to ride on
-    if (p.active == 0 && din.empty()) return false;
+    p.pmask = p.rotation ? cross_bits : (cross_bits & ~p.active);
+    if (p.active == 0 && p.pmask == 0 && outg.empty() && din.empty()) return false;
+    std::vector<std::complex<double>> dout;
+    if (p.rotation && p.active) {
+        // entry table times every q, exit table of every p
+        if (din.empty()) din.assign(1u << kTile, 1.0);
+        dout.assign(1u << kTile, 1.0);
+        for (uint32_t j = 0; j < (1u << kTile); ++j)
+            for (int b = 0; b < kTile; ++b)
+                if ((p.active >> b) & 1u) {
+                    din[j] *= rq[b][(j >> b) & 1u];
+                    dout[j] *= rp[b][(j >> b) & 1u];
+                }
+    }
     std::stable_sort(cross.begin(), cross.end(), [](const LayerGate& x, const LayerGate& y) { return x.a < y.a; });
     p.ncross = static_cast<int>(cross.size());
     p.nout = static_cast<int>(outg.size());
@@ -117,22 +165,30 @@ bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vec
         while (c < p.ncross && cross[c].a < b) ++c;
         p.cstart[b] = c;
     }
-    p.first_active = 0;   // the lowest active bit (none: only the table)
-    while (p.first_active < kTile && !((p.active >> p.first_active) & 1u)) ++p.first_active;
-    if (p.first_active == kTile) p.first_active = 0;
     align16(bytes);
     const size_t base = bytes->size();
     std::vector<float2> facf(4 * kTile);
-    for (int b = 0; b < kTile; ++b)
-        for (int c = 0; c < 4; ++c) facf[4 * b + c] = f2(fac[b][c]);
+    for (int b = 0; b < kTile; ++b) {
+        if (p.rotation)
+            facf[b] = make_float2(static_cast<float>(rc[b]), static_cast<float>(rs[b]));
+        else
+            for (int c = 0; c < 4; ++c) facf[4 * b + c] = f2(fac[b][c]);
+    }
     p.off_fac = append(bytes, facf.data(), facf.size()) - base;
     p.off_cross = append(bytes, cross.data(), cross.size()) - base;
     p.off_out = append(bytes, outg.data(), outg.size()) - base;
     if (!din.empty()) {
+        // round 0's order: entry (16 t + i) at i * 256 + t
         std::vector<float2> df(din.size());
-        for (size_t j = 0; j < din.size(); ++j) df[j] = f2(din[j]);
+        for (size_t j = 0; j < din.size(); ++j) df[(j & 15) * 256 + (j >> 4)] = f2(din[j]);
         p.off_din = append(bytes, df.data(), df.size()) - base;
         p.has_din = true;
+    }
+    if (!dout.empty()) {
+        std::vector<float2> df(dout.size());
+        for (size_t j = 0; j < dout.size(); ++j) df[j] = f2(dout[j]);
+        p.off_dout = append(bytes, df.data(), df.size()) - base;
+        p.has_dout = true;
     }
     align16(bytes);
     p.bytes = bytes->size() - base;

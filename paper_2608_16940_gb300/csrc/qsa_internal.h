@@ -104,12 +104,14 @@ struct LayerGate {
 };
 // Byte offsets of one launch's data in its device payload.
 struct LayerPayload {
-    uint32_t active = 0;      // tile bits with a factor or a per-tile phase
-    int first_active = 0;
+    uint32_t active = 0;      // tile bits with a factor
+    uint32_t pmask = 0;       // tile bits whose per-tile phases are multiplied in
     int ncross = 0, nout = 0;
     int cstart[13] = {};
-    bool has_din = false;     // 2^12-entry table of the gates with all qubits in the tile
-    size_t off_fac = 0, off_cross = 0, off_out = 0, off_din = 0, bytes = 0;
+    bool has_din = false;     // 2^12-entry entry table (gates with all qubits in the tile)
+    bool rotation = false;    // factors as real rotations (entry / exit tables hold their phases)
+    bool has_dout = false;    // rotation mode: exit table
+    size_t off_fac = 0, off_cross = 0, off_out = 0, off_din = 0, off_dout = 0, bytes = 0;
 };
 size_t layer_smem_bytes(bool with_din);
 cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const unsigned char* d_payload,

@@ -94,6 +94,26 @@ def test_layer_gate_classes(q):
     _run(q, n, diag, t, fac)
 
 
+@pytest.mark.parametrize("n,seed", [(16, 20), (13, 21)])
+def test_layer_non_unitary_factors(q, n, seed):
+    """Factors that are not unitary take the general complex butterflies (no
+    rotation split); mixed with unitary ones and with every gate class."""
+    rng = np.random.default_rng(seed)
+    t = [0, 2] + [int(v) for v in rng.choice(range(3, n), size=7, replace=False)]
+    fac = [W.haar_unitary(2, rng) for _ in t]
+    fac[3] = rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2))
+    _run(q, n, _diag_ops(n, 30, rng), t, fac)
+
+
+def test_layer_diagonal_and_antidiagonal_factors(q):
+    """Factors with a zero off-diagonal or a zero diagonal (the rotation split's
+    edge cases)."""
+    rng = np.random.default_rng(22)
+    t = [1, 5, 9, 14]
+    fac = [np.diag(np.exp(1j * rng.uniform(0, 6, 2))), W.X, np.array([[0, 1j], [1j, 0]]), W.H]
+    _run(q, 16, _diag_ops(16, 20, rng), t, fac)
+
+
 def test_layer_more_factors_than_a_tile_holds(q):
     """Twelve factors all at positions >= 3: two passes (diagonal ops in the first)."""
     n = 20
