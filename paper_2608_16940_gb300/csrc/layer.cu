@@ -41,6 +41,14 @@ constexpr int kLAmps = 1 << kLT;        // amplitudes per tile
 constexpr int kLThreads = 256;
 constexpr int kLStages = 2;
 
+// Per-tile phases of rotation mode, written by k_layer_records before the
+// pass: each pmask bit's (d0, d1) and the phases of round 0's 16 local
+// amplitudes (pmask bits 0..3) times the scalar of the out gates.
+struct LayerRec {
+    float2 ph[kLT][2];
+    float2 pl[16];
+};
+
 struct LayerArgs {
     float2* psi;
     uint64_t ntiles;
@@ -57,6 +65,7 @@ struct LayerArgs {
     const float2* din;        // entry table, 2^12 entries over tile-local bits stored as
                               // din[i * 256 + t] = entry(16 t + i) (round 0's access), or nullptr
     const float2* dout;       // rotation mode: exit table, 2^12 entries in tile-local order, or nullptr
+    const LayerRec* rec;      // rotation mode with per-tile phases: one record per tile, or nullptr
 };
 
 struct LayerShared {
@@ -122,8 +131,9 @@ __device__ __forceinline__ void rotation(float2 (&v)[16], float2 cs) {
 // or (last round) to HBM.
 template <bool ROT, int R>
 __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, const float2* dout_s,
-                                            const LayerShared& sh, const float2* rot, const uint64_t* runoff,
-                                            uint64_t base, bool last, bool phase) {
+                                            const float2 (*tf)[4], const float2 (*phs)[2], const float2* pls,
+                                            const float2* rot, const uint64_t* runoff, uint64_t base, bool last,
+                                            bool phase) {
     const int t = threadIdx.x;
     const int jb = (t & ((1 << (4 * R)) - 1)) | ((t >> (4 * R)) << (4 * R + 4));
     float2 v[16];
@@ -144,9 +154,9 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
             float2 ph = make_float2(1.f, 0.f);
 #pragma unroll
             for (int b = 4; b < kLT; ++b)
-                if ((a.pmask >> b) & 1u) ph = cmulf(ph, sh.ph[b][(jb >> b) & 1]);
+                if ((a.pmask >> b) & 1u) ph = cmulf(ph, phs[b][(jb >> b) & 1]);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = cmulf(v[i], cmulf(ph, sh.pl[i]));
+            for (int i = 0; i < 16; ++i) v[i] = cmulf(v[i], cmulf(ph, pls[i]));
         }
     } else {
 #pragma unroll
@@ -172,10 +182,10 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
             }
         }
     } else {
-        if (act & 1u) butterfly<0>(v, sh.tf[4 * R + 0]);
-        if (act & 2u) butterfly<1>(v, sh.tf[4 * R + 1]);
-        if (act & 4u) butterfly<2>(v, sh.tf[4 * R + 2]);
-        if (act & 8u) butterfly<3>(v, sh.tf[4 * R + 3]);
+        if (act & 1u) butterfly<0>(v, tf[4 * R + 0]);
+        if (act & 2u) butterfly<1>(v, tf[4 * R + 1]);
+        if (act & 4u) butterfly<2>(v, tf[4 * R + 2]);
+        if (act & 8u) butterfly<3>(v, tf[4 * R + 3]);
     }
     if (last) {
         if constexpr (R == 0) {
@@ -252,6 +262,59 @@ __device__ __forceinline__ void tile_phases(const LayerArgs& a, uint64_t base, L
     }
 }
 
+// Rotation mode: the per-tile phases of one tile into *out (one warp): the
+// scalar of the out gates and each pmask bit's cross phases; round 0's
+// local phases from bits 0..3 (shuffled from lanes 0..3).
+__device__ __forceinline__ void tile_record(const LayerArgs& a, uint64_t base, LayerRec* out) {
+    const int lane = threadIdx.x & 31;
+    float2 sc = make_float2(1.f, 0.f);
+    for (int g = lane; g < a.nout; g += 32) {
+        const LayerGate& G = a.outg[g];
+        int v = static_cast<int>((base >> G.a) & 1ull);
+        if (G.b >= 0) v |= static_cast<int>((base >> G.b) & 1ull) << 1;
+        sc = cmulf(sc, G.d[v]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float2 other;
+        other.x = __shfl_xor_sync(0xffffffffu, sc.x, o);
+        other.y = __shfl_xor_sync(0xffffffffu, sc.y, o);
+        sc = cmulf(sc, other);
+    }
+    float2 d0 = make_float2(1.f, 0.f), d1 = make_float2(1.f, 0.f);
+    if (lane < kLT && ((a.pmask >> lane) & 1u)) {
+        for (int g = a.cstart[lane]; g < a.cstart[lane + 1]; ++g) {
+            const LayerGate& G = a.cross[g];
+            const int o = static_cast<int>((base >> G.b) & 1ull);
+            d0 = cmulf(d0, G.d[2 * o]);
+            d1 = cmulf(d1, G.d[2 * o + 1]);
+        }
+    }
+    if (lane < kLT) {
+        out->ph[lane][0] = d0;
+        out->ph[lane][1] = d1;
+    }
+    float2 p = sc;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        float2 e0, e1;
+        e0.x = __shfl_sync(0xffffffffu, d0.x, b);
+        e0.y = __shfl_sync(0xffffffffu, d0.y, b);
+        e1.x = __shfl_sync(0xffffffffu, d1.x, b);
+        e1.y = __shfl_sync(0xffffffffu, d1.y, b);
+        p = cmulf(p, ((lane >> b) & 1) ? e1 : e0);
+    }
+    if (lane < 16) out->pl[lane] = p;
+}
+
+// One warp per tile: the records of a rotation-mode pass with per-tile phases.
+__global__ void __launch_bounds__(kLThreads) k_layer_records(LayerArgs a, LayerRec* recs) {
+    const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x >> 5);
+    for (uint64_t t = blockIdx.x * static_cast<uint64_t>(blockDim.x >> 5) + (threadIdx.x >> 5); t < a.ntiles;
+         t += warps)
+        tile_record(a, layer_base(a, t), recs + t);
+}
+
 template <bool ROT>
 __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -259,7 +322,8 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
     uint64_t* runoff = reinterpret_cast<uint64_t*>(stage + kLStages * kLAmps);  // 512
     LayerShared& sh = *reinterpret_cast<LayerShared*>(runoff + 512);
     float2* rot = reinterpret_cast<float2*>(&sh + 1);                           // kLT
-    float2* dout_s = a.dout ? rot + kLT : nullptr;                              // 4096, swizzled
+    LayerRec* recs = reinterpret_cast<LayerRec*>(rot + kLT);                    // kLStages
+    float2* dout_s = a.dout ? reinterpret_cast<float2*>(recs + kLStages) : nullptr;  // 4096, swizzled
 
     for (int r = threadIdx.x; r < (1 << a.nx); r += blockDim.x) {
         uint64_t off = 0;
@@ -287,32 +351,41 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
         }
 
     const uint64_t stride = gridDim.x;
-    auto load = [&](uint64_t t, float2* st) {
+    // rotation mode takes the per-tile phases from the records (fetched with
+    // the tile), general mode forms them in warp 0
+    const bool use_rec = ROT && a.rec;
+    auto load = [&](uint64_t t, int sidx) {
         const uint64_t base = layer_base(a, t);
+        float2* st = stage + sidx * kLAmps;
         for (int c = threadIdx.x; c < kLAmps / 2; c += blockDim.x)
             cp_async16(st + lsw(2 * c), a.psi + layer_global(a, runoff, base, 2 * c));
+        if (use_rec && threadIdx.x < static_cast<int>(sizeof(LayerRec) / 16))
+            cp_async16(reinterpret_cast<float4*>(recs + sidx) + threadIdx.x,
+                       reinterpret_cast<const float4*>(a.rec + t) + threadIdx.x);
     };
-    if (blockIdx.x < a.ntiles) load(blockIdx.x, stage);
+    if (blockIdx.x < a.ntiles) load(blockIdx.x, 0);
     cp_async_commit();
     int cur = 0;
     for (uint64_t t = blockIdx.x; t < a.ntiles; t += stride) {
         const uint64_t tn = t + stride;
-        if (tn < a.ntiles) load(tn, stage + (cur ^ 1) * kLAmps);
+        if (tn < a.ntiles) load(tn, cur ^ 1);
         cp_async_commit();
         const uint64_t base = layer_base(a, t);
-        if (dynamic && threadIdx.x < 32) tile_phases<ROT>(a, base, sh);
+        if (dynamic && !use_rec && threadIdx.x < 32) tile_phases<ROT>(a, base, sh);
         cp_async_wait<1>();
         __syncthreads();
         float2* st = stage + cur * kLAmps;
+        const float2(*phs)[2] = use_rec ? recs[cur].ph : sh.ph;
+        const float2* pls = use_rec ? recs[cur].pl : sh.pl;
         if (first == 0) {
-            layer_round<ROT, 0>(a, st, dout_s, sh, rot, runoff, base, last == 0, phase);
+            layer_round<ROT, 0>(a, st, dout_s, sh.tf, phs, pls, rot, runoff, base, last == 0, phase);
             if (last > 0) __syncthreads();
         }
         if (first <= 1 && last >= 1 && ((a.fmask >> 4) & 15u)) {
-            layer_round<ROT, 1>(a, st, dout_s, sh, rot, runoff, base, last == 1, phase);
+            layer_round<ROT, 1>(a, st, dout_s, sh.tf, phs, pls, rot, runoff, base, last == 1, phase);
             if (last > 1) __syncthreads();
         }
-        if (last == 2) layer_round<ROT, 2>(a, st, dout_s, sh, rot, runoff, base, true, phase);
+        if (last == 2) layer_round<ROT, 2>(a, st, dout_s, sh.tf, phs, pls, rot, runoff, base, true, phase);
         __syncthreads();
         cur ^= 1;
     }
@@ -323,11 +396,13 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
 
 size_t layer_smem_bytes(bool with_dout) {
     return sizeof(float2) * kLStages * kLAmps + sizeof(uint64_t) * 512 + sizeof(LayerShared) +
-           sizeof(float2) * kLT + (with_dout ? sizeof(float2) * kLAmps : 0);
+           sizeof(float2) * kLT + sizeof(LayerRec) * kLStages + (with_dout ? sizeof(float2) * kLAmps : 0);
 }
 
+size_t layer_record_bytes(int n) { return n < kLT ? 0 : sizeof(LayerRec) << (n - kLT); }
+
 cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const unsigned char* d_payload,
-                               const LayerPayload& p, cudaStream_t st, uint64_t* launches) {
+                               const LayerPayload& p, void* d_rec, cudaStream_t st, uint64_t* launches) {
     if (n < kLT || g.m + g.nx != kLT || g.m < 3) return cudaErrorInvalidValue;
     LayerArgs a{};
     a.psi = psi;
@@ -354,6 +429,15 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
             if (e != cudaSuccess) return e;
         }
         attr_set = true;
+    }
+    if (p.rotation && (p.ncross > 0 || p.nout > 0)) {
+        if (!d_rec) return cudaErrorInvalidValue;
+        a.rec = static_cast<const LayerRec*>(d_rec);
+        uint64_t nb = (a.ntiles + kLThreads / 32 - 1) / (kLThreads / 32);
+        const uint64_t cap = static_cast<uint64_t>(num_sms()) * 8;
+        if (nb > cap) nb = cap;
+        k_layer_records<<<static_cast<unsigned>(nb), kLThreads, 0, st>>>(a, static_cast<LayerRec*>(d_rec));
+        ++*launches;
     }
     auto kern = p.rotation ? k_apply_layer<true> : k_apply_layer<false>;
     int occ = 0;

@@ -234,10 +234,15 @@ std::vector<LayerLaunch> prepare_layer(int n, const int32_t* L, const LayerSpec&
 qsa_status run_layer_launches(qsa_state s, const std::vector<LayerLaunch>& ls, const unsigned char* d_base,
                               qsa_run_stats* rs) {
     for (const LayerLaunch& ll : ls) {
+        if (ll.p.rotation && (ll.p.ncross > 0 || ll.p.nout > 0)) {
+            qsa_status st = ensure_dev(s, &s->d_lrec, &s->lrec_cap, layer_record_bytes(s->n));
+            if (st != QSA_OK) return st;
+        }
         cudaError_t e;
         {
             Timer tm(s, rs ? &rs->layer_seconds : nullptr);
-            e = launch_apply_layer(s->psi, s->n, ll.g, d_base + ll.dev_off, ll.p, s->stream, &s->launches);
+            e = launch_apply_layer(s->psi, s->n, ll.g, d_base + ll.dev_off, ll.p, s->d_lrec, s->stream,
+                                   &s->launches);
             tm.stop();
         }
         if (e != cudaSuccess) return cuda_fail(s, e, "layer kernel");

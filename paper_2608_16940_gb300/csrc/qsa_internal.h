@@ -114,8 +114,11 @@ struct LayerPayload {
     size_t off_fac = 0, off_cross = 0, off_out = 0, off_din = 0, off_dout = 0, bytes = 0;
 };
 size_t layer_smem_bytes(bool with_din);
+// Rotation-mode passes with per-tile phases first write one record per tile
+// to d_rec (device, layer_record_bytes(n) bytes; the call fails without it).
+size_t layer_record_bytes(int n);
 cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const unsigned char* d_payload,
-                               const LayerPayload& p, cudaStream_t st, uint64_t* launches);
+                               const LayerPayload& p, void* d_rec, cudaStream_t st, uint64_t* launches);
 
 // In-place swap of physical bit pairs (pa[i] <-> pb[i]), all positions distinct.
 cudaError_t launch_permute(float2* psi, int n, const int* pa, const int* pb, int npairs, cudaStream_t st,

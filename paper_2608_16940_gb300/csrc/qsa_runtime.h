@@ -33,6 +33,8 @@ struct qsa_state_s {
     size_t mlp_cap = 0;
     double* d_dm = nullptr;           // density-matrix diagonal readout
     size_t dm_cap = 0;
+    void* d_lrec = nullptr;           // per-tile records of layer passes
+    size_t lrec_cap = 0;
     int* d_err = nullptr;             // device error word written by bounded waits
     // CUDA-event timers
     struct Pending {

@@ -357,6 +357,7 @@ qsa_status qsa_state_destroy(qsa_state s) {
     if (s->d_mat) cudaFree(s->d_mat);
     if (s->d_red) cudaFree(s->d_red);
     if (s->d_dm) cudaFree(s->d_dm);
+    if (s->d_lrec) cudaFree(s->d_lrec);
     if (s->d_samp) cudaFree(s->d_samp);
     if (s->d_err) cudaFree(s->d_err);
     if (s->d_mlp) cudaFree(s->d_mlp);
