@@ -14,11 +14,12 @@
 //           has no factor;
 //   out     (no qubit in the tile): a scalar per tile, multiplied in.
 // Unitary factors run in rotation mode: each factor is split on the host as
-// F = diag(p) R diag(q) with R = [[c, -s], [s, c]] real, all q folded into
-// the entry table, all p into an exit table, so a factor costs a real
-// rotation (4 multiply-adds per amplitude instead of 8); the cross phases of
-// every bit are then multiplied in (they precede the rotation).  Other
-// factors run in general mode (complex 2x2 butterflies, cross phases folded).
+// F = diag(p) R diag(q) with R = [[c, -s], [s, c]] real, so it costs a real
+// rotation (4 multiply-adds per amplitude instead of 8).  Its q phases join
+// the per-bit phases (with the cross phases, applied in round 0 before any
+// rotation) and its p phases a 16-entry table of its round (applied after
+// the round's rotations).  Other factors run in general mode (complex 2x2
+// butterflies, cross phases folded into them).
 // Per tile: 16-byte cp.async copies into a 2-stage ring (XOR-swizzled 16-byte
 // chunks); warp 0 forms the tile's phases; then three register rounds over
 // tile bits 0-3, 4-7 and 8-11 (each thread holds the 16 amplitudes that
@@ -62,9 +63,11 @@ struct LayerArgs {
                               // (cos, sin) of each factor's rotation
     const LayerGate* cross;   // a = tile bit, b = outside position, d[2 * o + v]
     const LayerGate* outg;    // a, b = positions (b < 0: one qubit), d[v_a + 2 v_b]
-    const float2* din;        // entry table, 2^12 entries over tile-local bits stored as
-                              // din[i * 256 + t] = entry(16 t + i) (round 0's access), or nullptr
-    const float2* dout;       // rotation mode: exit table, 2^12 entries in tile-local order, or nullptr
+    const float2* din;        // table of the gates with every qubit in the tile: 2^12 entries in
+                              // tile-local order (copied to shared memory), or nullptr
+    const float2* qph;        // rotation mode: each tile bit's entry phases q (kLT x 2)
+    const float2* rp;         // rotation mode: per round, the product of its factor bits' exit
+                              // phases p over the round's 16 local amplitudes (3 x 16)
     const LayerRec* rec;      // rotation mode with per-tile phases: one record per tile, or nullptr
 };
 
@@ -72,6 +75,7 @@ struct LayerShared {
     float2 tf[kLT][4];        // general mode: this tile's factors (cross phases folded in)
     float2 ph[kLT][2];        // per-tile phases of pmask bits
     float2 pl[16];            // per-tile phases of round 0's 16 local amplitudes times the scalar
+    float2 rp[3][16];         // rotation mode: per-round exit phases
 };
 
 // Slot of tile-local amplitude j: 16-byte chunk c = j / 2 is stored at
@@ -130,8 +134,8 @@ __device__ __forceinline__ void rotation(float2 (&v)[16], float2 cs) {
 // round, rotation mode) multiply by the exit table; write back to the stage
 // or (last round) to HBM.
 template <bool ROT, int R>
-__device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, const float2* dout_s,
-                                            const float2 (*tf)[4], const float2 (*phs)[2], const float2* pls,
+__device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, const float2* din_s,
+                                            const LayerShared& sh, const float2 (*phs)[2], const float2* pls,
                                             const float2* rot, const uint64_t* runoff, uint64_t base, bool last,
                                             bool phase) {
     const int t = threadIdx.x;
@@ -144,10 +148,13 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
             v[i] = make_float2(p.x, p.y);
             v[i + 1] = make_float2(p.z, p.w);
         }
-        if (a.din) {
-            const float2* dt = a.din + t;
+        if (din_s) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = cmulf(v[i], __ldg(dt + i * (kLThreads)));
+            for (int i = 0; i < 16; i += 2) {
+                const float4 d = *reinterpret_cast<const float4*>(din_s + lsw(jb | i));
+                v[i] = cmulf(v[i], make_float2(d.x, d.y));
+                v[i + 1] = cmulf(v[i + 1], make_float2(d.z, d.w));
+            }
         }
         if (phase) {
             // phases of pmask bits 4..11 (fixed for this thread) times those of the 16 local amplitudes
@@ -168,24 +175,16 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
         if (act & 2u) rotation<1>(v, rot[4 * R + 1]);
         if (act & 4u) rotation<2>(v, rot[4 * R + 2]);
         if (act & 8u) rotation<3>(v, rot[4 * R + 3]);
-        if (last && dout_s) {
-            if constexpr (R == 0) {
+        if (act) {
+            // exit phases of the round's factor bits (they follow only their own rotations)
 #pragma unroll
-                for (int i = 0; i < 16; i += 2) {
-                    const float4 d = *reinterpret_cast<const float4*>(dout_s + lsw(jb | i));
-                    v[i] = cmulf(v[i], make_float2(d.x, d.y));
-                    v[i + 1] = cmulf(v[i + 1], make_float2(d.z, d.w));
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] = cmulf(v[i], dout_s[lsw(jb | (i << (4 * R)))]);
-            }
+            for (int i = 0; i < 16; ++i) v[i] = cmulf(v[i], sh.rp[R][i]);
         }
     } else {
-        if (act & 1u) butterfly<0>(v, tf[4 * R + 0]);
-        if (act & 2u) butterfly<1>(v, tf[4 * R + 1]);
-        if (act & 4u) butterfly<2>(v, tf[4 * R + 2]);
-        if (act & 8u) butterfly<3>(v, tf[4 * R + 3]);
+        if (act & 1u) butterfly<0>(v, sh.tf[4 * R + 0]);
+        if (act & 2u) butterfly<1>(v, sh.tf[4 * R + 1]);
+        if (act & 4u) butterfly<2>(v, sh.tf[4 * R + 2]);
+        if (act & 8u) butterfly<3>(v, sh.tf[4 * R + 3]);
     }
     if (last) {
         if constexpr (R == 0) {
@@ -291,6 +290,9 @@ __device__ __forceinline__ void tile_record(const LayerArgs& a, uint64_t base, L
         }
     }
     if (lane < kLT) {
+        // the bit's entry phases of its rotation (identity without a factor)
+        d0 = cmulf(d0, a.qph[2 * lane]);
+        d1 = cmulf(d1, a.qph[2 * lane + 1]);
         out->ph[lane][0] = d0;
         out->ph[lane][1] = d1;
     }
@@ -323,7 +325,7 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
     LayerShared& sh = *reinterpret_cast<LayerShared*>(runoff + 512);
     float2* rot = reinterpret_cast<float2*>(&sh + 1);                           // kLT
     LayerRec* recs = reinterpret_cast<LayerRec*>(rot + kLT);                    // kLStages
-    float2* dout_s = a.dout ? reinterpret_cast<float2*>(recs + kLStages) : nullptr;  // 4096, swizzled
+    float2* din_s = a.din ? reinterpret_cast<float2*>(recs + kLStages) : nullptr;  // 4096, swizzled
 
     for (int r = threadIdx.x; r < (1 << a.nx); r += blockDim.x) {
         uint64_t off = 0;
@@ -335,11 +337,26 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
     const bool phase = a.pmask != 0 || a.nout > 0;
     if (ROT) {
         if (threadIdx.x < kLT) rot[threadIdx.x] = a.fac[threadIdx.x];
+        for (int i = threadIdx.x; i < 48; i += blockDim.x) sh.rp[i >> 4][i & 15] = a.rp[i];
+        if (!dynamic && threadIdx.x < 32) {
+            // static phases: the rotations' entry phases only
+            const int lane = threadIdx.x;
+            if (lane < kLT) {
+                sh.ph[lane][0] = a.qph[2 * lane];
+                sh.ph[lane][1] = a.qph[2 * lane + 1];
+            }
+            if (lane < 16) {
+                float2 p = make_float2(1.f, 0.f);
+                for (int b = 0; b < 4; ++b)
+                    if ((a.pmask >> b) & 1u) p = cmulf(p, a.qph[2 * b + ((lane >> b) & 1)]);
+                sh.pl[lane] = p;
+            }
+        }
     } else if (!dynamic) {
         for (int i = threadIdx.x; i < 4 * kLT; i += blockDim.x) sh.tf[i >> 2][i & 3] = a.fac[i];
     }
-    if (dout_s)
-        for (int j = threadIdx.x; j < kLAmps; j += blockDim.x) dout_s[lsw(j)] = a.dout[j];
+    if (din_s)
+        for (int j = threadIdx.x; j < kLAmps; j += blockDim.x) din_s[lsw(j)] = a.din[j];
     __syncthreads();
 
     // rounds that do work; the last of them writes to HBM
@@ -363,30 +380,43 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
             cp_async16(reinterpret_cast<float4*>(recs + sidx) + threadIdx.x,
                        reinterpret_cast<const float4*>(a.rec + t) + threadIdx.x);
     };
+    // Barriers per tile: one after the tile lands (it also frees the other
+    // buffer, whose tile every thread has finished, for the next copies) and
+    // one before round 2.  Round 0 hands data to round 1 inside a warp: round-1
+    // thread u reads what round-0 threads 16 (u >> 4) .. 16 (u >> 4) + 15 wrote,
+    // so a warp barrier suffices there.  General mode with per-tile factors
+    // rewrites the shared factors each tile and keeps an end-of-tile barrier.
+    const bool r1 = ((a.fmask >> 4) & 15u) != 0;
+    const bool end_sync = dynamic && !use_rec;
     if (blockIdx.x < a.ntiles) load(blockIdx.x, 0);
     cp_async_commit();
     int cur = 0;
     for (uint64_t t = blockIdx.x; t < a.ntiles; t += stride) {
+        const uint64_t base = layer_base(a, t);
+        if (end_sync && threadIdx.x < 32) tile_phases<ROT>(a, base, sh);
+        cp_async_wait<0>();
+        __syncthreads();
         const uint64_t tn = t + stride;
         if (tn < a.ntiles) load(tn, cur ^ 1);
         cp_async_commit();
-        const uint64_t base = layer_base(a, t);
-        if (dynamic && !use_rec && threadIdx.x < 32) tile_phases<ROT>(a, base, sh);
-        cp_async_wait<1>();
-        __syncthreads();
         float2* st = stage + cur * kLAmps;
         const float2(*phs)[2] = use_rec ? recs[cur].ph : sh.ph;
         const float2* pls = use_rec ? recs[cur].pl : sh.pl;
         if (first == 0) {
-            layer_round<ROT, 0>(a, st, dout_s, sh.tf, phs, pls, rot, runoff, base, last == 0, phase);
-            if (last > 0) __syncthreads();
+            layer_round<ROT, 0>(a, st, din_s, sh, phs, pls, rot, runoff, base, last == 0, phase);
+            if (last > 0) {
+                if (r1)
+                    __syncwarp();
+                else
+                    __syncthreads();
+            }
         }
-        if (first <= 1 && last >= 1 && ((a.fmask >> 4) & 15u)) {
-            layer_round<ROT, 1>(a, st, dout_s, sh.tf, phs, pls, rot, runoff, base, last == 1, phase);
+        if (first <= 1 && last >= 1 && r1) {
+            layer_round<ROT, 1>(a, st, din_s, sh, phs, pls, rot, runoff, base, last == 1, phase);
             if (last > 1) __syncthreads();
         }
-        if (last == 2) layer_round<ROT, 2>(a, st, dout_s, sh.tf, phs, pls, rot, runoff, base, true, phase);
-        __syncthreads();
+        if (last == 2) layer_round<ROT, 2>(a, st, din_s, sh, phs, pls, rot, runoff, base, true, phase);
+        if (end_sync) __syncthreads();
         cur ^= 1;
     }
     cp_async_wait<0>();
@@ -394,9 +424,9 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
 
 }  // namespace
 
-size_t layer_smem_bytes(bool with_dout) {
+size_t layer_smem_bytes(bool with_din) {
     return sizeof(float2) * kLStages * kLAmps + sizeof(uint64_t) * 512 + sizeof(LayerShared) +
-           sizeof(float2) * kLT + sizeof(LayerRec) * kLStages + (with_dout ? sizeof(float2) * kLAmps : 0);
+           sizeof(float2) * kLT + sizeof(LayerRec) * kLStages + (with_din ? sizeof(float2) * kLAmps : 0);
 }
 
 size_t layer_record_bytes(int n) { return n < kLT ? 0 : sizeof(LayerRec) << (n - kLT); }
@@ -419,8 +449,9 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
     a.cross = reinterpret_cast<const LayerGate*>(d_payload + p.off_cross);
     a.outg = reinterpret_cast<const LayerGate*>(d_payload + p.off_out);
     a.din = p.has_din ? reinterpret_cast<const float2*>(d_payload + p.off_din) : nullptr;
-    a.dout = p.has_dout ? reinterpret_cast<const float2*>(d_payload + p.off_dout) : nullptr;
-    const size_t smem = layer_smem_bytes(p.has_dout);
+    a.qph = reinterpret_cast<const float2*>(d_payload + p.off_qph);
+    a.rp = reinterpret_cast<const float2*>(d_payload + p.off_rp);
+    const size_t smem = layer_smem_bytes(p.has_din);
     static bool attr_set = false;
     if (!attr_set) {
         for (auto kern : {k_apply_layer<true>, k_apply_layer<false>}) {

@@ -144,19 +144,23 @@ bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vec
             }
         }
     }
-    p.pmask = p.rotation ? cross_bits : (cross_bits & ~p.active);
+    p.pmask = p.rotation ? (cross_bits | p.active) : (cross_bits & ~p.active);
     if (p.active == 0 && p.pmask == 0 && outg.empty() && din.empty()) return false;
-    std::vector<std::complex<double>> dout;
-    if (p.rotation && p.active) {
-        // entry table times every q, exit table of every p
-        if (din.empty()) din.assign(1u << kTile, 1.0);
-        dout.assign(1u << kTile, 1.0);
-        for (uint32_t j = 0; j < (1u << kTile); ++j)
-            for (int b = 0; b < kTile; ++b)
-                if ((p.active >> b) & 1u) {
-                    din[j] *= rq[b][(j >> b) & 1u];
-                    dout[j] *= rp[b][(j >> b) & 1u];
-                }
+    // rotation mode: each bit's q phases; per round, the product of its bits' p phases
+    std::vector<float2> qph(2 * kTile, make_float2(1.f, 0.f)), rpt(48, make_float2(1.f, 0.f));
+    if (p.rotation) {
+        for (int b = 0; b < kTile; ++b)
+            if ((p.active >> b) & 1u) {
+                qph[2 * b] = f2(rq[b][0]);
+                qph[2 * b + 1] = f2(rq[b][1]);
+            }
+        for (int r = 0; r < 3; ++r)
+            for (int i = 0; i < 16; ++i) {
+                std::complex<double> z = 1.0;
+                for (int lb = 0; lb < 4; ++lb)
+                    if ((p.active >> (4 * r + lb)) & 1u) z *= rp[4 * r + lb][(i >> lb) & 1];
+                rpt[16 * r + i] = f2(z);
+            }
     }
     std::stable_sort(cross.begin(), cross.end(), [](const LayerGate& x, const LayerGate& y) { return x.a < y.a; });
     p.ncross = static_cast<int>(cross.size());
@@ -175,20 +179,15 @@ bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vec
             for (int c = 0; c < 4; ++c) facf[4 * b + c] = f2(fac[b][c]);
     }
     p.off_fac = append(bytes, facf.data(), facf.size()) - base;
+    p.off_qph = append(bytes, qph.data(), qph.size()) - base;
+    p.off_rp = append(bytes, rpt.data(), rpt.size()) - base;
     p.off_cross = append(bytes, cross.data(), cross.size()) - base;
     p.off_out = append(bytes, outg.data(), outg.size()) - base;
     if (!din.empty()) {
-        // round 0's order: entry (16 t + i) at i * 256 + t
         std::vector<float2> df(din.size());
-        for (size_t j = 0; j < din.size(); ++j) df[(j & 15) * 256 + (j >> 4)] = f2(din[j]);
+        for (size_t j = 0; j < din.size(); ++j) df[j] = f2(din[j]);
         p.off_din = append(bytes, df.data(), df.size()) - base;
         p.has_din = true;
-    }
-    if (!dout.empty()) {
-        std::vector<float2> df(dout.size());
-        for (size_t j = 0; j < dout.size(); ++j) df[j] = f2(dout[j]);
-        p.off_dout = append(bytes, df.data(), df.size()) - base;
-        p.has_dout = true;
     }
     align16(bytes);
     p.bytes = bytes->size() - base;

@@ -108,10 +108,9 @@ struct LayerPayload {
     uint32_t pmask = 0;       // tile bits whose per-tile phases are multiplied in
     int ncross = 0, nout = 0;
     int cstart[13] = {};
-    bool has_din = false;     // 2^12-entry entry table (gates with all qubits in the tile)
-    bool rotation = false;    // factors as real rotations (entry / exit tables hold their phases)
-    bool has_dout = false;    // rotation mode: exit table
-    size_t off_fac = 0, off_cross = 0, off_out = 0, off_din = 0, off_dout = 0, bytes = 0;
+    bool has_din = false;     // 2^12-entry table of the gates with every qubit in the tile
+    bool rotation = false;    // factors as real rotations (their phases as per-bit and per-round tables)
+    size_t off_fac = 0, off_cross = 0, off_out = 0, off_din = 0, off_qph = 0, off_rp = 0, bytes = 0;
 };
 size_t layer_smem_bytes(bool with_din);
 // Rotation-mode passes with per-tile phases first write one record per tile
