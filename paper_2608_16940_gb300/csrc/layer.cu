@@ -116,16 +116,17 @@ __device__ __forceinline__ void butterfly(float2 (&v)[16], const float2* F) {
     }
 }
 
-// Real rotation [[c, -s], [s, c]] on local bit LB.
+// Real rotation [[c, -s], [s, c]] on local bit LB: both components of an
+// amplitude in one packed pair, two fma.rn.f32x2 per output.
 template <int LB>
 __device__ __forceinline__ void rotation(float2 (&v)[16], float2 cs) {
-    const float c = cs.x, s = cs.y;
+    const uint64_t c2 = pack2(cs.x, cs.x), s2 = pack2(cs.y, cs.y), ns2 = pack2(-cs.y, -cs.y);
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         if ((i >> LB) & 1) continue;
-        const float2 x0 = v[i], x1 = v[i | (1 << LB)];
-        v[i] = make_float2(fmaf(c, x0.x, -s * x1.x), fmaf(c, x0.y, -s * x1.y));
-        v[i | (1 << LB)] = make_float2(fmaf(s, x0.x, c * x1.x), fmaf(s, x0.y, c * x1.y));
+        const uint64_t x0 = pack2(v[i].x, v[i].y), x1 = pack2(v[i | (1 << LB)].x, v[i | (1 << LB)].y);
+        v[i] = unpack2(fma2(c2, x0, fma2(ns2, x1, 0ull)));
+        v[i | (1 << LB)] = unpack2(fma2(s2, x0, fma2(c2, x1, 0ull)));
     }
 }
 
