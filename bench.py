@@ -207,6 +207,17 @@ def cpu_baseline(n_s: int, seed: int, p: int, workload: str = "qaoa", p_dep: flo
             "sample": f"{what} at N={n_s}, {dt:.1f} s single-threaded FP64"}
 
 
+def interleaved_layout(n: int, ways: int = 3):
+    """Physical position of logical qubit q: qubits q = g (mod ways) fill the
+    g-th block of positions in order.  A run of consecutive qubits (a layer of
+    one-qubit gates taken in qubit order) then spreads over low, middle and
+    high positions, so no tile of a layer pass holds many of the highest
+    positions (each of those spreads a tile over more 2 MiB pages)."""
+    sizes = [len(range(g, n, ways)) for g in range(ways)]
+    off = [sum(sizes[:g]) for g in range(ways)]
+    return [off[q % ways] + q // ways for q in range(n)]
+
+
 def train_cost_model(q, s, precision, seed, n_samples):
     """Collect timings of the library's own kernels on the bench state, train
     the cost model on the GPU and install it; returns its held-out error."""
@@ -246,6 +257,8 @@ def main():
     ap.add_argument("--lowering", default="auto", choices=["auto", "strided", "permute"])
     ap.add_argument("--victim", default="first_free", choices=["first_free", "farthest"],
                     help="eviction rule of --lowering permute promotions")
+    ap.add_argument("--layout", default="interleave", choices=["identity", "interleave"],
+                    help="initial layout, set on |0...0> as a metadata-only relabel before each step")
     ap.add_argument("--cm-samples", type=int, default=240)
     ap.add_argument("--ref-qubits", type=int, default=28)
     ap.add_argument("--cpu-qubits", type=int, default=28)
@@ -293,7 +306,13 @@ def main():
     if planner == 3:
         cm = train_cost_model(q, s, prec, args.seed, args.cm_samples)
         q.qsa_state_reset(s)
-    plan = q.qsa_plan_create(ops, n, opts)
+    layout = interleaved_layout(n) if args.layout == "interleave" else None
+    plan = q.qsa_plan_create(ops, n, opts, layout=layout)
+
+    def reset():
+        q.qsa_state_reset(s)
+        if layout is not None:
+            q.qsa_set_layout(s, layout, 0)   # |0...0>: relabel only, no data moves
     pinfo = q.qsa_plan_info(plan)
     edge_mask = (1 << edges[0][0]) | (1 << edges[0][1])
 
@@ -302,7 +321,7 @@ def main():
            "diag_blocks": 0, "prod_blocks": 0, "layer_blocks": 0}
 
     def step(record):
-        q.qsa_state_reset(s)
+        reset()
         st = q.qsa_plan_execute(s, plan)
         if dm:
             norm = q.qsa_dm_probabilities(s, n_dm, want_probs=False)[1]
@@ -380,7 +399,7 @@ def main():
         for _ in range(max(1, min(3, args.steps))):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            q.qsa_state_reset(s)
+            reset()
             st = q.qsa_apply_circuit(s, ops, q.make_opts(planner=planner, kmax=args.kmax, kmax_diag=kdiag,
                                                           precision=prec, lowering=low, victim=victim,
                                                           kmax_prod=args.kmax_prod, layer=args.layer))
@@ -441,6 +460,7 @@ def main():
                            "kmax_prod": args.kmax_prod, "layer": args.layer,
                            "precision": args.precision,
                            "lowering": args.lowering, "victim": args.victim, "fused_blocks": pinfo["blocks"],
+                           "layout": args.layout,
                            "l2": "state 8 GiB > 129 MB L2; no flush needed", "parallelism": f"replicas x{ws}"},
                 "gpu_launches": launches, "clocks": clocks, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "passes_per_step": agg["passes"] / args.steps,

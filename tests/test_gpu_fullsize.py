@@ -78,17 +78,23 @@ def test_fusion28_qft_closed_form_and_inverse_return(q):
         st.close()
 
 
-@pytest.mark.parametrize("kmax,kdiag,kprod,prec,layer", [(4, 4, 0, 0, 0), (6, 6, 0, 1, 0), (6, 12, 6, 1, 0),
-                                                       (6, 12, 0, 1, 1)],
-                         ids=["kmax4-fp32", "kmax6-3xtf32", "kdiag12-kprod6-3xtf32", "bench-layer-kdiag12-3xtf32"])
-def test_qaoa30_symmetries_and_fused_equals_per_gate(q, kmax, kdiag, kprod, prec, layer):
-    """The bench's workload and launch configuration (layer units, kmax 6,
-    diagonal blocks up to 12 qubits, split-TF32 for k = 5, 6), the product-unit
-    configuration and two dense-only ones."""
+@pytest.mark.parametrize("kmax,kdiag,kprod,prec,layer,interleave",
+                         [(4, 4, 0, 0, 0, False), (6, 6, 0, 1, 0, False), (6, 12, 6, 1, 0, False),
+                          (6, 12, 0, 1, 1, False), (6, 12, 0, 1, 1, True)],
+                         ids=["kmax4-fp32", "kmax6-3xtf32", "kdiag12-kprod6-3xtf32", "layer-kdiag12-3xtf32",
+                              "bench-interleaved-layer-kdiag12-3xtf32"])
+def test_qaoa30_symmetries_and_fused_equals_per_gate(q, kmax, kdiag, kprod, prec, layer, interleave):
+    """The bench's workload and launch configuration (interleaved initial
+    layout set on |0...0>, layer units, kmax 6, diagonal blocks up to 12
+    qubits, split-TF32 for k = 5, 6), layer units on the identity layout, the
+    product-unit configuration and two dense-only ones."""
     n = 30
     ops, edges = W.qaoa_circuit(n=n, p=8, seed=0)
     st = Big(q, n)
     try:
+        if interleave:
+            import bench
+            q.qsa_set_layout(st.h, bench.interleaved_layout(n), 0)
         stats = q.qsa_apply_circuit(st.h, ops, q.make_opts(planner=q.QSA_PLAN_DP, kmax=kmax, kmax_diag=kdiag,
                                                            kmax_prod=kprod, precision=prec, layer=layer))
         if layer:
