@@ -57,6 +57,7 @@ struct LayerArgs {
     int xpos[kLT];            // positions of tile bits m..11, ascending
     uint32_t fmask;           // tile bits with a factor
     uint32_t pmask;           // tile bits with a per-tile phase applied as a multiply
+    uint32_t rpmask;          // rotation mode: rounds with exit phases
     int ncross, nout;
     int cstart[kLT + 1];      // cross gates of tile bit b: [cstart[b], cstart[b + 1])
     const float2* fac;        // general mode: kLT x 4 complex (2x2 row-major); rotation mode:
@@ -176,7 +177,7 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
         if (act & 2u) rotation<1>(v, rot[4 * R + 1]);
         if (act & 4u) rotation<2>(v, rot[4 * R + 2]);
         if (act & 8u) rotation<3>(v, rot[4 * R + 3]);
-        if (act) {
+        if (act && ((a.rpmask >> R) & 1u)) {
             // exit phases of the round's factor bits (they follow only their own rotations)
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = cmulf(v[i], sh.rp[R][i]);
@@ -443,6 +444,7 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
     for (int e = 0; e < kLT; ++e) a.xpos[e] = e < g.nx ? g.xpos[e] : 0;
     a.fmask = p.active;
     a.pmask = p.pmask;
+    a.rpmask = p.rpmask;
     a.ncross = p.ncross;
     a.nout = p.nout;
     for (int b = 0; b <= kLT; ++b) a.cstart[b] = p.cstart[b];

@@ -148,6 +148,7 @@ bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vec
     if (p.active == 0 && p.pmask == 0 && outg.empty() && din.empty()) return false;
     // rotation mode: each bit's q phases; per round, the product of its bits' p phases
     std::vector<float2> qph(2 * kTile, make_float2(1.f, 0.f)), rpt(48, make_float2(1.f, 0.f));
+    p.rpmask = 0;
     if (p.rotation) {
         for (int b = 0; b < kTile; ++b)
             if ((p.active >> b) & 1u) {
@@ -160,6 +161,7 @@ bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vec
                 for (int lb = 0; lb < 4; ++lb)
                     if ((p.active >> (4 * r + lb)) & 1u) z *= rp[4 * r + lb][(i >> lb) & 1];
                 rpt[16 * r + i] = f2(z);
+                if (std::abs(z - 1.0) > 1e-15) p.rpmask |= 1u << r;
             }
     }
     std::stable_sort(cross.begin(), cross.end(), [](const LayerGate& x, const LayerGate& y) { return x.a < y.a; });
@@ -198,6 +200,26 @@ bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vec
 }
 
 }  // namespace
+
+void layer_move_exit_phases(LayerSpec* from, LayerSpec* to) {
+    std::vector<LayerDiagOp> moved;
+    for (size_t j = 0; j < from->f.size(); ++j) {
+        double c, s;
+        std::complex<double> p[2], q[2];
+        if (!split_rotation(from->f[j], &c, &s, p, q)) continue;
+        if (std::abs(std::abs(p[0]) - 1.0) > 1e-12 || std::abs(std::abs(p[1]) - 1.0) > 1e-12) continue;
+        if (std::abs(p[0] - 1.0) < 1e-15 && std::abs(p[1] - 1.0) < 1e-15) continue;
+        auto& F = from->f[j];
+        F = {std::conj(p[0]) * F[0], std::conj(p[0]) * F[1], std::conj(p[1]) * F[2], std::conj(p[1]) * F[3]};
+        LayerDiagOp d;
+        d.k = 1;
+        d.q[0] = from->t[j];
+        d.d[0] = p[0];
+        d.d[1] = p[1];
+        moved.push_back(d);
+    }
+    to->diag.insert(to->diag.begin(), moved.begin(), moved.end());
+}
 
 bool layer_fits(int n, const int* pos, int k) {
     const int T = std::min(kTile, n);

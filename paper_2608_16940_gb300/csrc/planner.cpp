@@ -574,7 +574,6 @@ qsa_status qsa_plan_create(const qsa_op* ops, size_t n_ops, int n_qubits, const 
                 pl.spec.t.push_back(kv.first);
                 pl.spec.f.push_back(kv.second);
             }
-            pl.launches = prepare_layer(n_qubits, p->L0.data(), pl.spec, &p->host_layer);
             b.layer = static_cast<int>(p->layers.size());
             b.n_diag = u.nd;
             b.k = static_cast<int>(pl.spec.t.size());
@@ -641,6 +640,13 @@ qsa_status qsa_plan_create(const qsa_op* ops, size_t n_ops, int n_qubits, const 
         p->max_width = std::max(p->max_width, b.k);
         while (p->host_mat.size() % 4) p->host_mat.push_back(0.f);  // 16-byte aligned matrices
     }
+    // consecutive layer blocks: the exit phases of each block's factors move
+    // to the next block's diagonal part; then every layer block's passes for
+    // the plan's layout
+    for (size_t i = 0; i + 1 < p->blocks.size(); ++i)
+        if (p->blocks[i].layer >= 0 && p->blocks[i + 1].layer >= 0)
+            layer_move_exit_phases(&p->layers[p->blocks[i].layer].spec, &p->layers[p->blocks[i + 1].layer].spec);
+    for (PlanLayer& pl : p->layers) pl.launches = prepare_layer(n_qubits, p->L0.data(), pl.spec, &p->host_layer);
     build_next_use(p);
     *out = p;
     return QSA_OK;

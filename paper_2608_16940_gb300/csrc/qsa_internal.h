@@ -110,6 +110,7 @@ struct LayerPayload {
     int cstart[13] = {};
     bool has_din = false;     // 2^12-entry table of the gates with every qubit in the tile
     bool rotation = false;    // factors as real rotations (their phases as per-bit and per-round tables)
+    uint32_t rpmask = 0;      // rotation mode: rounds whose exit phases are not all 1
     size_t off_fac = 0, off_cross = 0, off_out = 0, off_din = 0, off_qph = 0, off_rp = 0, bytes = 0;
 };
 size_t layer_smem_bytes(bool with_din);

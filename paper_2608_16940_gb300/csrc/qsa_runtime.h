@@ -144,6 +144,11 @@ qsa_status run_layer_launches(qsa_state s, const std::vector<LayerLaunch>& ls, c
 // Prepare for the state's current layout, upload to scratch and run (N < 12:
 // the diagonal and product kernels, op by op).
 qsa_status apply_layer_logical(qsa_state s, const LayerSpec& spec, qsa_run_stats* rs);
+// Plan-time hand-over between consecutive layer blocks: each unitary factor
+// F = diag(p) R diag(q) of *from becomes R diag(q), and diag(p) (a one-qubit
+// diagonal gate, which precedes every op of *to) joins the front of *to's
+// diagonal part, where it costs nothing extra.
+void layer_move_exit_phases(LayerSpec* from, LayerSpec* to);
 // Diagonal entries of a k = 1, 2 op (QSA_E_ARG if an off-diagonal entry is non-zero).
 qsa_status layer_diag_from_op(const qsa_op& op, LayerDiagOp* out);
 
