@@ -16,7 +16,8 @@ Contents
     and the grouping of a circuit into product units,
   - layer blocks (one-qubit factors preceded by one- and two-qubit diagonal
     gates on any qubits, one tile pass) and the commutation-aware grouping of
-    a circuit into them,
+    a circuit into them; the prefix of a circuit that a plan for |0...0>
+    prepares as a product state times diagonal gates, and that state,
   - density-matrix evolution by Kraus operators, its column-major
     vectorisation and the superoperator of a channel,
   - the Kronecker embedding and block product used by fusion (§IV-C: "within a
@@ -277,6 +278,48 @@ def layer_units(ops: Sequence, n: int, layout: Sequence[int] | None = None, look
         units.append((start, len(order), True, len(diag_part)))
         pending = [x for x in pending if x not in taken]
     return order, units
+
+
+def zero_init_prefix(ops: Sequence) -> int:
+    """Length of the prefix a plan for |0...0> prepares in one write-only pass:
+    ops are taken in circuit order while each is a one-qubit op on a qubit no
+    taken diagonal gate touches (it multiplies that qubit's state) or a
+    diagonal gate on at most two qubits (it is applied after all of them).
+    The prefix leaves psi(x) = prod_q a_q[x_q] * prod_g d_g(x), a_q the qubit's
+    ops applied to |0>."""
+    diag_touched = set()
+    for i, op in enumerate(ops):
+        t = tuple(op.targets)
+        if len(t) == 1 and t[0] not in diag_touched:
+            continue
+        if op.diag and len(t) <= 2:
+            diag_touched |= set(t)
+            continue
+        return i
+    return len(ops)
+
+
+def zero_init_state(n: int, ops: Sequence) -> np.ndarray:
+    """The prefix's state from its closed form: per-qubit vectors a_q (the
+    qubit's one-qubit ops applied to |0>), their Kronecker product, then the
+    diagonal gates' entries (``apply_diag``)."""
+    a = [np.array([1.0, 0.0], dtype=np.complex128) for _ in range(n)]
+    diags = []
+    for op in ops:
+        if len(op.targets) == 1 and not diags_touch(diags, op.targets[0]):
+            a[op.targets[0]] = np.asarray(op.matrix, dtype=np.complex128) @ a[op.targets[0]]
+        else:
+            diags.append(op)
+    psi = np.ones(1, dtype=np.complex128)
+    for q in range(n):
+        psi = np.kron(a[q], psi)      # qubit q is bit q of the index
+    for g in diags:
+        apply_diag(psi, g.targets, np.diag(np.asarray(g.matrix, dtype=np.complex128)).copy())
+    return psi
+
+
+def diags_touch(diags, q: int) -> bool:
+    return any(q in g.targets for g in diags)
 
 
 def layer_block(ops: Sequence, idx: Sequence[int], n_diag: int):
