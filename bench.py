@@ -253,6 +253,8 @@ def main():
     ap.add_argument("--kmax-prod", type=int, default=0, help="product-unit cap (0: off, 2..11)")
     ap.add_argument("--layer", type=int, default=1, choices=[0, 1],
                     help="1: layer units (diagonal gates + one-qubit factors in one tile pass)")
+    ap.add_argument("--zero-init", type=int, default=1, choices=[0, 1],
+                    help="1: the circuit's product-state prefix on |0...0> in one write-only pass")
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3"])
     ap.add_argument("--lowering", default="auto", choices=["auto", "strided", "permute"])
     ap.add_argument("--victim", default="first_free", choices=["first_free", "farthest"],
@@ -297,7 +299,7 @@ def main():
     kdiag = args.kmax_diag
     victim = {"first_free": 0, "farthest": 1}[args.victim]
     opts = q.make_opts(planner=planner, kmax=args.kmax, kmax_diag=kdiag, precision=prec, lowering=low, timing=1,
-                       victim=victim, kmax_prod=args.kmax_prod, layer=args.layer)
+                       victim=victim, kmax_prod=args.kmax_prod, layer=args.layer, zero_init=args.zero_init)
 
     buf = torch.empty(1 << n, dtype=torch.complex64, device=dev)
     stream = torch.cuda.current_stream(dev).cuda_stream
@@ -402,7 +404,8 @@ def main():
             reset()
             st = q.qsa_apply_circuit(s, ops, q.make_opts(planner=planner, kmax=args.kmax, kmax_diag=kdiag,
                                                           precision=prec, lowering=low, victim=victim,
-                                                          kmax_prod=args.kmax_prod, layer=args.layer))
+                                                          kmax_prod=args.kmax_prod, layer=args.layer,
+                                                          zero_init=args.zero_init))
             if dm:
                 q.qsa_dm_probabilities(s, n_dm, want_probs=False)
                 d2h = 8.0
@@ -457,7 +460,7 @@ def main():
                                         f"complex64 ({8 * (1 << n) / 2**30:g} GiB), {args.shots} shots + norm + "
                                         f"<ZZ> per step"),
                            "planner": args.planner, "kmax": args.kmax, "kmax_diag": kdiag,
-                           "kmax_prod": args.kmax_prod, "layer": args.layer,
+                           "kmax_prod": args.kmax_prod, "layer": args.layer, "zero_init": args.zero_init,
                            "precision": args.precision,
                            "lowering": args.lowering, "victim": args.victim, "fused_blocks": pinfo["blocks"],
                            "layout": args.layout,

@@ -138,6 +138,13 @@ typedef struct {
                                fit a tile), moving ops only across ops they commute with (lookahead 256
                                skipped ops); a layer unit runs as one layer block while it stays a block
                                of its own.  Replaces kmax_prod.  0: off.  Not used by batches */
+    int32_t zero_init;      /* 1: the plan runs on |0..0> (the state must be known zero when it starts,
+                               else QSA_E_STATE).  Its prefix of one-qubit ops, each on a qubit no
+                               earlier diagonal gate of the prefix touches, and diagonal gates on at most
+                               two qubits leaves prod_q a_q[x_q] * prod_g d_g(x) (a_q: the qubit's ops
+                               applied to |0>), written in one write-only pass (§IV-D: |0..0> is the
+                               state whose relabelling is free; here its evolution by a product of
+                               one-qubit ops is too).  0: off.  Not used by batches */
 } qsa_plan_opts;
 
 typedef struct {
@@ -351,7 +358,8 @@ qsa_status qsa_plan_blocks(qsa_plan p, size_t* first_op, int32_t* widths, size_t
  * qsa_plan_blocks indexes this order.  capacity >= n_ops, else QSA_E_RANGE. */
 qsa_status qsa_plan_order(qsa_plan p, size_t* order, size_t capacity);
 
-/* Kind of every block (0 dense, 1 diagonal, 2 product, 3 layer) and, for
+/* Kind of every block (0 dense, 1 diagonal, 2 product, 3 layer, 4 zero-state
+ * preparation of the zero_init prefix) and, for
  * layer blocks, how many of its ops (the first ones in execution order) are
  * its diagonal part (0 for other kinds).  Nullable outputs; capacity >=
  * n_blocks, else QSA_E_RANGE. */

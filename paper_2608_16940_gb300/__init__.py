@@ -58,7 +58,8 @@ class qsa_op(_c.Structure):
 class qsa_plan_opts(_c.Structure):
     _fields_ = [("planner", _c.c_int32), ("kmax", _c.c_int32), ("kmax_diag", _c.c_int32), ("window", _c.c_int32),
                 ("rounds", _c.c_int32), ("precision", _c.c_int32), ("lowering", _c.c_int32),
-                ("timing", _c.c_int32), ("victim", _c.c_int32), ("kmax_prod", _c.c_int32), ("layer", _c.c_int32)]
+                ("timing", _c.c_int32), ("victim", _c.c_int32), ("kmax_prod", _c.c_int32), ("layer", _c.c_int32),
+                ("zero_init", _c.c_int32)]
 
 
 class qsa_run_stats(_c.Structure):

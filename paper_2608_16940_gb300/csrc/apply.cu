@@ -652,6 +652,23 @@ cudaError_t launch_batch_evolve(const BatchArgs& a, cudaStream_t st, uint64_t* l
     return cudaGetLastError();
 }
 
+__global__ void k_fill_one(float4* psi2, uint64_t npairs) {
+    for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < npairs;
+         i += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+        psi2[i] = make_float4(1.f, 0.f, 1.f, 0.f);
+}
+
+cudaError_t launch_fill_one(float2* psi, int n, cudaStream_t st, uint64_t* launches) {
+    if (n < 1) return cudaErrorInvalidValue;
+    const uint64_t npairs = (1ull << n) >> 1;
+    uint64_t blocks = (npairs + 255) / 256;
+    const uint64_t cap = static_cast<uint64_t>(num_sms()) * 16;
+    if (blocks > cap) blocks = cap;
+    k_fill_one<<<static_cast<unsigned>(blocks), 256, 0, st>>>(reinterpret_cast<float4*>(psi), npairs);
+    ++*launches;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init_zero(float2* psi, int n, cudaStream_t st, uint64_t* launches) {
     cudaError_t e = cudaMemsetAsync(psi, 0, sizeof(float2) << n, st);
     if (e != cudaSuccess) return e;

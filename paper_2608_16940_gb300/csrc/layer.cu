@@ -58,6 +58,7 @@ struct LayerArgs {
     uint32_t fmask;           // tile bits with a factor
     uint32_t pmask;           // tile bits with a per-tile phase applied as a multiply
     uint32_t rpmask;          // rotation mode: rounds with exit phases
+    int generate;             // write-only: every amplitude enters as 1 (nothing is read)
     int ncross, nout;
     int cstart[kLT + 1];      // cross gates of tile bit b: [cstart[b], cstart[b + 1])
     const float2* fac;        // general mode: kLT x 4 complex (2x2 row-major); rotation mode:
@@ -144,11 +145,16 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
     const int jb = (t & ((1 << (4 * R)) - 1)) | ((t >> (4 * R)) << (4 * R + 4));
     float2 v[16];
     if constexpr (R == 0) {
+        if (a.generate) {
 #pragma unroll
-        for (int i = 0; i < 16; i += 2) {
-            const float4 p = *reinterpret_cast<const float4*>(stage + lsw(jb | i));
-            v[i] = make_float2(p.x, p.y);
-            v[i + 1] = make_float2(p.z, p.w);
+            for (int i = 0; i < 16; ++i) v[i] = make_float2(1.f, 0.f);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; i += 2) {
+                const float4 p = *reinterpret_cast<const float4*>(stage + lsw(jb | i));
+                v[i] = make_float2(p.x, p.y);
+                v[i + 1] = make_float2(p.z, p.w);
+            }
         }
         if (din_s) {
 #pragma unroll
@@ -376,8 +382,9 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
     auto load = [&](uint64_t t, int sidx) {
         const uint64_t base = layer_base(a, t);
         float2* st = stage + sidx * kLAmps;
-        for (int c = threadIdx.x; c < kLAmps / 2; c += blockDim.x)
-            cp_async16(st + lsw(2 * c), a.psi + layer_global(a, runoff, base, 2 * c));
+        if (!a.generate)
+            for (int c = threadIdx.x; c < kLAmps / 2; c += blockDim.x)
+                cp_async16(st + lsw(2 * c), a.psi + layer_global(a, runoff, base, 2 * c));
         if (use_rec && threadIdx.x < static_cast<int>(sizeof(LayerRec) / 16))
             cp_async16(reinterpret_cast<float4*>(recs + sidx) + threadIdx.x,
                        reinterpret_cast<const float4*>(a.rec + t) + threadIdx.x);
@@ -445,6 +452,8 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
     a.fmask = p.active;
     a.pmask = p.pmask;
     a.rpmask = p.rpmask;
+    a.generate = p.generate ? 1 : 0;
+    if (p.generate && (p.active != 0)) return cudaErrorInvalidValue;   // write-only passes carry no factors
     a.ncross = p.ncross;
     a.nout = p.nout;
     for (int b = 0; b <= kLT; ++b) a.cstart[b] = p.cstart[b];

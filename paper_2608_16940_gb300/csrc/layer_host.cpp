@@ -247,7 +247,10 @@ std::vector<LayerLaunch> prepare_layer(int n, const int32_t* L, const LayerSpec&
     }
     for (size_t i = 0; i < groups.size(); ++i) {
         LayerLaunch ll;
-        if (prepare_pass(n, L, spec, groups[i], i == 0, bytes, &ll)) out.push_back(ll);
+        if (prepare_pass(n, L, spec, groups[i], i == 0, bytes, &ll)) {
+            ll.p.generate = spec.generate;
+            out.push_back(ll);
+        }
     }
     return out;
 }
@@ -270,7 +273,7 @@ qsa_status run_layer_launches(qsa_state s, const std::vector<LayerLaunch>& ls, c
         s->known_zero = false;
         if (rs) {
             rs->passes += 1;
-            rs->hbm_bytes += 16.0 * static_cast<double>(1ull << s->n);
+            rs->hbm_bytes += (ll.p.generate ? 8.0 : 16.0) * static_cast<double>(1ull << s->n);
         }
     }
     if (rs) {
@@ -309,6 +312,11 @@ qsa_status apply_layer_logical(qsa_state s, const LayerSpec& spec, qsa_run_stats
             tab.push_back(static_cast<float>(f[c].real()));
             tab.push_back(static_cast<float>(f[c].imag()));
         }
+    if (spec.generate) {
+        cudaError_t e = launch_fill_one(s->psi, s->n, s->stream, &s->launches);
+        if (e != cudaSuccess) return cuda_fail(s, e, "fill kernel");
+        s->known_zero = false;
+    }
     if (tab.empty()) return QSA_OK;
     qsa_status st = ensure_dev(s, reinterpret_cast<void**>(&s->d_mat), &s->mat_cap, tab.size() * sizeof(float));
     if (st != QSA_OK) return st;

@@ -48,6 +48,7 @@ struct Unit {
     bool prod = false;   // product unit (one-qubit ops on >= 2 qubits), while a block of its own
     bool layer = false;  // layer unit, while a block of its own
     int nd = 0;          // layer unit: its first nd ops are the diagonal part
+    bool init = false;   // zero-state prefix (opts.zero_init)
 };
 
 using Scorer = double (*)(void* ctx, int width, bool diag, bool prod, uint64_t mask);
@@ -218,6 +219,7 @@ qsa_status normalise_opts(const qsa_plan_opts* in, qsa_plan_opts* o) {
     if (o->victim < 0 || o->victim > 1) return fail(QSA_E_ARG, "unknown victim rule");
     if (o->kmax_prod < 0 || o->kmax_prod > QSA_MAX_PROD) return fail(QSA_E_ARG, "kmax_prod must be in 0..11");
     if (o->layer < 0 || o->layer > 1) return fail(QSA_E_ARG, "layer must be 0 or 1");
+    if (o->zero_init < 0 || o->zero_init > 1) return fail(QSA_E_ARG, "zero_init must be 0 or 1");
     return QSA_OK;
 }
 
@@ -319,10 +321,48 @@ void layer_prepass(const qsa_op* ops, size_t n_ops, int n, const int32_t* L, std
     }
 }
 
+// Zero-state prefix: ops are taken in circuit order while each is a one-qubit
+// op on a qubit no taken diagonal gate touches, or a diagonal gate on at most
+// two qubits.
+size_t zero_init_prefix(const qsa_op* ops, size_t n_ops) {
+    uint64_t diag_touched = 0;
+    for (size_t i = 0; i < n_ops; ++i) {
+        const uint64_t Q = op_mask(ops[i]);
+        if (ops[i].k == 1 && !(Q & diag_touched)) continue;
+        if ((ops[i].flags & QSA_OP_DIAG) && ops[i].k <= 2) {
+            diag_touched |= Q;
+            continue;
+        }
+        return i;
+    }
+    return n_ops;
+}
+
 // Units over the execution order *order (the identity unless the layer
-// pre-pass moved ops), then the planner.
+// pre-pass moved ops), then the planner; with opts.zero_init the zero-state
+// prefix is one unit ahead of the rest.
 std::vector<Unit> plan(const qsa_op* ops, size_t n_ops, int n_qubits, const qsa_plan_opts& o, const int32_t* L,
                        std::vector<size_t>* order) {
+    const size_t P = o.zero_init ? zero_init_prefix(ops, n_ops) : 0;
+    if (P > 0) {
+        qsa_plan_opts rest_opts = o;
+        rest_opts.zero_init = 0;
+        std::vector<size_t> rest_order;
+        std::vector<Unit> rest = plan(ops + P, n_ops - P, n_qubits, rest_opts, L, &rest_order);
+        order->clear();
+        for (size_t i = 0; i < P; ++i) order->push_back(i);
+        for (size_t x : rest_order) order->push_back(x + P);
+        std::vector<Unit> units;
+        Unit u{0, false, 0, P};
+        u.init = true;
+        units.push_back(u);
+        for (Unit r : rest) {
+            r.s += P;
+            r.e += P;
+            units.push_back(r);
+        }
+        return units;
+    }
     int32_t ident[QSA_MAX_QUBITS];
     for (int q = 0; q < n_qubits; ++q) ident[q] = q;
     order->clear();
@@ -476,6 +516,7 @@ void qsa_plan_opts_default(qsa_plan_opts* o) {
     o->victim = QSA_VICTIM_FIRST_FREE;
     o->kmax_prod = 0;
     o->layer = 0;
+    o->zero_init = 0;
 }
 
 qsa_status qsa_plan_circuit(const qsa_op* ops, size_t n_ops, int n_qubits, const qsa_plan_opts* opts,
@@ -545,6 +586,47 @@ qsa_status qsa_plan_create(const qsa_op* ops, size_t n_ops, int n_qubits, const 
         PlanBlock& b = p->blocks[i];
         b.off = p->host_mat.size();
         b.first_op = u.s;
+        if (u.init) {
+            // zero-state preparation: each qubit's one-qubit ops applied to |0>
+            // as a one-qubit diagonal on an all-ones input, then the diagonal gates
+            PlanLayer pl;
+            pl.spec.generate = true;
+            std::vector<std::array<std::complex<double>, 2>> a(n_qubits, {1.0, 0.0});
+            std::vector<LayerDiagOp> gates;
+            uint64_t diag_touched = 0;
+            for (size_t x = u.s; x < u.e; ++x) {
+                const uint64_t Q = op_mask(ops[x]);
+                if (ops[x].k == 1 && !(Q & diag_touched)) {
+                    const int q = ops[x].targets[0];
+                    const double* g = ops[x].matrix;
+                    const std::complex<double> h00(g[0], g[1]), h01(g[2], g[3]), h10(g[4], g[5]), h11(g[6], g[7]);
+                    a[q] = {h00 * a[q][0] + h01 * a[q][1], h10 * a[q][0] + h11 * a[q][1]};
+                } else {
+                    LayerDiagOp d;
+                    st = layer_diag_from_op(ops[x], &d);
+                    if (st != QSA_OK) {
+                        delete p;
+                        return st;
+                    }
+                    gates.push_back(d);
+                    diag_touched |= Q;
+                }
+            }
+            for (int q = 0; q < n_qubits; ++q) {
+                LayerDiagOp d;
+                d.k = 1;
+                d.q[0] = q;
+                d.d[0] = a[q][0];
+                d.d[1] = a[q][1];
+                pl.spec.diag.push_back(d);
+            }
+            pl.spec.diag.insert(pl.spec.diag.end(), gates.begin(), gates.end());
+            b.init = true;
+            b.layer = static_cast<int>(p->layers.size());
+            b.k = 0;
+            p->layers.push_back(std::move(pl));
+            continue;
+        }
         if (u.layer) {
             // diagonal part, then per-qubit factor products (qubits ascending,
             // later ops on the left)
@@ -723,7 +805,7 @@ qsa_status qsa_plan_block_kinds(qsa_plan p, int32_t* kinds, int32_t* n_diag, siz
     if (capacity < p->blocks.size()) return fail(QSA_E_RANGE, "capacity smaller than the number of blocks");
     for (size_t i = 0; i < p->blocks.size(); ++i) {
         const PlanBlock& b = p->blocks[i];
-        if (kinds) kinds[i] = b.layer >= 0 ? 3 : b.prod ? 2 : b.diag ? 1 : 0;
+        if (kinds) kinds[i] = b.init ? 4 : b.layer >= 0 ? 3 : b.prod ? 2 : b.diag ? 1 : 0;
         if (n_diag) n_diag[i] = b.layer >= 0 ? b.n_diag : 0;
     }
     return QSA_OK;
@@ -783,7 +865,9 @@ qsa_status qsa_plan_execute(qsa_state s, qsa_plan p, qsa_run_stats* stats) {
     s->timing = p->opts.timing != 0;
     for (size_t i = 0; i < p->blocks.size(); ++i) {
         const PlanBlock& b = p->blocks[i];
-        if (b.layer >= 0) {
+        if (b.init && !s->known_zero) {
+            st = fail(QSA_E_STATE, "a zero_init plan needs the state |0..0>");
+        } else if (b.layer >= 0) {
             const PlanLayer& pl = p->layers[b.layer];
             if (s->n >= QSA_LAYER_TILE_BITS && std::equal(p->L0.begin(), p->L0.end(), s->L))
                 st = run_layer_launches(s, pl.launches, p->d_layer, rs);
@@ -923,6 +1007,7 @@ qsa_status qsa_batch_create(int n_qubits, int n_traj, const qsa_op* ops, const s
     if (o.kmax > 4) return fail(QSA_E_ARG, "batched trajectories fuse blocks of at most 4 qubits (kmax <= 4)");
     if (o.kmax_diag > o.kmax) return fail(QSA_E_ARG, "batched trajectories need kmax_diag <= kmax");
     if (o.layer) return fail(QSA_E_ARG, "batched trajectories take no layer units");
+    if (o.zero_init) return fail(QSA_E_ARG, "batched trajectories take no zero_init prefix");
     if (o.kmax_prod >= 2) return fail(QSA_E_ARG, "batched trajectories do not use product blocks (kmax_prod <= 1)");
     if (op_offsets[0] != 0) return fail(QSA_E_ARG, "op_offsets[0] must be 0");
     for (int t = 0; t < n_traj; ++t)

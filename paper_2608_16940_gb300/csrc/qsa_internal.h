@@ -63,6 +63,8 @@ cudaError_t launch_batch_sample(const float2* states, int n, int n_traj, uint32_
 
 // ---- launchers (return the first CUDA error; *launches incremented) --------
 cudaError_t launch_init_zero(float2* psi, int n, cudaStream_t st, uint64_t* launches);
+// Every amplitude set to 1 (the start of a write-only preparation on small states).
+cudaError_t launch_fill_one(float2* psi, int n, cudaStream_t st, uint64_t* launches);
 
 // FP32 fused dense update: phys[j] = physical position of target j (V order),
 // d_mat = 2*4^k floats (row-major, interleaved) in device memory.
@@ -111,6 +113,7 @@ struct LayerPayload {
     bool has_din = false;     // 2^12-entry table of the gates with every qubit in the tile
     bool rotation = false;    // factors as real rotations (their phases as per-bit and per-round tables)
     uint32_t rpmask = 0;      // rotation mode: rounds whose exit phases are not all 1
+    bool generate = false;    // write-only: the input is taken as 1 for every amplitude (not read)
     size_t off_fac = 0, off_cross = 0, off_out = 0, off_din = 0, off_qph = 0, off_rp = 0, bytes = 0;
 };
 size_t layer_smem_bytes(bool with_din);

@@ -53,6 +53,7 @@ struct LayerDiagOp {
     std::complex<double> d[4];
 };
 struct LayerSpec {
+    bool generate = false;                                  // write-only on a state taken as all ones
     std::vector<LayerDiagOp> diag;
     std::vector<int32_t> t;                                 // factor qubits
     std::vector<std::array<std::complex<double>, 4>> f;     // factor j on t[j], row-major
@@ -71,6 +72,7 @@ struct PlanBlock {
     bool diag = false;         // diagonal mode: 2^k entries, streaming kernel
     bool prod = false;         // product of one-qubit factors: 8 floats per factor, product kernel
     int layer = -1;            // layer block: index into qsa_plan_s::layers
+    bool init = false;         // zero-state preparation (a write-only layer block)
     int n_diag = 0;            // layer block: ops of its diagonal part
     size_t off = 0;            // float offset of its matrix / diagonal in host_mat / d_mat
     size_t first_op = 0;       // in execution order

@@ -85,9 +85,9 @@ def test_fusion28_qft_closed_form_and_inverse_return(q):
                               "bench-interleaved-layer-kdiag12-3xtf32"])
 def test_qaoa30_symmetries_and_fused_equals_per_gate(q, kmax, kdiag, kprod, prec, layer, interleave):
     """The bench's workload and launch configuration (interleaved initial
-    layout set on |0...0>, layer units, kmax 6, diagonal blocks up to 12
-    qubits, split-TF32 for k = 5, 6), layer units on the identity layout, the
-    product-unit configuration and two dense-only ones."""
+    layout set on |0...0>, zero-state prefix, layer units, kmax 6, diagonal
+    blocks up to 12 qubits, split-TF32 for k = 5, 6), layer units on the
+    identity layout, the product-unit configuration and two dense-only ones."""
     n = 30
     ops, edges = W.qaoa_circuit(n=n, p=8, seed=0)
     st = Big(q, n)
@@ -96,9 +96,10 @@ def test_qaoa30_symmetries_and_fused_equals_per_gate(q, kmax, kdiag, kprod, prec
             import bench
             q.qsa_set_layout(st.h, bench.interleaved_layout(n), 0)
         stats = q.qsa_apply_circuit(st.h, ops, q.make_opts(planner=q.QSA_PLAN_DP, kmax=kmax, kmax_diag=kdiag,
-                                                           kmax_prod=kprod, precision=prec, layer=layer))
+                                                           kmax_prod=kprod, precision=prec, layer=layer,
+                                                           zero_init=1 if interleave else 0))
         if layer:
-            assert stats["layer_blocks"] == 27 and stats["passes"] == 27
+            assert stats["layer_blocks"] == (25 if interleave else 27) and stats["passes"] == stats["layer_blocks"]
         assert abs(q.qsa_expectation_z(st.h, 0) - 1) < 1e-5
         for qb in (0, 7, 29):
             assert abs(q.qsa_expectation_z(st.h, 1 << qb)) < 1e-5

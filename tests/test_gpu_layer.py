@@ -183,3 +183,50 @@ def test_layer_argument_errors(q):
             assert e.value.code == q.QSA_E_ARG
     finally:
         st.close()
+
+
+@pytest.mark.parametrize("kind,n,layer,permuted", [("qaoa", 16, 1, False), ("qaoa", 16, 1, True),
+                                                   ("brick", 14, 0, False), ("mixed", 13, 1, True),
+                                                   ("qaoa", 12, 1, False), ("qaoa", 8, 1, True)])
+def test_zero_init_plans_match_oracle(q, kind, n, layer, permuted):
+    """Plans with the zero-state prefix (a write-only pass; N < 12: all ones
+    then the diagonal kernels) against the oracle, on identity and relabelled
+    layouts."""
+    rng = np.random.default_rng(n + layer)
+    if kind == "qaoa":
+        ops, _ = W.qaoa_circuit(n, 2, seed=4)
+    elif kind == "brick":
+        ops = W.brick_circuit(n, 5, seed=4)
+    else:
+        from test_oracle_layer import _mixed_circuit
+        ops = [W.Op((qb,), W.haar_unitary(2, rng), False) for qb in range(n)] + _mixed_circuit(n, 80, rng)
+    st = GState(q, torch, n)
+    try:
+        if permuted:
+            q.qsa_set_layout(st.h, [int(v) for v in rng.permutation(n)], 0)
+        stats = q.qsa_apply_circuit(st.h, ops, q.make_opts(planner=2, kmax=4, kmax_diag=4, layer=layer,
+                                                           zero_init=1))
+        assert stats["layer_blocks"] + stats["diag_blocks"] >= 1   # N < 12: diagonal kernels
+        check_close(oracle.run_circuit(n, ops), st.logical())
+    finally:
+        st.close()
+
+
+def test_zero_init_plan_needs_the_zero_state_and_other_layouts(q):
+    n = 14
+    ops, _ = W.qaoa_circuit(n, 2, seed=5)
+    p = q.qsa_plan_create(ops, n, q.make_opts(planner=2, kmax=4, kmax_diag=4, layer=1, zero_init=1))
+    st = GState(q, torch, n)
+    try:
+        q.qsa_apply_fused(st.h, [0], W.H)
+        with pytest.raises(q.QsaError) as e:
+            q.qsa_plan_execute(st.h, p)
+        assert e.value.code == q.QSA_E_STATE
+        # built for the identity layout, run on a relabelled zero state
+        q.qsa_state_reset(st.h)
+        q.qsa_set_layout(st.h, [int(v) for v in np.random.default_rng(6).permutation(n)], 0)
+        q.qsa_plan_execute(st.h, p)
+        check_close(oracle.run_circuit(n, ops), st.logical())
+    finally:
+        st.close()
+        q.qsa_plan_destroy(p)

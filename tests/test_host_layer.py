@@ -73,3 +73,29 @@ def test_layer_options_validated(q):
     with pytest.raises(q.QsaError) as e:
         q.qsa_plan_create(ops, 12, q.make_opts(layer=2))
     assert e.value.code == q.QSA_E_ARG
+
+
+@pytest.mark.parametrize("kind,n", [("qaoa", 30), ("qaoa", 16), ("brick", 12), ("mixed", 14)])
+def test_zero_init_prefix_matches_oracle(q, kind, n):
+    """The zero_init plan's first block covers exactly the oracle's prefix, in
+    input order, and the rest is grouped as without it."""
+    rng = np.random.default_rng(n)
+    if kind == "qaoa":
+        ops, _ = W.qaoa_circuit(n, 3, seed=0)
+    elif kind == "brick":
+        ops = W.brick_circuit(n, 4, seed=0)
+    else:
+        ops = [W.Op((qb,), W.haar_unitary(2, rng), False) for qb in range(n)] + _mixed_circuit(n, 60, rng)
+    P = oracle.zero_init_prefix(ops)
+    p = q.qsa_plan_create(ops, n, q.make_opts(planner=2, kmax=4, kmax_diag=4, layer=1, zero_init=1))
+    try:
+        order = q.qsa_plan_order(p)
+        first, _ = q.qsa_plan_blocks(p)
+        kinds, _ = q.qsa_plan_block_kinds(p)
+    finally:
+        q.qsa_plan_destroy(p)
+    assert P > 0 and kinds[0] == 4 and 4 not in kinds[1:]
+    assert first[0] == 0 and (len(first) == 1 or first[1] == P)
+    assert order[:P] == list(range(P))
+    ref_order, _ = oracle.layer_units(ops[P:], n)
+    assert order[P:] == [x + P for x in ref_order]
