@@ -330,9 +330,8 @@ def main():
             zz = q.qsa_dm_expectation_z(s, n_dm, edge_mask)
             nshot = 0
         else:
-            norm = q.qsa_expectation_z(s, 0)
+            norm, zz = q.qsa_expectation_z_batch(s, [0, edge_mask])   # one pass for both sums
             vals, cnts = q.qsa_sample_counts(s, args.shots, seed=args.seed + 17)
-            zz = q.qsa_expectation_z(s, edge_mask)
             nshot = int(cnts.sum())
         if record:
             for k in agg:

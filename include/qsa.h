@@ -408,6 +408,14 @@ qsa_status qsa_probabilities_device(qsa_state s, double* out_dev, double* norm_o
  * logical_mask = 0 gives the norm.  Synchronises. */
 qsa_status qsa_expectation_z(qsa_state s, uint64_t logical_mask, double* out);
 
+/* Several masks in one pass over the state (each result bit-identical to
+ * qsa_expectation_z with that mask): logical_masks (host, n_masks entries,
+ * each < 2^N), out (host, n_masks doubles).  Synchronises the stream.
+ * Errors: QSA_E_ARG (n_masks outside 1..QSA_MAX_ZMASKS, a mask beyond N,
+ * NULL). */
+#define QSA_MAX_ZMASKS 4
+qsa_status qsa_expectation_z_batch(qsa_state s, const uint64_t* logical_masks, int n_masks, double* out);
+
 /* Draw `shots` outcomes (§IV-E): weights P_y = trunc(p_y * 2^62) (integer,
  * so the CDF does not depend on summation order) over physical indices in
  * 2^10-amplitude blocks; shot i draws Philox4x64-10(ctr = (i, 0, 0, 0),

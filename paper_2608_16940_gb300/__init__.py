@@ -119,6 +119,7 @@ _f = {
     "qsa_probabilities": _sig("qsa_probabilities", [_vp, _dp, _dp]),
     "qsa_probabilities_device": _sig("qsa_probabilities_device", [_vp, _vp, _dp]),
     "qsa_expectation_z": _sig("qsa_expectation_z", [_vp, _c.c_uint64, _dp]),
+    "qsa_expectation_z_batch": _sig("qsa_expectation_z_batch", [_vp, _u64p, _c.c_int, _dp]),
     "qsa_dm_apply_channel": _sig("qsa_dm_apply_channel", [_vp, _c.c_int, _i32p, _c.c_int, _dp, _c.c_int,
                                                            _c.c_int]),
     "qsa_dm_superoperator": _sig("qsa_dm_superoperator", [_c.c_int, _i32p, _c.c_int, _dp, _c.c_int, _i32p, _dp]),
@@ -454,6 +455,13 @@ def qsa_dm_expectation_z(s: int, n: int, mask: int) -> float:
     out = _c.c_double()
     _check(_f["qsa_dm_expectation_z"](_vp(s), n, _c.c_uint64(mask), _c.byref(out)))
     return out.value
+
+
+def qsa_expectation_z_batch(s: int, logical_masks) -> List[float]:
+    m = np.ascontiguousarray(np.asarray(list(logical_masks), dtype=np.uint64))
+    out = np.zeros(len(m), dtype=np.float64)
+    _check(_f["qsa_expectation_z_batch"](_vp(s), m.ctypes.data_as(_u64p), len(m), out.ctypes.data_as(_dp)))
+    return [float(v) for v in out]
 
 
 def qsa_sample_counts(s: int, shots: int, seed: int, capacity: Optional[int] = None) -> Tuple[np.ndarray, np.ndarray]:

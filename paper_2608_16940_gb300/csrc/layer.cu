@@ -412,12 +412,19 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
         const float2(*phs)[2] = use_rec ? recs[cur].ph : sh.ph;
         const float2* pls = use_rec ? recs[cur].pl : sh.pl;
         if (first == 0) {
-            layer_round<ROT, 0>(a, st, din_s, sh, phs, pls, rot, runoff, base, last == 0, phase);
-            if (last > 0) {
-                if (r1)
-                    __syncwarp();
-                else
-                    __syncthreads();
+            // round 0 always writes to the stage: its threads hold 16 consecutive
+            // amplitudes, so when it is the last round the tile is copied out in
+            // 16-byte chunks by consecutive threads instead (coalesced stores)
+            layer_round<ROT, 0>(a, st, din_s, sh, phs, pls, rot, runoff, base, false, phase);
+            if (last == 0) {
+                __syncthreads();
+                for (int c = threadIdx.x; c < kLAmps / 2; c += blockDim.x)
+                    __stcs(reinterpret_cast<float4*>(a.psi + layer_global(a, runoff, base, 2 * c)),
+                           *reinterpret_cast<const float4*>(st + lsw(2 * c)));
+            } else if (r1) {
+                __syncwarp();
+            } else {
+                __syncthreads();
             }
         }
         if (first <= 1 && last >= 1 && r1) {

@@ -130,6 +130,15 @@ cudaError_t launch_permute(float2* psi, int n, const int* pa, const int* pb, int
 // FP64 sum of (-1)^{popcount(y & physmask)} |psi_y|^2 into *d_out (device).
 // d_partials must hold reduce_partials() doubles.
 int reduce_partials();
+constexpr int kMaxZMasks = 4;
+struct ZMasks {
+    int n;
+    uint64_t m[kMaxZMasks];
+};
+// Several <Z_mask> sums in one pass: d_partials holds nmasks * reduce_partials()
+// doubles, d_out nmasks doubles (device).  nmasks in 1..kMaxZMasks.
+cudaError_t launch_reduce_z_multi(const float2* psi, int n, const uint64_t* physmasks, int nmasks,
+                                  double* d_partials, double* d_out, cudaStream_t st, uint64_t* launches);
 cudaError_t launch_reduce_z(const float2* psi, int n, uint64_t physmask, double* d_partials, double* d_out,
                             cudaStream_t st, uint64_t* launches);
 

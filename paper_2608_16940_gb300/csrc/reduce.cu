@@ -80,6 +80,42 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_z(const float4* __restri
     }
 }
 
+// Several sign masks in one pass: the squares are formed once per amplitude
+// and accumulated per mask exactly as k_reduce_z does (so each result equals
+// the single-mask one bit for bit).  Partials of mask m at m * gridDim.x.
+__global__ void __launch_bounds__(kRedThreads) k_reduce_z_multi(const float4* __restrict__ psi2, uint64_t npairs,
+                                                                ZMasks masks, double* __restrict__ partials) {
+    float s[kMaxZMasks] = {}, c[kMaxZMasks] = {};
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < npairs; i += stride) {
+        const float4 a = __ldcs(psi2 + i);
+        const uint64_t y0 = i << 1;
+#pragma unroll
+        for (int m = 0; m < kMaxZMasks; ++m) {
+            if (m >= masks.n) break;
+            const bool n0 = __popcll(y0 & masks.m[m]) & 1;
+            const bool n1 = __popcll((y0 | 1ull) & masks.m[m]) & 1;
+            acc_square(s[m], c[m], a.x, n0);
+            acc_square(s[m], c[m], a.y, n0);
+            acc_square(s[m], c[m], a.z, n1);
+            acc_square(s[m], c[m], a.w, n1);
+        }
+    }
+    __shared__ double ws[kRedThreads / 32];
+    for (int m = 0; m < masks.n; ++m) {
+        double acc = static_cast<double>(s[m]) + static_cast<double>(c[m]);
+        acc = warp_sum_d(acc);
+        if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double v = threadIdx.x < (kRedThreads / 32) ? ws[threadIdx.x] : 0.0;
+            v = warp_sum_d(v);
+            if (threadIdx.x == 0) partials[static_cast<uint64_t>(m) * gridDim.x + blockIdx.x] = v;
+        }
+        __syncthreads();
+    }
+}
+
 // Fixed-order sum of the partials (deterministic for a given grid).
 __global__ void k_finalize_sum(const double* __restrict__ partials, int n, double* __restrict__ out) {
     __shared__ double sh[1024];
@@ -477,6 +513,20 @@ cudaError_t launch_reduce_z(const float2* psi, int n, uint64_t physmask, double*
     k_reduce_z<<<nb, kRedThreads, 0, st>>>(reinterpret_cast<const float4*>(psi), npairs, physmask, d_partials);
     k_finalize_sum<<<1, 1024, 0, st>>>(d_partials, nb, d_out);
     *launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_z_multi(const float2* psi, int n, const uint64_t* physmasks, int nmasks,
+                                  double* d_partials, double* d_out, cudaStream_t st, uint64_t* launches) {
+    if (nmasks < 1 || nmasks > kMaxZMasks || n < 1) return cudaErrorInvalidValue;
+    const uint64_t npairs = (1ull << n) >> 1;
+    const int nb = reduce_partials();
+    ZMasks zm{};
+    zm.n = nmasks;
+    for (int m = 0; m < nmasks; ++m) zm.m[m] = physmasks[m];
+    k_reduce_z_multi<<<nb, kRedThreads, 0, st>>>(reinterpret_cast<const float4*>(psi), npairs, zm, d_partials);
+    for (int m = 0; m < nmasks; ++m) k_finalize_sum<<<1, 1024, 0, st>>>(d_partials + m * nb, nb, d_out + m);
+    *launches += 1 + nmasks;
     return cudaGetLastError();
 }
 

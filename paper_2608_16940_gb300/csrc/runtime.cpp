@@ -542,6 +542,30 @@ qsa_status qsa_expectation_z(qsa_state s, uint64_t logical_mask, double* out) {
     return sync_and_check(s, "reduction result");
 }
 
+qsa_status qsa_expectation_z_batch(qsa_state s, const uint64_t* logical_masks, int n_masks, double* out) {
+    qsa_status st = check_state(s);
+    if (st != QSA_OK) return st;
+    if (!logical_masks || !out) return fail(QSA_E_ARG, "NULL argument");
+    if (n_masks < 1 || n_masks > QSA_MAX_ZMASKS) return fail(QSA_E_ARG, "n_masks must be in 1..4");
+    uint64_t pm[QSA_MAX_ZMASKS];
+    for (int m = 0; m < n_masks; ++m) {
+        if (s->n < 64 && (logical_masks[m] >> s->n)) return fail(QSA_E_ARG, "mask has bits beyond N");
+        pm[m] = 0;
+        for (int q = 0; q < s->n; ++q)
+            if ((logical_masks[m] >> q) & 1) pm[m] |= 1ull << s->L[q];
+    }
+    const size_t nb = static_cast<size_t>(reduce_partials());
+    st = ensure_dev(s, reinterpret_cast<void**>(&s->d_red), &s->red_cap,
+                    sizeof(double) * (QSA_MAX_ZMASKS * nb + 8));
+    if (st != QSA_OK) return st;
+    double* d_out = s->d_red + QSA_MAX_ZMASKS * nb;
+    cudaError_t e = launch_reduce_z_multi(s->psi, s->n, pm, n_masks, s->d_red, d_out, s->stream, &s->launches);
+    if (e != cudaSuccess) return cuda_fail(s, e, "reduction kernel");
+    e = cudaMemcpyAsync(out, d_out, sizeof(double) * n_masks, cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "reduction results");
+    return sync_and_check(s, "reduction results");
+}
+
 qsa_status qsa_state_sync(qsa_state s) {
     qsa_status st = check_state(s);
     if (st != QSA_OK) return st;

@@ -229,6 +229,27 @@ def test_expectation_z_matches_oracle(q):
         st.close()
 
 
+def test_expectation_z_batch_equals_single_masks(q):
+    """Several masks in one pass: each result bit-identical to the one-mask
+    reduction (same per-thread accumulation order) and to the oracle."""
+    n = 15
+    psi = W.random_state(n, 6).astype(np.complex64)
+    st = GState(q, n, init=psi)
+    p64 = psi.astype(np.complex128)
+    try:
+        q.qsa_set_layout(st.h, [int(v) for v in np.random.default_rng(6).permutation(n)], 1)
+        for masks in ([0], [0, 1 << 14], [3, 0b1010, (1 << n) - 1, 1 << 7]):
+            got = q.qsa_expectation_z_batch(st.h, masks)
+            for m, g in zip(masks, got):
+                assert g == q.qsa_expectation_z(st.h, m)
+                assert abs(g - oracle.expect_z(p64, m)) < 1e-12
+        for bad in ([], [0] * 5, [1 << n]):
+            with pytest.raises(q.QsaError):
+                q.qsa_expectation_z_batch(st.h, bad)
+    finally:
+        st.close()
+
+
 @pytest.mark.parametrize("n,shots,perm,zero_frac", [(4, 100, False, 0.0), (10, 1000, True, 0.5),
                                                     (13, 5000, True, 0.0), (16, 9000, False, 0.9)])
 def test_sampler_bit_exact_vs_oracle(q, n, shots, perm, zero_frac):
