@@ -19,8 +19,10 @@
 // diagonal branch) and runs on the streaming kernel, up to QSA_MAX_DIAG wide.
 // With opts.layer, a pre-pass first groups the circuit into layer units
 // (diagonal gates on at most two qubits, then one-qubit ops whose qubits fit
-// one tile), moving an op ahead only of ops it commutes with; the planners
-// then run on the reordered stream, a layer unit counting as one pass.
+// one tile), moving an op ahead only of ops it commutes with (the
+// semantics-preserving reorder of §IV-C: disjoint targets, or both diagonal);
+// the planners then run on the reordered stream, a layer unit counting as one
+// pass.
 #include <cuda_runtime.h>
 
 #include <algorithm>
