@@ -48,10 +48,12 @@ UNIT = "amp-updates/s"
 # DRAM bytes (read + write) per amplitude of one launch, from single ncu captures
 # at N=28 (profiles/k_apply_tc6_n28.md: 4.241 GB; profiles/k_apply_fp32_k4_n28.md:
 # 4.234 GB; profiles/k_apply_diag_n28.md: 4.234 GB; profiles/k_apply_prod_n28.md:
-# 4.260 GB; each / 2^28).  Traffic scales with the state size, so a launch at N
-# moves this many bytes times 2^N.
+# 4.260 GB; profiles/k_apply_layer_n28.md: 4.261 GB (a regular pass); each /
+# 2^28).  Traffic scales with the state size, so a launch at N moves this many
+# bytes times 2^N.
 DRAM_BYTES_PER_AMP = {"k_apply_tc": 4.241e9 / 2**28, "k_apply_fp32": 4.234e9 / 2**28,
-                      "k_apply_diag": 4.234e9 / 2**28, "k_apply_prod": 4.260e9 / 2**28}
+                      "k_apply_diag": 4.234e9 / 2**28, "k_apply_prod": 4.260e9 / 2**28,
+                      "k_apply_layer": 4.261e9 / 2**28}
 
 
 def _peaks():
@@ -385,10 +387,14 @@ def main():
         kinds.append(("k_permute (qubit permutation)", agg["permute_seconds"], agg["permutes"]))
     name, tot, cnt = max(kinds, key=lambda kv: kv[1])
     avg = tot / cnt
-    achieved = bytes_per_launch / avg / 1e9
+    kernel_bytes = bytes_per_launch * cnt
+    if name.startswith("k_apply_layer"):
+        # zero-state preparation passes only write (8 B per amplitude)
+        kernel_bytes -= bytes_per_launch / 2 * q.qsa_plan_block_kinds(plan)[0].count(4) * args.steps
+    achieved = kernel_bytes / tot / 1e9
     dram = DRAM_BYTES_PER_AMP.get(name.split(" ")[0])
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-            "traffic": dram * (1 << n) if dram else None, "kernel": name, "peak_source": peak_kind, "bytes_per_launch": bytes_per_launch,
+            "traffic": dram * (1 << n) if dram else None, "kernel": name, "peak_source": peak_kind, "bytes_per_launch": kernel_bytes / cnt,
             "avg_launch_ms": avg * 1e3, "launches_per_step": cnt / args.steps,
             "share_of_step": tot / args.steps / per_step}
 
