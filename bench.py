@@ -398,7 +398,8 @@ def main():
             "avg_launch_ms": avg * 1e3, "launches_per_step": cnt / args.steps,
             "share_of_step": tot / args.steps / per_step}
 
-    # end to end through the public API from host data: plan + upload + apply + counts copied back
+    # end to end through the public API from host data: plan + upload + apply + the step's norm, <ZZ>
+    # and counts copied back
     e2e = None
     if not args.no_e2e:
         e2e_times = []
@@ -413,10 +414,12 @@ def main():
                                                           zero_init=args.zero_init))
             if dm:
                 q.qsa_dm_probabilities(s, n_dm, want_probs=False)
-                d2h = 8.0
+                q.qsa_dm_expectation_z(s, n_dm, edge_mask)
+                d2h = 16.0
             else:
+                q.qsa_expectation_z_batch(s, [0, edge_mask])
                 vals, cnts = q.qsa_sample_counts(s, args.shots, seed=args.seed + 17)
-                d2h = 16.0 * len(vals) + 16
+                d2h = 16.0 * len(vals) + 16 + 16
             torch.cuda.synchronize()
             e2e_times.append(time.perf_counter() - t0)
             h2d = st["h2d_bytes"]
