@@ -82,10 +82,10 @@ struct LayerShared {
 
 // Slot of tile-local amplitude j: 16-byte chunk c = j / 2 is stored at
 // c ^ ((c >> 3) & 7), which spreads each round's warp accesses over all banks.
-__device__ __forceinline__ int lsw(int j) {
-    const int c = j >> 1;
-    return ((c ^ ((c >> 3) & 7)) << 1) | (j & 1);
-}
+// The map is linear over XOR, so for j and x with disjoint bits
+// lsw(j | x) = lsw(j) ^ lsw(x): a thread forms lsw of its own bits once and
+// combines it with compile-time constants.
+__host__ __device__ constexpr int lsw(int j) { return (((j >> 1) ^ ((j >> 4) & 7)) << 1) | (j & 1); }
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -99,6 +99,7 @@ __device__ __forceinline__ uint64_t layer_base(const LayerArgs& a, uint64_t t) {
     return b;
 }
 
+// Global offset of tile-local index j within the tile (OR-linear over disjoint bits).
 __device__ __forceinline__ uint64_t layer_global(const LayerArgs& a, const uint64_t* runoff, uint64_t base, int j) {
     return base | static_cast<uint64_t>(j & ((1 << a.m) - 1)) | runoff[j >> a.m];
 }
@@ -139,10 +140,11 @@ __device__ __forceinline__ void rotation(float2 (&v)[16], float2 cs) {
 template <bool ROT, int R>
 __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, const float2* din_s,
                                             const LayerShared& sh, const float2 (*phs)[2], const float2* pls,
-                                            const float2* rot, const uint64_t* runoff, uint64_t base, bool last,
-                                            bool phase) {
+                                            const float2* rot, const uint64_t* runoff, const uint64_t* goff,
+                                            uint64_t base, bool last, bool phase) {
     const int t = threadIdx.x;
     const int jb = (t & ((1 << (4 * R)) - 1)) | ((t >> (4 * R)) << (4 * R + 4));
+    const int sb = lsw(jb);   // slot of (jb | x) = sb ^ lsw(x)
     float2 v[16];
     if constexpr (R == 0) {
         if (a.generate) {
@@ -151,7 +153,7 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
         } else {
 #pragma unroll
             for (int i = 0; i < 16; i += 2) {
-                const float4 p = *reinterpret_cast<const float4*>(stage + lsw(jb | i));
+                const float4 p = *reinterpret_cast<const float4*>(stage + (sb ^ lsw(i)));
                 v[i] = make_float2(p.x, p.y);
                 v[i + 1] = make_float2(p.z, p.w);
             }
@@ -159,7 +161,7 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
         if (din_s) {
 #pragma unroll
             for (int i = 0; i < 16; i += 2) {
-                const float4 d = *reinterpret_cast<const float4*>(din_s + lsw(jb | i));
+                const float4 d = *reinterpret_cast<const float4*>(din_s + (sb ^ lsw(i)));
                 v[i] = cmulf(v[i], make_float2(d.x, d.y));
                 v[i + 1] = cmulf(v[i + 1], make_float2(d.z, d.w));
             }
@@ -175,7 +177,7 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = stage[lsw(jb | (i << (4 * R)))];
+        for (int i = 0; i < 16; ++i) v[i] = stage[sb ^ lsw(i << (4 * R))];
     }
     const uint32_t act = (a.fmask >> (4 * R)) & 15u;
     if constexpr (ROT) {
@@ -195,25 +197,26 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
         if (act & 8u) butterfly<3>(v, sh.tf[4 * R + 3]);
     }
     if (last) {
+        // global offset of (jb | x) = offset(jb) | offset(x); goff[R][i] holds offset(i << 4R)
+        const uint64_t gb = layer_global(a, runoff, base, jb);
         if constexpr (R == 0) {
             // m >= 3: amplitudes jb | i and jb | (i + 1) are adjacent in HBM
 #pragma unroll
             for (int i = 0; i < 16; i += 2)
-                __stcs(reinterpret_cast<float4*>(a.psi + layer_global(a, runoff, base, jb | i)),
+                __stcs(reinterpret_cast<float4*>(a.psi + (gb | goff[i])),
                        make_float4(v[i].x, v[i].y, v[i + 1].x, v[i + 1].y));
         } else {
 #pragma unroll
-            for (int i = 0; i < 16; ++i)
-                __stcs(a.psi + layer_global(a, runoff, base, jb | (i << (4 * R))), v[i]);
+            for (int i = 0; i < 16; ++i) __stcs(a.psi + (gb | goff[16 * R + i]), v[i]);
         }
     } else {
         if constexpr (R == 0) {
 #pragma unroll
             for (int i = 0; i < 16; i += 2)
-                *reinterpret_cast<float4*>(stage + lsw(jb | i)) = make_float4(v[i].x, v[i].y, v[i + 1].x, v[i + 1].y);
+                *reinterpret_cast<float4*>(stage + (sb ^ lsw(i))) = make_float4(v[i].x, v[i].y, v[i + 1].x, v[i + 1].y);
         } else {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) stage[lsw(jb | (i << (4 * R)))] = v[i];
+            for (int i = 0; i < 16; ++i) stage[sb ^ lsw(i << (4 * R))] = v[i];
         }
     }
 }
@@ -333,13 +336,21 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
     LayerShared& sh = *reinterpret_cast<LayerShared*>(runoff + 512);
     float2* rot = reinterpret_cast<float2*>(&sh + 1);                           // kLT
     LayerRec* recs = reinterpret_cast<LayerRec*>(rot + kLT);                    // kLStages
-    float2* din_s = a.din ? reinterpret_cast<float2*>(recs + kLStages) : nullptr;  // 4096, swizzled
+    uint64_t* goff = reinterpret_cast<uint64_t*>(recs + kLStages);              // 48 + 8
+    float2* din_s = a.din ? reinterpret_cast<float2*>(goff + 56) : nullptr;     // 4096, swizzled
 
     for (int r = threadIdx.x; r < (1 << a.nx); r += blockDim.x) {
         uint64_t off = 0;
         for (int e = 0; e < a.nx; ++e)
             if ((r >> e) & 1) off |= 1ull << a.xpos[e];
         runoff[r] = off;
+    }
+    __syncthreads();
+    // offsets of a round's local bits (goff[16 R + i] for tile-local i << 4R) and of
+    // the load loop's chunk strides (goff[48 + k] for tile-local 512 k)
+    if (threadIdx.x < 56) {
+        const int j = threadIdx.x < 48 ? (threadIdx.x & 15) << (4 * (threadIdx.x >> 4)) : (threadIdx.x - 48) << 9;
+        goff[threadIdx.x] = layer_global(a, runoff, 0, j);
     }
     const bool dynamic = a.ncross > 0 || a.nout > 0;
     const bool phase = a.pmask != 0 || a.nout > 0;
@@ -379,12 +390,16 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
     // rotation mode takes the per-tile phases from the records (fetched with
     // the tile), general mode forms them in warp 0
     const bool use_rec = ROT && a.rec;
+    // this thread's chunks are 2 * threadIdx.x + 512 k, k = 0..7
+    const uint64_t gld = layer_global(a, runoff, 0, 2 * threadIdx.x);
+    const int sld = lsw(2 * threadIdx.x);
     auto load = [&](uint64_t t, int sidx) {
-        const uint64_t base = layer_base(a, t);
+        const uint64_t base = layer_base(a, t) | gld;
         float2* st = stage + sidx * kLAmps;
         if (!a.generate)
-            for (int c = threadIdx.x; c < kLAmps / 2; c += blockDim.x)
-                cp_async16(st + lsw(2 * c), a.psi + layer_global(a, runoff, base, 2 * c));
+#pragma unroll
+            for (int k = 0; k < kLAmps / 2 / kLThreads; ++k)
+                cp_async16(st + (sld ^ lsw(512 * k)), a.psi + (base | goff[48 + k]));
         if (use_rec && threadIdx.x < static_cast<int>(sizeof(LayerRec) / 16))
             cp_async16(reinterpret_cast<float4*>(recs + sidx) + threadIdx.x,
                        reinterpret_cast<const float4*>(a.rec + t) + threadIdx.x);
@@ -415,12 +430,13 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
             // round 0 always writes to the stage: its threads hold 16 consecutive
             // amplitudes, so when it is the last round the tile is copied out in
             // 16-byte chunks by consecutive threads instead (coalesced stores)
-            layer_round<ROT, 0>(a, st, din_s, sh, phs, pls, rot, runoff, base, false, phase);
+            layer_round<ROT, 0>(a, st, din_s, sh, phs, pls, rot, runoff, goff, base, false, phase);
             if (last == 0) {
                 __syncthreads();
-                for (int c = threadIdx.x; c < kLAmps / 2; c += blockDim.x)
-                    __stcs(reinterpret_cast<float4*>(a.psi + layer_global(a, runoff, base, 2 * c)),
-                           *reinterpret_cast<const float4*>(st + lsw(2 * c)));
+#pragma unroll
+                for (int k = 0; k < kLAmps / 2 / kLThreads; ++k)
+                    __stcs(reinterpret_cast<float4*>(a.psi + (base | gld | goff[48 + k])),
+                           *reinterpret_cast<const float4*>(st + (sld ^ lsw(512 * k))));
             } else if (r1) {
                 __syncwarp();
             } else {
@@ -428,10 +444,10 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
             }
         }
         if (first <= 1 && last >= 1 && r1) {
-            layer_round<ROT, 1>(a, st, din_s, sh, phs, pls, rot, runoff, base, last == 1, phase);
+            layer_round<ROT, 1>(a, st, din_s, sh, phs, pls, rot, runoff, goff, base, last == 1, phase);
             if (last > 1) __syncthreads();
         }
-        if (last == 2) layer_round<ROT, 2>(a, st, din_s, sh, phs, pls, rot, runoff, base, true, phase);
+        if (last == 2) layer_round<ROT, 2>(a, st, din_s, sh, phs, pls, rot, runoff, goff, base, true, phase);
         if (end_sync) __syncthreads();
         cur ^= 1;
     }
@@ -442,7 +458,8 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
 
 size_t layer_smem_bytes(bool with_din) {
     return sizeof(float2) * kLStages * kLAmps + sizeof(uint64_t) * 512 + sizeof(LayerShared) +
-           sizeof(float2) * kLT + sizeof(LayerRec) * kLStages + (with_din ? sizeof(float2) * kLAmps : 0);
+           sizeof(float2) * kLT + sizeof(LayerRec) * kLStages + sizeof(uint64_t) * 56 +
+           (with_din ? sizeof(float2) * kLAmps : 0);
 }
 
 size_t layer_record_bytes(int n) { return n < kLT ? 0 : sizeof(LayerRec) << (n - kLT); }
