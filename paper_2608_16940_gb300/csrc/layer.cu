@@ -337,7 +337,8 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
     float2* rot = reinterpret_cast<float2*>(&sh + 1);                           // kLT
     LayerRec* recs = reinterpret_cast<LayerRec*>(rot + kLT);                    // kLStages
     uint64_t* goff = reinterpret_cast<uint64_t*>(recs + kLStages);              // 48 + 8
-    float2* din_s = a.din ? reinterpret_cast<float2*>(goff + 56) : nullptr;     // 4096, swizzled
+    uint64_t* dep = goff + 56;                                                  // 3 x 256
+    float2* din_s = a.din ? reinterpret_cast<float2*>(dep + 768) : nullptr;     // 4096, swizzled
 
     for (int r = threadIdx.x; r < (1 << a.nx); r += blockDim.x) {
         uint64_t off = 0;
@@ -352,6 +353,10 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
         const int j = threadIdx.x < 48 ? (threadIdx.x & 15) << (4 * (threadIdx.x >> 4)) : (threadIdx.x - 48) << 9;
         goff[threadIdx.x] = layer_global(a, runoff, 0, j);
     }
+    // tile bases: the tile index's bits deposited into the positions outside the
+    // tile, ascending; dep[c][v] deposits v << 8c, so base(t) is an OR of three
+    for (int i = threadIdx.x; i < 768; i += blockDim.x)
+        dep[i] = layer_base(a, static_cast<uint64_t>(i & 255) << (8 * (i >> 8)));
     const bool dynamic = a.ncross > 0 || a.nout > 0;
     const bool phase = a.pmask != 0 || a.nout > 0;
     if (ROT) {
@@ -393,8 +398,11 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
     // this thread's chunks are 2 * threadIdx.x + 512 k, k = 0..7
     const uint64_t gld = layer_global(a, runoff, 0, 2 * threadIdx.x);
     const int sld = lsw(2 * threadIdx.x);
+    auto tile_base = [&](uint64_t t) {
+        return dep[t & 255] | dep[256 + ((t >> 8) & 255)] | dep[512 + ((t >> 16) & 255)];
+    };
     auto load = [&](uint64_t t, int sidx) {
-        const uint64_t base = layer_base(a, t) | gld;
+        const uint64_t base = tile_base(t) | gld;
         float2* st = stage + sidx * kLAmps;
         if (!a.generate)
 #pragma unroll
@@ -416,7 +424,7 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
     cp_async_commit();
     int cur = 0;
     for (uint64_t t = blockIdx.x; t < a.ntiles; t += stride) {
-        const uint64_t base = layer_base(a, t);
+        const uint64_t base = tile_base(t);
         if (end_sync && threadIdx.x < 32) tile_phases<ROT>(a, base, sh);
         cp_async_wait<0>();
         __syncthreads();
@@ -458,7 +466,7 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
 
 size_t layer_smem_bytes(bool with_din) {
     return sizeof(float2) * kLStages * kLAmps + sizeof(uint64_t) * 512 + sizeof(LayerShared) +
-           sizeof(float2) * kLT + sizeof(LayerRec) * kLStages + sizeof(uint64_t) * 56 +
+           sizeof(float2) * kLT + sizeof(LayerRec) * kLStages + sizeof(uint64_t) * (56 + 768) +
            (with_din ? sizeof(float2) * kLAmps : 0);
 }
 
@@ -466,7 +474,8 @@ size_t layer_record_bytes(int n) { return n < kLT ? 0 : sizeof(LayerRec) << (n -
 
 cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const unsigned char* d_payload,
                                const LayerPayload& p, void* d_rec, cudaStream_t st, uint64_t* launches) {
-    if (n < kLT || g.m + g.nx != kLT || g.m < 3) return cudaErrorInvalidValue;
+    // three deposit tables of 8 tile-index bits cover N - 12 <= 24 bits
+    if (n < kLT || n - kLT > 24 || g.m + g.nx != kLT || g.m < 3) return cudaErrorInvalidValue;
     LayerArgs a{};
     a.psi = psi;
     a.ntiles = 1ull << (n - kLT);
