@@ -43,11 +43,11 @@ constexpr int kLThreads = 256;
 constexpr int kLStages = 2;
 
 // Per-tile phases of rotation mode, written by k_layer_records before the
-// pass: each pmask bit's (d0, d1) and the phases of round 0's 16 local
-// amplitudes (pmask bits 0..3) times the scalar of the out gates.
+// pass: the product of the pmask bits' phases (d0, d1) split over tile bits
+// 0..3 (times the scalar of the out gates), 4..7 and 8..11, 16 entries each.
 struct LayerRec {
-    float2 ph[kLT][2];
-    float2 pl[16];
+    float2 pl[16];            // bits 0..3 of round 0's local index, times the scalar
+    float2 pa[16], pb[16];    // products over tile bits 4..7 and 8..11 (fixed per thread in round 0)
 };
 
 struct LayerArgs {
@@ -75,8 +75,7 @@ struct LayerArgs {
 
 struct LayerShared {
     float2 tf[kLT][4];        // general mode: this tile's factors (cross phases folded in)
-    float2 ph[kLT][2];        // per-tile phases of pmask bits
-    float2 pl[16];            // per-tile phases of round 0's 16 local amplitudes times the scalar
+    LayerRec ph;              // per-tile phases (general mode and static rotation mode)
     float2 rp[3][16];         // rotation mode: per-round exit phases
 };
 
@@ -139,7 +138,7 @@ __device__ __forceinline__ void rotation(float2 (&v)[16], float2 cs) {
 // or (last round) to HBM.
 template <bool ROT, int R>
 __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, const float2* din_s,
-                                            const LayerShared& sh, const float2 (*phs)[2], const float2* pls,
+                                            const LayerShared& sh, const LayerRec& pr,
                                             const float2* rot, const uint64_t* runoff, const uint64_t* goff,
                                             uint64_t base, bool last, bool phase) {
     const int t = threadIdx.x;
@@ -167,13 +166,10 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
             }
         }
         if (phase) {
-            // phases of pmask bits 4..11 (fixed for this thread) times those of the 16 local amplitudes
-            float2 ph = make_float2(1.f, 0.f);
+            // phases of tile bits 4..11 (fixed for this thread) times those of the 16 local amplitudes
+            const float2 ph = cmulf(pr.pa[(jb >> 4) & 15], pr.pb[(jb >> 8) & 15]);
 #pragma unroll
-            for (int b = 4; b < kLT; ++b)
-                if ((a.pmask >> b) & 1u) ph = cmulf(ph, phs[b][(jb >> b) & 1]);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = cmulf(v[i], cmulf(ph, pls[i]));
+            for (int i = 0; i < 16; ++i) v[i] = cmulf(v[i], cmulf(ph, pr.pl[i]));
         }
     } else {
 #pragma unroll
@@ -221,6 +217,34 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
     }
 }
 
+// Lane l < 16 of a warp forms entry l of the three phase tables from lane b's
+// phases (d0, d1) of tile bit b (all lanes take part in the shuffles).
+__device__ __forceinline__ void phase_tables(uint32_t pmask, float2 d0, float2 d1, float2 sc, LayerRec* out) {
+    const int lane = threadIdx.x & 31;
+    float2 pl = sc, pa = make_float2(1.f, 0.f), pb = make_float2(1.f, 0.f);
+#pragma unroll
+    for (int b = 0; b < kLT; ++b) {
+        float2 e0, e1;
+        e0.x = __shfl_sync(0xffffffffu, d0.x, b);
+        e0.y = __shfl_sync(0xffffffffu, d0.y, b);
+        e1.x = __shfl_sync(0xffffffffu, d1.x, b);
+        e1.y = __shfl_sync(0xffffffffu, d1.y, b);
+        if (!((pmask >> b) & 1u)) continue;
+        const float2 e = ((lane >> (b & 3)) & 1) ? e1 : e0;
+        if (b < 4)
+            pl = cmulf(pl, e);
+        else if (b < 8)
+            pa = cmulf(pa, e);
+        else
+            pb = cmulf(pb, e);
+    }
+    if (lane < 16) {
+        out->pl[lane] = pl;
+        out->pa[lane] = pa;
+        out->pb[lane] = pb;
+    }
+}
+
 // The tile's factors and phases (warp 0): the scalar of the out gates (lanes
 // over gates, product across lanes); each tile bit's cross phases (lane b),
 // folded into the bit's factor (general mode, factor bits) or kept as a
@@ -243,8 +267,8 @@ __device__ __forceinline__ void tile_phases(const LayerArgs& a, uint64_t base, L
         sc = cmulf(sc, other);
     }
     const bool fold = !ROT && ((a.fmask >> lane) & 1u);
+    float2 d0 = make_float2(1.f, 0.f), d1 = make_float2(1.f, 0.f);
     if (lane < kLT && (fold || ((a.pmask >> lane) & 1u))) {
-        float2 d0 = make_float2(1.f, 0.f), d1 = make_float2(1.f, 0.f);
         for (int g = a.cstart[lane]; g < a.cstart[lane + 1]; ++g) {
             const LayerGate& G = a.cross[g];
             const int o = static_cast<int>((base >> G.b) & 1ull);
@@ -257,19 +281,9 @@ __device__ __forceinline__ void tile_phases(const LayerArgs& a, uint64_t base, L
             sh.tf[lane][1] = cmulf(F[1], d1);
             sh.tf[lane][2] = cmulf(F[2], d0);
             sh.tf[lane][3] = cmulf(F[3], d1);
-        } else {
-            sh.ph[lane][0] = d0;
-            sh.ph[lane][1] = d1;
         }
     }
-    __syncwarp();
-    if (lane < 16) {
-        float2 p = sc;
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-            if ((a.pmask >> b) & 1u) p = cmulf(p, sh.ph[b][(lane >> b) & 1]);
-        sh.pl[lane] = p;
-    }
+    phase_tables(a.pmask, d0, d1, sc, &sh.ph);
 }
 
 // Rotation mode: the per-tile phases of one tile into *out (one warp): the
@@ -304,20 +318,8 @@ __device__ __forceinline__ void tile_record(const LayerArgs& a, uint64_t base, L
         // the bit's entry phases of its rotation (identity without a factor)
         d0 = cmulf(d0, a.qph[2 * lane]);
         d1 = cmulf(d1, a.qph[2 * lane + 1]);
-        out->ph[lane][0] = d0;
-        out->ph[lane][1] = d1;
     }
-    float2 p = sc;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        float2 e0, e1;
-        e0.x = __shfl_sync(0xffffffffu, d0.x, b);
-        e0.y = __shfl_sync(0xffffffffu, d0.y, b);
-        e1.x = __shfl_sync(0xffffffffu, d1.x, b);
-        e1.y = __shfl_sync(0xffffffffu, d1.y, b);
-        p = cmulf(p, ((lane >> b) & 1) ? e1 : e0);
-    }
-    if (lane < 16) out->pl[lane] = p;
+    phase_tables(a.pmask, d0, d1, sc, out);
 }
 
 // One warp per tile: the records of a rotation-mode pass with per-tile phases.
@@ -365,16 +367,9 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
         if (!dynamic && threadIdx.x < 32) {
             // static phases: the rotations' entry phases only
             const int lane = threadIdx.x;
-            if (lane < kLT) {
-                sh.ph[lane][0] = a.qph[2 * lane];
-                sh.ph[lane][1] = a.qph[2 * lane + 1];
-            }
-            if (lane < 16) {
-                float2 p = make_float2(1.f, 0.f);
-                for (int b = 0; b < 4; ++b)
-                    if ((a.pmask >> b) & 1u) p = cmulf(p, a.qph[2 * b + ((lane >> b) & 1)]);
-                sh.pl[lane] = p;
-            }
+            const float2 d0 = lane < kLT ? a.qph[2 * lane] : make_float2(1.f, 0.f);
+            const float2 d1 = lane < kLT ? a.qph[2 * lane + 1] : make_float2(1.f, 0.f);
+            phase_tables(a.pmask, d0, d1, make_float2(1.f, 0.f), &sh.ph);
         }
     } else if (!dynamic) {
         for (int i = threadIdx.x; i < 4 * kLT; i += blockDim.x) sh.tf[i >> 2][i & 3] = a.fac[i];
@@ -432,13 +427,12 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
         if (tn < a.ntiles) load(tn, cur ^ 1);
         cp_async_commit();
         float2* st = stage + cur * kLAmps;
-        const float2(*phs)[2] = use_rec ? recs[cur].ph : sh.ph;
-        const float2* pls = use_rec ? recs[cur].pl : sh.pl;
+        const LayerRec& pr = use_rec ? recs[cur] : sh.ph;
         if (first == 0) {
             // round 0 always writes to the stage: its threads hold 16 consecutive
             // amplitudes, so when it is the last round the tile is copied out in
             // 16-byte chunks by consecutive threads instead (coalesced stores)
-            layer_round<ROT, 0>(a, st, din_s, sh, phs, pls, rot, runoff, goff, base, false, phase);
+            layer_round<ROT, 0>(a, st, din_s, sh, pr, rot, runoff, goff, base, false, phase);
             if (last == 0) {
                 __syncthreads();
 #pragma unroll
@@ -452,10 +446,10 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
             }
         }
         if (first <= 1 && last >= 1 && r1) {
-            layer_round<ROT, 1>(a, st, din_s, sh, phs, pls, rot, runoff, goff, base, last == 1, phase);
+            layer_round<ROT, 1>(a, st, din_s, sh, pr, rot, runoff, goff, base, last == 1, phase);
             if (last > 1) __syncthreads();
         }
-        if (last == 2) layer_round<ROT, 2>(a, st, din_s, sh, phs, pls, rot, runoff, goff, base, true, phase);
+        if (last == 2) layer_round<ROT, 2>(a, st, din_s, sh, pr, rot, runoff, goff, base, true, phase);
         if (end_sync) __syncthreads();
         cur ^= 1;
     }
