@@ -444,10 +444,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_tc(TcArgs a) {
         const uint32_t rslot = slot_of(squeeze(lbg));
         const uint64_t gq4 = gbit(a.tls[4]), gq5 = K == 6 ? gbit(a.tls[K - 1]) : 0ull;
         const uint32_t raw0 = smem_u32(Raw);
+        uint64_t base_t = ~0ull, base_v = 0;   // the tile base, formed once per tile
         auto issue = [&](uint64_t idx, int slot) {
             const uint64_t t = blockIdx.x + (idx / KC) * gridDim.x;
             const int j = static_cast<int>(idx % KC);
-            const uint64_t o0 = tc_tile_base(a, t) | ((j & 1) ? gq4 : 0ull) | ((j & 2) ? gq5 : 0ull) | goffT;
+            if (t != base_t) {
+                base_t = t;
+                base_v = tc_tile_base(a, t);
+            }
+            const uint64_t o0 = base_v | ((j & 1) ? gq4 : 0ull) | ((j & 2) ? gq5 : 0ull) | goffT;
             const uint32_t d0 = raw0 + static_cast<uint32_t>(slot) * C::RAW_BYTES;
 #pragma unroll
             for (int i = 0; i < 8; ++i)   // unit t + 128 i: element 2t + 256 i, slot part 2048 i
