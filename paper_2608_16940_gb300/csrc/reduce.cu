@@ -185,6 +185,41 @@ __global__ void __launch_bounds__(1024) k_scan_inclusive(uint64_t* __restrict__ 
 }
 
 
+// Multi-CTA inclusive scan of cum[0..n-1]: each CTA scans one segment of
+// kScanSeg entries in place and writes its total to parts[b]; parts is then
+// scanned by k_scan_inclusive and k_scan_add adds parts[b - 1] to segment b.
+// Integer sums, so the result is the same as the one-CTA scan.
+constexpr int kScanSeg = 4096;
+
+__global__ void __launch_bounds__(1024) k_scan_segments(uint64_t* __restrict__ cum, uint64_t n,
+                                                        uint64_t* __restrict__ parts) {
+    __shared__ uint64_t wsum[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint64_t i0 = static_cast<uint64_t>(blockIdx.x) * kScanSeg + 4ull * threadIdx.x;
+    uint64_t v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = i0 + k < n ? cum[i0 + k] : 0;
+    v[1] += v[0];
+    v[2] += v[1];
+    v[3] += v[2];
+    const uint64_t inc = warp_incl_scan_u64(v[3]);
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    if (wid == 0) wsum[lane] = warp_incl_scan_u64(wsum[lane]);
+    __syncthreads();
+    const uint64_t off = inc - v[3] + (wid ? wsum[wid - 1] : 0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (i0 + k < n) cum[i0 + k] = v[k] + off;
+    if (threadIdx.x == 1023) parts[blockIdx.x] = wsum[31];
+}
+
+__global__ void k_scan_add(uint64_t* __restrict__ cum, uint64_t n, const uint64_t* __restrict__ parts) {
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    for (uint64_t i = kScanSeg + static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
+        cum[i] += parts[i / kScanSeg - 1];
+}
+
 // One warp per shot: draw u, find the block (first cum > u), then the amplitude.
 __global__ void k_draw(const float2* __restrict__ psi, const uint64_t* __restrict__ cum, uint64_t nblocks, int bsz,
                        Layout lay, uint64_t shots, uint64_t seed, uint64_t stream_id, uint64_t* __restrict__ keys) {
@@ -578,7 +613,19 @@ cudaError_t launch_sample(const float2* psi, int n, const int32_t* layout_host, 
 
     const unsigned wpb = 8;  // warps per CTA
     k_block_weights<<<static_cast<unsigned>((nblocks + wpb - 1) / wpb), wpb * 32, 0, st>>>(psi, nblocks, bsz, cum);
-    k_scan_inclusive<<<1, 1024, 0, st>>>(cum, nblocks);
+    const uint64_t nseg = (nblocks + kScanSeg - 1) / kScanSeg;
+    if (nseg > 1 && nseg <= P + shots) {
+        // segment totals in the key area, which k_draw fills only afterwards
+        k_scan_segments<<<static_cast<unsigned>(nseg), 1024, 0, st>>>(cum, nblocks, keys);
+        k_scan_inclusive<<<1, 1024, 0, st>>>(keys, nseg);
+        uint64_t ab = (nblocks - kScanSeg + 255) / 256;
+        const uint64_t cap = static_cast<uint64_t>(num_sms()) * 8;
+        if (ab > cap) ab = cap;
+        k_scan_add<<<static_cast<unsigned>(ab), 256, 0, st>>>(cum, nblocks, keys);
+        *launches += 2;
+    } else {
+        k_scan_inclusive<<<1, 1024, 0, st>>>(cum, nblocks);
+    }
     k_draw<<<static_cast<unsigned>((shots + wpb - 1) / wpb), wpb * 32, 0, st>>>(psi, cum, nblocks, bsz, lay, shots,
                                                                                  seed, stream_id, keys);
     *launches += 3;

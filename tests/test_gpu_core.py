@@ -251,8 +251,12 @@ def test_expectation_z_batch_equals_single_masks(q):
 
 
 @pytest.mark.parametrize("n,shots,perm,zero_frac", [(4, 100, False, 0.0), (10, 1000, True, 0.5),
-                                                    (13, 5000, True, 0.0), (16, 9000, False, 0.9)])
+                                                    (13, 5000, True, 0.0), (16, 9000, False, 0.9),
+                                                    (23, 3000, True, 0.0), (24, 1000, False, 0.3),
+                                                    (24, 1, False, 0.0)])
 def test_sampler_bit_exact_vs_oracle(q, n, shots, perm, zero_frac):
+    """N >= 23 has more than one 4096-entry segment of block weights (the
+    multi-CTA scan; with one shot the one-CTA scan)."""
     psi = W.random_state(n, 6 + n, zero_frac=zero_frac).astype(np.complex64)
     st = GState(q, n, init=psi)
     L = [int(v) for v in np.random.default_rng(n).permutation(n)] if perm else list(range(n))
