@@ -286,54 +286,48 @@ __device__ __forceinline__ void tile_phases(const LayerArgs& a, uint64_t base, L
     phase_tables(a.pmask, d0, d1, sc, &sh.ph);
 }
 
-// One thread per tile: the records of a rotation-mode pass with per-tile
-// phases (the scalar of the out gates, each pmask bit's cross phases times its
-// rotation's entry phases, then the three 16-entry tables by doubling).
-__global__ void __launch_bounds__(kLThreads) k_layer_records(LayerArgs a, LayerRec* recs) {
-    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-    for (uint64_t t = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < a.ntiles; t += stride) {
-        const uint64_t base = layer_base(a, t);
-        float2 sc = make_float2(1.f, 0.f);
-        for (int g = 0; g < a.nout; ++g) {
-            const LayerGate& G = a.outg[g];
-            int v = static_cast<int>((base >> G.a) & 1ull);
-            if (G.b >= 0) v |= static_cast<int>((base >> G.b) & 1ull) << 1;
-            sc = cmulf(sc, G.d[v]);
-        }
-        float2 tab[3][16];
+// Rotation mode: the per-tile phases of one tile into *out (one warp): the
+// scalar of the out gates and each pmask bit's cross phases; round 0's
+// local phases from bits 0..3 (shuffled from lanes 0..3).
+__device__ __forceinline__ void tile_record(const LayerArgs& a, uint64_t base, LayerRec* out) {
+    const int lane = threadIdx.x & 31;
+    float2 sc = make_float2(1.f, 0.f);
+    for (int g = lane; g < a.nout; g += 32) {
+        const LayerGate& G = a.outg[g];
+        int v = static_cast<int>((base >> G.a) & 1ull);
+        if (G.b >= 0) v |= static_cast<int>((base >> G.b) & 1ull) << 1;
+        sc = cmulf(sc, G.d[v]);
+    }
 #pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            tab[r][0] = r == 0 ? sc : make_float2(1.f, 0.f);
-#pragma unroll
-            for (int lb = 0; lb < 4; ++lb) {
-                const int b = 4 * r + lb;
-                float2 d0 = make_float2(1.f, 0.f), d1 = make_float2(1.f, 0.f);
-                if ((a.pmask >> b) & 1u) {
-                    for (int g = a.cstart[b]; g < a.cstart[b + 1]; ++g) {
-                        const LayerGate& G = a.cross[g];
-                        const int o = static_cast<int>((base >> G.b) & 1ull);
-                        d0 = cmulf(d0, G.d[2 * o]);
-                        d1 = cmulf(d1, G.d[2 * o + 1]);
-                    }
-                    d0 = cmulf(d0, a.qph[2 * b]);
-                    d1 = cmulf(d1, a.qph[2 * b + 1]);
-                }
-                // entries with local bit lb set are the ones below it times d1
-#pragma unroll
-                for (int i = 0; i < (1 << lb); ++i) {
-                    tab[r][i | (1 << lb)] = cmulf(tab[r][i], d1);
-                    tab[r][i] = cmulf(tab[r][i], d0);
-                }
-            }
-        }
-        LayerRec* out = recs + t;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            out->pl[i] = tab[0][i];
-            out->pa[i] = tab[1][i];
-            out->pb[i] = tab[2][i];
+    for (int o = 16; o > 0; o >>= 1) {
+        float2 other;
+        other.x = __shfl_xor_sync(0xffffffffu, sc.x, o);
+        other.y = __shfl_xor_sync(0xffffffffu, sc.y, o);
+        sc = cmulf(sc, other);
+    }
+    float2 d0 = make_float2(1.f, 0.f), d1 = make_float2(1.f, 0.f);
+    if (lane < kLT && ((a.pmask >> lane) & 1u)) {
+        for (int g = a.cstart[lane]; g < a.cstart[lane + 1]; ++g) {
+            const LayerGate& G = a.cross[g];
+            const int o = static_cast<int>((base >> G.b) & 1ull);
+            d0 = cmulf(d0, G.d[2 * o]);
+            d1 = cmulf(d1, G.d[2 * o + 1]);
         }
     }
+    if (lane < kLT) {
+        // the bit's entry phases of its rotation (identity without a factor)
+        d0 = cmulf(d0, a.qph[2 * lane]);
+        d1 = cmulf(d1, a.qph[2 * lane + 1]);
+    }
+    phase_tables(a.pmask, d0, d1, sc, out);
+}
+
+// One warp per tile: the records of a rotation-mode pass with per-tile phases.
+__global__ void __launch_bounds__(kLThreads) k_layer_records(LayerArgs a, LayerRec* recs) {
+    const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x >> 5);
+    for (uint64_t t = blockIdx.x * static_cast<uint64_t>(blockDim.x >> 5) + (threadIdx.x >> 5); t < a.ntiles;
+         t += warps)
+        tile_record(a, layer_base(a, t), recs + t);
 }
 
 template <bool ROT>
@@ -509,7 +503,7 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
     if (p.rotation && (p.ncross > 0 || p.nout > 0)) {
         if (!d_rec) return cudaErrorInvalidValue;
         a.rec = static_cast<const LayerRec*>(d_rec);
-        uint64_t nb = (a.ntiles + kLThreads - 1) / kLThreads;
+        uint64_t nb = (a.ntiles + kLThreads / 32 - 1) / (kLThreads / 32);
         const uint64_t cap = static_cast<uint64_t>(num_sms()) * 8;
         if (nb > cap) nb = cap;
         k_layer_records<<<static_cast<unsigned>(nb), kLThreads, 0, st>>>(a, static_cast<LayerRec*>(d_rec));
