@@ -172,3 +172,35 @@ def test_diag33_beyond_2_32_closed_form_and_inverse(q):
         assert abs(q.qsa_expectation_z(st.h, 0) - 1) < 1e-5
     finally:
         st.close()
+
+
+def test_layer33_beyond_2_32_closed_form_and_inverse(q):
+    """N = 33 layer blocks whose factors and phase gates reach qubit 32 (indices
+    beyond 2^32): after H on qubits 0, 17, 32 with ZZ(32, 5), ZZ(17, 32) and a
+    phase on 32 the populated amplitudes match their closed form; the inverse
+    blocks (factors first, then the conjugate phases) return to |0...0>."""
+    n = 33
+    zz = lambda g: np.diag(np.exp(-0.5j * g * np.array([1, -1, -1, 1])))
+    diag = [W.Op((32, 5), zz(0.7), True), W.Op((17, 32), zz(1.9), True),
+            W.Op((32,), np.diag([1, np.exp(0.3j)]), True)]
+    t = [0, 17, 32]
+    st = Big(q, n)
+    try:
+        q.qsa_apply_layer(st.h, [], t, [W.H] * 3)
+        q.qsa_apply_layer(st.h, diag, [], [])
+        xs = np.array([0, 1, 1 << 17, 1 << 32, (1 << 32) | 1, (1 << 32) | (1 << 17) | 1, 1 << 5], dtype=np.int64)
+        got = st.amps(xs)
+        ref = []
+        for x in xs:
+            populated = (int(x) & ~((1 << 0) | (1 << 17) | (1 << 32))) == 0
+            b = [(int(x) >> k) & 1 for k in (32, 5, 17)]
+            ph = np.exp(-0.5j * 0.7 * (1 - 2 * (b[0] ^ b[1]))) * np.exp(-0.5j * 1.9 * (1 - 2 * (b[2] ^ b[0])))
+            ph *= np.exp(0.3j) if b[0] else 1.0
+            ref.append(ph / np.sqrt(8) if populated else 0.0)
+        assert np.max(np.abs(got - np.array(ref))) < 1e-6
+        inv = [W.Op(o.targets, o.matrix.conj().T, True) for o in diag]
+        q.qsa_apply_layer(st.h, inv, [], [])
+        q.qsa_apply_layer(st.h, [], t, [W.H] * 3)
+        assert abs(st.amps([0])[0] - 1) < 1e-5
+    finally:
+        st.close()
