@@ -287,9 +287,10 @@ __device__ __forceinline__ void tile_phases(const LayerArgs& a, uint64_t base, L
 }
 
 // Rotation mode: the per-tile phases of one tile into *out (one warp): the
-// scalar of the out gates and each pmask bit's cross phases; round 0's
-// local phases from bits 0..3 (shuffled from lanes 0..3).
-__device__ __forceinline__ void tile_record(const LayerArgs& a, uint64_t base, LayerRec* out) {
+// scalar of the out gates (lanes over gates, product across lanes); each
+// pmask bit's cross phases times its rotation's entry phases (lane b, into
+// the warp's scratch dsh); then lane l < 16 forms entry l of the three tables.
+__device__ __forceinline__ void tile_record(const LayerArgs& a, uint64_t base, float2 (*dsh)[2], LayerRec* out) {
     const int lane = threadIdx.x & 31;
     float2 sc = make_float2(1.f, 0.f);
     for (int g = lane; g < a.nout; g += 32) {
@@ -316,18 +317,33 @@ __device__ __forceinline__ void tile_record(const LayerArgs& a, uint64_t base, L
     }
     if (lane < kLT) {
         // the bit's entry phases of its rotation (identity without a factor)
-        d0 = cmulf(d0, a.qph[2 * lane]);
-        d1 = cmulf(d1, a.qph[2 * lane + 1]);
+        dsh[lane][0] = (a.pmask >> lane) & 1u ? cmulf(d0, a.qph[2 * lane]) : make_float2(1.f, 0.f);
+        dsh[lane][1] = (a.pmask >> lane) & 1u ? cmulf(d1, a.qph[2 * lane + 1]) : make_float2(1.f, 0.f);
     }
-    phase_tables(a.pmask, d0, d1, sc, out);
+    __syncwarp();
+    if (lane < 16) {
+        float2 pl = sc, pa = make_float2(1.f, 0.f), pb = make_float2(1.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int v = (lane >> b) & 1;
+            pl = cmulf(pl, dsh[b][v]);
+            pa = cmulf(pa, dsh[4 + b][v]);
+            pb = cmulf(pb, dsh[8 + b][v]);
+        }
+        out->pl[lane] = pl;
+        out->pa[lane] = pa;
+        out->pb[lane] = pb;
+    }
+    __syncwarp();
 }
 
 // One warp per tile: the records of a rotation-mode pass with per-tile phases.
 __global__ void __launch_bounds__(kLThreads) k_layer_records(LayerArgs a, LayerRec* recs) {
+    __shared__ float2 dsh[kLThreads / 32][kLT][2];
     const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x >> 5);
     for (uint64_t t = blockIdx.x * static_cast<uint64_t>(blockDim.x >> 5) + (threadIdx.x >> 5); t < a.ntiles;
          t += warps)
-        tile_record(a, layer_base(a, t), recs + t);
+        tile_record(a, layer_base(a, t), dsh[threadIdx.x >> 5], recs + t);
 }
 
 template <bool ROT>
