@@ -325,15 +325,14 @@ def main():
            "diag_blocks": 0, "prod_blocks": 0, "layer_blocks": 0}
 
     def step(record):
-        reset()
-        st = q.qsa_plan_execute(s, plan)
+        st = q.qsa_plan_execute_from_zero(s, plan)   # |0...0> in the plan's layout, then the plan
         if dm:
             norm = q.qsa_dm_probabilities(s, n_dm, want_probs=False)[1]
             zz = q.qsa_dm_expectation_z(s, n_dm, edge_mask)
             nshot = 0
         else:
-            norm, zz = q.qsa_expectation_z_batch(s, [0, edge_mask])   # one pass for both sums
-            vals, cnts = q.qsa_sample_counts(s, args.shots, seed=args.seed + 17)
+            # norm, <Z_a Z_b> and the shots from one read of the state
+            (norm, zz), vals, cnts = q.qsa_measure(s, [0, edge_mask], args.shots, seed=args.seed + 17)
             nshot = int(cnts.sum())
         if record:
             for k in agg:
@@ -417,8 +416,7 @@ def main():
                 q.qsa_dm_expectation_z(s, n_dm, edge_mask)
                 d2h = 16.0
             else:
-                q.qsa_expectation_z_batch(s, [0, edge_mask])
-                vals, cnts = q.qsa_sample_counts(s, args.shots, seed=args.seed + 17)
+                _, vals, cnts = q.qsa_measure(s, [0, edge_mask], args.shots, seed=args.seed + 17)
                 d2h = 16.0 * len(vals) + 16 + 16
             torch.cuda.synchronize()
             e2e_times.append(time.perf_counter() - t0)

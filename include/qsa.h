@@ -353,6 +353,13 @@ qsa_status qsa_plan_info(qsa_plan p, size_t* n_blocks, size_t* n_ops, int* max_w
 /* First input op and width of every block (capacity >= n_blocks, else QSA_E_RANGE). */
 qsa_status qsa_plan_blocks(qsa_plan p, size_t* first_op, int32_t* widths, size_t capacity);
 
+/* qsa_state_reset + a relabel of |0..0> to the plan's layout + qsa_plan_execute,
+ * without the reset's clearing pass when the plan begins with a zero-state
+ * preparation (opts.zero_init, N >= 12), which writes every amplitude.  The
+ * state's previous contents and layout are discarded.  Errors: as
+ * qsa_plan_execute. */
+qsa_status qsa_plan_execute_from_zero(qsa_state s, qsa_plan p, qsa_run_stats* stats);
+
 /* Execution order of the input ops (order[i] = input index of the i-th op
  * executed; the identity unless opts.layer moved ops); first_op of
  * qsa_plan_blocks indexes this order.  capacity >= n_ops, else QSA_E_RANGE. */
@@ -415,6 +422,15 @@ qsa_status qsa_expectation_z(qsa_state s, uint64_t logical_mask, double* out);
  * NULL). */
 #define QSA_MAX_ZMASKS 4
 qsa_status qsa_expectation_z_batch(qsa_state s, const uint64_t* logical_masks, int n_masks, double* out);
+
+/* qsa_expectation_z for each of z_masks[0..n_masks) (logical, n_masks in
+ * 0..QSA_MAX_ZMASKS) into z_out (host) and qsa_sample_counts (same draws and
+ * outputs), the sums taken in the sampler's pass over the state, so the state
+ * is read once for both (each sum agrees with qsa_expectation_z to FP64
+ * rounding; the summation order differs).  Synchronises the stream.  Errors:
+ * as qsa_sample_counts, and QSA_E_ARG for n_masks, a mask beyond N or NULL. */
+qsa_status qsa_measure(qsa_state s, const uint64_t* z_masks, int n_masks, double* z_out, uint64_t shots,
+                       uint64_t seed, uint64_t* outcomes, uint64_t* counts, size_t capacity, size_t* n_distinct);
 
 /* Draw `shots` outcomes (§IV-E): weights P_y = trunc(p_y * 2^62) (integer,
  * so the CDF does not depend on summation order) over physical indices in

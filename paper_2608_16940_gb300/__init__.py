@@ -99,6 +99,7 @@ _f = {
     "qsa_apply_product": _sig("qsa_apply_product", [_vp, _i32p, _c.c_int, _dp]),
     "qsa_apply_layer": _sig("qsa_apply_layer", [_vp, _vp, _c.c_size_t, _i32p, _c.c_int, _dp]),
     "qsa_plan_order": _sig("qsa_plan_order", [_vp, _vp, _c.c_size_t]),
+    "qsa_plan_execute_from_zero": _sig("qsa_plan_execute_from_zero", [_vp, _vp, _c.POINTER(qsa_run_stats)]),
     "qsa_plan_block_kinds": _sig("qsa_plan_block_kinds", [_vp, _i32p, _i32p, _c.c_size_t]),
     "qsa_plan_opts_default": _sig("qsa_plan_opts_default", [_c.POINTER(qsa_plan_opts)], None),
     "qsa_plan_circuit": _sig("qsa_plan_circuit", [_c.POINTER(qsa_op), _c.c_size_t, _c.c_int,
@@ -120,6 +121,8 @@ _f = {
     "qsa_probabilities_device": _sig("qsa_probabilities_device", [_vp, _vp, _dp]),
     "qsa_expectation_z": _sig("qsa_expectation_z", [_vp, _c.c_uint64, _dp]),
     "qsa_expectation_z_batch": _sig("qsa_expectation_z_batch", [_vp, _u64p, _c.c_int, _dp]),
+    "qsa_measure": _sig("qsa_measure", [_vp, _u64p, _c.c_int, _dp, _c.c_uint64, _c.c_uint64, _u64p, _u64p,
+                                        _c.c_size_t, _c.POINTER(_c.c_size_t)]),
     "qsa_dm_apply_channel": _sig("qsa_dm_apply_channel", [_vp, _c.c_int, _i32p, _c.c_int, _dp, _c.c_int,
                                                            _c.c_int]),
     "qsa_dm_superoperator": _sig("qsa_dm_superoperator", [_c.c_int, _i32p, _c.c_int, _dp, _c.c_int, _i32p, _dp]),
@@ -372,6 +375,13 @@ def qsa_plan_execute(s: int, p: int) -> dict:
     return st.as_dict()
 
 
+def qsa_plan_execute_from_zero(s: int, p: int) -> dict:
+    """Run the plan from |0...0> (in the plan's layout), discarding the state."""
+    st = qsa_run_stats()
+    _check(_f["qsa_plan_execute_from_zero"](_vp(s), _vp(p), _c.byref(st)))
+    return st.as_dict()
+
+
 def qsa_plan_destroy(p: int) -> None:
     _check(_f["qsa_plan_destroy"](_vp(p)))
 
@@ -472,6 +482,20 @@ def qsa_sample_counts(s: int, shots: int, seed: int, capacity: Optional[int] = N
     _check(_f["qsa_sample_counts"](_vp(s), shots, _c.c_uint64(seed), outc.ctypes.data_as(_u64p),
                                    cnt.ctypes.data_as(_u64p), cap, _c.byref(nd)))
     return outc[: nd.value].copy(), cnt[: nd.value].copy()
+
+
+def qsa_measure(s: int, z_masks, shots: int, seed: int, capacity: Optional[int] = None):
+    """(<Z_mask> for each mask, outcomes, counts) from one pass over the state."""
+    cap = shots if capacity is None else capacity
+    m = np.ascontiguousarray(np.asarray(list(z_masks), dtype=np.uint64))
+    z = np.zeros(max(1, len(m)), dtype=np.float64)
+    outc = np.zeros(max(1, cap), dtype=np.uint64)
+    cnt = np.zeros(max(1, cap), dtype=np.uint64)
+    nd = _c.c_size_t()
+    _check(_f["qsa_measure"](_vp(s), m.ctypes.data_as(_u64p) if len(m) else None, len(m),
+                             z.ctypes.data_as(_dp) if len(m) else None, shots, _c.c_uint64(seed),
+                             outc.ctypes.data_as(_u64p), cnt.ctypes.data_as(_u64p), cap, _c.byref(nd)))
+    return [float(v) for v in z[: len(m)]], outc[: nd.value].copy(), cnt[: nd.value].copy()
 
 
 # ---- cost model -------------------------------------------------------------

@@ -905,6 +905,23 @@ qsa_status qsa_plan_execute(qsa_state s, qsa_plan p, qsa_run_stats* stats) {
     return QSA_OK;
 }
 
+qsa_status qsa_plan_execute_from_zero(qsa_state s, qsa_plan p, qsa_run_stats* stats) {
+    if (!s) return fail(QSA_E_ARG, "state is NULL");
+    if (!p) return fail(QSA_E_ARG, "plan is NULL");
+    if (p->n != s->n) return fail(QSA_E_ARG, "plan and state have different qubit counts");
+    if (!p->blocks.empty() && p->blocks[0].init && s->n >= QSA_LAYER_TILE_BITS && !s->failed) {
+        // the preparation pass writes every amplitude: |0..0> in the plan's
+        // layout needs no clearing first
+        for (int q = 0; q < s->n; ++q) s->L[q] = p->L0[q];
+        s->known_zero = true;
+    } else {
+        qsa_status st = qsa_state_reset(s);
+        if (st != QSA_OK) return st;
+        for (int q = 0; q < s->n; ++q) s->L[q] = p->L0[q];   // relabelling |0..0> is free
+    }
+    return qsa_plan_execute(s, p, stats);
+}
+
 qsa_status qsa_apply_circuit(qsa_state s, const qsa_op* ops, size_t n_ops, const qsa_plan_opts* opts,
                              qsa_run_stats* stats) {
     qsa_status st = check_state(s);

@@ -152,5 +152,12 @@ size_t sample_scratch_bytes(int n, uint64_t shots);
 cudaError_t launch_sample(const float2* psi, int n, const int32_t* d_layout, uint64_t shots, uint64_t seed,
                           uint64_t stream_id, void* d_scratch, uint64_t* d_out_keys, uint64_t* d_out_counts,
                           uint64_t* d_n_distinct, cudaStream_t st, uint64_t* launches);
+// The same with <Z_mask> sums for nmasks (0..kMaxZMasks) physical masks taken in
+// the weights pass: d_zpartials holds nmasks * reduce_partials() doubles, the
+// sums go to d_zout[0..nmasks) (device).
+cudaError_t launch_sample_z(const float2* psi, int n, const int32_t* layout_host, uint64_t shots, uint64_t seed,
+                            uint64_t stream_id, void* d_scratch, uint64_t* d_out_keys, uint64_t* d_out_counts,
+                            uint64_t* d_n_distinct, const uint64_t* physmasks, int nmasks, double* d_zpartials,
+                            double* d_zout, cudaStream_t st, uint64_t* launches);
 
 }  // namespace qsa

@@ -158,6 +158,49 @@ __global__ void k_block_weights(const float2* __restrict__ psi, uint64_t nblocks
     if (lane == 0) cum[w] = s;
 }
 
+// The block weights and, in the same read of the state, <Z_mask> sums for up to
+// kMaxZMasks masks: persistent warps walk the 2^bsz-amplitude blocks; each
+// thread accumulates its amplitudes' squares per mask as k_reduce_z does
+// (double-float); per-CTA partials of mask m at m * gridDim.x.
+__global__ void __launch_bounds__(kRedThreads) k_block_weights_z(const float2* __restrict__ psi, uint64_t nblocks,
+                                                                 int bsz, uint64_t* __restrict__ cum, ZMasks masks,
+                                                                 double* __restrict__ partials) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x >> 5);
+    float zs[kMaxZMasks] = {}, zc[kMaxZMasks] = {};
+    for (uint64_t w = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; w < nblocks; w += warps) {
+        const uint64_t y0 = w * bsz;
+        const float2* p = psi + y0;
+        uint64_t s = 0;
+        for (int j = lane; j < bsz; j += 32) {
+            const float2 a = __ldcs(p + j);
+            s += weight(a);
+#pragma unroll
+            for (int m = 0; m < kMaxZMasks; ++m) {
+                if (m >= masks.n) break;
+                const bool neg = __popcll((y0 + j) & masks.m[m]) & 1;
+                acc_square(zs[m], zc[m], a.x, neg);
+                acc_square(zs[m], zc[m], a.y, neg);
+            }
+        }
+        s = warp_sum_u64(s);
+        if (lane == 0) cum[w] = s;
+    }
+    __shared__ double ws[kRedThreads / 32];
+    for (int m = 0; m < masks.n; ++m) {
+        double acc = static_cast<double>(zs[m]) + static_cast<double>(zc[m]);
+        acc = warp_sum_d(acc);
+        if (lane == 0) ws[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double v = threadIdx.x < (kRedThreads / 32) ? ws[threadIdx.x] : 0.0;
+            v = warp_sum_d(v);
+            if (threadIdx.x == 0) partials[static_cast<uint64_t>(m) * gridDim.x + blockIdx.x] = v;
+        }
+        __syncthreads();
+    }
+}
+
 // In-place inclusive scan of cum[0..n-1] by one CTA of 1024 threads.
 __global__ void __launch_bounds__(1024) k_scan_inclusive(uint64_t* __restrict__ cum, uint64_t n) {
     __shared__ uint64_t wsum[32];
@@ -601,6 +644,15 @@ size_t sample_scratch_bytes(int n, uint64_t shots) {
 cudaError_t launch_sample(const float2* psi, int n, const int32_t* layout_host, uint64_t shots, uint64_t seed,
                           uint64_t stream_id, void* d_scratch, uint64_t* d_out_keys, uint64_t* d_out_counts,
                           uint64_t* d_n_distinct, cudaStream_t st, uint64_t* launches) {
+    return launch_sample_z(psi, n, layout_host, shots, seed, stream_id, d_scratch, d_out_keys, d_out_counts,
+                           d_n_distinct, nullptr, 0, nullptr, nullptr, st, launches);
+}
+
+cudaError_t launch_sample_z(const float2* psi, int n, const int32_t* layout_host, uint64_t shots, uint64_t seed,
+                            uint64_t stream_id, void* d_scratch, uint64_t* d_out_keys, uint64_t* d_out_counts,
+                            uint64_t* d_n_distinct, const uint64_t* physmasks, int nmasks, double* d_zpartials,
+                            double* d_zout, cudaStream_t st, uint64_t* launches) {
+    if (nmasks < 0 || nmasks > kMaxZMasks) return cudaErrorInvalidValue;
     Layout lay{};
     lay.n = n;
     for (int q = 0; q < n; ++q) lay.L[q] = layout_host[q];
@@ -612,7 +664,18 @@ cudaError_t launch_sample(const float2* psi, int n, const int32_t* layout_host, 
     uint64_t* starts = keys + P;
 
     const unsigned wpb = 8;  // warps per CTA
-    k_block_weights<<<static_cast<unsigned>((nblocks + wpb - 1) / wpb), wpb * 32, 0, st>>>(psi, nblocks, bsz, cum);
+    if (nmasks > 0) {
+        ZMasks zm{};
+        zm.n = nmasks;
+        for (int m = 0; m < nmasks; ++m) zm.m[m] = physmasks[m];
+        const int nb = reduce_partials();
+        k_block_weights_z<<<nb, kRedThreads, 0, st>>>(psi, nblocks, bsz, cum, zm, d_zpartials);
+        for (int m = 0; m < nmasks; ++m) k_finalize_sum<<<1, 1024, 0, st>>>(d_zpartials + m * nb, nb, d_zout + m);
+        *launches += nmasks;
+    } else {
+        k_block_weights<<<static_cast<unsigned>((nblocks + wpb - 1) / wpb), wpb * 32, 0, st>>>(psi, nblocks, bsz,
+                                                                                                cum);
+    }
     const uint64_t nseg = (nblocks + kScanSeg - 1) / kScanSeg;
     if (nseg > 1 && nseg <= P + shots) {
         // segment totals in the key area, which k_draw fills only afterwards

@@ -612,11 +612,30 @@ qsa_status qsa_probabilities(qsa_state s, double* out_host, double* norm_out) {
 
 qsa_status qsa_sample_counts(qsa_state s, uint64_t shots, uint64_t seed, uint64_t* outcomes, uint64_t* counts,
                              size_t capacity, size_t* n_distinct) {
+    return qsa_measure(s, nullptr, 0, nullptr, shots, seed, outcomes, counts, capacity, n_distinct);
+}
+
+qsa_status qsa_measure(qsa_state s, const uint64_t* z_masks, int n_masks, double* z_out, uint64_t shots,
+                       uint64_t seed, uint64_t* outcomes, uint64_t* counts, size_t capacity, size_t* n_distinct) {
     qsa_status st = check_state(s);
     if (st != QSA_OK) return st;
     if (!n_distinct) return fail(QSA_E_ARG, "n_distinct is NULL");
     if (shots < 1 || shots > (1ull << 26)) return fail(QSA_E_ARG, "shots must be in 1..2^26");
     if (capacity > 0 && (!outcomes || !counts)) return fail(QSA_E_ARG, "output arrays are NULL");
+    if (n_masks < 0 || n_masks > QSA_MAX_ZMASKS) return fail(QSA_E_ARG, "n_masks must be in 0..4");
+    if (n_masks > 0 && (!z_masks || !z_out)) return fail(QSA_E_ARG, "z_masks or z_out is NULL");
+    uint64_t pm[QSA_MAX_ZMASKS] = {};
+    for (int m = 0; m < n_masks; ++m) {
+        if (s->n < 64 && (z_masks[m] >> s->n)) return fail(QSA_E_ARG, "mask has bits beyond N");
+        for (int q = 0; q < s->n; ++q)
+            if ((z_masks[m] >> q) & 1) pm[m] |= 1ull << s->L[q];
+    }
+    const size_t nbp = static_cast<size_t>(reduce_partials());
+    if (n_masks > 0) {
+        st = ensure_dev(s, reinterpret_cast<void**>(&s->d_red), &s->red_cap,
+                        sizeof(double) * (QSA_MAX_ZMASKS * nbp + 8));
+        if (st != QSA_OK) return st;
+    }
     const size_t scratch = sample_scratch_bytes(s->n, shots);
     const size_t outb = sizeof(uint64_t) * (2 * shots + 4);
     st = ensure_dev(s, &s->d_samp, &s->samp_cap, scratch + outb);
@@ -624,9 +643,14 @@ qsa_status qsa_sample_counts(qsa_state s, uint64_t shots, uint64_t seed, uint64_
     uint64_t* d_keys = reinterpret_cast<uint64_t*>(static_cast<char*>(s->d_samp) + scratch);
     uint64_t* d_cnts = d_keys + shots;
     uint64_t* d_nd = d_cnts + shots;
-    cudaError_t e = launch_sample(s->psi, s->n, s->L, shots, seed, 0, s->d_samp, d_keys, d_cnts, d_nd, s->stream,
-                                  &s->launches);
+    double* d_zout = n_masks > 0 ? s->d_red + QSA_MAX_ZMASKS * nbp : nullptr;
+    cudaError_t e = launch_sample_z(s->psi, s->n, s->L, shots, seed, 0, s->d_samp, d_keys, d_cnts, d_nd, pm, n_masks,
+                                    n_masks > 0 ? s->d_red : nullptr, d_zout, s->stream, &s->launches);
     if (e != cudaSuccess) return cuda_fail(s, e, "sampler kernels");
+    if (n_masks > 0) {
+        e = cudaMemcpyAsync(z_out, d_zout, sizeof(double) * n_masks, cudaMemcpyDeviceToHost, s->stream);
+        if (e != cudaSuccess) return cuda_fail(s, e, "expectation results");
+    }
     uint64_t hdr[2] = {0, 0};
     const int bsz = s->n >= 10 ? 1024 : (1 << s->n);
     const uint64_t nblocks = (1ull << s->n) / bsz;

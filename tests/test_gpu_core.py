@@ -270,6 +270,31 @@ def test_sampler_bit_exact_vs_oracle(q, n, shots, perm, zero_frac):
         st.close()
 
 
+@pytest.mark.parametrize("n,perm", [(12, True), (23, False)])
+def test_measure_equals_expectations_and_sampling(q, n, perm):
+    """qsa_measure: the same counts as qsa_sample_counts (bit for bit) and the
+    same sums as qsa_expectation_z to FP64 rounding, from one pass."""
+    psi = W.random_state(n, 40 + n).astype(np.complex64)
+    st = GState(q, n, init=psi)
+    p64 = psi.astype(np.complex128)
+    try:
+        if perm:
+            q.qsa_set_layout(st.h, [int(v) for v in np.random.default_rng(n).permutation(n)], 1)
+        masks = [0, 1 << (n - 1), 0b1011, (1 << n) - 1]
+        z, vals, cnts = q.qsa_measure(st.h, masks, 2000, seed=77)
+        v2, c2 = q.qsa_sample_counts(st.h, 2000, seed=77)
+        assert np.array_equal(vals, v2) and np.array_equal(cnts, c2)
+        for m, g in zip(masks, z):
+            assert abs(g - q.qsa_expectation_z(st.h, m)) < 1e-13
+            assert abs(g - oracle.expect_z(p64, m)) < 1e-12
+        z0, v0, c0 = q.qsa_measure(st.h, [], 500, seed=1)
+        assert z0 == [] and int(c0.sum()) == 500
+        with pytest.raises(q.QsaError):
+            q.qsa_measure(st.h, [0] * 5, 10, seed=1)
+    finally:
+        st.close()
+
+
 def test_sampler_capacity_and_basis_state(q):
     n = 12
     st = GState(q, n)

@@ -230,3 +230,25 @@ def test_zero_init_plan_needs_the_zero_state_and_other_layouts(q):
     finally:
         st.close()
         q.qsa_plan_destroy(p)
+
+
+@pytest.mark.parametrize("zero_init,n", [(1, 16), (0, 14), (1, 9)])
+def test_execute_from_zero_discards_the_state(q, zero_init, n):
+    """qsa_plan_execute_from_zero on a state holding arbitrary data: the result
+    is the circuit applied to |0...0> (without clearing when the plan starts
+    with the zero-state preparation), in the plan's layout."""
+    ops, _ = W.qaoa_circuit(n if n % 2 == 0 else n + 1, 2, seed=7)
+    if n % 2:
+        ops = [o for o in ops if max(o.targets) < n]
+    layout = [int(v) for v in np.random.default_rng(n).permutation(n)]
+    p = q.qsa_plan_create(ops, n, q.make_opts(planner=2, kmax=4, kmax_diag=4, layer=1, zero_init=zero_init),
+                          layout=layout)
+    st = GState(q, torch, n, init=W.random_state(n, seed=3))
+    try:
+        for _ in range(2):
+            q.qsa_plan_execute_from_zero(st.h, p)
+            assert q.qsa_get_layout(st.h) == layout
+            check_close(oracle.run_circuit(n, ops), st.logical())
+    finally:
+        st.close()
+        q.qsa_plan_destroy(p)
