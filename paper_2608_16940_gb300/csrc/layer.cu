@@ -14,10 +14,13 @@
 //           has no factor;
 //   out     (no qubit in the tile): a scalar per tile, multiplied in.
 // Unitary factors run in rotation mode: each factor is split on the host as
-// F = diag(p) R diag(q) with R = [[c, -s], [s, c]] real, so it costs a real
-// rotation (4 multiply-adds per amplitude instead of 8).  Its q phases join
-// the per-bit phases (with the cross phases, applied in round 0 before any
-// rotation) and its p phases a 16-entry table of its round (applied after
+// F = diag(p) R diag(q) with R = [[c, -s], [s, c]] real, and R in turn as
+// kappa * M with one coefficient of each row of M equal to 1 (tangent form
+// M = [[1, -t], [t, 1]], t = s / c, when c >= s; else the cotangent form
+// M = [[u, -1], [1, u]], u = c / s, whose first row is negated into p), so a
+// factor costs one packed multiply-add per amplitude.  kappa and the q phases
+// join the per-bit phases (with the cross phases, applied in round 0 before
+// any rotation) and the p phases a 16-entry table of its round (applied after
 // the round's rotations).  Other factors run in general mode (complex 2x2
 // butterflies, cross phases folded into them).
 // Per tile: 16-byte cp.async copies into a 2-stage ring (XOR-swizzled 16-byte
@@ -58,11 +61,12 @@ struct LayerArgs {
     uint32_t fmask;           // tile bits with a factor
     uint32_t pmask;           // tile bits with a per-tile phase applied as a multiply
     uint32_t rpmask;          // rotation mode: rounds with exit phases
+    uint32_t rform;           // rotation mode: tile bits in the cotangent form
     int generate;             // write-only: every amplitude enters as 1 (nothing is read)
     int ncross, nout;
     int cstart[kLT + 1];      // cross gates of tile bit b: [cstart[b], cstart[b + 1])
     const float2* fac;        // general mode: kLT x 4 complex (2x2 row-major); rotation mode:
-                              // (cos, sin) of each factor's rotation
+                              // (t or u, 0) of each factor's rotation
     const LayerGate* cross;   // a = tile bit, b = outside position, d[2 * o + v]
     const LayerGate* outg;    // a, b = positions (b < 0: one qubit), d[v_a + 2 v_b]
     const float2* din;        // table of the gates with every qubit in the tile: 2^12 entries in
@@ -118,17 +122,29 @@ __device__ __forceinline__ void butterfly(float2 (&v)[16], const float2* F) {
     }
 }
 
-// Real rotation [[c, -s], [s, c]] on local bit LB: both components of an
-// amplitude in one packed pair, two fma.rn.f32x2 per output.
+// Scaled real rotation on local bit LB, both components of an amplitude in
+// one packed pair, one fma.rn.f32x2 per output:
+//   tangent form   (x0, x1) <- (x0 - t x1, x1 + t x0)
+//   cotangent form (x0, x1) <- (x1 - u x0, x0 + u x1)
 template <int LB>
-__device__ __forceinline__ void rotation(float2 (&v)[16], float2 cs) {
-    const uint64_t c2 = pack2(cs.x, cs.x), s2 = pack2(cs.y, cs.y), ns2 = pack2(-cs.y, -cs.y);
+__device__ __forceinline__ void rotation(float2 (&v)[16], float coef, bool cot) {
+    const uint64_t t2 = pack2(coef, coef), nt2 = pack2(-coef, -coef);
+    if (!cot) {
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        if ((i >> LB) & 1) continue;
-        const uint64_t x0 = pack2(v[i].x, v[i].y), x1 = pack2(v[i | (1 << LB)].x, v[i | (1 << LB)].y);
-        v[i] = unpack2(fma2(c2, x0, fma2(ns2, x1, 0ull)));
-        v[i | (1 << LB)] = unpack2(fma2(s2, x0, fma2(c2, x1, 0ull)));
+        for (int i = 0; i < 16; ++i) {
+            if ((i >> LB) & 1) continue;
+            const uint64_t x0 = pack2(v[i].x, v[i].y), x1 = pack2(v[i | (1 << LB)].x, v[i | (1 << LB)].y);
+            v[i] = unpack2(fma2(nt2, x1, x0));
+            v[i | (1 << LB)] = unpack2(fma2(t2, x0, x1));
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            if ((i >> LB) & 1) continue;
+            const uint64_t x0 = pack2(v[i].x, v[i].y), x1 = pack2(v[i | (1 << LB)].x, v[i | (1 << LB)].y);
+            v[i] = unpack2(fma2(nt2, x0, x1));
+            v[i | (1 << LB)] = unpack2(fma2(t2, x1, x0));
+        }
     }
 }
 
@@ -177,10 +193,11 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
     }
     const uint32_t act = (a.fmask >> (4 * R)) & 15u;
     if constexpr (ROT) {
-        if (act & 1u) rotation<0>(v, rot[4 * R + 0]);
-        if (act & 2u) rotation<1>(v, rot[4 * R + 1]);
-        if (act & 4u) rotation<2>(v, rot[4 * R + 2]);
-        if (act & 8u) rotation<3>(v, rot[4 * R + 3]);
+        const uint32_t cot = a.rform >> (4 * R);
+        if (act & 1u) rotation<0>(v, rot[4 * R + 0].x, cot & 1u);
+        if (act & 2u) rotation<1>(v, rot[4 * R + 1].x, cot & 2u);
+        if (act & 4u) rotation<2>(v, rot[4 * R + 2].x, cot & 4u);
+        if (act & 8u) rotation<3>(v, rot[4 * R + 3].x, cot & 8u);
         if (act && ((a.rpmask >> R) & 1u)) {
             // exit phases of the round's factor bits (they follow only their own rotations)
 #pragma unroll
@@ -495,6 +512,7 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
     a.fmask = p.active;
     a.pmask = p.pmask;
     a.rpmask = p.rpmask;
+    a.rform = p.rform;
     a.generate = p.generate ? 1 : 0;
     if (p.generate && (p.active != 0)) return cudaErrorInvalidValue;   // write-only passes carry no factors
     a.ncross = p.ncross;

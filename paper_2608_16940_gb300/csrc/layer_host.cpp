@@ -89,6 +89,9 @@ bool split_rotation(const std::array<std::complex<double>, 4>& F, double* c, dou
     return true;
 }
 
+// The rotation [[c, -s], [s, c]] runs in the cotangent form when s > c.
+bool rotation_cotangent(double c, double s) { return s > c; }
+
 // One pass: factors fsel (indices into spec.f), the diagonal ops if with_diag.
 // Returns false when there is nothing to apply.
 bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vector<int>& fsel, bool with_diag,
@@ -111,6 +114,27 @@ bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vec
     p.rotation = true;
     for (int b = 0; b < kTile && p.rotation; ++b)
         if ((p.active >> b) & 1u) p.rotation = split_rotation(fac[b], &rc[b], &rs[b], rp[b].data(), rq[b].data());
+    // R = kappa M: tangent form (c >= s) M = [[1, -t], [t, 1]], kappa = c;
+    // cotangent form M = [[u, -1], [1, u]], kappa = s, computed as (-row 0, row 1)
+    // with the sign moved into p0; kappa joins the entry phases q
+    std::vector<double> rcoef(kTile, 0.0);
+    p.rform = 0;
+    if (p.rotation)
+        for (int b = 0; b < kTile; ++b) {
+            if (!((p.active >> b) & 1u)) continue;
+            double kappa;
+            if (rotation_cotangent(rc[b], rs[b])) {
+                rcoef[b] = rc[b] / rs[b];
+                kappa = rs[b];
+                rp[b][0] = -rp[b][0];
+                p.rform |= 1u << b;
+            } else {
+                rcoef[b] = rs[b] / rc[b];
+                kappa = rc[b];
+            }
+            rq[b][0] *= kappa;
+            rq[b][1] *= kappa;
+        }
     std::vector<LayerGate> cross, outg;
     uint32_t cross_bits = 0;
     std::vector<std::complex<double>> din;
@@ -176,7 +200,7 @@ bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vec
     std::vector<float2> facf(4 * kTile);
     for (int b = 0; b < kTile; ++b) {
         if (p.rotation)
-            facf[b] = make_float2(static_cast<float>(rc[b]), static_cast<float>(rs[b]));
+            facf[b] = make_float2(static_cast<float>(rcoef[b]), 0.f);
         else
             for (int c = 0; c < 4; ++c) facf[4 * b + c] = f2(fac[b][c]);
     }
@@ -207,6 +231,8 @@ void layer_move_exit_phases(LayerSpec* from, LayerSpec* to) {
         double c, s;
         std::complex<double> p[2], q[2];
         if (!split_rotation(from->f[j], &c, &s, p, q)) continue;
+        // the cotangent form's pass negates p0: hand over -p0 so that it meets 1 there
+        if (rotation_cotangent(c, s)) p[0] = -p[0];
         if (std::abs(std::abs(p[0]) - 1.0) > 1e-12 || std::abs(std::abs(p[1]) - 1.0) > 1e-12) continue;
         if (std::abs(p[0] - 1.0) < 1e-15 && std::abs(p[1] - 1.0) < 1e-15) continue;
         auto& F = from->f[j];
