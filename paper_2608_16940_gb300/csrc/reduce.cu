@@ -201,6 +201,96 @@ __global__ void __launch_bounds__(kRedThreads) k_block_weights_z(const float2* _
     }
 }
 
+// |x + iy|^2 as an unevaluated pair hi + lo: each square split exactly by the
+// FMA two-product, the two high parts added by Knuth's two-sum, the low parts
+// (about 2^-24 of hi) rounded into lo.
+__device__ __forceinline__ void square_pair(float x, float y, float& hi, float& lo) {
+    const float h1 = __fmul_rn(x, x), l1 = __fmaf_rn(x, x, -h1);
+    const float h2 = __fmul_rn(y, y), l2 = __fmaf_rn(y, y, -h2);
+    const float t = __fadd_rn(h1, h2);
+    const float bp = __fsub_rn(t, h1);
+    const float e = __fadd_rn(__fsub_rn(h1, __fsub_rn(t, bp)), __fsub_rn(h2, bp));
+    hi = t;
+    lo = __fadd_rn(e, __fadd_rn(l1, l2));
+}
+
+// s + c += (-1)^sign (hi + lo), sign given as the FP32 sign bit.
+__device__ __forceinline__ void add_signed(float& s, float& c, float hi, float lo, uint32_t signbit) {
+    const float h = __uint_as_float(__float_as_uint(hi) ^ signbit);
+    const float l = __uint_as_float(__float_as_uint(lo) ^ signbit);
+    const float t = __fadd_rn(s, h);
+    const float bp = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(h, bp));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(e, l));
+}
+
+// Blocks of 1024 amplitudes: the block weights and the <Z_mask> sums of NM
+// masks in one read.  A warp takes a block; lane l loads the 16-byte pairs
+// l + 32 k (k = 0..15) up front, so 8 KiB per warp are in flight.  Amplitude
+// y = 1024 w + 2 (l + 32 k) + b has its index bits split over (w, l, k, b), so
+// its sign parity is a per-block, a per-lane, a per-k and a per-b part.  Per
+// CTA partials of mask m at m * gridDim.x.
+template <int NM>
+__global__ void __launch_bounds__(kRedThreads, 2) k_weights_z1024(const float4* __restrict__ psi2, uint64_t nblocks,
+                                                                  uint64_t* __restrict__ cum, ZMasks masks,
+                                                                  double* __restrict__ partials) {
+    constexpr int NA = NM > 0 ? NM : 1;
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x >> 5);
+    float zs[NA] = {}, zc[NA] = {};
+    uint32_t kb[NA] = {}, lb[NA] = {}, b1[NA] = {};
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+        for (int k = 0; k < 16; ++k) kb[m] |= static_cast<uint32_t>(__popcll((64ull * k) & masks.m[m]) & 1) << k;
+        lb[m] = __popcll((2ull * lane) & masks.m[m]) & 1;
+        b1[m] = static_cast<uint32_t>(masks.m[m] & 1ull) << 31;
+    }
+    for (uint64_t w = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; w < nblocks; w += warps) {
+        const float4* p = psi2 + w * 512 + lane;
+        float4 a[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) a[k] = __ldcs(p + 32 * k);
+        uint32_t pb[NA] = {};
+#pragma unroll
+        for (int m = 0; m < NM; ++m) pb[m] = (__popcll((w << 10) & masks.m[m]) & 1) ^ lb[m];
+        uint64_t s = 0;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            s += sq_fixed60(a[k].x) + sq_fixed60(a[k].y) + sq_fixed60(a[k].z) + sq_fixed60(a[k].w);
+            if constexpr (NM > 0) {
+                float h0, l0, h1, l1;
+                square_pair(a[k].x, a[k].y, h0, l0);
+                square_pair(a[k].z, a[k].w, h1, l1);
+#pragma unroll
+                for (int m = 0; m < NM; ++m) {
+                    const uint32_t s0 = ((pb[m] ^ (kb[m] >> k)) & 1u) << 31;
+                    add_signed(zs[m], zc[m], h0, l0, s0);
+                    add_signed(zs[m], zc[m], h1, l1, s0 ^ b1[m]);
+                }
+            }
+        }
+        s = warp_sum_u64(s);
+        if (lane == 0) cum[w] = s;
+    }
+    if constexpr (NM > 0) {
+        __shared__ double ws[kRedThreads / 32];
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            double acc = static_cast<double>(zs[m]) + static_cast<double>(zc[m]);
+            acc = warp_sum_d(acc);
+            if (lane == 0) ws[threadIdx.x >> 5] = acc;
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                double v = threadIdx.x < (kRedThreads / 32) ? ws[threadIdx.x] : 0.0;
+                v = warp_sum_d(v);
+                if (threadIdx.x == 0) partials[static_cast<uint64_t>(m) * gridDim.x + blockIdx.x] = v;
+            }
+            __syncthreads();
+        }
+    }
+}
+
 // In-place inclusive scan of cum[0..n-1] by one CTA of 1024 threads.
 __global__ void __launch_bounds__(1024) k_scan_inclusive(uint64_t* __restrict__ cum, uint64_t n) {
     __shared__ uint64_t wsum[32];
@@ -664,7 +754,31 @@ cudaError_t launch_sample_z(const float2* psi, int n, const int32_t* layout_host
     uint64_t* starts = keys + P;
 
     const unsigned wpb = 8;  // warps per CTA
-    if (nmasks > 0) {
+    if (bsz == 1024) {
+        ZMasks zm{};
+        zm.n = nmasks;
+        for (int m = 0; m < nmasks; ++m) zm.m[m] = physmasks[m];
+        // at most reduce_partials() CTAs (the partials' size), two resident per SM
+        uint64_t nb = (nblocks + wpb - 1) / wpb;
+        const uint64_t cap = static_cast<uint64_t>(num_sms()) * 2;
+        if (nb > cap) nb = cap;
+        const auto* psi2 = reinterpret_cast<const float4*>(psi);
+        switch (nmasks) {
+            case 0: k_weights_z1024<0><<<static_cast<unsigned>(nb), kRedThreads, 0, st>>>(psi2, nblocks, cum, zm,
+                                                                                          d_zpartials); break;
+            case 1: k_weights_z1024<1><<<static_cast<unsigned>(nb), kRedThreads, 0, st>>>(psi2, nblocks, cum, zm,
+                                                                                          d_zpartials); break;
+            case 2: k_weights_z1024<2><<<static_cast<unsigned>(nb), kRedThreads, 0, st>>>(psi2, nblocks, cum, zm,
+                                                                                          d_zpartials); break;
+            case 3: k_weights_z1024<3><<<static_cast<unsigned>(nb), kRedThreads, 0, st>>>(psi2, nblocks, cum, zm,
+                                                                                          d_zpartials); break;
+            default: k_weights_z1024<4><<<static_cast<unsigned>(nb), kRedThreads, 0, st>>>(psi2, nblocks, cum, zm,
+                                                                                           d_zpartials); break;
+        }
+        for (int m = 0; m < nmasks; ++m)
+            k_finalize_sum<<<1, 1024, 0, st>>>(d_zpartials + m * nb, static_cast<int>(nb), d_zout + m);
+        *launches += nmasks;
+    } else if (nmasks > 0) {
         ZMasks zm{};
         zm.n = nmasks;
         for (int m = 0; m < nmasks; ++m) zm.m[m] = physmasks[m];
