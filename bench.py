@@ -48,12 +48,12 @@ UNIT = "amp-updates/s"
 # DRAM bytes (read + write) per amplitude of one launch, from single ncu captures
 # at N=28 (profiles/k_apply_tc6_n28.md: 4.241 GB; profiles/k_apply_fp32_k4_n28.md:
 # 4.234 GB; profiles/k_apply_diag_n28.md: 4.234 GB; profiles/k_apply_prod_n28.md:
-# 4.260 GB; profiles/k_apply_layer_n28.md: 4.261 GB (a regular pass); each /
+# 4.260 GB; profiles/k_apply_layer_n28.md: 4.265 GB (a regular pass); each /
 # 2^28).  Traffic scales with the state size, so a launch at N moves this many
 # bytes times 2^N.
 DRAM_BYTES_PER_AMP = {"k_apply_tc": 4.241e9 / 2**28, "k_apply_fp32": 4.234e9 / 2**28,
                       "k_apply_diag": 4.234e9 / 2**28, "k_apply_prod": 4.260e9 / 2**28,
-                      "k_apply_layer": 4.261e9 / 2**28}
+                      "k_apply_layer": 4.265e9 / 2**28}
 
 
 def _peaks():
