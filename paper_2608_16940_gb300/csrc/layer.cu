@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
     // rounds that do work; the last of them writes to HBM
     int first = -1, last = -1;
     for (int r = 0; r < 3; ++r)
-        if (((a.fmask >> (4 * r)) & 15u) || (r == 0 && (a.din || phase))) {
+        if (((a.fmask >> (4 * r)) & 15u) || (r == 0 && (a.din || phase || a.generate))) {
             if (first < 0) first = r;
             last = r;
         }
@@ -514,7 +514,6 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
     a.rpmask = p.rpmask;
     a.rform = p.rform;
     a.generate = p.generate ? 1 : 0;
-    if (p.generate && (p.active != 0)) return cudaErrorInvalidValue;   // write-only passes carry no factors
     a.ncross = p.ncross;
     a.nout = p.nout;
     for (int b = 0; b <= kLT; ++b) a.cstart[b] = p.cstart[b];

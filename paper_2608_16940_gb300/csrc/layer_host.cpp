@@ -274,7 +274,8 @@ std::vector<LayerLaunch> prepare_layer(int n, const int32_t* L, const LayerSpec&
     for (size_t i = 0; i < groups.size(); ++i) {
         LayerLaunch ll;
         if (prepare_pass(n, L, spec, groups[i], i == 0, bytes, &ll)) {
-            ll.p.generate = spec.generate;
+            // only the first pass generates; later ones read what it wrote
+            ll.p.generate = spec.generate && out.empty();
             out.push_back(ll);
         }
     }

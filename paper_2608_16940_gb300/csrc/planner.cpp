@@ -724,6 +724,22 @@ qsa_status qsa_plan_create(const qsa_op* ops, size_t n_ops, int n_qubits, const 
         p->max_width = std::max(p->max_width, b.k);
         while (p->host_mat.size() % 4) p->host_mat.push_back(0.f);  // 16-byte aligned matrices
     }
+    // the zero-state block takes over the layer block after it: the generated
+    // product state passes through that block's diagonal part and factors in
+    // the same write-only pass (its record is left empty and never referenced)
+    if (p->blocks.size() >= 2 && p->blocks[0].init && p->blocks[1].layer >= 0 && !p->blocks[1].init) {
+        LayerSpec& a = p->layers[p->blocks[0].layer].spec;
+        LayerSpec& b = p->layers[p->blocks[1].layer].spec;
+        a.diag.insert(a.diag.end(), b.diag.begin(), b.diag.end());
+        a.t = b.t;
+        a.f = b.f;
+        b = LayerSpec{};
+        PlanBlock& b0 = p->blocks[0];
+        b0.k = p->blocks[1].k;
+        for (int j = 0; j < b0.k; ++j) b0.t[j] = p->blocks[1].t[j];
+        b0.n_diag = static_cast<int>(a.diag.size());
+        p->blocks.erase(p->blocks.begin() + 1);
+    }
     // consecutive layer blocks: the exit phases of each block's factors move
     // to the next block's diagonal part; then every layer block's passes for
     // the plan's layout

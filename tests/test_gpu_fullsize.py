@@ -99,7 +99,7 @@ def test_qaoa30_symmetries_and_fused_equals_per_gate(q, kmax, kdiag, kprod, prec
                                                            kmax_prod=kprod, precision=prec, layer=layer,
                                                            zero_init=1 if interleave else 0))
         if layer:
-            assert stats["layer_blocks"] == (25 if interleave else 27) and stats["passes"] == stats["layer_blocks"]
+            assert stats["layer_blocks"] == (24 if interleave else 27) and stats["passes"] == stats["layer_blocks"]
         assert abs(q.qsa_expectation_z(st.h, 0) - 1) < 1e-5
         for qb in (0, 7, 29):
             assert abs(q.qsa_expectation_z(st.h, 1 << qb)) < 1e-5

@@ -78,7 +78,8 @@ def test_layer_options_validated(q):
 @pytest.mark.parametrize("kind,n", [("qaoa", 30), ("qaoa", 16), ("brick", 12), ("mixed", 14)])
 def test_zero_init_prefix_matches_oracle(q, kind, n):
     """The zero_init plan's first block covers exactly the oracle's prefix, in
-    input order, and the rest is grouped as without it."""
+    input order, together with the first unit after it when that is a layer
+    unit (both share the write-only pass); the rest is grouped as without it."""
     rng = np.random.default_rng(n)
     if kind == "qaoa":
         ops, _ = W.qaoa_circuit(n, 3, seed=0)
@@ -95,7 +96,8 @@ def test_zero_init_prefix_matches_oracle(q, kind, n):
     finally:
         q.qsa_plan_destroy(p)
     assert P > 0 and kinds[0] == 4 and 4 not in kinds[1:]
-    assert first[0] == 0 and (len(first) == 1 or first[1] == P)
     assert order[:P] == list(range(P))
-    ref_order, _ = oracle.layer_units(ops[P:], n)
+    ref_order, ref_units = oracle.layer_units(ops[P:], n)
     assert order[P:] == [x + P for x in ref_order]
+    end0 = P + ref_units[0][1] if ref_units and ref_units[0][2] else P
+    assert first[0] == 0 and (len(first) == 1 or first[1] == end0)
