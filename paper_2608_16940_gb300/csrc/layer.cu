@@ -61,7 +61,9 @@ struct LayerArgs {
     uint32_t fmask;           // tile bits with a factor
     uint32_t pmask;           // tile bits with a per-tile phase applied as a multiply
     uint32_t rpmask;          // rotation mode: rounds with exit phases
-    uint32_t rform;           // rotation mode: tile bits in the cotangent form
+    uint32_t rform;           // rotation mode: tile bits 0..3 in the cotangent form
+    uint32_t rswap;           // rotation mode: tile bits 4..11 left exchanged (their place i holds
+                              // the amplitude of local index i ^ rswap)
     int generate;             // write-only: every amplitude enters as 1 (nothing is read)
     int ncross, nout;
     int cstart[kLT + 1];      // cross gates of tile bit b: [cstart[b], cstart[b + 1])
@@ -193,11 +195,20 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
     }
     const uint32_t act = (a.fmask >> (4 * R)) & 15u;
     if constexpr (ROT) {
-        const uint32_t cot = a.rform >> (4 * R);
-        if (act & 1u) rotation<0>(v, rot[4 * R + 0].x, cot & 1u);
-        if (act & 2u) rotation<1>(v, rot[4 * R + 1].x, cot & 2u);
-        if (act & 4u) rotation<2>(v, rot[4 * R + 2].x, cot & 4u);
-        if (act & 8u) rotation<3>(v, rot[4 * R + 3].x, cot & 8u);
+        if constexpr (R == 0) {
+            const uint32_t cot = a.rform;
+            if (act & 1u) rotation<0>(v, rot[0].x, cot & 1u);
+            if (act & 2u) rotation<1>(v, rot[1].x, cot & 2u);
+            if (act & 4u) rotation<2>(v, rot[2].x, cot & 4u);
+            if (act & 8u) rotation<3>(v, rot[3].x, cot & 8u);
+        } else {
+            // all four in the tangent form without branches (t = 0 on bits
+            // without a factor is the identity)
+            rotation<0>(v, rot[4 * R + 0].x, false);
+            rotation<1>(v, rot[4 * R + 1].x, false);
+            rotation<2>(v, rot[4 * R + 2].x, false);
+            rotation<3>(v, rot[4 * R + 3].x, false);
+        }
         if (act && ((a.rpmask >> R) & 1u)) {
             // exit phases of the round's factor bits (they follow only their own rotations)
 #pragma unroll
@@ -211,7 +222,8 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
     }
     if (last) {
         // global offset of (jb | x) = offset(jb) | offset(x); goff[R][i] holds offset(i << 4R)
-        const uint64_t gb = layer_global(a, runoff, base, jb);
+        // at the exchanged index, and round 2's jb carries round 1's exchanged bits
+        const uint64_t gb = layer_global(a, runoff, base, R == 2 ? jb ^ static_cast<int>(a.rswap & 0xf0u) : jb);
         if constexpr (R == 0) {
             // m >= 3: amplitudes jb | i and jb | (i + 1) are adjacent in HBM
 #pragma unroll
@@ -385,7 +397,9 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
     // offsets of a round's local bits (goff[16 R + i] for tile-local i << 4R) and of
     // the load loop's chunk strides (goff[48 + k] for tile-local 512 k)
     if (threadIdx.x < 56) {
-        const int j = threadIdx.x < 48 ? (threadIdx.x & 15) << (4 * (threadIdx.x >> 4)) : (threadIdx.x - 48) << 9;
+        const int R = threadIdx.x >> 4;
+        const int j = threadIdx.x < 48 ? ((threadIdx.x & 15) ^ static_cast<int>((a.rswap >> (4 * R)) & 15u)) << (4 * R)
+                                       : (threadIdx.x - 48) << 9;
         goff[threadIdx.x] = layer_global(a, runoff, 0, j);
     }
     // tile bases: the tile index's bits deposited into the positions outside the
@@ -513,6 +527,7 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
     a.pmask = p.pmask;
     a.rpmask = p.rpmask;
     a.rform = p.rform;
+    a.rswap = p.rswap;
     a.generate = p.generate ? 1 : 0;
     a.ncross = p.ncross;
     a.nout = p.nout;
