@@ -18,7 +18,10 @@
 // kappa * M with one coefficient of each row of M equal to 1 (tangent form
 // M = [[1, -t], [t, 1]], t = s / c, when c >= s; else the cotangent form
 // M = [[u, -1], [1, u]], u = c / s, whose first row is negated into p), so a
-// factor costs one packed multiply-add per amplitude.  kappa and the q phases
+// factor costs one packed multiply-add per amplitude.  The cotangent form runs
+// as the tangent form with t = -u, which yields row 1 and -row 0 in exchanged
+// places; the pass leaves them exchanged and takes every later table entry and
+// store offset at the exchanged index, so no round branches per factor.  kappa and the q phases
 // join the per-bit phases (with the cross phases, applied in round 0 before
 // any rotation) and the p phases a 16-entry table of its round (applied after
 // the round's rotations).  Other factors run in general mode (complex 2x2
@@ -61,9 +64,8 @@ struct LayerArgs {
     uint32_t fmask;           // tile bits with a factor
     uint32_t pmask;           // tile bits with a per-tile phase applied as a multiply
     uint32_t rpmask;          // rotation mode: rounds with exit phases
-    uint32_t rform;           // rotation mode: tile bits 0..3 in the cotangent form
-    uint32_t rswap;           // rotation mode: tile bits 4..11 left exchanged (their place i holds
-                              // the amplitude of local index i ^ rswap)
+    uint32_t rswap;           // rotation mode: tile bits left exchanged (place j of the tile holds
+                              // the amplitude of tile-local index j ^ rswap after their rotations)
     int generate;             // write-only: every amplitude enters as 1 (nothing is read)
     int ncross, nout;
     int cstart[kLT + 1];      // cross gates of tile bit b: [cstart[b], cstart[b + 1])
@@ -124,29 +126,18 @@ __device__ __forceinline__ void butterfly(float2 (&v)[16], const float2* F) {
     }
 }
 
-// Scaled real rotation on local bit LB, both components of an amplitude in
-// one packed pair, one fma.rn.f32x2 per output:
-//   tangent form   (x0, x1) <- (x0 - t x1, x1 + t x0)
-//   cotangent form (x0, x1) <- (x1 - u x0, x0 + u x1)
+// Scaled real rotation in the tangent form on local bit LB, both components
+// of an amplitude in one packed pair, one fma.rn.f32x2 per output:
+// (x0, x1) <- (x0 - t x1, x1 + t x0); t = 0 is the identity.
 template <int LB>
-__device__ __forceinline__ void rotation(float2 (&v)[16], float coef, bool cot) {
+__device__ __forceinline__ void rotation(float2 (&v)[16], float coef) {
     const uint64_t t2 = pack2(coef, coef), nt2 = pack2(-coef, -coef);
-    if (!cot) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            if ((i >> LB) & 1) continue;
-            const uint64_t x0 = pack2(v[i].x, v[i].y), x1 = pack2(v[i | (1 << LB)].x, v[i | (1 << LB)].y);
-            v[i] = unpack2(fma2(nt2, x1, x0));
-            v[i | (1 << LB)] = unpack2(fma2(t2, x0, x1));
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            if ((i >> LB) & 1) continue;
-            const uint64_t x0 = pack2(v[i].x, v[i].y), x1 = pack2(v[i | (1 << LB)].x, v[i | (1 << LB)].y);
-            v[i] = unpack2(fma2(nt2, x0, x1));
-            v[i | (1 << LB)] = unpack2(fma2(t2, x1, x0));
-        }
+    for (int i = 0; i < 16; ++i) {
+        if ((i >> LB) & 1) continue;
+        const uint64_t x0 = pack2(v[i].x, v[i].y), x1 = pack2(v[i | (1 << LB)].x, v[i | (1 << LB)].y);
+        v[i] = unpack2(fma2(nt2, x1, x0));
+        v[i | (1 << LB)] = unpack2(fma2(t2, x0, x1));
     }
 }
 
@@ -195,19 +186,19 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
     }
     const uint32_t act = (a.fmask >> (4 * R)) & 15u;
     if constexpr (ROT) {
-        if constexpr (R == 0) {
-            const uint32_t cot = a.rform;
-            if (act & 1u) rotation<0>(v, rot[0].x, cot & 1u);
-            if (act & 2u) rotation<1>(v, rot[1].x, cot & 2u);
-            if (act & 4u) rotation<2>(v, rot[2].x, cot & 4u);
-            if (act & 8u) rotation<3>(v, rot[3].x, cot & 8u);
+        // rounds 1 and 2 (and a full round 0) run all four without branches
+        // (t = 0 on bits without a factor); round 0 often carries one factor
+        // only (on the lowest position above the run) and branches per bit
+        if (R > 0 || act == 15u) {
+            rotation<0>(v, rot[4 * R + 0].x);
+            rotation<1>(v, rot[4 * R + 1].x);
+            rotation<2>(v, rot[4 * R + 2].x);
+            rotation<3>(v, rot[4 * R + 3].x);
         } else {
-            // all four in the tangent form without branches (t = 0 on bits
-            // without a factor is the identity)
-            rotation<0>(v, rot[4 * R + 0].x, false);
-            rotation<1>(v, rot[4 * R + 1].x, false);
-            rotation<2>(v, rot[4 * R + 2].x, false);
-            rotation<3>(v, rot[4 * R + 3].x, false);
+            if (act & 1u) rotation<0>(v, rot[0].x);
+            if (act & 2u) rotation<1>(v, rot[1].x);
+            if (act & 4u) rotation<2>(v, rot[2].x);
+            if (act & 8u) rotation<3>(v, rot[3].x);
         }
         if (act && ((a.rpmask >> R) & 1u)) {
             // exit phases of the round's factor bits (they follow only their own rotations)
@@ -221,9 +212,10 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
         if (act & 8u) butterfly<3>(v, sh.tf[4 * R + 3]);
     }
     if (last) {
-        // global offset of (jb | x) = offset(jb) | offset(x); goff[R][i] holds offset(i << 4R)
-        // at the exchanged index, and round 2's jb carries round 1's exchanged bits
-        const uint64_t gb = layer_global(a, runoff, base, R == 2 ? jb ^ static_cast<int>(a.rswap & 0xf0u) : jb);
+        // global offset of (jb | x) = offset(jb) | offset(x) at the exchanged index:
+        // goff[R][i] holds offset((i ^ exchanged round bits) << 4R)
+        const uint64_t gb =
+            layer_global(a, runoff, base, jb ^ static_cast<int>(a.rswap & ~(15u << (4 * R)) & 0xfffu));
         if constexpr (R == 0) {
             // m >= 3: amplitudes jb | i and jb | (i + 1) are adjacent in HBM
 #pragma unroll
@@ -481,11 +473,17 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
             // 16-byte chunks by consecutive threads instead (coalesced stores)
             layer_round<ROT, 0>(a, st, din_s, sh, pr, rot, runoff, goff, base, false, phase);
             if (last == 0) {
+                // the amplitudes of tile-local j, j + 1 are in place (j ^ rswap),
+                // (j + 1) ^ rswap: chunk (j ^ rswap) / 2, halves exchanged if bit 0 is
                 __syncthreads();
+                const int sx = lsw((2 * threadIdx.x) ^ static_cast<int>(a.rswap & 14u));
+                const bool hx = a.rswap & 1u;
 #pragma unroll
-                for (int k = 0; k < kLAmps / 2 / kLThreads; ++k)
-                    __stcs(reinterpret_cast<float4*>(a.psi + (base | gld | goff[48 + k])),
-                           *reinterpret_cast<const float4*>(st + (sld ^ lsw(512 * k))));
+                for (int k = 0; k < kLAmps / 2 / kLThreads; ++k) {
+                    float4 c = *reinterpret_cast<const float4*>(st + (sx ^ lsw(512 * k)));
+                    if (hx) c = make_float4(c.z, c.w, c.x, c.y);
+                    __stcs(reinterpret_cast<float4*>(a.psi + (base | gld | goff[48 + k])), c);
+                }
             } else if (r1) {
                 __syncwarp();
             } else {
@@ -526,7 +524,6 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
     a.fmask = p.active;
     a.pmask = p.pmask;
     a.rpmask = p.rpmask;
-    a.rform = p.rform;
     a.rswap = p.rswap;
     a.generate = p.generate ? 1 : 0;
     a.ncross = p.ncross;

@@ -116,13 +116,12 @@ bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vec
         if ((p.active >> b) & 1u) p.rotation = split_rotation(fac[b], &rc[b], &rs[b], rp[b].data(), rq[b].data());
     // R = kappa M: tangent form (c >= s) M = [[1, -t], [t, 1]], kappa = c;
     // cotangent form M = [[u, -1], [1, u]], kappa = s, computed as (-row 0, row 1)
-    // with the sign moved into p0; kappa joins the entry phases q.  On tile bits
-    // 4..11 the cotangent form runs as the tangent form with t = -u, whose
-    // outputs are row 1 and -row 0 in exchanged places: the kernel leaves them
-    // there and the pass reads its later tables and store offsets at the
-    // exchanged index (rswap), so rounds 1 and 2 need no per-factor branches.
+    // with the sign moved into p0; kappa joins the entry phases q.  The kernel
+    // runs the cotangent form as the tangent form with t = -u, whose outputs
+    // are row 1 and -row 0 in exchanged places: it leaves them there and the
+    // pass reads its later tables and store offsets at the exchanged index
+    // (rswap), so the rounds need no per-factor branches.
     std::vector<double> rcoef(kTile, 0.0);
-    p.rform = 0;
     p.rswap = 0;
     if (p.rotation)
         for (int b = 0; b < kTile; ++b) {
@@ -132,12 +131,8 @@ bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vec
                 rcoef[b] = rc[b] / rs[b];
                 kappa = rs[b];
                 rp[b][0] = -rp[b][0];
-                if (b < 4) {
-                    p.rform |= 1u << b;
-                } else {
-                    rcoef[b] = -rcoef[b];
-                    p.rswap |= 1u << b;
-                }
+                rcoef[b] = -rcoef[b];
+                p.rswap |= 1u << b;
             } else {
                 rcoef[b] = rs[b] / rc[b];
                 kappa = rc[b];

@@ -113,8 +113,7 @@ struct LayerPayload {
     bool has_din = false;     // 2^12-entry table of the gates with every qubit in the tile
     bool rotation = false;    // factors as real rotations (their phases as per-bit and per-round tables)
     uint32_t rpmask = 0;      // rotation mode: rounds whose exit phases are not all 1
-    uint32_t rform = 0;       // rotation mode: tile bits 0..3 whose rotation uses the cotangent form
-    uint32_t rswap = 0;       // rotation mode: tile bits 4..11 whose halves the pass leaves exchanged
+    uint32_t rswap = 0;       // rotation mode: tile bits whose halves the pass leaves exchanged
     bool generate = false;    // write-only: the input is taken as 1 for every amplitude (not read)
     size_t off_fac = 0, off_cross = 0, off_out = 0, off_din = 0, off_qph = 0, off_rp = 0, bytes = 0;
 };
