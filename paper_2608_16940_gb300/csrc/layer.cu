@@ -141,11 +141,13 @@ __device__ __forceinline__ void rotation(float2 (&v)[16], float coef) {
     }
 }
 
+// Whether a pass has a diagonal table (DIN) and per-tile phases (PH): known
+// at compile time (1 present, 0 absent) or read at run time (2).
 // One round over tile bits 4R..4R+3: read the stage; (R = 0) multiply by the
 // entry table and the per-tile phases; apply the round's factors; (last
 // round, rotation mode) multiply by the exit table; write back to the stage
 // or (last round) to HBM.
-template <bool ROT, int R>
+template <bool ROT, int R, int DIN, int PH>
 __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, const float2* din_s,
                                             const LayerShared& sh, const LayerRec& pr,
                                             const float2* rot, const uint64_t* runoff, const uint64_t* goff,
@@ -166,7 +168,7 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
                 v[i + 1] = make_float2(p.z, p.w);
             }
         }
-        if (din_s) {
+        if (DIN == 1 || (DIN == 2 && din_s)) {
 #pragma unroll
             for (int i = 0; i < 16; i += 2) {
                 const float4 d = *reinterpret_cast<const float4*>(din_s + (sb ^ lsw(i)));
@@ -174,7 +176,7 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
                 v[i + 1] = cmulf(v[i + 1], make_float2(d.z, d.w));
             }
         }
-        if (phase) {
+        if (PH == 1 || (PH == 2 && phase)) {
             // phases of tile bits 4..11 (fixed for this thread) times those of the 16 local amplitudes
             const float2 ph = cmulf(pr.pa[(jb >> 4) & 15], pr.pb[(jb >> 8) & 15]);
 #pragma unroll
@@ -367,7 +369,7 @@ __global__ void __launch_bounds__(kLThreads) k_layer_records(LayerArgs a, LayerR
         tile_record(a, layer_base(a, t), dsh[threadIdx.x >> 5], recs + t);
 }
 
-template <bool ROT>
+template <bool ROT, int DIN, int PH>
 __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* stage = reinterpret_cast<float2*>(smem_raw);                        // kLStages x 4096
@@ -471,7 +473,7 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
             // round 0 always writes to the stage: its threads hold 16 consecutive
             // amplitudes, so when it is the last round the tile is copied out in
             // 16-byte chunks by consecutive threads instead (coalesced stores)
-            layer_round<ROT, 0>(a, st, din_s, sh, pr, rot, runoff, goff, base, false, phase);
+            layer_round<ROT, 0, DIN, PH>(a, st, din_s, sh, pr, rot, runoff, goff, base, false, phase);
             if (last == 0) {
                 // the amplitudes of tile-local j, j + 1 are in place (j ^ rswap),
                 // (j + 1) ^ rswap: chunk (j ^ rswap) / 2, halves exchanged if bit 0 is
@@ -491,10 +493,10 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
             }
         }
         if (first <= 1 && last >= 1 && r1) {
-            layer_round<ROT, 1>(a, st, din_s, sh, pr, rot, runoff, goff, base, last == 1, phase);
+            layer_round<ROT, 1, DIN, PH>(a, st, din_s, sh, pr, rot, runoff, goff, base, last == 1, phase);
             if (last > 1) __syncthreads();
         }
-        if (last == 2) layer_round<ROT, 2>(a, st, din_s, sh, pr, rot, runoff, goff, base, true, phase);
+        if (last == 2) layer_round<ROT, 2, DIN, PH>(a, st, din_s, sh, pr, rot, runoff, goff, base, true, phase);
         if (end_sync) __syncthreads();
         cur ^= 1;
     }
@@ -538,7 +540,8 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
     const size_t smem = layer_smem_bytes(p.has_din);
     static bool attr_set = false;
     if (!attr_set) {
-        for (auto kern : {k_apply_layer<true>, k_apply_layer<false>}) {
+        for (auto kern : {k_apply_layer<true, 0, 0>, k_apply_layer<true, 0, 1>, k_apply_layer<true, 1, 0>,
+                          k_apply_layer<true, 1, 1>, k_apply_layer<false, 2, 2>}) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  static_cast<int>(layer_smem_bytes(true)));
             if (e != cudaSuccess) return e;
@@ -554,7 +557,11 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
         k_layer_records<<<static_cast<unsigned>(nb), kLThreads, 0, st>>>(a, static_cast<LayerRec*>(d_rec));
         ++*launches;
     }
-    auto kern = p.rotation ? k_apply_layer<true> : k_apply_layer<false>;
+    // rotation mode: the diagonal table and the per-tile phases fixed at compile time
+    const bool ph = p.pmask != 0 || p.nout > 0;
+    auto kern = !p.rotation ? k_apply_layer<false, 2, 2>
+                : p.has_din ? (ph ? k_apply_layer<true, 1, 1> : k_apply_layer<true, 1, 0>)
+                            : (ph ? k_apply_layer<true, 0, 1> : k_apply_layer<true, 0, 0>);
     int occ = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kLThreads, smem);
     if (e != cudaSuccess) return e;
