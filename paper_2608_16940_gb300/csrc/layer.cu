@@ -141,13 +141,14 @@ __device__ __forceinline__ void rotation(float2 (&v)[16], float coef) {
     }
 }
 
-// Whether a pass has a diagonal table (DIN) and per-tile phases (PH): known
-// at compile time (1 present, 0 absent) or read at run time (2).
+// Whether a pass has a diagonal table (DIN), per-tile phases (PH) and exit
+// phases (RP): known at compile time (1 present, 0 absent) or read at run
+// time (2).
 // One round over tile bits 4R..4R+3: read the stage; (R = 0) multiply by the
 // entry table and the per-tile phases; apply the round's factors; (last
 // round, rotation mode) multiply by the exit table; write back to the stage
 // or (last round) to HBM.
-template <bool ROT, int R, int DIN, int PH>
+template <bool ROT, int R, int DIN, int PH, int RP>
 __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, const float2* din_s,
                                             const LayerShared& sh, const LayerRec& pr,
                                             const float2* rot, const uint64_t* runoff, const uint64_t* goff,
@@ -190,19 +191,22 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
     if constexpr (ROT) {
         // rounds 1 and 2 (and a full round 0) run all four without branches
         // (t = 0 on bits without a factor); round 0 often carries one factor
-        // only (on the lowest position above the run) and branches per bit
+        // only, on tile bit 3 (the lowest position above the run), and
+        // otherwise branches per bit
         if (R > 0 || act == 15u) {
             rotation<0>(v, rot[4 * R + 0].x);
             rotation<1>(v, rot[4 * R + 1].x);
             rotation<2>(v, rot[4 * R + 2].x);
             rotation<3>(v, rot[4 * R + 3].x);
+        } else if (act == 8u) {
+            rotation<3>(v, rot[3].x);
         } else {
             if (act & 1u) rotation<0>(v, rot[0].x);
             if (act & 2u) rotation<1>(v, rot[1].x);
             if (act & 4u) rotation<2>(v, rot[2].x);
             if (act & 8u) rotation<3>(v, rot[3].x);
         }
-        if (act && ((a.rpmask >> R) & 1u)) {
+        if (RP != 0 && act && ((a.rpmask >> R) & 1u)) {
             // exit phases of the round's factor bits (they follow only their own rotations)
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = cmulf(v[i], sh.rp[R][i]);
@@ -369,7 +373,7 @@ __global__ void __launch_bounds__(kLThreads) k_layer_records(LayerArgs a, LayerR
         tile_record(a, layer_base(a, t), dsh[threadIdx.x >> 5], recs + t);
 }
 
-template <bool ROT, int DIN, int PH>
+template <bool ROT, int DIN, int PH, int RP>
 __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* stage = reinterpret_cast<float2*>(smem_raw);                        // kLStages x 4096
@@ -473,7 +477,7 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
             // round 0 always writes to the stage: its threads hold 16 consecutive
             // amplitudes, so when it is the last round the tile is copied out in
             // 16-byte chunks by consecutive threads instead (coalesced stores)
-            layer_round<ROT, 0, DIN, PH>(a, st, din_s, sh, pr, rot, runoff, goff, base, false, phase);
+            layer_round<ROT, 0, DIN, PH, RP>(a, st, din_s, sh, pr, rot, runoff, goff, base, false, phase);
             if (last == 0) {
                 // the amplitudes of tile-local j, j + 1 are in place (j ^ rswap),
                 // (j + 1) ^ rswap: chunk (j ^ rswap) / 2, halves exchanged if bit 0 is
@@ -493,10 +497,10 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
             }
         }
         if (first <= 1 && last >= 1 && r1) {
-            layer_round<ROT, 1, DIN, PH>(a, st, din_s, sh, pr, rot, runoff, goff, base, last == 1, phase);
+            layer_round<ROT, 1, DIN, PH, RP>(a, st, din_s, sh, pr, rot, runoff, goff, base, last == 1, phase);
             if (last > 1) __syncthreads();
         }
-        if (last == 2) layer_round<ROT, 2, DIN, PH>(a, st, din_s, sh, pr, rot, runoff, goff, base, true, phase);
+        if (last == 2) layer_round<ROT, 2, DIN, PH, RP>(a, st, din_s, sh, pr, rot, runoff, goff, base, true, phase);
         if (end_sync) __syncthreads();
         cur ^= 1;
     }
@@ -540,8 +544,9 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
     const size_t smem = layer_smem_bytes(p.has_din);
     static bool attr_set = false;
     if (!attr_set) {
-        for (auto kern : {k_apply_layer<true, 0, 0>, k_apply_layer<true, 0, 1>, k_apply_layer<true, 1, 0>,
-                          k_apply_layer<true, 1, 1>, k_apply_layer<false, 2, 2>}) {
+        for (auto kern : {k_apply_layer<true, 0, 0, 0>, k_apply_layer<true, 0, 1, 0>, k_apply_layer<true, 1, 0, 0>,
+                          k_apply_layer<true, 1, 1, 0>, k_apply_layer<true, 0, 0, 2>, k_apply_layer<true, 0, 1, 2>,
+                          k_apply_layer<true, 1, 0, 2>, k_apply_layer<true, 1, 1, 2>, k_apply_layer<false, 2, 2, 2>}) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  static_cast<int>(layer_smem_bytes(true)));
             if (e != cudaSuccess) return e;
@@ -559,9 +564,12 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
     }
     // rotation mode: the diagonal table and the per-tile phases fixed at compile time
     const bool ph = p.pmask != 0 || p.nout > 0;
-    auto kern = !p.rotation ? k_apply_layer<false, 2, 2>
-                : p.has_din ? (ph ? k_apply_layer<true, 1, 1> : k_apply_layer<true, 1, 0>)
-                            : (ph ? k_apply_layer<true, 0, 1> : k_apply_layer<true, 0, 0>);
+    auto kern = !p.rotation ? k_apply_layer<false, 2, 2, 2>
+                : p.rpmask == 0
+                    ? (p.has_din ? (ph ? k_apply_layer<true, 1, 1, 0> : k_apply_layer<true, 1, 0, 0>)
+                                 : (ph ? k_apply_layer<true, 0, 1, 0> : k_apply_layer<true, 0, 0, 0>))
+                    : (p.has_din ? (ph ? k_apply_layer<true, 1, 1, 2> : k_apply_layer<true, 1, 0, 2>)
+                                 : (ph ? k_apply_layer<true, 0, 1, 2> : k_apply_layer<true, 0, 0, 2>));
     int occ = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kLThreads, smem);
     if (e != cudaSuccess) return e;
