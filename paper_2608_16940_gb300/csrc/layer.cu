@@ -142,23 +142,24 @@ __device__ __forceinline__ void rotation(float2 (&v)[16], float coef) {
 }
 
 // Whether a pass has a diagonal table (DIN), per-tile phases (PH) and exit
-// phases (RP): known at compile time (1 present, 0 absent) or read at run
-// time (2).
+// phases (RP), and whether it generates its input (GEN): known at compile
+// time (1 present, 0 absent) or read at run time (2); LAST: the round stores
+// to HBM.
 // One round over tile bits 4R..4R+3: read the stage; (R = 0) multiply by the
 // entry table and the per-tile phases; apply the round's factors; (last
 // round, rotation mode) multiply by the exit table; write back to the stage
 // or (last round) to HBM.
-template <bool ROT, int R, int DIN, int PH, int RP>
+template <bool ROT, int R, int DIN, int PH, int RP, int GEN, bool LAST>
 __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, const float2* din_s,
                                             const LayerShared& sh, const LayerRec& pr,
                                             const float2* rot, const uint64_t* runoff, const uint64_t* goff,
-                                            uint64_t base, bool last, bool phase) {
+                                            uint64_t base, bool phase) {
     const int t = threadIdx.x;
     const int jb = (t & ((1 << (4 * R)) - 1)) | ((t >> (4 * R)) << (4 * R + 4));
     const int sb = lsw(jb);   // slot of (jb | x) = sb ^ lsw(x)
     float2 v[16];
     if constexpr (R == 0) {
-        if (a.generate) {
+        if (GEN == 1 || (GEN == 2 && a.generate)) {
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = make_float2(1.f, 0.f);
         } else {
@@ -217,21 +218,15 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
         if (act & 4u) butterfly<2>(v, sh.tf[4 * R + 2]);
         if (act & 8u) butterfly<3>(v, sh.tf[4 * R + 3]);
     }
-    if (last) {
+    if constexpr (LAST) {
         // global offset of (jb | x) = offset(jb) | offset(x) at the exchanged index:
         // goff[R][i] holds offset((i ^ exchanged round bits) << 4R)
         const uint64_t gb =
             layer_global(a, runoff, base, jb ^ static_cast<int>(a.rswap & ~(15u << (4 * R)) & 0xfffu));
-        if constexpr (R == 0) {
-            // m >= 3: amplitudes jb | i and jb | (i + 1) are adjacent in HBM
+        // (round 0 never stores: as the last round it goes through the stage)
+        static_assert(R > 0, "round 0 writes to the stage");
 #pragma unroll
-            for (int i = 0; i < 16; i += 2)
-                __stcs(reinterpret_cast<float4*>(a.psi + (gb | goff[i])),
-                       make_float4(v[i].x, v[i].y, v[i + 1].x, v[i + 1].y));
-        } else {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) __stcs(a.psi + (gb | goff[16 * R + i]), v[i]);
-        }
+        for (int i = 0; i < 16; ++i) __stcs(a.psi + (gb | goff[16 * R + i]), v[i]);
     } else {
         if constexpr (R == 0) {
 #pragma unroll
@@ -373,7 +368,7 @@ __global__ void __launch_bounds__(kLThreads) k_layer_records(LayerArgs a, LayerR
         tile_record(a, layer_base(a, t), dsh[threadIdx.x >> 5], recs + t);
 }
 
-template <bool ROT, int DIN, int PH, int RP>
+template <bool ROT, int DIN, int PH, int RP, int GEN>
 __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* stage = reinterpret_cast<float2*>(smem_raw);                        // kLStages x 4096
@@ -444,7 +439,7 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
     auto load = [&](uint64_t t, int sidx) {
         const uint64_t base = tile_base(t) | gld;
         float2* st = stage + sidx * kLAmps;
-        if (!a.generate)
+        if (GEN == 0 || (GEN == 2 && !a.generate))
 #pragma unroll
             for (int k = 0; k < kLAmps / 2 / kLThreads; ++k)
                 cp_async16(st + (sld ^ lsw(512 * k)), a.psi + (base | goff[48 + k]));
@@ -477,7 +472,7 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
             // round 0 always writes to the stage: its threads hold 16 consecutive
             // amplitudes, so when it is the last round the tile is copied out in
             // 16-byte chunks by consecutive threads instead (coalesced stores)
-            layer_round<ROT, 0, DIN, PH, RP>(a, st, din_s, sh, pr, rot, runoff, goff, base, false, phase);
+            layer_round<ROT, 0, DIN, PH, RP, GEN, false>(a, st, din_s, sh, pr, rot, runoff, goff, base, phase);
             if (last == 0) {
                 // the amplitudes of tile-local j, j + 1 are in place (j ^ rswap),
                 // (j + 1) ^ rswap: chunk (j ^ rswap) / 2, halves exchanged if bit 0 is
@@ -497,10 +492,13 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
             }
         }
         if (first <= 1 && last >= 1 && r1) {
-            layer_round<ROT, 1, DIN, PH, RP>(a, st, din_s, sh, pr, rot, runoff, goff, base, last == 1, phase);
+            if (last == 1)
+                layer_round<ROT, 1, DIN, PH, RP, GEN, true>(a, st, din_s, sh, pr, rot, runoff, goff, base, phase);
+            else
+                layer_round<ROT, 1, DIN, PH, RP, GEN, false>(a, st, din_s, sh, pr, rot, runoff, goff, base, phase);
             if (last > 1) __syncthreads();
         }
-        if (last == 2) layer_round<ROT, 2, DIN, PH, RP>(a, st, din_s, sh, pr, rot, runoff, goff, base, true, phase);
+        if (last == 2) layer_round<ROT, 2, DIN, PH, RP, GEN, true>(a, st, din_s, sh, pr, rot, runoff, goff, base, phase);
         if (end_sync) __syncthreads();
         cur ^= 1;
     }
@@ -544,9 +542,10 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
     const size_t smem = layer_smem_bytes(p.has_din);
     static bool attr_set = false;
     if (!attr_set) {
-        for (auto kern : {k_apply_layer<true, 0, 0, 0>, k_apply_layer<true, 0, 1, 0>, k_apply_layer<true, 1, 0, 0>,
-                          k_apply_layer<true, 1, 1, 0>, k_apply_layer<true, 0, 0, 2>, k_apply_layer<true, 0, 1, 2>,
-                          k_apply_layer<true, 1, 0, 2>, k_apply_layer<true, 1, 1, 2>, k_apply_layer<false, 2, 2, 2>}) {
+        for (auto kern : {k_apply_layer<true, 0, 0, 0, 0>, k_apply_layer<true, 0, 1, 0, 0>, k_apply_layer<true, 1, 0, 0, 0>,
+                          k_apply_layer<true, 1, 1, 0, 0>, k_apply_layer<true, 0, 0, 2, 0>, k_apply_layer<true, 0, 1, 2, 0>,
+                          k_apply_layer<true, 1, 0, 2, 0>, k_apply_layer<true, 1, 1, 2, 0>, k_apply_layer<true, 2, 2, 2, 1>,
+                          k_apply_layer<false, 2, 2, 2, 2>}) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  static_cast<int>(layer_smem_bytes(true)));
             if (e != cudaSuccess) return e;
@@ -564,12 +563,13 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
     }
     // rotation mode: the diagonal table and the per-tile phases fixed at compile time
     const bool ph = p.pmask != 0 || p.nout > 0;
-    auto kern = !p.rotation ? k_apply_layer<false, 2, 2, 2>
+    auto kern = !p.rotation ? k_apply_layer<false, 2, 2, 2, 2>
+                : p.generate ? k_apply_layer<true, 2, 2, 2, 1>
                 : p.rpmask == 0
-                    ? (p.has_din ? (ph ? k_apply_layer<true, 1, 1, 0> : k_apply_layer<true, 1, 0, 0>)
-                                 : (ph ? k_apply_layer<true, 0, 1, 0> : k_apply_layer<true, 0, 0, 0>))
-                    : (p.has_din ? (ph ? k_apply_layer<true, 1, 1, 2> : k_apply_layer<true, 1, 0, 2>)
-                                 : (ph ? k_apply_layer<true, 0, 1, 2> : k_apply_layer<true, 0, 0, 2>));
+                    ? (p.has_din ? (ph ? k_apply_layer<true, 1, 1, 0, 0> : k_apply_layer<true, 1, 0, 0, 0>)
+                                 : (ph ? k_apply_layer<true, 0, 1, 0, 0> : k_apply_layer<true, 0, 0, 0, 0>))
+                    : (p.has_din ? (ph ? k_apply_layer<true, 1, 1, 2, 0> : k_apply_layer<true, 1, 0, 2, 0>)
+                                 : (ph ? k_apply_layer<true, 0, 1, 2, 0> : k_apply_layer<true, 0, 0, 2, 0>));
     int occ = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kLThreads, smem);
     if (e != cudaSuccess) return e;
