@@ -758,23 +758,18 @@ cudaError_t launch_sample_z(const float2* psi, int n, const int32_t* layout_host
         ZMasks zm{};
         zm.n = nmasks;
         for (int m = 0; m < nmasks; ++m) zm.m[m] = physmasks[m];
-        // at most reduce_partials() CTAs (the partials' size), two resident per SM
+        auto kern = nmasks == 0 ? k_weights_z1024<0> : nmasks == 1 ? k_weights_z1024<1>
+                  : nmasks == 2 ? k_weights_z1024<2> : nmasks == 3 ? k_weights_z1024<3> : k_weights_z1024<4>;
+        // as many CTAs as stay resident (at most reduce_partials(), the partials' size)
+        int occ = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kRedThreads, 0);
+        if (e != cudaSuccess) return e;
+        occ = occ < 1 ? 1 : (occ > kRedBlocksPerSM ? kRedBlocksPerSM : occ);
         uint64_t nb = (nblocks + wpb - 1) / wpb;
-        const uint64_t cap = static_cast<uint64_t>(num_sms()) * 2;
+        const uint64_t cap = static_cast<uint64_t>(num_sms()) * occ;
         if (nb > cap) nb = cap;
-        const auto* psi2 = reinterpret_cast<const float4*>(psi);
-        switch (nmasks) {
-            case 0: k_weights_z1024<0><<<static_cast<unsigned>(nb), kRedThreads, 0, st>>>(psi2, nblocks, cum, zm,
-                                                                                          d_zpartials); break;
-            case 1: k_weights_z1024<1><<<static_cast<unsigned>(nb), kRedThreads, 0, st>>>(psi2, nblocks, cum, zm,
-                                                                                          d_zpartials); break;
-            case 2: k_weights_z1024<2><<<static_cast<unsigned>(nb), kRedThreads, 0, st>>>(psi2, nblocks, cum, zm,
-                                                                                          d_zpartials); break;
-            case 3: k_weights_z1024<3><<<static_cast<unsigned>(nb), kRedThreads, 0, st>>>(psi2, nblocks, cum, zm,
-                                                                                          d_zpartials); break;
-            default: k_weights_z1024<4><<<static_cast<unsigned>(nb), kRedThreads, 0, st>>>(psi2, nblocks, cum, zm,
-                                                                                           d_zpartials); break;
-        }
+        kern<<<static_cast<unsigned>(nb), kRedThreads, 0, st>>>(reinterpret_cast<const float4*>(psi), nblocks, cum,
+                                                                 zm, d_zpartials);
         for (int m = 0; m < nmasks; ++m)
             k_finalize_sum<<<1, 1024, 0, st>>>(d_zpartials + m * nb, static_cast<int>(nb), d_zout + m);
         *launches += nmasks;
