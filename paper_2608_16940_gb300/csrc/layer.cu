@@ -32,6 +32,7 @@
 // differ in the round's bits); the last active round stores to HBM.
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstdint>
 
 #include "qsa_device.cuh"
@@ -55,6 +56,8 @@ struct LayerRec {
     float2 pl[16];            // bits 0..3 of round 0's local index, times the scalar
     float2 pa[16], pb[16];    // products over tile bits 4..7 and 8..11 (fixed per thread in round 0)
 };
+static_assert(sizeof(LayerRec) == 48 * sizeof(float2) && offsetof(LayerRec, pa) == 16 * sizeof(float2),
+              "the records kernel writes pl and pa as one 32-entry array");
 
 struct LayerArgs {
     float2* psi;
@@ -308,64 +311,65 @@ __device__ __forceinline__ void tile_phases(const LayerArgs& a, uint64_t base, L
     phase_tables(a.pmask, d0, d1, sc, &sh.ph);
 }
 
-// Rotation mode: the per-tile phases of one tile into *out (one warp): the
-// scalar of the out gates (lanes over gates, product across lanes); each
-// pmask bit's cross phases times its rotation's entry phases (lane b, into
-// the warp's scratch dsh); then lane l < 16 forms entry l of the three tables.
-__device__ __forceinline__ void tile_record(const LayerArgs& a, uint64_t base, float2 (*dsh)[2], LayerRec* out) {
-    const int lane = threadIdx.x & 31;
-    float2 sc = make_float2(1.f, 0.f);
-    for (int g = lane; g < a.nout; g += 32) {
-        const LayerGate& G = a.outg[g];
-        int v = static_cast<int>((base >> G.a) & 1ull);
-        if (G.b >= 0) v |= static_cast<int>((base >> G.b) & 1ull) << 1;
-        sc = cmulf(sc, G.d[v]);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        float2 other;
-        other.x = __shfl_xor_sync(0xffffffffu, sc.x, o);
-        other.y = __shfl_xor_sync(0xffffffffu, sc.y, o);
-        sc = cmulf(sc, other);
-    }
-    float2 d0 = make_float2(1.f, 0.f), d1 = make_float2(1.f, 0.f);
-    if (lane < kLT && ((a.pmask >> lane) & 1u)) {
-        for (int g = a.cstart[lane]; g < a.cstart[lane + 1]; ++g) {
-            const LayerGate& G = a.cross[g];
-            const int o = static_cast<int>((base >> G.b) & 1ull);
-            d0 = cmulf(d0, G.d[2 * o]);
-            d1 = cmulf(d1, G.d[2 * o + 1]);
-        }
-    }
-    if (lane < kLT) {
-        // the bit's entry phases of its rotation (identity without a factor)
-        dsh[lane][0] = (a.pmask >> lane) & 1u ? cmulf(d0, a.qph[2 * lane]) : make_float2(1.f, 0.f);
-        dsh[lane][1] = (a.pmask >> lane) & 1u ? cmulf(d1, a.qph[2 * lane + 1]) : make_float2(1.f, 0.f);
-    }
-    __syncwarp();
-    if (lane < 16) {
-        float2 pl = sc, pa = make_float2(1.f, 0.f), pb = make_float2(1.f, 0.f);
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int v = (lane >> b) & 1;
-            pl = cmulf(pl, dsh[b][v]);
-            pa = cmulf(pa, dsh[4 + b][v]);
-            pb = cmulf(pb, dsh[8 + b][v]);
-        }
-        out->pl[lane] = pl;
-        out->pa[lane] = pa;
-        out->pb[lane] = pb;
-    }
-    __syncwarp();
-}
-
-// One warp per tile: the records of a rotation-mode pass with per-tile phases.
-__global__ void __launch_bounds__(kLThreads) k_layer_records(LayerArgs a, LayerRec* recs) {
-    __shared__ float2 dsh[kLThreads / 32][kLT][2];
+// Rotation mode, one warp per 32 consecutive tiles: lane j forms tile t0 + j's
+// scalar of the out gates and each pmask bit's cross phases times its
+// rotation's entry phases (every tile reads the same gates, so their loads
+// are broadcasts and the lanes do not diverge), into shared memory; then,
+// tile by tile, lane l forms entry l of the record's pl and pa tables and
+// lanes 0..15 entry l of pb, so each record is written by consecutive lanes.
+constexpr int kRecThreads = 128;
+__global__ void __launch_bounds__(kRecThreads) k_layer_records(LayerArgs a, LayerRec* recs) {
+    __shared__ float2 ph[kRecThreads / 32][2 * kLT + 1][32];   // [bit phase (2 b + v) | scalar][tile]
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x >> 5);
-    for (uint64_t t = blockIdx.x * static_cast<uint64_t>(blockDim.x >> 5) + (threadIdx.x >> 5); t < a.ntiles;
-         t += warps)
-        tile_record(a, layer_base(a, t), dsh[threadIdx.x >> 5], recs + t);
+    for (uint64_t t0 = (static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + w) * 32; t0 < a.ntiles;
+         t0 += warps * 32) {
+        const uint64_t t = t0 + lane;
+        if (t < a.ntiles) {
+            const uint64_t base = layer_base(a, t);
+            float2 sc = make_float2(1.f, 0.f);
+            for (int g = 0; g < a.nout; ++g) {
+                const LayerGate& G = a.outg[g];
+                int v = static_cast<int>((base >> G.a) & 1ull);
+                if (G.b >= 0) v |= static_cast<int>((base >> G.b) & 1ull) << 1;
+                sc = cmulf(sc, G.d[v]);
+            }
+            ph[w][2 * kLT][lane] = sc;
+#pragma unroll
+            for (int b = 0; b < kLT; ++b) {
+                float2 d0 = make_float2(1.f, 0.f), d1 = make_float2(1.f, 0.f);
+                if ((a.pmask >> b) & 1u) {
+                    for (int g = a.cstart[b]; g < a.cstart[b + 1]; ++g) {
+                        const LayerGate& G = a.cross[g];
+                        const int o = static_cast<int>((base >> G.b) & 1ull);
+                        d0 = cmulf(d0, G.d[2 * o]);
+                        d1 = cmulf(d1, G.d[2 * o + 1]);
+                    }
+                    d0 = cmulf(d0, a.qph[2 * b]);
+                    d1 = cmulf(d1, a.qph[2 * b + 1]);
+                }
+                ph[w][2 * b][lane] = d0;
+                ph[w][2 * b + 1][lane] = d1;
+            }
+        }
+        __syncwarp();
+        const uint64_t left = a.ntiles - t0;
+        const int nt = left < 32 ? static_cast<int>(left) : 32;
+        const int i = lane & 15, r = lane >> 4;   // lanes 0..15: pl[i], lanes 16..31: pa[i]
+        for (int j = 0; j < nt; ++j) {
+            float2 x = r == 0 ? ph[w][2 * kLT][j] : make_float2(1.f, 0.f);
+            float2 y = make_float2(1.f, 0.f);
+#pragma unroll
+            for (int lb = 0; lb < 4; ++lb) {
+                x = cmulf(x, ph[w][2 * (4 * r + lb) + ((i >> lb) & 1)][j]);
+                y = cmulf(y, ph[w][2 * (8 + lb) + ((i >> lb) & 1)][j]);
+            }
+            LayerRec* out = recs + t0 + j;
+            reinterpret_cast<float2*>(out->pl)[lane] = x;   // pl[0..15], then pa[0..15]
+            if (lane < 16) out->pb[i] = y;
+        }
+        __syncwarp();
+    }
 }
 
 template <bool ROT, int DIN, int PH, int RP, int GEN>
@@ -555,10 +559,11 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
     if (p.rotation && (p.ncross > 0 || p.nout > 0)) {
         if (!d_rec) return cudaErrorInvalidValue;
         a.rec = static_cast<const LayerRec*>(d_rec);
-        uint64_t nb = (a.ntiles + kLThreads / 32 - 1) / (kLThreads / 32);
-        const uint64_t cap = static_cast<uint64_t>(num_sms()) * 8;
+        // 32 tiles per warp
+        uint64_t nb = (a.ntiles + kRecThreads - 1) / kRecThreads;
+        const uint64_t cap = static_cast<uint64_t>(num_sms()) * 16;
         if (nb > cap) nb = cap;
-        k_layer_records<<<static_cast<unsigned>(nb), kLThreads, 0, st>>>(a, static_cast<LayerRec*>(d_rec));
+        k_layer_records<<<static_cast<unsigned>(nb), kRecThreads, 0, st>>>(a, static_cast<LayerRec*>(d_rec));
         ++*launches;
     }
     // rotation mode: the diagonal table and the per-tile phases fixed at compile time
