@@ -164,7 +164,7 @@ typedef struct {
     uint64_t prod_blocks;   /* product blocks (one-qubit factors) applied */
     double prod_seconds;    /* device time of product kernels */
     uint64_t layer_blocks;  /* layer blocks applied */
-    double layer_seconds;   /* device time of layer kernels */
+    double layer_seconds;   /* device time of layer passes (their per-tile record kernels excluded) */
 } qsa_run_stats;
 
 /* A compiled circuit: the planner's blocks with their fused FP32 matrices. */

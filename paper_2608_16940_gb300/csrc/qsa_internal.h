@@ -121,6 +121,8 @@ size_t layer_smem_bytes(bool with_din);
 // Rotation-mode passes with per-tile phases first write one record per tile
 // to d_rec (device, layer_record_bytes(n) bytes; the call fails without it).
 size_t layer_record_bytes(int n);
+cudaError_t launch_layer_records(float2* psi, int n, const LayerGeom& g, const unsigned char* d_payload,
+                                 const LayerPayload& p, void* d_rec, cudaStream_t st, uint64_t* launches);
 cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const unsigned char* d_payload,
                                const LayerPayload& p, void* d_rec, cudaStream_t st, uint64_t* launches);
 
