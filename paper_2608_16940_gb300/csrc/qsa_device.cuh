@@ -54,8 +54,12 @@ __device__ __forceinline__ uint64_t sq_fixed60(float v) {
     const int E = static_cast<int>(e8 ? e8 : 1u) - 150;
     const uint64_t sq = static_cast<uint64_t>(M) * M;
     const int s = 2 * E + 60;
-    if (s >= 0) return s < 16 ? (sq << s) : (1ull << 62);
-    return (-s) >= 64 ? 0ull : (sq >> (-s));
+    // without branches: one of the two shifts is 0; a right shift by 63 leaves
+    // 0 (sq < 2^48) like any larger one; |v| >= 2 (s >= 16) saturates at 2^62
+    const uint32_t ls = static_cast<uint32_t>(min(max(s, 0), 15));
+    const uint32_t rs = static_cast<uint32_t>(min(max(-s, 0), 63));
+    const uint64_t r = (sq << ls) >> rs;
+    return s >= 16 ? (1ull << 62) : r;
 }
 
 // Sampling weight of one amplitude: floor(re^2 2^60) + floor(im^2 2^60).
