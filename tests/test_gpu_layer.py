@@ -69,6 +69,34 @@ def test_layer_matches_oracle(q, n, k, n_diag, seed, permuted):
     _run(q, n, _diag_ops(n, n_diag, rng, unit=seed % 2 == 0), t, fac, layout if permuted else None, seed)
 
 
+_X = np.array([[0, 1], [1, 0]], dtype=complex)
+_Y = np.array([[0, -1j], [1j, 0]], dtype=complex)
+_S = np.diag([1, 1j])
+_RX = np.array([[1, -1j], [-1j, 1]], dtype=complex) / np.sqrt(2)   # |F00| = |F01|
+_SXY = _X @ np.diag([np.exp(0.3j), np.exp(-1.1j)])                 # F00 = 0, F01 = phase
+
+
+@pytest.mark.parametrize("n,targets", [(12, [0, 1, 2, 3]), (14, [0, 1, 2, 3]), (14, [0, 4, 5, 7]),
+                                       (16, [1, 3, 6, 9, 10, 11]), (18, [0, 1, 2, 12, 13, 14, 15, 16, 17]),
+                                       (20, [2, 4, 8, 11, 15, 19])],
+                         ids=["n12-round0", "n14-round0", "n14-rounds01", "n16-rounds012", "n18-high",
+                              "n20-spread"])
+def test_layer_rotation_forms(q, n, targets):
+    """Factors at the boundaries of the rotation forms on every round: cotangent
+    form with u = 0 (X, Y, X times phases: halves exchanged, stored back through
+    the exchanged index, including round 0 as the last round where a 16-byte
+    chunk's two halves trade places), |c| = |s| (tangent form, t = 1), s = 0
+    (phases only, t = 0) and Haar factors; with and without diagonal gates."""
+    rng = np.random.default_rng(n + len(targets))
+    kinds = [_X, _Y, _SXY, _RX, _S, W.H]
+    fac = [kinds[j % len(kinds)] if j < len(kinds) else W.haar_unitary(2, rng) for j in range(len(targets))]
+    fac = fac[len(targets) % 3:] + fac[:len(targets) % 3]
+    _run(q, n, [], targets, fac, seed=n)
+    _run(q, n, _diag_ops(n, 3 * n, rng), targets, fac, seed=n + 1)
+    # every factor in the cotangent form with u = 0
+    _run(q, n, _diag_ops(n, n, rng), targets, [_X for _ in targets], seed=n + 2)
+
+
 def test_layer_diagonal_only_and_factors_only(q):
     rng = np.random.default_rng(10)
     _run(q, 14, _diag_ops(14, 50, rng), [], [])
