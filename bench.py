@@ -27,6 +27,7 @@ Tr(rho Z_0 Z_14)).  Its metric counts 4^n amplitude updates per channel.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -66,9 +67,11 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms; started
+    before the warm-up so that it is running when the timed region begins, and
+    read back for the samples stamped inside that region."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -80,11 +83,13 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
+        """Median SM clock, maximum clock and throttle reasons of the samples
+        stamped in [t0, t1] (wall-clock seconds; all samples if none are)."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -93,22 +98,28 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in out.splitlines():
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            try:
+                rows.append((ts, float(parts[2]), float(parts[3]),
+                             [nm for nm, v in zip(names, parts[6:10]) if v.lower() == "active"]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
+        inside = [r for r in rows if t0 is not None and r[0] is not None and t0 <= r[0] <= t1]
+        use = inside or rows
+        sm = [r[1] for r in use]
+        mx = [r[2] for r in use]
+        reasons = sorted({nm for r in use for nm in r[3]})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": reasons, "samples": len(sm), "window": "timed region" if inside else "whole run"}
 
 
 def _dist():
@@ -239,7 +250,7 @@ def train_cost_model(q, s, precision, seed, n_samples):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="qaoa", choices=["qaoa", "dm_ghz"])
@@ -339,26 +350,28 @@ def main():
                 agg[k] += st[k]
         return norm, zz, nshot
 
+    clk = ClockSampler(local)
+    clk.start()
     for _ in range(args.warmup):
         step(False)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
-    clk = ClockSampler(local)
-    clk.start()
     l0 = q.qsa_state_counters(s)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("qsa_timed")
+    t_wall0 = time.time()
     ev0.record()
     for _ in range(args.steps):
         norm, zz, nshot = step(True)
     ev1.record()
     torch.cuda.synchronize()
+    t_wall1 = time.time()
     torch.cuda.nvtx.range_pop()
     launches = q.qsa_state_counters(s) - l0
-    clocks = clk.stop()
+    clocks = clk.stop(t_wall0, t_wall1)
     elapsed = job_seconds(ev0.elapsed_time(ev1) * 1e-3, ws, dev)
     per_step = elapsed / args.steps
     amp_updates = len(ops) * float(1 << n)
