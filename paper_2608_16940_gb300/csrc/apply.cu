@@ -215,7 +215,7 @@ struct ApplyCfg;
 template <> struct ApplyCfg<1> { static constexpr int T = 11, R = 2, S = 3; };
 template <> struct ApplyCfg<2> { static constexpr int T = 11, R = 4, S = 3; };
 template <> struct ApplyCfg<3> { static constexpr int T = 11, R = 8, S = 3; };
-template <> struct ApplyCfg<4> { static constexpr int T = 11, R = 8, S = 3; };
+template <> struct ApplyCfg<4> { static constexpr int T = 11, R = 16, S = 3; };
 template <> struct ApplyCfg<5> { static constexpr int T = 12, R = 8, S = 2; };
 template <> struct ApplyCfg<6> { static constexpr int T = 12, R = 8, S = 2; };
 
