@@ -20,16 +20,20 @@
 // M = [[u, -1], [1, u]], u = c / s, whose first row is negated into p), so a
 // factor costs one packed multiply-add per amplitude.  The cotangent form runs
 // as the tangent form with t = -u, which yields row 1 and -row 0 in exchanged
-// places; the pass leaves them exchanged and takes every later table entry and
-// store offset at the exchanged index, so no round branches per factor.  kappa and the q phases
-// join the per-bit phases (with the cross phases, applied in round 0 before
-// any rotation) and the p phases a 16-entry table of its round (applied after
-// the round's rotations).  Other factors run in general mode (complex 2x2
-// butterflies, cross phases folded into them).
+// places; the pass leaves them exchanged and takes every later table entry
+// and store offset at the exchanged index, so no round branches per factor.
+// kappa and the q phases join the per-bit phases (with the cross phases,
+// applied in round 0 before any rotation) and the p phases a 16-entry table
+// of its round (applied after the round's rotations).  Other factors run in
+// general mode (complex 2x2 butterflies, cross phases folded into them).
 // Per tile: 16-byte cp.async copies into a 2-stage ring (XOR-swizzled 16-byte
-// chunks); warp 0 forms the tile's phases; then three register rounds over
-// tile bits 0-3, 4-7 and 8-11 (each thread holds the 16 amplitudes that
-// differ in the round's bits); the last active round stores to HBM.
+// chunks), with the tile's per-tile phase record (rotation mode: written by
+// k_layer_records before the pass; general mode: formed by warp 0); then
+// three register rounds over tile bits 0-3, 4-7 and 8-11 (each thread holds
+// the 16 amplitudes that differ in the round's bits); the last active round
+// stores to HBM.  Whether the pass has a diagonal table, per-tile phases,
+// exit phases or a generated input is a template argument, so the rounds are
+// straight-line code.
 #include <cuda_runtime.h>
 
 #include <cstddef>
