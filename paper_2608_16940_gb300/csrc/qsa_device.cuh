@@ -45,21 +45,19 @@ __device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
     return d;
 }
 
-// floor(v^2 * 2^60) exactly, in integers: v = M * 2^E with a 24-bit M, so
-// v^2 2^60 = M^2 2^(2E+60).  Valid for |v| < 2.
+// floor(v^2 * 2^60) exactly, in integers: v = M * 2^(E - 150) with a 24-bit M
+// (E = max(biased exponent, 1)), so v^2 2^60 = M^2 2^(2E - 240).  One 32 x 32
+// -> 64-bit product forms M^2 2^15 = (M 2^8)(M 2^7) < 2^63, and one right
+// shift by 255 - 2E (>= 1 for |v| < 2; from 63 on it leaves 0, like any
+// larger shift) takes it to the scale; |v| >= 2 saturates at 2^62.
 __device__ __forceinline__ uint64_t sq_fixed60(float v) {
     const uint32_t b = __float_as_uint(v) & 0x7fffffffu;
     const uint32_t e8 = b >> 23;
     const uint32_t M = (b & 0x7fffffu) | (e8 ? 0x800000u : 0u);
-    const int E = static_cast<int>(e8 ? e8 : 1u) - 150;
-    const uint64_t sq = static_cast<uint64_t>(M) * M;
-    const int s = 2 * E + 60;
-    // without branches: one of the two shifts is 0; a right shift by 63 leaves
-    // 0 (sq < 2^48) like any larger one; |v| >= 2 (s >= 16) saturates at 2^62
-    const uint32_t ls = static_cast<uint32_t>(min(max(s, 0), 15));
-    const uint32_t rs = static_cast<uint32_t>(min(max(-s, 0), 63));
-    const uint64_t r = (sq << ls) >> rs;
-    return s >= 16 ? (1ull << 62) : r;
+    const int E = e8 ? static_cast<int>(e8) : 1;
+    const uint64_t sq15 = static_cast<uint64_t>(M << 8) * (M << 7);
+    const uint64_t r = sq15 >> min(max(255 - 2 * E, 0), 63);
+    return E >= 128 ? (1ull << 62) : r;
 }
 
 // Sampling weight of one amplitude: floor(re^2 2^60) + floor(im^2 2^60).
