@@ -116,7 +116,7 @@ def test_learned_planner_gain_over_heuristics(q, capsys):
     """Collect timings from the library's own kernels at N = 26, train the
     model on the GPU, then plan the QAOA workload (3-regular graph, p = 8) with
     the width-limit greedy heuristic, the 4^k DP and the model-scored DP; the
-    measured time of each plan is the judge of the model."""
+    measured time of each plan is what the model is scored against."""
     n = 26
     st = GState(q, torch, n)
     try:
