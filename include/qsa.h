@@ -353,9 +353,10 @@ qsa_status qsa_plan_info(qsa_plan p, size_t* n_blocks, size_t* n_ops, int* max_w
 /* First input op and width of every block (capacity >= n_blocks, else QSA_E_RANGE). */
 qsa_status qsa_plan_blocks(qsa_plan p, size_t* first_op, int32_t* widths, size_t capacity);
 
-/* qsa_state_reset + a relabel of |0..0> to the plan's layout + qsa_plan_execute,
- * without the reset's clearing pass when the plan begins with a zero-state
- * preparation (opts.zero_init, N >= 12), which writes every amplitude.  The
+/* qsa_state_reset + a relabel of |0..0> to the plan's layout (metadata only,
+ * valid for |0..0>, §IV-D) + qsa_plan_execute, without the reset's clearing
+ * pass when the plan begins with a zero-state preparation (opts.zero_init,
+ * N >= 12), which writes every amplitude.  The
  * state's previous contents and layout are discarded.  Errors: as
  * qsa_plan_execute. */
 qsa_status qsa_plan_execute_from_zero(qsa_state s, qsa_plan p, qsa_run_stats* stats);
@@ -425,8 +426,8 @@ qsa_status qsa_expectation_z_batch(qsa_state s, const uint64_t* logical_masks, i
 
 /* qsa_expectation_z for each of z_masks[0..n_masks) (logical, n_masks in
  * 0..QSA_MAX_ZMASKS) into z_out (host) and qsa_sample_counts (same draws and
- * outputs), the sums taken in the sampler's pass over the state, so the state
- * is read once for both (each sum agrees with qsa_expectation_z to FP64
+ * outputs; §IV-E hierarchical sampling), the sums taken in the sampler's pass
+ * over the state, so the state is read once for both (each sum agrees with qsa_expectation_z to FP64
  * rounding; the summation order differs).  Synchronises the stream.  Errors:
  * as qsa_sample_counts, and QSA_E_ARG for n_masks, a mask beyond N or NULL. */
 qsa_status qsa_measure(qsa_state s, const uint64_t* z_masks, int n_masks, double* z_out, uint64_t shots,
