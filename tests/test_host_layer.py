@@ -58,6 +58,30 @@ def test_qaoa_layers_match_oracle(q, n, p, seed):
         assert len(kinds) == 27
 
 
+def test_bench_plan_has_24_passes(q):
+    """The bench's plan (N = 30 QAOA, p = 8, interleaved layout, layer units,
+    zero-state prefix): one preparation block that also takes the first layer
+    block, then 23 layer blocks; each fits one tile in the plan's layout (so
+    24 passes, the floor for 216 factors on positions >= 3 at 9 per pass)."""
+    import bench
+    n = 30
+    ops, _ = W.qaoa_circuit(n, 8, seed=0)
+    layout = bench.interleaved_layout(n)
+    p = q.qsa_plan_create(ops, n, q.make_opts(planner=2, kmax=6, kmax_diag=12, layer=1, zero_init=1), layout=layout)
+    try:
+        kinds, _ = q.qsa_plan_block_kinds(p)
+        first, _ = q.qsa_plan_blocks(p)
+        order = q.qsa_plan_order(p)
+    finally:
+        q.qsa_plan_destroy(p)
+    assert kinds == [4] + [3] * 23
+    run = [ops[i] for i in order]                  # execution order; block j is run[first[j]:first[j + 1]]
+    P = oracle.zero_init_prefix(ops)               # the prefix's one-qubit ops are generated, not factors
+    for j, (s, e) in enumerate(zip(first, first[1:] + [len(ops)])):
+        qubits = {qb for o in run[max(s, P):e] if len(o.targets) == 1 and not o.diag for qb in o.targets}
+        assert len(qubits) <= 12 and sum(1 for qb in qubits if layout[qb] >= 3) <= 9
+
+
 def test_layer_off_keeps_the_input_order(q):
     ops = W.brick_circuit(12, 6, seed=1)
     p = q.qsa_plan_create(ops, 12, q.make_opts(planner=2, kmax=4))
