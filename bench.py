@@ -148,6 +148,31 @@ def job_value(units_per_rank: float, ws: int, seconds: float) -> float:
     return ws * units_per_rank / seconds
 
 
+def host_cpu():
+    """The host's logical core count and CPU model (lscpu's model name, else
+    /proc/cpuinfo, else the platform string)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return {"host_nproc": os.cpu_count(), "host_cpu": model or platform.processor() or platform.machine(),
+            "host_arch": platform.machine()}
+
+
 def run_reference(args):
     """The FP64 CPU oracle, unmodified, on a bounded sample of the workload."""
     ws, rank, _ = _dist()
@@ -179,7 +204,7 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl, "sample": f"one gate per step at N={n_s}"},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"alternating {what} at N={n_s}, {args.steps} timed gates"},
+                             "sample": f"alternating {what} at N={n_s}, {args.steps} timed gates", **host_cpu()},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -217,7 +242,27 @@ def cpu_baseline(n_s: int, seed: int, p: int, workload: str = "qaoa", p_dep: flo
     dt = time.perf_counter() - t0
     rate = len(picks) * (1 << n_s) / dt
     return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{what} at N={n_s}, {dt:.1f} s single-threaded FP64"}
+            "sample": f"{what} at N={n_s}, {dt:.1f} s single-threaded FP64", **host_cpu()}
+
+
+def step_dtype(agg):
+    """The arithmetic the timed steps ran, from the kinds of block they
+    applied (not from the options asked for)."""
+    ran = []
+    if agg["layer_blocks"]:
+        ran.append("f32 layer passes")
+    if agg["diag_blocks"]:
+        ran.append("f32 diagonal passes")
+    if agg["prod_blocks"]:
+        ran.append("f32 product passes")
+    n_fp32 = agg["blocks"] - agg["tc_blocks"] - agg["diag_blocks"] - agg["prod_blocks"] - agg["layer_blocks"]
+    if n_fp32:
+        ran.append("f32 dense fused products on CUDA cores")
+    if agg["tc_blocks"]:
+        ran.append("k=5/6 products as 3xTF32 on tensor cores with f32 accumulation")
+    if agg["permutes"]:
+        ran.append("bit permutations")
+    return "c64 state; " + ", ".join(ran) + "; f64 reductions"
 
 
 def interleaved_layout(n: int, ways: int = 3):
@@ -468,8 +513,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None,
-                "dtype": ("c64 state, f32 arithmetic (k=5/6 products as 3xTF32 on tensor cores, f32 accumulation), "
-                          "f64 reductions") if prec else "c64 state, f32 arithmetic, f64 reductions",
+                "dtype": step_dtype(agg),
                 "data": "synthetic",
                 "config": {"workload": (f"dm_ghz{n_dm}: noisy GHZ density matrix, {len(ops)} channels "
                                         f"(depolarising p={args.dm_p:g} after each gate) lowered to superoperators, "

@@ -433,8 +433,11 @@ qsa_status qsa_expectation_z_batch(qsa_state s, const uint64_t* logical_masks, i
 qsa_status qsa_measure(qsa_state s, const uint64_t* z_masks, int n_masks, double* z_out, uint64_t shots,
                        uint64_t seed, uint64_t* outcomes, uint64_t* counts, size_t capacity, size_t* n_distinct);
 
-/* Draw `shots` outcomes (§IV-E): weights P_y = trunc(p_y * 2^62) (integer,
- * so the CDF does not depend on summation order) over physical indices in
+/* Draw `shots` outcomes (§IV-E): integer weights
+ * P_y = floor(re_y^2 * 2^60) + floor(im_y^2 * 2^60) of the stored FP32
+ * amplitude (each square exact in FP64, so the weight is too; |amplitude| < 2
+ * keeps it below 2^62), so the CDF does not depend on summation order, over
+ * physical indices in
  * 2^10-amplitude blocks; shot i draws Philox4x64-10(ctr = (i, 0, 0, 0),
  *  key = (seed, 0)).word0 = r, maps it to u = floor(r * total / 2^64) and takes the first physical index whose
  * cumulative weight is strictly greater (a zero-weight bin is never drawn);

@@ -44,8 +44,11 @@ def _noalloc(q, buf, n, layout, shots, seed, stream):
     return outc[:k].cpu().numpy().astype(np.uint64), cnts[:k].cpu().numpy().astype(np.uint64)
 
 
-@pytest.mark.parametrize("n,shots", [(14, 3000), (9, 500)])
+@pytest.mark.parametrize("n,shots", [(14, 3000), (9, 500), (24, 5000)])
 def test_noalloc_sampler_matches_allocating_sampler(q, n, shots):
+    """N = 24 has 2^14 block totals (more than one 4096-entry scan segment,
+    whose totals share the array with the sort keys) and 5000 shots (more than
+    one launch of the bitonic sort): 16384 + 8192 + 5000 words of the array."""
     buf = torch.zeros(1 << n, dtype=torch.complex64, device="cuda:0")
     stream = torch.cuda.current_stream().cuda_stream
     s = q.qsa_state_create_ex(n, buf.data_ptr(), buf.numel() * 8, stream, 1)
