@@ -1,51 +1,63 @@
 // Split-TF32 (3xTF32) fused dense update on tcgen05 tensor cores, k = 5, 6.
 //
 // The update of one group of 2^k amplitudes (§IV-B: M' = G M on the
-// 2^k x 2^(N-k) view) is a real matrix-vector product after embedding
-// complex numbers as 2x2 real blocks:  u[2c+t] = (Re, Im)(psi_c),
-// R[2r+s][2c+t] = [[Re G, -Im G], [Im G, Re G]][s][t],  u' = R u.
-// A tile of 128 groups is one GEMM  D (128 x 2^(k+1)) = U (128 x K) R^T with
-// K = 2^(k+1):  the state tile is the MMA's A operand (M = 128 rows, one
-// group per row, K-major), R is the B operand (N = K rows, K-major).  Both
-// are split into hi/lo parts and D = U_hi R_hi^T + (U_lo R_hi^T + U_hi R_lo^T)
-// (the three-product split-TF32 scheme of Ootomo & Yokota 2022, "Recovering
-// single precision accuracy from Tensor Cores while surpassing the FP32
-// theoretical peak performance").
+// 2^k x 2^(N-k) view) is a real matrix-vector product after embedding complex
+// numbers as 2x2 real blocks: u[2c+t] = (Re, Im)(psi_c) and
+// R[2r+s][2c+t] = [[Re G, -Im G], [Im G, Re G]][s][t], u' = R u.
+//
+// Work unit: a chunk of 2^11 amplitudes, the state restricted to 11 bit
+// positions (the targets and the lowest non-target positions) with every
+// other bit fixed.  A chunk is 32 rows of 64 amplitudes: a row fixes the five
+// lowest non-target positions ("row bits"), and its 64 amplitudes run over
+// six "K bits" (k = 6: the targets in ascending position; k = 5: the targets
+// and the sixth non-target position, so a row holds two groups).  One chunk
+// is the GEMM
+//     D (128 x 32) = A (128 x 128) . B (32 x 128)^T,
+// A = R (k = 6) or blockdiag(R, R) (k = 5) in the K-bit numbering, B = the
+// chunk's rows as real vectors of 128 floats: D[2 nu + s][row] is part s of
+// output amplitude nu of the row.  Both operands are split into hi and lo
+// parts and D = A_hi B_hi + (A_hi B_lo + A_lo B_hi), the three-product
+// split-TF32 scheme of Ootomo & Yokota 2022 ("Recovering single precision
+// accuracy from Tensor Cores while surpassing the FP32 theoretical peak
+// performance").
 //
 // Tensor cores round their FP32 accumulation toward zero, which biases every
 // rounded sum towards zero; over a deep circuit that shrinks the norm
-// linearly with depth.  Two measures remove the bias from the dominant term:
-//   - as the split-TF32 method prescribes, U_hi R_hi^T is accumulated outside
-//     the tensor core: every segment of two K-steps (16 values of K) writes a
-//     fresh partial product into one of NMAIN tensor-memory buffers and the
-//     epilogue warps add the partials in FP32 with round-to-nearest;
-//   - hi parts are block-quantised per 16-value segment (a shared
-//     power-of-two quantum, integer multiples of magnitude <= 1024, as in
-//     Ozaki-type splittings), so each 16-term partial and its 8-term half
-//     are exactly representable FP32 numbers and the tensor core has
-//     nothing to round.
-// lo = x - hi (exact) is rounded to TF32 to nearest; the two small
-// correction products (about 2^-10 of the result) accumulate in tensor
-// memory, where their rounding is far below FP32 resolution of the output.
-// Combinations are numbered by ascending tile-local target position, so a
-// K-chunk (16 combinations) fixes the highest target bits and its 2048
-// amplitudes run in address order.
+// linearly with depth.  The dominant product is therefore made exact: hi
+// parts are block-quantised per row and K half (64 values) to integer
+// multiples c q of a power-of-two quantum q (|c| <= 2048 for the matrix,
+// <= 128 for the state), so every partial sum of a 64-term half of
+// A_hi B_hi is an integer multiple of q_A q_B of magnitude at most 2^24:
+// exact in FP32, nothing for the tensor core to round.
+// Each half accumulates into its own tensor-memory columns and the epilogue
+// adds the two and the correction accumulator in FP32 with round-to-nearest.
+// lo = x - hi (exact) is rounded to TF32 to nearest; the correction products
+// (about 2^-9 of the result) accumulate in tensor memory, where their
+// rounding is far below FP32 resolution of the output.
 //
-// CTA roles (one persistent CTA per SM, 416 threads):
-//   warps 0-3   loaders: copy each K-chunk in address order (16-byte
-//               cp.async, mbarrier-tracked NR-stage ring), then thread g
-//               gathers row g, splits it hi/lo and stores both into its
-//               tensor-memory lane: the MMA's A operand (two chunk buffers);
-//   warps 4-11  epilogue: warp w reads tensor-memory lanes 32*(w%4).. and
-//               half (w-4)/4 of the columns, sums the partials, adds the
-//               correction accumulator and writes the outputs back through
-//               a small shared staging area, one coalesced run per store;
-//   warp 12     allocates tensor memory and issues the MMAs (one thread);
-//               B (the split R) stays in shared memory for the whole launch.
-// Tensor memory (512 columns): NMAIN main partials + NCORR corrections of NK
-// columns, and 128 columns of A (k = 6: 2 + 1, k = 5: 4 + 2).
+// CTA roles (one persistent CTA per SM, 320 threads):
+//   warp 8      producer: copies each chunk from HBM into an NR-stage ring
+//               with 16-byte cp.async (mbarrier-tracked), in an XOR layout
+//               chosen per launch so that the converters' reads are free of
+//               bank conflicts for any target positions;
+//   warps 0-3   converters in two teams of two warps; team t converts chunks
+//               t, t + 2, ... into B buffer t (so each buffer has one owner
+//               and every parity wait on it is for the next completion).  A
+//               lane holds one K half (32 amplitudes) of one row: the values
+//               into registers (the raw stage is released right away), the
+//               half's quantum, the hi / lo split and the B operand (K-major,
+//               128-byte swizzle) in shared memory;
+//   warp 9      allocates tensor memory and issues the MMAs (one thread);
+//               A (hi and lo) stays in tensor memory for the whole launch;
+//   warps 4-7   epilogue, warp w on tensor-memory lanes 32 (w % 4) ...: sums
+//               the accumulators, transposes its 16 outputs x 32 rows through
+//               its own shared staging area and writes them back (one row
+//               block of consecutive addresses per warp store).  At the start
+//               the same warps build A in tensor memory.
+// Tensor memory (512 columns): A_hi 128, A_lo 128, and two accumulator sets
+// of 96 columns (two exact main halves and the corrections, 32 rows each).
 // Every mbarrier wait is bounded; on timeout the CTA records an error code,
-// drains its MMAs, frees tensor memory and returns.
+// drains its copies and MMAs, frees tensor memory and returns.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -58,10 +70,41 @@ namespace qsa {
 
 namespace {
 
-constexpr int kTcThreads = 416;
-constexpr int kEpiThreads = 256;
-constexpr int kGroups = 128;                 // MMA M
+constexpr int kThreads = 320;
+constexpr int kConvWarps = 4;                // warps 0-3
+constexpr int kProdWarp = 8;
+constexpr int kMmaWarp = 9;                  // warps 4-7: epilogue
+constexpr int kChunkBits = 11;               // amplitudes per chunk: 2^11
+constexpr int kNR = 8;                       // raw chunk stages
+constexpr int kNB = 2;                       // B operand stages: one per converter team
+constexpr int kND = 2;                       // accumulator sets
 constexpr uint32_t kWaitLimit = 1u << 22;    // try_wait rounds before giving up
+
+constexpr uint32_t kRawBytes = (1u << kChunkBits) * 8;   // 16 KiB
+constexpr uint32_t kHalfB = 32 * 128 * 4;                // one split part of B: 32 rows x 128 floats
+constexpr uint32_t kBBytes = 2 * kHalfB;                 // hi + lo
+constexpr uint32_t kStgPitch = 33;                       // float2 per staged output (32 rows + 1 pad)
+constexpr uint32_t kStgWarpBytes = 16 * kStgPitch * 8;   // 16 outputs per epilogue warp
+// shared memory carve-up (from a 1024-byte aligned base)
+constexpr uint32_t OFF_B = 0;
+constexpr uint32_t OFF_RAW = OFF_B + kNB * kBBytes;
+constexpr uint32_t OFF_STG = OFF_RAW + kNR * kRawBytes;
+constexpr uint32_t OFF_GI = OFF_STG + 4 * kStgWarpBytes;   // producer: 32 global offsets
+constexpr uint32_t OFF_SI = OFF_GI + 32 * 8;               // producer: 32 stage offsets
+constexpr uint32_t OFF_GNU = OFF_SI + 32 * 4;              // epilogue: 64 global output offsets
+constexpr uint32_t OFF_BARS = OFF_GNU + 64 * 8;
+constexpr int BAR_RFULL = 0, BAR_REMPTY = kNR, BAR_BFULL = 2 * kNR, BAR_BEMPTY = BAR_BFULL + kNB,
+              BAR_DFULL = BAR_BEMPTY + kNB, BAR_DEMPTY = BAR_DFULL + kND, BAR_AREADY = BAR_DEMPTY + kND,
+              BAR_FIN = BAR_AREADY + 1, NBARS = BAR_FIN + 1;
+constexpr uint32_t OFF_MISC = OFF_BARS + NBARS * 8;        // tensor-memory address, abort word
+constexpr size_t kSmem = 1024 + OFF_MISC + 16;
+static_assert(kSmem <= 232448, "shared memory per CTA");
+// tensor memory columns
+constexpr uint32_t COL_AHI = 0, COL_ALO = 128, COL_D = 256, D_COLS = 96;
+constexpr uint32_t kTmemCols = 512;
+static_assert(COL_D + kND * D_COLS <= kTmemCols, "tensor memory");
+// instruction descriptor: D FP32, A and B TF32, both K-major, N = 32, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -83,14 +126,19 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
     return ok != 0;
 }
 // Bounded wait; gives up (and raises the CTA abort word) after kWaitLimit
-// rounds or as soon as another role has aborted.
-__device__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag, int* gerr, int code) {
+// rounds or as soon as another role has aborted.  The first give-up on the
+// device records its code, the chunk it waited for and the CTA in gerr[0..2].
+__device__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag, int* gerr, int code,
+                          uint64_t item = 0) {
     for (uint32_t i = 0; i < kWaitLimit; ++i) {
         if (mbar_try(a, parity)) return true;
         if (*abort_flag) return false;
     }
     *abort_flag = 1;
-    atomicExch(gerr, code);
+    if (atomicCAS(gerr, 0, code) == 0) {
+        gerr[1] = static_cast<int>(item);
+        gerr[2] = static_cast<int>(blockIdx.x);
+    }
     return false;
 }
 
@@ -166,39 +214,30 @@ __device__ __forceinline__ float tf32_rna(float x) {
     return __uint_as_float(r);
 }
 
-// Block split of S values (S <= 16: two MMA K-steps): hi = c * q with the
-// shared quantum q = 2^(E-9), E = exponent of max |x|, and the integer
-// c = round(x / q), |c| <= 1024.  Every dot product of two such segments, and
-// every partial sum of it, is an integer multiple of q_a q_b of magnitude at
-// most 16 * 2^20 = 2^24: exactly representable in FP32, so the tensor core
-// adds the two K-steps of a segment without rounding and its round-toward-
-// zero never engages on the main product.  The rounding to a multiple of q is
-// (x + M) - M with M = 1.5 * 2^(E+14), whose ulp is q (round to nearest even,
-// valid for |x| < 2^(E+1)).  lo = x - hi is exact in FP32 (|lo| <= q / 2) and
-// is rounded to TF32 to nearest.  Segments below 2^-95 keep everything in lo.
-struct SegQuant {
-    float m;   // 1.5 * 2^(E+14)
-};
-__device__ __forceinline__ SegQuant seg_quant(float mx) {
-    int e = static_cast<int>((__float_as_uint(mx) >> 23) & 0xFFu);
-    e = e < 32 ? 32 : (e > 240 ? 240 : e);
-    SegQuant sq;
-    sq.m = __uint_as_float((static_cast<uint32_t>(e + 14) << 23) | 0x400000u);
-    return sq;
-}
-__device__ __forceinline__ void split_one(float x, const SegQuant& sq, float& hi, float& lo) {
-    hi = __fsub_rn(__fadd_rn(x, sq.m), sq.m);
-    lo = tf32_rna(__fsub_rn(x, hi));
-}
+// Block split of a 64-value segment (one row, one K half): hi = c q with the
+// shared power-of-two quantum q = 2^(E+1-S), E = exponent of the segment's
+// largest magnitude, and the integer c = round(x / q), |c| <= 2^S.  The
+// matrix A takes S = 11 (c is then an exact TF32 integer) and the state B
+// S = 7: every partial sum of a 64-term dot product of the two is an integer
+// multiple of q_A q_B of magnitude at most 64 * 2^11 * 2^7 = 2^24, exactly
+// representable in FP32, so the tensor core adds the segment's products
+// without rounding.  The split is asymmetric because the matrix's rounding
+// error (lo rounded to TF32) is the same for every group of the state and so
+// changes the norm coherently, while the state's is independent from
+// amplitude to amplitude.  The rounding to a multiple of q is (x + M) - M
+// with M = 1.5 * 2^(E+24-S), whose ulp is q (round to nearest even, valid for
+// |x| < 2^(E+1)).  lo = x - hi is exact in FP32 (|lo| <= q / 2) and is rounded
+// to TF32 to nearest.  Segments below 2^-95 keep everything in lo.
+constexpr int kSplitA = 11, kSplitB = 7;
 template <int S>
-__device__ __forceinline__ void block_split(const float* x, float* hi, float* lo) {
-    static_assert(S <= 16, "segment too long for an exact FP32 partial");
-    float mx = 0.f;
-#pragma unroll
-    for (int i = 0; i < S; ++i) mx = fmaxf(mx, fabsf(x[i]));
-    const SegQuant sq = seg_quant(mx);
-#pragma unroll
-    for (int i = 0; i < S; ++i) split_one(x[i], sq, hi[i], lo[i]);
+__device__ __forceinline__ float seg_magic(float mx) {
+    int e = static_cast<int>((__float_as_uint(mx) >> 23) & 0xFFu);
+    e = e < 32 ? 32 : (e > 254 - (24 - S) ? 254 - (24 - S) : e);
+    return __uint_as_float((static_cast<uint32_t>(e + 24 - S) << 23) | 0x400000u);
+}
+__device__ __forceinline__ void split_one(float x, float magic, float& hi, float& lo) {
+    hi = __fsub_rn(__fadd_rn(x, magic), magic);
+    lo = tf32_rna(__fsub_rn(x, hi));
 }
 
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms
@@ -208,11 +247,6 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
            (static_cast<uint64_t>(1024 >> 4) << 32) | (static_cast<uint64_t>(1) << 46) |
            (static_cast<uint64_t>(2) << 61);
 }
-// Byte offset of 32-bit element kin (< 32) of row `row` in a K-major region
-// of 128-byte rows with the 128-byte swizzle (16-byte chunk index XOR row%8).
-__device__ __forceinline__ uint32_t sw128_off(uint32_t row, uint32_t kin) {
-    return (row >> 3) * 1024u + (row & 7u) * 128u + ((((kin >> 2) ^ (row & 7u))) << 4) + ((kin & 3u) << 2);
-}
 
 __device__ __forceinline__ uint64_t insert_zero(uint64_t v, int p) {
     uint64_t lo = v & ((1ull << p) - 1ull);
@@ -221,16 +255,20 @@ __device__ __forceinline__ uint64_t insert_zero(uint64_t v, int p) {
 
 struct TcArgs {
     float2* psi;
-    const float* mat;   // G, 2 * 4^k floats (row-major, interleaved)
+    const float* mat;     // G, 2 * 4^k floats (row-major, interleaved), operator order
     int* err;
-    uint64_t ntiles;
-    int m, nx;
+    uint64_t nchunks;
+    uint64_t gbit[kChunkBits];   // global amplitude offset of chunk-local position p
+    uint32_t sbit[kChunkBits];   // stage byte address (XOR) contribution of chunk-local position p
+    int m, nx;                   // chunk-local positions: 0..m-1 and xpos[0..nx-1]
     int xpos[6];
-    int tl[6];          // tile-local position of target j (V order)
-    int tls[6];         // ascending
+    int kp[6];                   // chunk-local position of K bit b
+    int rp[5];                   // chunk-local position of row bit b
+    int vbit[6];                 // operator bit of K bit b (b < k; for k = 5, K bit 5 is the group bit)
+    int k;
 };
 
-__device__ __forceinline__ uint64_t tc_tile_base(const TcArgs& a, uint64_t t) {
+__device__ __forceinline__ uint64_t chunk_base(const TcArgs& a, uint64_t t) {
     uint64_t b = t << a.m;
 #pragma unroll
     for (int e = 0; e < 6; ++e)
@@ -238,185 +276,84 @@ __device__ __forceinline__ uint64_t tc_tile_base(const TcArgs& a, uint64_t t) {
     return b;
 }
 
-template <int K>
-struct TcCfg {
-    static constexpr int D = 1 << K;                 // amplitudes per group
-    static constexpr int NK = 2 * D;                 // GEMM N and K
-    static constexpr int KC = NK / 32;               // K-chunks of 32 floats (16 combinations)
-    static constexpr int KSEGS = NK / 16;            // exact main partials per tile
-    static constexpr int NR = K == 6 ? 5 : 8;        // raw chunk stages
-    static constexpr int NMAIN = K == 6 ? 2 : 4;     // main partial buffers
-    static constexpr int NCORR = K == 6 ? 1 : 2;     // correction accumulators
-    static constexpr uint32_t B_REGION = NK * 128;   // one K-block of B
-    static constexpr uint32_t B_BYTES = KC * B_REGION;
-    static constexpr uint32_t RAW_BYTES = kGroups * 128;   // one chunk: 2048 complex64 in address order
-    // tensor memory: main partials, correction accumulators, and the A operand
-    // (two chunk buffers of 32 hi + 32 lo columns)
-    static constexpr uint32_t COL_MAIN = 0, COL_CORR = NMAIN * NK, COL_A = COL_CORR + NCORR * NK;
-    static constexpr uint32_t TMEM_COLS = COL_A + 128;
-    static_assert(TMEM_COLS == 512, "one CTA owns all tensor memory of its SM");
-    static constexpr uint32_t IDESC = (1u << 4)      // D: FP32
-                                      | (2u << 7)    // A: TF32
-                                      | (2u << 10)   // B: TF32
-                                      | (static_cast<uint32_t>(NK >> 3) << 17) |
-                                      (static_cast<uint32_t>(kGroups >> 4) << 24);
-    // per epilogue warp: 256 staged outputs, one padding slot per 32
-    static constexpr uint32_t STAGE_ELEMS = 256 + 8;
-    // shared memory carve-up (from a 1024-byte aligned base)
-    static constexpr uint32_t OFF_BLO = B_BYTES, OFF_RAW = 2 * B_BYTES;
-    static constexpr uint32_t OFF_RUNOFF = OFF_RAW + NR * RAW_BYTES;
-    static constexpr uint32_t OFF_LOFF = OFF_RUNOFF + 64 * 8;
-    static constexpr uint32_t OFF_CPY = OFF_LOFF + 64 * 4;   // copy offsets (8), row read slots (16)
-    static constexpr uint32_t OFF_BARS = OFF_CPY + 8 * 8 + 16 * 4;
-    // barriers: A chunk full/empty (2+2), main full/empty (NMAIN+NMAIN),
-    // correction full/empty (NCORR+NCORR), raw stage full/empty (NR+NR), drain (1)
-    static constexpr int BAR_FULL = 0, BAR_EMPTY = 2, BAR_MFULL = 4, BAR_MEMPTY = 4 + NMAIN,
-                         BAR_CFULL = 4 + 2 * NMAIN, BAR_CEMPTY = BAR_CFULL + NCORR, BAR_RFULL = BAR_CEMPTY + NCORR,
-                         BAR_REMPTY = BAR_RFULL + NR, BAR_FIN = BAR_REMPTY + NR, NBARS = BAR_FIN + 1;
-    static constexpr uint32_t OFF_MISC = OFF_BARS + NBARS * 8;   // tensor-memory address, abort word
-    static constexpr uint32_t OFF_STAGE = OFF_MISC + 16;
-    static constexpr size_t SMEM = 1024 + OFF_STAGE + kEpiThreads / 32 * STAGE_ELEMS * 8;
-};
+// Entry [2 nu + s][2 kap + t] of A: the real embedding of G in the K-bit
+// numbering (k = 5: blockdiag(R, R), the block given by bit 5).
+__device__ float a_entry(const TcArgs& a, int nu, int kap, int s, int t) {
+    int r = nu, c = kap;
+    if (a.k == 5) {
+        if ((nu >> 5) != (kap >> 5)) return 0.f;
+        r &= 31;
+        c &= 31;
+    }
+    int ro = 0, co = 0;
+    for (int b = 0; b < a.k; ++b) {
+        ro |= ((r >> b) & 1) << a.vbit[b];
+        co |= ((c >> b) & 1) << a.vbit[b];
+    }
+    const float2 g = reinterpret_cast<const float2*>(a.mat)[(ro << a.k) + co];
+    return s == 0 ? (t == 0 ? g.x : -g.y) : (t == 0 ? g.y : g.x);
+}
 
-template <int K>
-__global__ void __launch_bounds__(kTcThreads, 1) k_apply_tc(TcArgs a) {
-    using C = TcCfg<K>;
-    constexpr int D = C::D, NK = C::NK, KC = C::KC, NR = C::NR, NMAIN = C::NMAIN, NCORR = C::NCORR,
-                  HALF = NK / 2;
+// PAIR: chunk-local position 0 is a K bit (a target at position 0), so the
+// two amplitudes of a K pair are one 16-byte unit of the stage.
+template <bool PAIR>
+__global__ void __launch_bounds__(kThreads, 1) k_apply_tc(TcArgs a) {
     extern __shared__ unsigned char smem_raw[];
-    const uint32_t raw = smem_u32(smem_raw);
-    unsigned char* sm = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
-    unsigned char* Bhi = sm;
-    unsigned char* Blo = sm + C::OFF_BLO;
-    unsigned char* Raw = sm + C::OFF_RAW;   // [stage][row g][16 complex64]
-    uint64_t* runoff = reinterpret_cast<uint64_t*>(sm + C::OFF_RUNOFF);
-    int* loff = reinterpret_cast<int*>(sm + C::OFF_LOFF);
-    uint64_t* cpy_goff = reinterpret_cast<uint64_t*>(sm + C::OFF_CPY);
-    uint32_t* rd_slot = reinterpret_cast<uint32_t*>(sm + C::OFF_CPY + 8 * 8);
-    const uint32_t bar0 = smem_u32(sm + C::OFF_BARS);
+    const uint32_t raw_addr = smem_u32(smem_raw);
+    unsigned char* sm = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
+    unsigned char* Bsm = sm + OFF_B;
+    unsigned char* Raw = sm + OFF_RAW;
+    uint64_t* gi_tab = reinterpret_cast<uint64_t*>(sm + OFF_GI);
+    uint32_t* si_tab = reinterpret_cast<uint32_t*>(sm + OFF_SI);
+    uint64_t* gnu_tab = reinterpret_cast<uint64_t*>(sm + OFF_GNU);
+    const uint32_t bar0 = smem_u32(sm + OFF_BARS);
     auto bar = [&](int i) { return bar0 + 8u * static_cast<uint32_t>(i); };
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + C::OFF_MISC);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + C::OFF_MISC + 4);
-    float2* stage = reinterpret_cast<float2*>(sm + C::OFF_STAGE);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_MISC);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + OFF_MISC + 4);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // Combinations are numbered in ascending tile-local target position
-    // (bit i of c <-> position tls[i]); vpos[i] is the operator's own index of
-    // that target, so combination c is the operator's basis index vo(c).
-    int vpos[6];
+    // Producer copy units: unit U = lane + 32 i (16 bytes: elements 2U, 2U+1);
+    // the bits of i are chunk-local positions 6..10.
+    if (tid < 32) {
+        uint64_t g = 0;
+        uint32_t s = 0;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        vpos[i] = 0;
+        for (int b = 0; b < 5; ++b)
+            if ((tid >> b) & 1) {
+                g |= a.gbit[6 + b];
+                s ^= a.sbit[6 + b];
+            }
+        gi_tab[tid] = g;
+        si_tab[tid] = s;
+    } else if (tid >= 64 && tid < 128) {   // global offset of output nu within its row
+        const int nu = tid - 64;
+        uint64_t g = 0;
 #pragma unroll
-        for (int j = 0; j < K; ++j)
-            if (i < K && a.tl[j] == a.tls[i]) vpos[i] = j;
-    }
-    auto vo = [&](int c) {
-        int r = 0;
-#pragma unroll
-        for (int i = 0; i < K; ++i) r |= ((c >> i) & 1) << vpos[i];
-        return r;
-    };
-
-    for (int r = tid; r < (1 << a.nx); r += blockDim.x) {
-        uint64_t off = 0;
-#pragma unroll
-        for (int e = 0; e < 6; ++e)
-            if (e < a.nx && ((r >> e) & 1)) off |= 1ull << a.xpos[e];
-        runoff[r] = off;
-    }
-    for (int c = tid; c < D; c += blockDim.x) {
-        int o = 0;
-#pragma unroll
-        for (int i = 0; i < K; ++i)
-            if ((c >> i) & 1) o |= 1 << a.tls[i];
-        loff[c] = o;
-    }
-    // Chunk copies: a K-chunk holds the 2048 amplitudes whose tile-local index
-    // l has the chunk's combination bits tls[4..k-1] fixed; element e is l
-    // with those bits squeezed out, so e runs in address order.  The raw stage
-    // keeps e in address order, 16-byte units XOR-swizzled within 128-byte
-    // rows (unit ^= row % 8); thread t copies units t + 128 i, i < 8.  Global
-    // offsets and stage slots are bitwise linear in e, so each splits into a
-    // per-thread part and a shared table.
-    auto gbit = [&](int p) -> uint64_t { return p < a.m ? (1ull << p) : (1ull << a.xpos[p - a.m]); };
-    auto goff_of = [&](uint32_t l) {
-        uint64_t o = 0;
-        for (int p = 0; p < 7 + K; ++p)
-            if ((l >> p) & 1u) o |= gbit(p);
-        return o;
-    };
-    auto spread = [&](uint32_t e) {   // element index -> tile-local index
-#pragma unroll
-        for (int q = 4; q < K; ++q) e = static_cast<uint32_t>(insert_zero(e, a.tls[q]));
-        return e;
-    };
-    auto squeeze = [&](uint32_t l) {   // tile-local index (fixed bits 0) -> element index
-        uint32_t e = 0;
-        int kb = 0;
-        for (int p = 0; p < 7 + K; ++p) {
-            bool fixed = false;
-#pragma unroll
-            for (int q = 4; q < K; ++q) fixed |= (p == a.tls[q]);
-            if (!fixed) e |= ((l >> p) & 1u) << kb++;
-        }
-        return e;
-    };
-    auto slot_of = [](uint32_t e) { return ((((e >> 1) ^ ((e >> 4) & 7u)) << 4) | ((e & 1u) << 3)); };
-    if (tid < 8) cpy_goff[tid] = goff_of(spread(static_cast<uint32_t>(tid) << 8));
-    if (tid >= 32 && tid < 48) {   // combination c4 of a row: its element part and stage slot
-        const int c4 = tid - 32;
-        uint32_t l = 0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) l |= ((static_cast<uint32_t>(c4) >> q) & 1u) << a.tls[q];
-        rd_slot[c4] = slot_of(squeeze(l));
-    }
-    // B operand: the real embedding R of G in the sorted numbering, split hi / lo.
-    const float2* G = reinterpret_cast<const float2*>(a.mat);
-    for (int e = tid; e < NK * (NK / 16); e += blockDim.x) {
-        const int n = e / (NK / 16), s16 = e - n * (NK / 16);   // row n, segment s16 (two K-steps)
-        const int row = vo(n >> 1) * D;
-        float x[16], hi[16], lo[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int kk = 16 * s16 + i;
-            const float2 g = G[row + vo(kk >> 1)];
-            x[i] = (n & 1) ? ((kk & 1) ? g.x : g.y) : ((kk & 1) ? -g.y : g.x);
-        }
-        block_split<16>(x, hi, lo);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int kk = 16 * s16 + i;
-            const uint32_t off = static_cast<uint32_t>(kk >> 5) * C::B_REGION + sw128_off(n, kk & 31);
-            *reinterpret_cast<float*>(Bhi + off) = hi[i];
-            *reinterpret_cast<float*>(Blo + off) = lo[i];
-        }
+        for (int b = 0; b < 6; ++b)
+            if ((nu >> b) & 1) g |= a.gbit[a.kp[b]];
+        gnu_tab[nu] = g;
     }
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(bar(C::BAR_FULL + i), 128);
-            mbar_init(bar(C::BAR_EMPTY + i), 1);
+        for (int i = 0; i < kNR; ++i) {
+            mbar_init(bar(BAR_RFULL + i), 32);
+            mbar_init(bar(BAR_REMPTY + i), 64);   // the converting team
         }
-        for (int i = 0; i < NMAIN; ++i) {
-            mbar_init(bar(C::BAR_MFULL + i), 1);
-            mbar_init(bar(C::BAR_MEMPTY + i), kEpiThreads);
+        for (int i = 0; i < kNB; ++i) {
+            mbar_init(bar(BAR_BFULL + i), 64);
+            mbar_init(bar(BAR_BEMPTY + i), 1);
         }
-        for (int i = 0; i < NCORR; ++i) {
-            mbar_init(bar(C::BAR_CFULL + i), 1);
-            mbar_init(bar(C::BAR_CEMPTY + i), kEpiThreads);
+        for (int i = 0; i < kND; ++i) {
+            mbar_init(bar(BAR_DFULL + i), 1);
+            mbar_init(bar(BAR_DEMPTY + i), 128);
         }
-        for (int i = 0; i < NR; ++i) {
-            mbar_init(bar(C::BAR_RFULL + i), 128);
-            mbar_init(bar(C::BAR_REMPTY + i), 128);
-        }
-        mbar_init(bar(C::BAR_FIN), 1);
+        mbar_init(bar(BAR_AREADY), 128);
+        mbar_init(bar(BAR_FIN), 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
-    fence_async_smem();
-    if (warp == 12) {
-        tmem_alloc(smem_u32(tmem_slot), C::TMEM_COLS);
+    if (warp == kMmaWarp) {
+        tmem_alloc(smem_u32(tmem_slot), kTmemCols);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -424,328 +361,306 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_tc(TcArgs a) {
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const uint64_t ntiles = a.ntiles;
-    const uint64_t my_tiles = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-    const uint32_t mmask = (1u << a.m) - 1u;
+    const uint64_t nch = a.nchunks;
+    const uint64_t my = nch > blockIdx.x ? (nch - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
 
-    if (warp < 4) {
-        // ---------------- loaders ----------------
-        // The loaders copy every K-chunk in address order (8-byte cp.async,
-        // consecutive threads on consecutive amplitudes) into an NR-stage raw
-        // ring, NR - 1 chunks ahead; thread g then reads row g, splits it into
-        // hi / lo and writes both into its tensor-memory lane (the MMA's A
-        // operand, two chunk buffers).
-        const int g = tid;
-        const uint64_t goffT = goff_of(spread(static_cast<uint32_t>(tid) << 1));
-        const uint32_t sdstT = slot_of(static_cast<uint32_t>(tid) << 1);
-        uint32_t lbg = static_cast<uint32_t>(g);   // row g's own tile-local bits (targets zero)
+    if (warp == kProdWarp) {
+        // ---------------- producer ----------------
+        uint64_t gl = 0;   // this lane's part of its units (unit bits 0..4 = positions 1..5)
+        uint32_t sl = 0;
 #pragma unroll
-        for (int j = 0; j < K; ++j) lbg = static_cast<uint32_t>(insert_zero(lbg, a.tls[j]));
-        const uint32_t rslot = slot_of(squeeze(lbg));
-        const uint64_t gq4 = gbit(a.tls[4]), gq5 = K == 6 ? gbit(a.tls[K - 1]) : 0ull;
+        for (int b = 0; b < 5; ++b)
+            if ((lane >> b) & 1) {
+                gl |= a.gbit[1 + b];
+                sl ^= a.sbit[1 + b];
+            }
         const uint32_t raw0 = smem_u32(Raw);
-        uint64_t base_t = ~0ull, base_v = 0;   // the tile base, formed once per tile
-        auto issue = [&](uint64_t idx, int slot) {
-            const uint64_t t = blockIdx.x + (idx / KC) * gridDim.x;
-            const int j = static_cast<int>(idx % KC);
-            if (t != base_t) {
-                base_t = t;
-                base_v = tc_tile_base(a, t);
+        for (uint64_t i = 0; i < my; ++i) {
+            const int s = static_cast<int>(i % kNR);
+            if (i >= kNR) {
+                const bool ok = mbar_wait(bar(BAR_REMPTY + s), static_cast<uint32_t>(i / kNR - 1) & 1u, abort_flag,
+                                          a.err, 21, i);
+                if (!__all_sync(0xffffffffu, ok)) break;
             }
-            const uint64_t o0 = base_v | ((j & 1) ? gq4 : 0ull) | ((j & 2) ? gq5 : 0ull) | goffT;
-            const uint32_t d0 = raw0 + static_cast<uint32_t>(slot) * C::RAW_BYTES;
+            const uint64_t base = chunk_base(a, blockIdx.x + i * gridDim.x) | gl;
+            const uint32_t d0 = raw0 + static_cast<uint32_t>(s) * kRawBytes;
+#pragma unroll 8
+            for (int u = 0; u < 32; ++u) cp_async16(d0 + (sl ^ si_tab[u]), a.psi + (base | gi_tab[u]));
+            cp_async_arrive_noinc(bar(BAR_RFULL + s));
+        }
+        cp_async_wait_all();   // no copy may land after the CTA has left
+    } else if (warp < kConvWarps) {
+        // ---------------- converters ----------------
+        const int team = warp >> 1;
+        const int rho = 16 * (warp & 1) + (lane & 15), h = lane >> 4;   // row and K half of this lane
+        uint32_t srow = 0;
 #pragma unroll
-            for (int i = 0; i < 8; ++i)   // unit t + 128 i: element 2t + 256 i, slot part 2048 i
-                cp_async16(d0 + (sdstT ^ (static_cast<uint32_t>(i) << 11)), a.psi + (o0 | cpy_goff[i]));
-            cp_async_arrive_noinc(bar(C::BAR_RFULL + slot));
+        for (int b = 0; b < 5; ++b)
+            if ((rho >> b) & 1) srow ^= a.sbit[a.rp[b]];
+        if (h) srow ^= a.sbit[a.kp[5]];
+        uint32_t ks[5];
+#pragma unroll
+        for (int b = 0; b < 5; ++b) ks[b] = a.sbit[a.kp[b]];
+        auto kaddr = [&](int c) {   // c < 32 is a compile-time constant in the unrolled loops
+            uint32_t o = 0;
+#pragma unroll
+            for (int b = 0; b < 5; ++b)
+                if ((c >> b) & 1) o ^= ks[b];
+            return o;
         };
-        const uint64_t total = my_tiles * KC;
+        const uint32_t brow = static_cast<uint32_t>(rho >> 3) * 1024u + static_cast<uint32_t>(rho & 7) * 128u;
+        const uint32_t bsw = static_cast<uint32_t>(rho & 7);
+        for (uint64_t i = static_cast<uint64_t>(team); i < my; i += 2) {
+            const int s = static_cast<int>(i % kNR), bb = static_cast<int>(i % kNB);   // bb == team
+            bool ok = mbar_wait(bar(BAR_RFULL + s), static_cast<uint32_t>(i / kNR) & 1u, abort_flag, a.err, 22, i);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            // x[2 c + t] = part t of amplitude 32 h + c of the row
+            const unsigned char* stg = Raw + static_cast<uint32_t>(s) * kRawBytes;   // element at srow ^ kaddr
+            float x[64];
+            if (PAIR) {
 #pragma unroll
-        for (int s0 = 0; s0 < NR; ++s0)
-            if (static_cast<uint64_t>(s0) < total) issue(s0, s0);
-        const uint32_t lane_a = tmem + (static_cast<uint32_t>(warp * 32) << 16) + C::COL_A;
-        for (uint64_t idx = 0; idx < total; ++idx) {
-            const int slot = static_cast<int>(idx % NR);
-            const bool wr = mbar_wait(bar(C::BAR_RFULL + slot), static_cast<uint32_t>(idx / NR) & 1u, abort_flag,
-                                      a.err, 7);
-            if (!__all_sync(0xffffffffu, wr)) break;
-            float2 v[16];
-            const unsigned char* stg0 = Raw + static_cast<uint32_t>(slot) * C::RAW_BYTES;
+                for (int c2 = 0; c2 < 16; ++c2) {
+                    const float4 v = *reinterpret_cast<const float4*>(stg + (srow ^ kaddr(2 * c2)));
+                    x[4 * c2] = v.x;
+                    x[4 * c2 + 1] = v.y;
+                    x[4 * c2 + 2] = v.z;
+                    x[4 * c2 + 3] = v.w;
+                }
+            } else {
 #pragma unroll
-            for (int c4 = 0; c4 < 16; ++c4) v[c4] = *reinterpret_cast<const float2*>(stg0 + (rslot ^ rd_slot[c4]));
-            mbar_arrive(bar(C::BAR_REMPTY + slot));
-            // refill the previous chunk's stage (every loader has read it by now)
-            if (idx >= 1 && idx - 1 + NR < total) {
-                const int ps = static_cast<int>((idx - 1) % NR);
-                const bool we = mbar_wait(bar(C::BAR_REMPTY + ps), static_cast<uint32_t>((idx - 1) / NR) & 1u,
-                                          abort_flag, a.err, 8);
-                if (!__all_sync(0xffffffffu, we)) break;
-                issue(idx - 1 + NR, ps);
+                for (int c = 0; c < 32; ++c) {
+                    const float2 v = *reinterpret_cast<const float2*>(stg + (srow ^ kaddr(c)));
+                    x[2 * c] = v.x;
+                    x[2 * c + 1] = v.y;
+                }
             }
-            const uint32_t b = static_cast<uint32_t>(idx & 1), f = static_cast<uint32_t>(idx >> 1);
-            // tcgen05.st is warp-collective: leave together if any lane gave up
-            const bool w = f < 1 || mbar_wait(bar(C::BAR_EMPTY + b), (f - 1) & 1, abort_flag, a.err, 1);
-            if (!__all_sync(0xffffffffu, w)) break;
-            tc_fence_after();
+            mbar_arrive(bar(BAR_REMPTY + s));   // the values are in registers: the stage may refill
+            if (i >= kNB) {
+                ok = mbar_wait(bar(BAR_BEMPTY + bb), static_cast<uint32_t>(i / kNB - 1) & 1u, abort_flag, a.err, 23,
+                               i);
+                if (!__all_sync(0xffffffffu, ok)) break;
+            }
+            unsigned char* Bhi = Bsm + static_cast<uint32_t>(bb) * kBBytes;
+            unsigned char* Blo = Bhi + kHalfB;
+            float mx = 0.f;
 #pragma unroll
-            for (int s16 = 0; s16 < 2; ++s16) {   // the chunk's 2 segments of 16 floats
-                const float2* x = v + 8 * s16;
+            for (int j = 0; j < 64; ++j) mx = fmaxf(mx, fabsf(x[j]));
+            const float magic = seg_magic<kSplitB>(mx);
+            // K = 64 h + 4 u16 + (0..3): K block 2 h + (u16 >> 3), 16-byte unit u16 & 7
+#pragma unroll
+            for (int u16 = 0; u16 < 16; ++u16) {
+                float4 hv, lv;
+                split_one(x[4 * u16], magic, hv.x, lv.x);
+                split_one(x[4 * u16 + 1], magic, hv.y, lv.y);
+                split_one(x[4 * u16 + 2], magic, hv.z, lv.z);
+                split_one(x[4 * u16 + 3], magic, hv.w, lv.w);
+                const uint32_t off = static_cast<uint32_t>(2 * h + (u16 >> 3)) * 4096u + brow +
+                                     ((static_cast<uint32_t>(u16 & 7) ^ bsw) << 4);
+                *reinterpret_cast<float4*>(Bhi + off) = hv;
+                *reinterpret_cast<float4*>(Blo + off) = lv;
+            }
+            fence_async_smem();   // the operand, visible to the tensor core
+            mbar_arrive(bar(BAR_BFULL + bb));
+        }
+    } else if (warp == kMmaWarp) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            bool ok = mbar_wait(bar(BAR_AREADY), 0, abort_flag, a.err, 24);
+            tc_fence_after();
+            const uint32_t b0 = smem_u32(Bsm);
+            for (uint64_t i = 0; i < my && ok; ++i) {
+                const int bb = static_cast<int>(i % kNB), d = static_cast<int>(i % kND);
+                if (!mbar_wait(bar(BAR_BFULL + bb), static_cast<uint32_t>(i / kNB) & 1u, abort_flag, a.err, 25, i))
+                    break;
+                if (i >= kND &&
+                    !mbar_wait(bar(BAR_DEMPTY + d), static_cast<uint32_t>(i / kND - 1) & 1u, abort_flag, a.err, 26, i))
+                    break;
+                tc_fence_after();
+                const uint32_t dm = tmem + COL_D + static_cast<uint32_t>(d) * D_COLS;
+                const uint32_t bhi = b0 + static_cast<uint32_t>(bb) * kBBytes, blo = bhi + kHalfB;
+#pragma unroll
+                for (int kk = 0; kk < 16; ++kk) {   // K-steps of 8
+                    const uint32_t boff = static_cast<uint32_t>(kk >> 2) * 4096u + 32u * static_cast<uint32_t>(kk & 3);
+                    const uint64_t dhi = sw128_desc(bhi + boff), dlo = sw128_desc(blo + boff);
+                    mma_tf32_ts(dm + 32u * static_cast<uint32_t>(kk >> 3), tmem + COL_AHI + 8u * kk, dhi, kIdesc,
+                                (kk & 7) != 0);
+                    mma_tf32_ts(dm + 64u, tmem + COL_AHI + 8u * kk, dlo, kIdesc, kk != 0);
+                    mma_tf32_ts(dm + 64u, tmem + COL_ALO + 8u * kk, dhi, kIdesc, 1);
+                }
+                mma_commit(bar(BAR_BEMPTY + bb));
+                mma_commit(bar(BAR_DFULL + d));
+            }
+            // drain: no MMA may be in flight when the CTA tears down
+            mma_commit(bar(BAR_FIN));
+            for (uint32_t it = 0; it < kWaitLimit; ++it)
+                if (mbar_try(bar(BAR_FIN), 0)) break;
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue (warps 4-7) ----------------
+        const int q = warp & 3;   // tensor-memory lane quarter
+        const uint32_t lane_t = tmem + (static_cast<uint32_t>(q * 32) << 16);
+        {
+            // A: row n = 32 q + lane of the embedding, hi and lo per K half
+            const int n = 32 * q + lane, nu = n >> 1, s = n & 1;
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                float x[64];
                 float mx = 0.f;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) mx = fmaxf(mx, fmaxf(fabsf(x[i].x), fabsf(x[i].y)));
-                const SegQuant sq = seg_quant(mx);
-                float h[16], l[16];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    split_one(x[i].x, sq, h[2 * i], l[2 * i]);
-                    split_one(x[i].y, sq, h[2 * i + 1], l[2 * i + 1]);
+                for (int j = 0; j < 64; ++j) {
+                    x[j] = a_entry(a, nu, 32 * h + (j >> 1), s, j & 1);
+                    mx = fmaxf(mx, fabsf(x[j]));
                 }
-                tmem_st16(lane_a + b * 64 + 16 * s16, h);
-                tmem_st16(lane_a + b * 64 + 32 + 16 * s16, l);
+                const float magic = seg_magic<kSplitA>(mx);
+                float hi[64], lo[64];
+#pragma unroll
+                for (int j = 0; j < 64; ++j) split_one(x[j], magic, hi[j], lo[j]);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    tmem_st16(lane_t + COL_AHI + 64u * h + 16u * c, hi + 16 * c);
+                    tmem_st16(lane_t + COL_ALO + 64u * h + 16u * c, lo + 16 * c);
+                }
             }
             tmem_st_wait();
             tc_fence_before();
-            mbar_arrive(bar(C::BAR_FULL + b));
+            mbar_arrive(bar(BAR_AREADY));
         }
-        cp_async_wait_all();   // no copy may land after the CTA has left
-    } else if (warp < 12) {
-        // ---------------- epilogue ----------------
-        const int qw = warp & 3;              // tensor-memory lane quarter
-        const int half = (warp - 4) >> 2;     // column half
-        const uint32_t lane_base = tmem + (static_cast<uint32_t>(qw * 32) << 16) + half * HALF;
-        // Store rounds: the outputs (g = 32 qw + lane, 8 combinations) of one
-        // round vary in the 5 lowest non-target local bits and in positions
-        // tls[0..2]; rank r numbers them in ascending local position.
-        float2* stg = stage + (warp - 4) * C::STAGE_ELEMS;
-        uint32_t tmask = 0;
+        uint64_t grow = 0;   // row `lane` within the chunk
 #pragma unroll
-        for (int j = 0; j < K; ++j) tmask |= 1u << a.tls[j];
-        uint32_t vmask = (1u << a.tls[0]) | (1u << a.tls[1]) | (1u << a.tls[2]);
-        uint32_t rank_g = 0;
-        {
-            int kb = 0;
-            for (int b = 0; b < 7 + K && kb < 5; ++b)
-                if (!((tmask >> b) & 1u)) {
-                    vmask |= 1u << b;
-                    ++kb;
-                }
-            kb = 0;
-            for (int b = 0; b < 7 + K && kb < 5; ++b)
-                if (!((tmask >> b) & 1u)) {
-                    rank_g |= ((static_cast<uint32_t>(lane) >> kb) & 1u) << __popc(vmask & ((1u << b) - 1u));
-                    ++kb;
-                }
-        }
-        const uint32_t rc0 = 1u << __popc(vmask & ((1u << a.tls[0]) - 1u));
-        const uint32_t rc1 = 1u << __popc(vmask & ((1u << a.tls[1]) - 1u));
-        const uint32_t rc2 = 1u << __popc(vmask & ((1u << a.tls[2]) - 1u));
-        // local position of rank bit q, and the global offset of each rank bit
-        auto goff1 = [&](uint32_t l) -> uint64_t { return (l & mmask) | runoff[l >> a.m]; };
-        uint64_t goL = 0, gb5 = 0, gb6 = 0, gb7 = 0;
-        {
-            int q = 0;
-            for (int b = 0; b < 7 + K; ++b)
-                if ((vmask >> b) & 1u) {
-                    const uint64_t gq = goff1(1u << b);
-                    if (q < 5 && ((lane >> q) & 1)) goL |= gq;
-                    if (q == 5) gb5 = gq;
-                    if (q == 6) gb6 = gq;
-                    if (q == 7) gb7 = gq;
-                    ++q;
-                }
-        }
-        // group bits above the lowest five (the lane-quarter index qw)
-        uint32_t lfix = static_cast<uint32_t>(qw) << 5;
-#pragma unroll
-        for (int j = 0; j < K; ++j) lfix = static_cast<uint32_t>(insert_zero(lfix, a.tls[j]));
-        uint64_t sc = 0;   // global segment counter (main buffers)
-        bool ok = true;
-        for (uint64_t i = 0; i < my_tiles && ok; ++i) {
-            float acc[HALF];
-#pragma unroll
-            for (int c = 0; c < HALF; ++c) acc[c] = 0.f;
-#pragma unroll 1
-            for (int s = 0; s < C::KSEGS; ++s, ++sc) {
-                const uint32_t mb = static_cast<uint32_t>(sc % NMAIN), mu = static_cast<uint32_t>(sc / NMAIN);
-                const bool w = mbar_wait(bar(C::BAR_MFULL + mb), mu & 1, abort_flag, a.err, 2);
-                // tcgen05.ld is warp-collective: leave together if any lane gave up
-                if (!__all_sync(0xffffffffu, w)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                uint32_t r[HALF];
-#pragma unroll
-                for (int h = 0; h < HALF / 32; ++h) tmem_ld32(lane_base + C::COL_MAIN + mb * NK + 32 * h, r + 32 * h);
-                tmem_ld_wait();
-                tc_fence_before();
-                mbar_arrive(bar(C::BAR_MEMPTY + mb));
-#pragma unroll
-                for (int c = 0; c < HALF; ++c) acc[c] += __uint_as_float(r[c]);
-            }
-            if (!ok) break;
-            const uint32_t d = static_cast<uint32_t>(i % NCORR), u = static_cast<uint32_t>(i / NCORR);
-            const bool w = mbar_wait(bar(C::BAR_CFULL + d), u & 1, abort_flag, a.err, 3);
-            if (!__all_sync(0xffffffffu, w)) break;
+        for (int b = 0; b < 5; ++b)
+            if ((lane >> b) & 1) grow |= a.gbit[a.rp[b]];
+        float* stg = reinterpret_cast<float*>(sm + OFF_STG + static_cast<uint32_t>(q) * kStgWarpBytes);
+        const float2* stg2 = reinterpret_cast<const float2*>(stg);
+        const uint32_t wslot = static_cast<uint32_t>(lane >> 1) * kStgPitch * 2u + static_cast<uint32_t>(lane & 1);
+        for (uint64_t i = 0; i < my; ++i) {
+            const int d = static_cast<int>(i % kND);
+            const bool ok =
+                mbar_wait(bar(BAR_DFULL + d), static_cast<uint32_t>(i / kND) & 1u, abort_flag, a.err, 27, i);
+            // tcgen05.ld is warp-collective: leave together if any lane gave up
+            if (!__all_sync(0xffffffffu, ok)) break;
             tc_fence_after();
-            {
-                uint32_t r[HALF];
+            uint32_t m0[32], m1[32], c[32];
+            const uint32_t dcol = lane_t + COL_D + static_cast<uint32_t>(d) * D_COLS;
+            tmem_ld32(dcol, m0);
+            tmem_ld32(dcol + 32u, m1);
+            tmem_ld32(dcol + 64u, c);
+            tmem_ld_wait();
+            tc_fence_before();
+            mbar_arrive(bar(BAR_DEMPTY + d));
+            // output part (lane & 1) of amplitude 16 q + (lane >> 1), rows 0..31
 #pragma unroll
-                for (int h = 0; h < HALF / 32; ++h) tmem_ld32(lane_base + C::COL_CORR + d * NK + 32 * h, r + 32 * h);
-                tmem_ld_wait();
-                tc_fence_before();
-                mbar_arrive(bar(C::BAR_CEMPTY + d));
-#pragma unroll
-                for (int c = 0; c < HALF; ++c) acc[c] += __uint_as_float(r[c]);
-            }
-            // Write-out in rounds of 8 combinations: the warp's 256 outputs of a
-            // round go through its shared staging area in tile-local index
-            // order, so each warp store covers consecutive addresses.
-            const uint64_t t = blockIdx.x + i * gridDim.x;
-            const uint64_t base = tc_tile_base(a, t);
-#pragma unroll
-            for (int rd = 0; rd < HALF / 16; ++rd) {
-#pragma unroll
-                for (int c3 = 0; c3 < 8; ++c3) {
-                    const int o = 8 * rd + c3;
-                    const uint32_t r = rank_g | ((c3 & 1) ? rc0 : 0u) | ((c3 & 2) ? rc1 : 0u) | ((c3 & 4) ? rc2 : 0u);
-                    stg[r + (r >> 5)] = make_float2(acc[2 * o], acc[2 * o + 1]);
-                }
-                __syncwarp();
-                const uint32_t lf = lfix | static_cast<uint32_t>(loff[half * (HALF / 2) + 8 * rd]);
-                float2* dst = a.psi + (base | (lf & mmask) | runoff[lf >> a.m]) + goL;
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const uint64_t off = ((j & 1) ? gb5 : 0ull) | ((j & 2) ? gb6 : 0ull) | ((j & 4) ? gb7 : 0ull);
-                    __stcs(dst + off, stg[33 * j + lane]);
-                }
-                __syncwarp();
-            }
+            for (int r = 0; r < 32; ++r)
+                stg[wslot + 2u * r] =
+                    __fadd_rn(__fadd_rn(__uint_as_float(m0[r]), __uint_as_float(m1[r])), __uint_as_float(c[r]));
+            __syncwarp();
+            // back out with lane = row: one warp store per output amplitude
+            const uint64_t base = chunk_base(a, blockIdx.x + i * gridDim.x) | grow;
+#pragma unroll 4
+            for (int j = 0; j < 16; ++j) __stcs(a.psi + (base | gnu_tab[16 * q + j]), stg2[j * kStgPitch + lane]);
+            __syncwarp();
         }
-    } else if (lane == 0) {
-        // ---------------- MMA issuer ----------------
-        const uint32_t bhi = smem_u32(Bhi), blo = smem_u32(Blo);
-        uint64_t cc = 0, sc = 0;
-        bool ok = true;
-        for (uint64_t i = 0; i < my_tiles && ok; ++i) {
-            const uint32_t d = static_cast<uint32_t>(i % NCORR), u = static_cast<uint32_t>(i / NCORR);
-            const uint32_t corr = tmem + C::COL_CORR + d * NK;
-            for (int j = 0; j < KC && ok; ++j, ++cc) {
-                const uint32_t b = static_cast<uint32_t>(cc & 1), f = static_cast<uint32_t>(cc >> 1);
-                if (!mbar_wait(bar(C::BAR_FULL + b), f & 1, abort_flag, a.err, 5)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t ahi = tmem + C::COL_A + b * 64, alo = ahi + 32;
-#pragma unroll
-                for (int s2 = 0; s2 < 2; ++s2, ++sc) {   // the chunk's two 16-value segments
-                    const uint32_t mb = static_cast<uint32_t>(sc % NMAIN), mu = static_cast<uint32_t>(sc / NMAIN);
-                    if (mu >= 1 && !mbar_wait(bar(C::BAR_MEMPTY + mb), (mu - 1) & 1, abort_flag, a.err, 6)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    // the segment's main partial first (exact in FP32), committed
-                    // before its correction products so the epilogue starts early
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int kk = 2 * s2 + h;
-                        const uint32_t boff = static_cast<uint32_t>(j) * C::B_REGION + 32 * kk;
-                        mma_tf32_ts(tmem + C::COL_MAIN + mb * NK, ahi + 8 * kk, sw128_desc(bhi + boff), C::IDESC, h);
-                    }
-                    mma_commit(bar(C::BAR_MFULL + mb));
-                    // the tile's first correction product overwrites the accumulator:
-                    // the epilogue must have read it for tile i - NCORR
-                    if (j == 0 && s2 == 0 && u >= 1) {
-                        if (!mbar_wait(bar(C::BAR_CEMPTY + d), (u - 1) & 1, abort_flag, a.err, 4)) {
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                    }
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int kk = 2 * s2 + h;
-                        const uint32_t boff = static_cast<uint32_t>(j) * C::B_REGION + 32 * kk;
-                        mma_tf32_ts(corr, alo + 8 * kk, sw128_desc(bhi + boff), C::IDESC, (j | kk) != 0);
-                        mma_tf32_ts(corr, ahi + 8 * kk, sw128_desc(blo + boff), C::IDESC, 1);
-                    }
-                }
-                if (!ok) break;
-                mma_commit(bar(C::BAR_EMPTY + b));
-            }
-            if (ok) mma_commit(bar(C::BAR_CFULL + d));
-        }
-        // drain: no MMA may be in flight when the CTA tears down
-        mma_commit(bar(C::BAR_FIN));
-        for (uint32_t it = 0; it < kWaitLimit; ++it)
-            if (mbar_try(bar(C::BAR_FIN), 0)) break;
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 12) {
+    if (warp == kMmaWarp) {
         tc_fence_after();
-        tmem_dealloc(tmem, C::TMEM_COLS);
+        tmem_dealloc(tmem, kTmemCols);
     }
 }
 
-template <int K>
-cudaError_t launch_tc_k(float2* psi, int n, const int* phys, const float* d_mat, int* d_err, cudaStream_t st,
-                        uint64_t* launches) {
-    using C = TcCfg<K>;
-    const int T = 7 + K;
-    TileGeom g;
-    if (n < T || !make_geom(n, phys, K, T, &g) || g.T != T) return cudaErrorInvalidValue;
-    TcArgs a{};
-    a.psi = psi;
-    a.mat = d_mat;
-    a.err = d_err;
-    a.ntiles = g.ntiles;
-    a.m = g.m;
-    a.nx = g.nx;
-    for (int e = 0; e < 6; ++e) a.xpos[e] = g.xpos[e];
-    for (int j = 0; j < K; ++j) {
-        int p = phys[j], loc = p;
-        if (p >= g.m) {
-            int e = 0;
-            while (g.xpos[e] != p) ++e;
-            loc = g.m + e;
+// Stage byte address contributions of the 11 chunk-local positions: element
+// l sits at 16-byte unit U = l >> 1 (byte 8 (l & 1) within it), in 128-byte
+// line U >> 3 at slot (U & 7) ^ f(U >> 3), f linear.  Lanes of a converter
+// warp differ in the row bits; f is chosen so that the row bits read
+// together (16 lanes of 8-byte reads, or 8 lanes of 16-byte reads when
+// position 0 is a K bit) land on distinct slots.
+void stage_layout(const int* rp, bool pair, uint32_t* sbit) {
+    uint32_t fvec[kChunkBits] = {};   // slot vector of line bit p - 4
+    const int first = pair ? 0 : 1;
+    uint32_t used = 0;
+    for (int b = first; b < first + 3; ++b)
+        if (rp[b] >= 1 && rp[b] <= 3) used |= 1u << (rp[b] - 1);
+    for (int b = first; b < first + 3; ++b)
+        if (rp[b] >= 4) {
+            int j = 0;
+            while ((used >> j) & 1u) ++j;
+            used |= 1u << j;
+            fvec[rp[b]] = 1u << j;
         }
-        a.tl[j] = loc;
-        a.tls[j] = loc;
+    for (int p = 0; p < kChunkBits; ++p) {
+        if (p == 0)
+            sbit[p] = 8u;
+        else if (p <= 3)
+            sbit[p] = 16u << (p - 1);
+        else
+            sbit[p] = (128u << (p - 4)) ^ (fvec[p] << 4);
     }
-    std::sort(a.tls, a.tls + K);
-    auto kern = k_apply_tc<K>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(C::SMEM));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTcThreads, C::SMEM);
+}
+
+template <bool PAIR>
+cudaError_t launch_pair(const TcArgs& a, uint64_t nchunks, cudaStream_t st, uint64_t* launches) {
+    auto kern = k_apply_tc<PAIR>;
+    cudaError_t e = set_smem_attr(reinterpret_cast<const void*>(kern), static_cast<int>(kSmem));
     if (e != cudaSuccess) return e;
-    if (occ < 1) return cudaErrorInvalidConfiguration;
-    // tensor memory: at most 512 columns per SM across resident CTAs
-    const int per_sm = std::min(occ, static_cast<int>(512 / C::TMEM_COLS));
-    uint64_t grid = static_cast<uint64_t>(num_sms()) * per_sm;
-    if (grid > g.ntiles) grid = g.ntiles;
-    kern<<<static_cast<unsigned>(grid), kTcThreads, C::SMEM, st>>>(a);
+    uint64_t grid = static_cast<uint64_t>(num_sms());   // one CTA per SM (all tensor memory)
+    if (grid > nchunks) grid = nchunks;
+    kern<<<static_cast<unsigned>(grid), kThreads, kSmem, st>>>(a);
     ++*launches;
     return cudaGetLastError();
 }
 
 }  // namespace
 
-bool tc_available(qsa_state s, int k) { return (k == 5 && s->n >= 12) || (k == 6 && s->n >= 13); }
+bool tc_available(qsa_state s, int k) { return (k == 5 || k == 6) && s->n >= kChunkBits; }
 
 cudaError_t launch_apply_tc(float2* psi, int n, const int* phys, int k, const float* d_mat, int* d_err,
                             cudaStream_t st, uint64_t* launches) {
-    if (k == 5) return launch_tc_k<5>(psi, n, phys, d_mat, d_err, st, launches);
-    if (k == 6) return launch_tc_k<6>(psi, n, phys, d_mat, d_err, st, launches);
-    return cudaErrorNotSupported;
+    if (k != 5 && k != 6) return cudaErrorNotSupported;
+    if (n < kChunkBits) return cudaErrorInvalidValue;
+    TileGeom g;
+    if (!make_geom(n, phys, k, kChunkBits, &g) || g.T != kChunkBits || g.m < 5) return cudaErrorInvalidValue;
+    TcArgs a{};
+    a.psi = psi;
+    a.mat = d_mat;
+    a.err = d_err;
+    a.nchunks = g.ntiles;
+    a.m = g.m;
+    a.nx = g.nx;
+    a.k = k;
+    for (int e = 0; e < 6; ++e) a.xpos[e] = g.xpos[e];
+    for (int p = 0; p < kChunkBits; ++p) a.gbit[p] = p < g.m ? (1ull << p) : (1ull << g.xpos[p - g.m]);
+    auto local_of = [&](int p) {
+        if (p < g.m) return p;
+        for (int e = 0; e < g.nx; ++e)
+            if (g.xpos[e] == p) return g.m + e;
+        return -1;
+    };
+    int tl[6], tls[6];
+    bool is_t[kChunkBits] = {};
+    for (int j = 0; j < k; ++j) {
+        tl[j] = local_of(phys[j]);
+        if (tl[j] < 0) return cudaErrorInvalidValue;
+        tls[j] = tl[j];
+        is_t[tl[j]] = true;
+    }
+    std::sort(tls, tls + k);
+    int np[kChunkBits], nn = 0;
+    for (int p = 0; p < kChunkBits; ++p)
+        if (!is_t[p]) np[nn++] = p;
+    for (int b = 0; b < k; ++b) {
+        a.kp[b] = tls[b];
+        for (int j = 0; j < k; ++j)
+            if (tl[j] == tls[b]) a.vbit[b] = j;
+    }
+    if (k == 5) {
+        a.kp[5] = np[5];
+        a.vbit[5] = 0;
+    }
+    for (int b = 0; b < 5; ++b) a.rp[b] = np[b];
+    const bool pair = tls[0] == 0;
+    stage_layout(a.rp, pair, a.sbit);
+    return pair ? launch_pair<true>(a, g.ntiles, st, launches) : launch_pair<false>(a, g.ntiles, st, launches);
 }
 
 }  // namespace qsa
