@@ -385,6 +385,37 @@ qsa_status qsa_plan_block_kinds(qsa_plan p, int32_t* kinds, int32_t* n_diag, siz
 qsa_status qsa_plan_promotions(qsa_plan p, const int32_t* layout_in, int victim, uint64_t* promotions,
                                uint64_t* passes, int32_t* layout_out);
 
+/* A state sharded over 2^rank_bits ranks (§IV-D, Alg. lazy-mpi): the highest
+ * rank_bits physical positions address the rank, rank R holding the slab of
+ * 2^(N - rank_bits) amplitudes whose rank bits equal R.  A block whose
+ * targets include a rank position needs that position swapped with a local
+ * one first: one exchange step.  For the swap of rank position P with local
+ * position l (j = P - (N - rank_bits)), rank R and its partner R ^ (1 << j)
+ * exchange the halves of their slabs whose bit l differs from bit j of their
+ * own rank index (2^(N - rank_bits - 1) amplitudes each way, written to the
+ * same local slots); afterwards the layout holds the swap (the lazy
+ * remapping of §IV-D, Eq. lazy-vol). */
+typedef struct {
+    uint64_t block;      /* the plan block the exchange precedes */
+    int32_t rank_pos;    /* physical rank position (>= N - rank_bits) */
+    int32_t local_pos;   /* physical local position (< N - rank_bits) it swaps with */
+} qsa_exchange;
+
+/* Host-only: the exchange steps of running plan p on 2^rank_bits ranks
+ * (rank_bits in 1..N-1) from layout_in (host, phys_of_logical; NULL =
+ * identity).  Every non-diagonal block (dense, product and layer blocks: the
+ * qubits of their factors) has its targets made local before it runs, the
+ * victim of each promotion chosen per `victim` (qsa_victim) among the local
+ * positions not holding a target of the block; diagonal blocks need no
+ * exchange (a rank knows its own rank bits).  Exchanges are listed in
+ * execution order in out[0..capacity) (host; nullable when capacity is 0),
+ * their count in *n_out; layout_out (host, N entries, nullable) receives the
+ * final layout.  No data moves and no device is touched.  Errors: QSA_E_ARG
+ * (NULL plan or n_out, rank_bits, layout, victim, a block wider than the
+ * local positions), QSA_E_RANGE (capacity < *n_out; *n_out is set). */
+qsa_status qsa_plan_exchanges(qsa_plan p, int rank_bits, const int32_t* layout_in, int victim, qsa_exchange* out,
+                              size_t capacity, size_t* n_out, int32_t* layout_out);
+
 /* Apply the plan's blocks to s in order (asynchronous unless opts.timing).
  * The first execution on a device uploads the fused matrices once
  * (stats->h2d_bytes).  Errors: QSA_E_ARG if the plan's N differs from s. */
@@ -504,6 +535,23 @@ qsa_status qsa_costmodel_set(const float* params);
  * QSA_E_STATE if none is installed. */
 qsa_status qsa_costmodel_predict(const float* features, size_t n, double* seconds_out);
 
+/* Write the process-wide model to the file `path`: the 8 bytes "QSACM001",
+ * the parameter count as a little-endian uint32 (6657), then the parameters
+ * as little-endian float32 in the layout above.  Errors: QSA_E_STATE when no
+ * model is installed, QSA_E_ARG when path is NULL or the file cannot be
+ * written. */
+qsa_status qsa_costmodel_save(const char* path);
+
+/* Read a model file written by qsa_costmodel_save.  s == NULL installs it
+ * process-wide (as qsa_costmodel_set); otherwise it is attached to s alone:
+ * qsa_apply_circuit on s plans QSA_PLAN_DP_MLP with it, while other states,
+ * qsa_plan_create and qsa_plan_circuit keep the process-wide model.  path ==
+ * NULL detaches the state's model (s != NULL) or removes the process-wide one
+ * (s == NULL).  The library keeps its own copy.  Errors: QSA_E_ARG for a file
+ * that cannot be read, has the wrong header or count, trailing bytes, or a
+ * non-finite parameter (nothing is changed then). */
+qsa_status qsa_costmodel_load(qsa_state s, const char* path);
+
 /* He-uniform initial parameters from a seed (host out). */
 qsa_status qsa_costmodel_init(uint64_t seed, float* params_host);
 
@@ -569,6 +617,20 @@ qsa_status qsa_costmodel_train(const float* X_host, const float* y_host, size_t 
 qsa_status qsa_sample_counts_noalloc(const void* dev_amplitudes, int n_qubits, const int32_t* phys_of_logical,
                                      uint64_t shots, uint64_t seed, uint64_t* out_outcomes_dev,
                                      uint64_t* out_counts_dev, uint64_t* out_n_distinct_dev, void* cuda_stream);
+
+/* ---- test hooks (host side) ------------------------------------------------
+ * Failure injection without any device fault: the nth device allocation the
+ * library makes from now on (0 = the next one) fails as if the device were
+ * out of memory, so callers see QSA_E_NOMEM and the error paths release what
+ * they had allocated; nth < 0 turns injection off.  The environment variable
+ * QSA_FAULT_ALLOC=<n> sets the same when the library is loaded.  Not
+ * thread-safe with respect to which allocation fails when several threads
+ * allocate. */
+qsa_status qsa_debug_fail_alloc(int64_t nth);
+
+/* Device allocations the library currently holds (states it allocated, plan
+ * and batch uploads, scratch): a leak check for the error paths. */
+uint64_t qsa_debug_live_allocations(void);
 
 const char* qsa_last_error(void);
 

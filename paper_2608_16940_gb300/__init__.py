@@ -369,6 +369,29 @@ def qsa_plan_promotions(p: int, n_qubits: int, victim: int, layout=None) -> Tupl
     return int(pr.value), int(ps.value), [int(v) for v in out]
 
 
+class qsa_exchange(_c.Structure):
+    _fields_ = [("block", _c.c_uint64), ("rank_pos", _c.c_int32), ("local_pos", _c.c_int32)]
+
+
+_f["qsa_plan_exchanges"] = _sig("qsa_plan_exchanges", [_vp, _c.c_int, _i32p, _c.c_int, _c.POINTER(qsa_exchange),
+                                                       _c.c_size_t, _szp, _i32p])
+
+
+def qsa_plan_exchanges(p: int, n_qubits: int, rank_bits: int, layout=None, victim: int = 0):
+    """(list of (block, rank_pos, local_pos), final layout) of running plan p
+    on 2^rank_bits ranks."""
+    n = n_qubits
+    lay = (_c.c_int32 * n)(*layout) if layout is not None else None
+    cnt = _c.c_size_t()
+    out_l = (_c.c_int32 * n)()
+    rc = _f["qsa_plan_exchanges"](_vp(p), rank_bits, lay, victim, None, 0, _c.byref(cnt), out_l)
+    if rc not in (QSA_OK, QSA_E_RANGE):
+        _check(rc)
+    buf = (qsa_exchange * max(1, cnt.value))()
+    _check(_f["qsa_plan_exchanges"](_vp(p), rank_bits, lay, victim, buf, cnt.value, _c.byref(cnt), out_l))
+    return [(int(buf[i].block), int(buf[i].rank_pos), int(buf[i].local_pos)) for i in range(cnt.value)], list(out_l)
+
+
 def qsa_plan_execute(s: int, p: int) -> dict:
     st = qsa_run_stats()
     _check(_f["qsa_plan_execute"](_vp(s), _vp(p), _c.byref(st)))
@@ -532,6 +555,29 @@ _f["qsa_costmodel_collect"] = _sig("qsa_costmodel_collect", [_vp, _c.c_size_t, _
                                                              _fp, _fp])
 _f["qsa_costmodel_train"] = _sig("qsa_costmodel_train", [_fp, _fp, _c.c_size_t, _c.c_int, _c.c_int, _c.c_float,
                                                          _c.c_float, _c.c_uint64, _fp, _fp])
+
+
+_f["qsa_costmodel_save"] = _sig("qsa_costmodel_save", [_c.c_char_p])
+_f["qsa_costmodel_load"] = _sig("qsa_costmodel_load", [_vp, _c.c_char_p])
+_f["qsa_debug_fail_alloc"] = _sig("qsa_debug_fail_alloc", [_c.c_int64])
+_f["qsa_debug_live_allocations"] = _sig("qsa_debug_live_allocations", [], _c.c_uint64)
+
+
+def qsa_costmodel_save(path: str) -> None:
+    _check(_f["qsa_costmodel_save"](os.fsencode(path)))
+
+
+def qsa_costmodel_load(s: Optional[int], path: Optional[str]) -> None:
+    """s = None: install process-wide; else attach to state s.  path = None removes."""
+    _check(_f["qsa_costmodel_load"](_vp(s) if s else None, os.fsencode(path) if path is not None else None))
+
+
+def qsa_debug_fail_alloc(nth: int) -> None:
+    _check(_f["qsa_debug_fail_alloc"](nth))
+
+
+def qsa_debug_live_allocations() -> int:
+    return int(_f["qsa_debug_live_allocations"]())
 
 
 def qsa_costmodel_init(seed: int) -> np.ndarray:

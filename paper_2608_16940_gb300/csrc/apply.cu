@@ -22,6 +22,9 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "qsa_device.cuh"
 #include "qsa_internal.h"
@@ -215,7 +218,9 @@ struct ApplyCfg;
 template <> struct ApplyCfg<1> { static constexpr int T = 11, R = 2, S = 3; };
 template <> struct ApplyCfg<2> { static constexpr int T = 11, R = 4, S = 3; };
 template <> struct ApplyCfg<3> { static constexpr int T = 11, R = 8, S = 3; };
-template <> struct ApplyCfg<4> { static constexpr int T = 11, R = 16, S = 3; };
+// k = 4: 2^12-amplitude tiles, so that a tile has one 16-row item per thread
+// (2^11 left half of the CTA idle in the compute phase)
+template <> struct ApplyCfg<4> { static constexpr int T = 12, R = 16, S = 3; };
 template <> struct ApplyCfg<5> { static constexpr int T = 12, R = 8, S = 2; };
 template <> struct ApplyCfg<6> { static constexpr int T = 12, R = 8, S = 2; };
 
@@ -254,14 +259,11 @@ cudaError_t launch_apply_k(float2* psi, int n, const int* phys, const float* d_m
     const size_t smem = sizeof(float2) * (static_cast<size_t>(C::S) << g.T) + sizeof(float2) * D * D +
                         sizeof(uint64_t) * 64 + sizeof(int) * 64;
     auto kern = k_apply_fp32<K, C::R, C::S>;
-    static int max_set = 0;
-    if (static_cast<int>(smem) > max_set) {
-        size_t full = sizeof(float2) * (static_cast<size_t>(C::S) << C::T) + sizeof(float2) * D * D +
-                      sizeof(uint64_t) * 64 + sizeof(int) * 64;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(full));
+    {
+        const size_t full = sizeof(float2) * (static_cast<size_t>(C::S) << C::T) + sizeof(float2) * D * D +
+                            sizeof(uint64_t) * 64 + sizeof(int) * 64;
+        cudaError_t e = set_smem_attr(reinterpret_cast<const void*>(kern), static_cast<int>(full));
         if (e != cudaSuccess) return e;
-        max_set = static_cast<int>(full);
     }
     int occ = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
@@ -578,14 +580,34 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch_evolve(BatchArgs a) {
 }  // namespace
 
 int num_sms() {
-    static int cached = 0;
-    if (!cached) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
-        if (cached <= 0) cached = 1;
-    }
-    return cached;
+    static std::mutex mu;
+    static std::map<int, int> cached;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cached.find(dev);
+    if (it != cached.end()) return it->second;
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    if (v <= 0) v = 1;
+    cached[dev] = v;
+    return v;
+}
+
+cudaError_t set_smem_attr(const void* kernel, int bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, int> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_pair(dev, kernel);
+    auto it = done.find(key);
+    if (it != done.end() && it->second >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    done[key] = bytes;
+    return cudaSuccess;
 }
 
 bool make_geom(int n, const int* special, int ns, int T_want, TileGeom* g) {
@@ -633,12 +655,9 @@ bool make_batch_block(int n, const int* phys, int k, uint32_t mat_off, BatchBloc
 cudaError_t launch_batch_evolve(const BatchArgs& a, cudaStream_t st, uint64_t* launches) {
     const size_t smem = sizeof(float2) * (static_cast<size_t>(kBatchS) << kBatchT) + sizeof(float2) * 256 +
                         sizeof(uint64_t) * 64 + sizeof(int) * 64;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_batch_evolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem));
+    {
+        cudaError_t e = set_smem_attr(reinterpret_cast<const void*>(k_batch_evolve), static_cast<int>(smem));
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     int occ = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_evolve, kThreads, smem);
@@ -723,14 +742,11 @@ cudaError_t launch_apply_prod(float2* psi, int n, const int* phys, int k, const 
         local_targets(g, phys + j0, a.k, a.tl, tls);
         const size_t smem = sizeof(float2) * (static_cast<size_t>(kProdS) << g.T) + sizeof(float2) * 4 * QSA_MAX_PROD +
                             sizeof(uint64_t) * 64;
-        static bool attr = false;
-        if (!attr) {
+        {
             const size_t full = sizeof(float2) * (static_cast<size_t>(kProdS) << kProdT) +
                                 sizeof(float2) * 4 * QSA_MAX_PROD + sizeof(uint64_t) * 64;
-            cudaError_t e = cudaFuncSetAttribute(k_apply_prod, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 static_cast<int>(full));
+            cudaError_t e = set_smem_attr(reinterpret_cast<const void*>(k_apply_prod), static_cast<int>(full));
             if (e != cudaSuccess) return e;
-            attr = true;
         }
         int occ = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_apply_prod, kThreads, smem);
@@ -796,13 +812,10 @@ cudaError_t launch_permute(float2* psi, int n, const int* pa, const int* pb, int
         }
         const size_t smem = sizeof(float2) * (static_cast<size_t>(S) << g.T) + sizeof(uint64_t) * 64;
         auto kern = k_permute<S>;
-        static bool attr = false;
-        if (!attr) {
-            size_t full = sizeof(float2) * (static_cast<size_t>(S) << T) + sizeof(uint64_t) * 64;
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 static_cast<int>(full));
+        {
+            const size_t full = sizeof(float2) * (static_cast<size_t>(S) << T) + sizeof(uint64_t) * 64;
+            cudaError_t e = set_smem_attr(reinterpret_cast<const void*>(kern), static_cast<int>(full));
             if (e != cudaSuccess) return e;
-            attr = true;
         }
         int occ = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);

@@ -99,12 +99,10 @@ cudaError_t launch_apply_diag(float2* psi, int n, const int* phys, int k, const 
     a.d = reinterpret_cast<const float2*>(d_tab);
     a.k = k;
     for (int j = 0; j < k; ++j) a.p[j] = phys[j];
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_apply_diag, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(diag_smem(QSA_MAX_DIAG)));
+    {
+        cudaError_t e = set_smem_attr(reinterpret_cast<const void*>(k_apply_diag),
+                                      static_cast<int>(diag_smem(QSA_MAX_DIAG)));
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     const size_t sm = diag_smem(k);
     int occ = 0;

@@ -85,6 +85,9 @@ struct LayerArgs {
     const float2* qph;        // rotation mode: each tile bit's entry phases q (kLT x 2)
     const float2* rp;         // rotation mode: per round, the product of its factor bits' exit
                               // phases p over the round's 16 local amplitudes (3 x 16)
+    const float2* sph;        // rotation mode without per-tile phases: per round, the product of
+                              // its bits' entry phases q (3 x 16, the LayerRec layout), formed on
+                              // the host
     const LayerRec* rec;      // rotation mode with per-tile phases: one record per tile, or nullptr
 };
 
@@ -412,13 +415,8 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
     if (ROT) {
         if (threadIdx.x < kLT) rot[threadIdx.x] = a.fac[threadIdx.x];
         for (int i = threadIdx.x; i < 48; i += blockDim.x) sh.rp[i >> 4][i & 15] = a.rp[i];
-        if (!dynamic && threadIdx.x < 32) {
-            // static phases: the rotations' entry phases only
-            const int lane = threadIdx.x;
-            const float2 d0 = lane < kLT ? a.qph[2 * lane] : make_float2(1.f, 0.f);
-            const float2 d1 = lane < kLT ? a.qph[2 * lane + 1] : make_float2(1.f, 0.f);
-            phase_tables(a.pmask, d0, d1, make_float2(1.f, 0.f), &sh.ph);
-        }
+        if (!dynamic)   // static phases: the rotations' entry phases only, tables from the host
+            for (int i = threadIdx.x; i < 48; i += blockDim.x) reinterpret_cast<float2*>(&sh.ph)[i] = a.sph[i];
     } else if (!dynamic) {
         for (int i = threadIdx.x; i < 4 * kLT; i += blockDim.x) sh.tf[i >> 2][i & 3] = a.fac[i];
     }
@@ -550,6 +548,7 @@ bool layer_args(float2* psi, int n, const LayerGeom& g, const unsigned char* d_p
     a.din = p.has_din ? reinterpret_cast<const float2*>(d_payload + p.off_din) : nullptr;
     a.qph = reinterpret_cast<const float2*>(d_payload + p.off_qph);
     a.rp = reinterpret_cast<const float2*>(d_payload + p.off_rp);
+    a.sph = reinterpret_cast<const float2*>(d_payload + p.off_sph);
     return true;
 }
 
@@ -576,17 +575,14 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
     LayerArgs a;
     if (!layer_args(psi, n, g, d_payload, p, &a)) return cudaErrorInvalidValue;
     const size_t smem = layer_smem_bytes(p.has_din);
-    static bool attr_set = false;
-    if (!attr_set) {
+    {
         for (auto kern : {k_apply_layer<true, 0, 0, 0, 0>, k_apply_layer<true, 0, 1, 0, 0>, k_apply_layer<true, 1, 0, 0, 0>,
                           k_apply_layer<true, 1, 1, 0, 0>, k_apply_layer<true, 0, 0, 2, 0>, k_apply_layer<true, 0, 1, 2, 0>,
                           k_apply_layer<true, 1, 0, 2, 0>, k_apply_layer<true, 1, 1, 2, 0>, k_apply_layer<true, 2, 2, 2, 1>,
                           k_apply_layer<false, 2, 2, 2, 2>}) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 static_cast<int>(layer_smem_bytes(true)));
+            cudaError_t e = set_smem_attr(reinterpret_cast<const void*>(kern), static_cast<int>(layer_smem_bytes(true)));
             if (e != cudaSuccess) return e;
         }
-        attr_set = true;
     }
     if (needs_records(p)) {
         if (!d_rec) return cudaErrorInvalidValue;

@@ -5,7 +5,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
+#include <limits>
 #include <vector>
 
 #include "qsa.h"
@@ -60,6 +62,10 @@ size_t append(std::vector<unsigned char>* b, const T* data, size_t count) {
 
 float2 f2(std::complex<double> z) { return make_float2(static_cast<float>(z.real()), static_cast<float>(z.imag())); }
 
+float2 f2m(std::complex<double> z, double weight, ModulusCarry* carry) {
+    return f2_modulus(z, std::norm(z), weight, carry);
+}
+
 // F = diag(p) [[c, -s], [s, c]] diag(q) with q[0] = 1, c = |F00|, s = |F01|;
 // false unless the product reproduces F to 1e-10 (a unitary F does).
 bool split_rotation(const std::array<std::complex<double>, 4>& F, double* c, double* s, std::complex<double>* p,
@@ -95,7 +101,7 @@ bool rotation_cotangent(double c, double s) { return s > c; }
 // One pass: factors fsel (indices into spec.f), the diagonal ops if with_diag.
 // Returns false when there is nothing to apply.
 bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vector<int>& fsel, bool with_diag,
-                  std::vector<unsigned char>* bytes, LayerLaunch* out) {
+                  std::vector<unsigned char>* bytes, LayerLaunch* out, ModulusCarry* carry) {
     std::vector<int> pos;
     for (int j : fsel) pos.push_back(L[spec.t[j]]);
     LayerGeom g;
@@ -161,14 +167,15 @@ bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vec
                 G.a = first_in ? b0 : b1;
                 G.b = first_in ? p1 : p0;
                 for (int o = 0; o < 2; ++o)
-                    for (int v = 0; v < 2; ++v) G.d[2 * o + v] = f2(op.d[first_in ? (v | (o << 1)) : (o | (v << 1))]);
+                    for (int v = 0; v < 2; ++v)
+                        G.d[2 * o + v] = f2m(op.d[first_in ? (v | (o << 1)) : (o | (v << 1))], 0.25, carry);
                 cross.push_back(G);
                 cross_bits |= 1u << G.a;
             } else {
                 LayerGate G{};
                 G.a = p0;
                 G.b = p1;
-                for (int c = 0; c < (1 << op.k); ++c) G.d[c] = f2(op.d[c]);
+                for (int c = 0; c < (1 << op.k); ++c) G.d[c] = f2m(op.d[c], 1.0 / (1 << op.k), carry);
                 outg.push_back(G);
             }
         }
@@ -177,12 +184,21 @@ bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vec
     if (p.active == 0 && p.pmask == 0 && outg.empty() && din.empty()) return false;
     // rotation mode: each bit's q phases; per round, the product of its bits' p phases
     std::vector<float2> qph(2 * kTile, make_float2(1.f, 0.f)), rpt(48, make_float2(1.f, 0.f));
+    // with no per-tile phases the pass multiplies by per-round products of the q phases,
+    // the same for every tile: formed here in FP64 and rounded as the pass's constants
+    const bool static_tables = p.rotation && cross.empty() && outg.empty();
+    std::vector<float2> sph(48, make_float2(1.f, 0.f));
     p.rpmask = 0;
     if (p.rotation) {
         for (int b = 0; b < kTile; ++b)
             if ((p.active >> b) & 1u) {
-                qph[2 * b] = f2(rq[b][0]);
-                qph[2 * b + 1] = f2(rq[b][1]);
+                // the pass scales by |q|^2 (1 + t^2) with t as rounded: aim q's
+                // modulus at the exact rotation's |q|^2 (1 + t^2) over (1 + t_f^2)
+                const double tf = static_cast<float>(rcoef[b]);
+                const double scale = (1.0 + rcoef[b] * rcoef[b]) / (1.0 + tf * tf);
+                qph[2 * b] = f2_modulus(rq[b][0], std::norm(rq[b][0]) * scale, 0.5, static_tables ? nullptr : carry);
+                qph[2 * b + 1] =
+                    f2_modulus(rq[b][1], std::norm(rq[b][1]) * scale, 0.5, static_tables ? nullptr : carry);
             }
         for (int r = 0; r < 3; ++r)
             for (int i = 0; i < 16; ++i) {
@@ -191,9 +207,23 @@ bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vec
                 std::complex<double> z = 1.0;
                 for (int lb = 0; lb < 4; ++lb)
                     if ((p.active >> (4 * r + lb)) & 1u) z *= rp[4 * r + lb][(li >> lb) & 1];
-                rpt[16 * r + i] = f2(z);
+                rpt[16 * r + i] = f2m(z, 1.0 / 16, carry);
                 if (std::abs(z - 1.0) > 1e-15) p.rpmask |= 1u << r;
             }
+        if (static_tables)
+            for (int r = 0; r < 3; ++r)
+                for (int i = 0; i < 16; ++i) {
+                    std::complex<double> z = 1.0;
+                    double m2 = 1.0;
+                    for (int lb = 0; lb < 4; ++lb) {
+                        const int b = 4 * r + lb, v = (i >> lb) & 1;
+                        if (!((p.pmask >> b) & 1u)) continue;
+                        const double tf = static_cast<float>(rcoef[b]);
+                        z *= rq[b][v];
+                        m2 *= std::norm(rq[b][v]) * (1.0 + rcoef[b] * rcoef[b]) / (1.0 + tf * tf);
+                    }
+                    sph[16 * r + i] = f2_modulus(z, m2, 1.0 / 16, carry);
+                }
     }
     std::stable_sort(cross.begin(), cross.end(), [](const LayerGate& x, const LayerGate& y) { return x.a < y.a; });
     p.ncross = static_cast<int>(cross.size());
@@ -214,11 +244,12 @@ bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vec
     p.off_fac = append(bytes, facf.data(), facf.size()) - base;
     p.off_qph = append(bytes, qph.data(), qph.size()) - base;
     p.off_rp = append(bytes, rpt.data(), rpt.size()) - base;
+    p.off_sph = append(bytes, sph.data(), sph.size()) - base;
     p.off_cross = append(bytes, cross.data(), cross.size()) - base;
     p.off_out = append(bytes, outg.data(), outg.size()) - base;
     if (!din.empty()) {
         std::vector<float2> df(din.size());
-        for (size_t j = 0; j < din.size(); ++j) df[j] = f2(din[j]);
+        for (size_t j = 0; j < din.size(); ++j) df[j] = f2m(din[j], 1.0 / (1u << kTile), carry);
         p.off_din = append(bytes, df.data(), df.size()) - base;
         p.has_din = true;
     }
@@ -231,6 +262,55 @@ bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vec
 }
 
 }  // namespace
+
+// Modulus-faithful rounding of the FP32 constants of a plan.  A constant (a
+// gate phase, a phase-table entry, an entry phase) multiplies a large share
+// of the state, so the modulus error of its rounding changes the norm
+// systematically, and circuits that repeat an angle (a QAOA round applies the
+// same ZZ phase to every edge) add those errors coherently.  The candidates
+// are the nine FP32 numbers one ulp or less from the rounded real and
+// imaginary parts (the direction moves by at most about an ulp: a phase
+// error, second order in the fidelity).  With a carry the choice is error
+// feedback: the candidate whose weighted modulus error brings the carry
+// nearest zero, so repeated constants alternate between values just above
+// and just below the exact modulus and their errors cancel instead of adding
+// up (weight = the share of the state's indices the constant multiplies).
+// Without a carry: the smallest modulus error.  Ties go to the smaller error,
+// then to the candidate nearer z.
+float2 f2_modulus(std::complex<double> z, double m2, double weight, ModulusCarry* carry) {
+    constexpr float kInf = std::numeric_limits<float>::infinity();
+    const float r0 = static_cast<float>(z.real()), i0 = static_cast<float>(z.imag());
+    const float rs[3] = {std::nextafter(r0, -kInf), r0, std::nextafter(r0, kInf)};
+    const float is[3] = {std::nextafter(i0, -kInf), i0, std::nextafter(i0, kInf)};
+    const double acc = carry ? carry->acc : 0.0;
+    float best_r = r0, best_i = i0;
+    double bk = 0.0, be = 0.0, bd = 0.0;
+    bool first = true;
+    for (const float r : rs)
+        for (const float i : is) {
+            const double e = static_cast<double>(r) * r + static_cast<double>(i) * i - m2;
+            const double key = std::fabs(acc + weight * e), d = std::norm(std::complex<double>(r, i) - z);
+            if (first || key < bk || (key == bk && (std::fabs(e) < std::fabs(be) || (std::fabs(e) == std::fabs(be) && d < bd)))) {
+                first = false;
+                bk = key;
+                be = e;
+                bd = d;
+                best_r = r;
+                best_i = i;
+            }
+        }
+    if (carry) carry->acc += weight * be;
+    return make_float2(best_r, best_i);
+}
+
+void to_float_moduli(const double* z, size_t count, float* out, double weight, ModulusCarry* carry) {
+    for (size_t i = 0; i < count; ++i) {
+        const std::complex<double> v(z[2 * i], z[2 * i + 1]);
+        const float2 f = f2_modulus(v, std::norm(v), weight, carry);
+        out[2 * i] = f.x;
+        out[2 * i + 1] = f.y;
+    }
+}
 
 void layer_move_exit_phases(LayerSpec* from, LayerSpec* to) {
     std::vector<LayerDiagOp> moved;
@@ -263,7 +343,7 @@ bool layer_fits(int n, const int* pos, int k) {
 }
 
 std::vector<LayerLaunch> prepare_layer(int n, const int32_t* L, const LayerSpec& spec,
-                                       std::vector<unsigned char>* bytes) {
+                                       std::vector<unsigned char>* bytes, ModulusCarry* carry) {
     std::vector<LayerLaunch> out;
     if (n < kTile) return out;
     // factor groups that fit a tile, in target order
@@ -280,7 +360,7 @@ std::vector<LayerLaunch> prepare_layer(int n, const int32_t* L, const LayerSpec&
     }
     for (size_t i = 0; i < groups.size(); ++i) {
         LayerLaunch ll;
-        if (prepare_pass(n, L, spec, groups[i], i == 0, bytes, &ll)) {
+        if (prepare_pass(n, L, spec, groups[i], i == 0, bytes, &ll, carry)) {
             // only the first pass generates; later ones read what it wrote
             ll.p.generate = spec.generate && out.empty();
             out.push_back(ll);

@@ -252,7 +252,7 @@ qsa_status qsa_costmodel_train(const float* X_host, const float* y_host, size_t 
     cudaStream_t st = nullptr;
     cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     auto A = [&](float** p, size_t cnt) {
-        if (e == cudaSuccess) e = cudaMalloc(p, sizeof(float) * cnt);
+        if (e == cudaSuccess) e = dev_malloc(p, sizeof(float) * cnt);
     };
     A(&dX, n * IN);
     A(&dY, n);
@@ -309,7 +309,7 @@ qsa_status qsa_costmodel_train(const float* X_host, const float* y_host, size_t 
     if (e == cudaSuccess) e = cudaMemcpyAsync(params_inout_host, dP, sizeof(float) * np, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     for (float* p : {dX, dY, dP, dG, dM, dV, dWs, dLoss, dXb, dYb, dOut})
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
     if (st) cudaStreamDestroy(st);
     // fold the standardisation back into the output layer (also on failure,
     // so the caller's parameters keep their meaning)

@@ -63,6 +63,7 @@ double gamma_score(void*, int width, bool diag, bool prod, uint64_t) {
 struct MlpCtx {
     int n;
     const int32_t* L;
+    const CostParams* P;
     std::unordered_map<uint64_t, double> cache;
 };
 
@@ -75,8 +76,8 @@ double mlp_score(void* ctx, int width, bool diag, bool prod, uint64_t mask) {
     uint64_t pm = 0;
     for (int q = 0; q < c->n; ++q)
         if ((mask >> q) & 1) pm |= 1ull << c->L[q];
-    const double v = diag ? costmodel_predict_seconds(1, pm & (~pm + 1), c->n, 1)
-                          : costmodel_predict_seconds(width, pm, c->n, 1);
+    const double v = diag ? costmodel_eval(*c->P, 1, pm & (~pm + 1), c->n, 1)
+                          : costmodel_eval(*c->P, width, pm, c->n, 1);
     c->cache[key] = v;
     return v;
 }
@@ -344,13 +345,13 @@ size_t zero_init_prefix(const qsa_op* ops, size_t n_ops) {
 // pre-pass moved ops), then the planner; with opts.zero_init the zero-state
 // prefix is one unit ahead of the rest.
 std::vector<Unit> plan(const qsa_op* ops, size_t n_ops, int n_qubits, const qsa_plan_opts& o, const int32_t* L,
-                       std::vector<size_t>* order) {
+                       std::vector<size_t>* order, const CostModel& model) {
     const size_t P = o.zero_init ? zero_init_prefix(ops, n_ops) : 0;
     if (P > 0) {
         qsa_plan_opts rest_opts = o;
         rest_opts.zero_init = 0;
         std::vector<size_t> rest_order;
-        std::vector<Unit> rest = plan(ops + P, n_ops - P, n_qubits, rest_opts, L, &rest_order);
+        std::vector<Unit> rest = plan(ops + P, n_ops - P, n_qubits, rest_opts, L, &rest_order, model);
         order->clear();
         for (size_t i = 0; i < P; ++i) order->push_back(i);
         for (size_t x : rest_order) order->push_back(x + P);
@@ -402,9 +403,9 @@ std::vector<Unit> plan(const qsa_op* ops, size_t n_ops, int n_qubits, const qsa_
     if (o.planner == QSA_PLAN_PER_GATE) return gates;
     if (o.planner == QSA_PLAN_GREEDY) return greedy(gates, o.kmax);
     if (o.planner == QSA_PLAN_DP_MLP) {
-        if (!costmodel_loaded()) return greedy(gates, o.kmax);
+        if (!model) return greedy(gates, o.kmax);   // no network: the width-limit heuristic
         if (!L) L = ident;
-        MlpCtx ctx{n_qubits, L, {}};
+        MlpCtx ctx{n_qubits, L, model.get(), {}};
         return dp_pipeline(gates, o, mlp_score, &ctx);
     }
     return dp_pipeline(gates, o, gamma_score, nullptr);
@@ -531,7 +532,7 @@ qsa_status qsa_plan_circuit(const qsa_op* ops, size_t n_ops, int n_qubits, const
     st = validate_ops(ops, n_ops, n_qubits);
     if (st != QSA_OK) return st;
     std::vector<size_t> order;
-    auto blocks = plan(ops, n_ops, n_qubits, o, nullptr, &order);
+    auto blocks = plan(ops, n_ops, n_qubits, o, nullptr, &order, costmodel_global());
     for (size_t i = 0; i < blocks.size(); ++i) block_start[i] = blocks[i].s;
     *n_blocks = blocks.size();
     return QSA_OK;
@@ -554,6 +555,15 @@ qsa_status qsa_fuse_ops(const qsa_op* ops, size_t n_ops, int32_t* block_targets_
 
 qsa_status qsa_plan_create(const qsa_op* ops, size_t n_ops, int n_qubits, const qsa_plan_opts* opts,
                            const int32_t* layout, qsa_plan* out) {
+    return plan_create(ops, n_ops, n_qubits, opts, layout, costmodel_global(), out);
+}
+
+}  // extern "C"
+
+namespace qsa {
+
+qsa_status plan_create(const qsa_op* ops, size_t n_ops, int n_qubits, const qsa_plan_opts* opts,
+                       const int32_t* layout, const CostModel& model, qsa_plan* out) {
     if (!out) return fail(QSA_E_ARG, "out is NULL");
     *out = nullptr;
     if (n_qubits < 1 || n_qubits > QSA_MAX_QUBITS) return fail(QSA_E_ARG, "n_qubits must be in 1..34");
@@ -576,13 +586,14 @@ qsa_status qsa_plan_create(const qsa_op* ops, size_t n_ops, int n_qubits, const 
     p->n_ops = n_ops;
     p->L0.resize(n_qubits);
     for (int q = 0; q < n_qubits; ++q) p->L0[q] = layout ? layout[q] : q;
-    auto blocks = plan(ops, n_ops, n_qubits, o, layout, &p->order);
+    auto blocks = plan(ops, n_ops, n_qubits, o, layout, &p->order, model);
     // the ops in execution order
     std::vector<qsa_op> perm(n_ops);
     for (size_t i = 0; i < n_ops; ++i) perm[i] = ops[p->order[i]];
     ops = perm.data();
     p->blocks.resize(blocks.size());
     std::vector<double> M;
+    ModulusCarry carry;   // modulus errors of the plan's FP32 constants (error feedback)
     for (size_t i = 0; i < blocks.size(); ++i) {
         const Unit& u = blocks[i];
         PlanBlock& b = p->blocks[i];
@@ -704,7 +715,8 @@ qsa_status qsa_plan_create(const qsa_op* ops, size_t n_ops, int n_qubits, const 
                 return st;
             }
             p->host_mat.resize(b.off + M.size());
-            for (size_t j = 0; j < M.size(); ++j) p->host_mat[b.off + j] = static_cast<float>(M[j]);
+            to_float_moduli(M.data(), M.size() / 2, p->host_mat.data() + b.off, 1.0 / static_cast<double>(M.size() / 2),
+                            &carry);
         } else if (u.e - u.s == 1) {
             const qsa_op& op = ops[u.s];
             b.k = op.k;
@@ -746,11 +758,16 @@ qsa_status qsa_plan_create(const qsa_op* ops, size_t n_ops, int n_qubits, const 
     for (size_t i = 0; i + 1 < p->blocks.size(); ++i)
         if (p->blocks[i].layer >= 0 && p->blocks[i + 1].layer >= 0)
             layer_move_exit_phases(&p->layers[p->blocks[i].layer].spec, &p->layers[p->blocks[i + 1].layer].spec);
-    for (PlanLayer& pl : p->layers) pl.launches = prepare_layer(n_qubits, p->L0.data(), pl.spec, &p->host_layer);
+    for (PlanLayer& pl : p->layers)
+        pl.launches = prepare_layer(n_qubits, p->L0.data(), pl.spec, &p->host_layer, &carry);
     build_next_use(p);
     *out = p;
     return QSA_OK;
 }
+
+}  // namespace qsa
+
+extern "C" {
 
 qsa_status qsa_plan_promotions(qsa_plan p, const int32_t* layout_in, int victim, uint64_t* promotions,
                                uint64_t* passes, int32_t* layout_out) {
@@ -789,6 +806,57 @@ qsa_status qsa_plan_promotions(qsa_plan p, const int32_t* layout_in, int victim,
     if (promotions) *promotions = pr;
     if (passes) *passes = ps;
     if (layout_out) std::memcpy(layout_out, L, sizeof(int32_t) * n);
+    return QSA_OK;
+}
+
+qsa_status qsa_plan_exchanges(qsa_plan p, int rank_bits, const int32_t* layout_in, int victim, qsa_exchange* out,
+                              size_t capacity, size_t* n_out, int32_t* layout_out) {
+    if (!p || !n_out) return fail(QSA_E_ARG, "NULL argument");
+    if (victim < 0 || victim > 1) return fail(QSA_E_ARG, "unknown victim rule");
+    const int n = p->n;
+    if (rank_bits < 1 || rank_bits >= n) return fail(QSA_E_ARG, "rank_bits must be in 1..N-1");
+    const int local = n - rank_bits;
+    int32_t L[QSA_MAX_QUBITS];
+    uint64_t seen = 0;
+    for (int q = 0; q < n; ++q) {
+        L[q] = layout_in ? layout_in[q] : q;
+        if (L[q] < 0 || L[q] >= n || ((seen >> L[q]) & 1)) return fail(QSA_E_ARG, "layout is not a bijection");
+        seen |= 1ull << L[q];
+    }
+    // next use of each logical qubit by a block that needs its qubits local
+    // (every block but the diagonal ones: a rank fixes its own rank bits)
+    const size_t B = p->blocks.size();
+    std::vector<int32_t> next(B * static_cast<size_t>(n), INT32_MAX), cur(n, INT32_MAX);
+    for (size_t i = B; i-- > 0;) {
+        std::copy(cur.begin(), cur.end(), next.begin() + i * n);
+        const PlanBlock& b = p->blocks[i];
+        if (!b.diag)
+            for (int j = 0; j < b.k; ++j) cur[b.t[j]] = static_cast<int32_t>(i);
+    }
+    size_t cnt = 0;
+    for (size_t i = 0; i < B; ++i) {
+        const PlanBlock& b = p->blocks[i];
+        if (b.diag) continue;
+        if (b.k > local) return fail(QSA_E_ARG, "a block is wider than the local positions of a rank");
+        int phys[QSA_MAX_DIAG], pa[QSA_MAX_DIAG], pb[QSA_MAX_DIAG];
+        for (int j = 0; j < b.k; ++j) phys[j] = L[b.t[j]];
+        const int np = choose_promotions(L, n, phys, b.k, local, victim, next.data() + i * n, pa, pb);
+        if (np < 0) return fail(QSA_E_ARG, "not enough free local positions");
+        for (int m = 0; m < np; ++m) {
+            if (out && cnt < capacity) out[cnt] = qsa_exchange{static_cast<uint64_t>(i), pa[m], pb[m]};
+            ++cnt;
+            int qa = -1, qb = -1;
+            for (int q = 0; q < n; ++q) {
+                if (L[q] == pa[m]) qa = q;
+                if (L[q] == pb[m]) qb = q;
+            }
+            L[qa] = pb[m];
+            L[qb] = pa[m];
+        }
+    }
+    *n_out = cnt;
+    if (layout_out) std::memcpy(layout_out, L, sizeof(int32_t) * n);
+    if (cnt > capacity) return fail(QSA_E_RANGE, "capacity smaller than the number of exchanges");
     return QSA_OK;
 }
 
@@ -832,8 +900,8 @@ qsa_status qsa_plan_block_kinds(qsa_plan p, int32_t* kinds, int32_t* n_diag, siz
 qsa_status qsa_plan_destroy(qsa_plan p) {
     if (!p) return fail(QSA_E_ARG, "plan is NULL");
     if (p->d_mat || p->d_layer) cudaDeviceSynchronize();
-    if (p->d_mat) cudaFree(p->d_mat);
-    if (p->d_layer) cudaFree(p->d_layer);
+    if (p->d_mat) dev_free(p->d_mat);
+    if (p->d_layer) dev_free(p->d_layer);
     delete p;
     return QSA_OK;
 }
@@ -853,17 +921,17 @@ qsa_status qsa_plan_execute(qsa_state s, qsa_plan p, qsa_run_stats* stats) {
         // first execution on this device: upload the fused matrices and the
         // layer payloads once
         if (p->d_mat || p->d_layer) cudaStreamSynchronize(s->stream);
-        if (p->d_mat) cudaFree(p->d_mat);
-        if (p->d_layer) cudaFree(p->d_layer);
+        if (p->d_mat) dev_free(p->d_mat);
+        if (p->d_layer) dev_free(p->d_layer);
         p->d_mat = nullptr;
         p->d_layer = nullptr;
         const size_t bytes = p->host_mat.size() * sizeof(float);
         const size_t lbytes = p->host_layer.size();
-        cudaError_t e = bytes ? cudaMalloc(&p->d_mat, bytes) : cudaSuccess;
-        if (e == cudaSuccess && lbytes) e = cudaMalloc(&p->d_layer, lbytes);
+        cudaError_t e = bytes ? dev_malloc(&p->d_mat, bytes) : cudaSuccess;
+        if (e == cudaSuccess && lbytes) e = dev_malloc(&p->d_layer, lbytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            if (p->d_mat) cudaFree(p->d_mat);
+            if (p->d_mat) dev_free(p->d_mat);
             p->d_mat = nullptr;
             p->d_layer = nullptr;
             return fail(QSA_E_NOMEM, "cudaMalloc of plan matrices failed");
@@ -943,14 +1011,14 @@ qsa_status qsa_apply_circuit(qsa_state s, const qsa_op* ops, size_t n_ops, const
     qsa_status st = check_state(s);
     if (st != QSA_OK) return st;
     qsa_plan p = nullptr;
-    st = qsa_plan_create(ops, n_ops, s->n, opts, s->L, &p);
+    st = plan_create(ops, n_ops, s->n, opts, s->L, s->cm ? s->cm : costmodel_global(), &p);
     if (st != QSA_OK) return st;
     st = qsa_plan_execute(s, p, stats);
     if (p->d_mat || p->d_layer) {
         // free after the stream has consumed the matrices
         cudaStreamSynchronize(s->stream);
-        if (p->d_mat) cudaFree(p->d_mat);
-        if (p->d_layer) cudaFree(p->d_layer);
+        if (p->d_mat) dev_free(p->d_mat);
+        if (p->d_layer) dev_free(p->d_layer);
         p->d_mat = nullptr;
         p->d_layer = nullptr;
     }
@@ -997,7 +1065,7 @@ namespace {
 void batch_free_device(qsa_batch b) {
     for (void* p : {static_cast<void*>(b->d_blocks), static_cast<void*>(b->d_bstart), static_cast<void*>(b->d_order),
                     static_cast<void*>(b->d_mats), static_cast<void*>(b->d_queue), static_cast<void*>(b->d_out)})
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
@@ -1059,7 +1127,7 @@ qsa_status qsa_batch_create(int n_qubits, int n_traj, const qsa_op* ops, const s
         const qsa_op* tops = ops + op_offsets[t];
         const size_t cnt = op_offsets[t + 1] - op_offsets[t];
         std::vector<size_t> order;   // the identity: batches take no layer units
-        auto units = plan(tops, cnt, n_qubits, o, nullptr, &order);
+        auto units = plan(tops, cnt, n_qubits, o, nullptr, &order, costmodel_global());
         for (const Unit& u : units) {
             int32_t tg[QSA_MAX_K];
             int k = 0;
@@ -1099,14 +1167,14 @@ qsa_status qsa_batch_create(int n_qubits, int n_traj, const qsa_op* ops, const s
     cudaError_t e = cudaSuccess;
     auto up = [&](void** dst, const void* src, size_t bytes) {
         if (e != cudaSuccess) return;
-        e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
+        e = dev_malloc(dst, std::max<size_t>(bytes, 16));
         if (e == cudaSuccess && bytes) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
     };
     up(reinterpret_cast<void**>(&b->d_blocks), b->blocks.data(), b->blocks.size() * sizeof(qsa::BatchBlock));
     up(reinterpret_cast<void**>(&b->d_bstart), b->bstart.data(), b->bstart.size() * sizeof(uint32_t));
     up(reinterpret_cast<void**>(&b->d_order), b->order.data(), b->order.size() * sizeof(int32_t));
     up(reinterpret_cast<void**>(&b->d_mats), b->mats.data(), b->mats.size() * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = dev_malloc(&b->d_queue, 2 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1138,7 +1206,7 @@ qsa_status qsa_batch_run(qsa_batch b, void* dev_states, size_t bytes, uint64_t s
     if (need > b->out_cap) {
         if (b->d_out) {
             cudaDeviceSynchronize();
-            cudaFree(b->d_out);
+            dev_free(b->d_out);
         }
         b->d_out = nullptr;
         b->out_cap = 0;
@@ -1148,7 +1216,7 @@ qsa_status qsa_batch_run(qsa_batch b, void* dev_states, size_t bytes, uint64_t s
             b->gexec = nullptr;
             b->graph = nullptr;
         }
-        cudaError_t e = cudaMalloc(&b->d_out, need);
+        cudaError_t e = dev_malloc(&b->d_out, need);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(QSA_E_NOMEM, "cudaMalloc of batch outputs failed");

@@ -28,8 +28,24 @@ struct TileGeom {
 // six special positions would be extra bits.
 bool make_geom(int n, const int* special, int ns, int T_want, TileGeom* g);
 
-// Number of SMs of the current device (cached).
+// Every device allocation of the library goes through these: a host-side
+// test hook can make the n-th allocation fail as if the device were out of
+// memory (qsa_debug_fail_alloc, QSA_FAULT_ALLOC), and the live allocations
+// are counted (qsa_debug_live_allocations), so the error paths and their
+// cleanup are tested without any device fault.
+cudaError_t dev_malloc_raw(void** p, size_t bytes);
+template <typename T>
+cudaError_t dev_malloc(T** p, size_t bytes) {
+    return dev_malloc_raw(reinterpret_cast<void**>(p), bytes);
+}
+void dev_free(void* p);
+
+// Number of SMs of the current device (cached per device).
 int num_sms();
+// cudaFuncSetAttribute(kernel, MaxDynamicSharedMemorySize, bytes) on the
+// current device unless a size at least as large was set there before (the
+// attribute belongs to the device's context; cached per device and kernel).
+cudaError_t set_smem_attr(const void* kernel, int bytes);
 
 // One fused block of a trajectory in the batched kernel (k <= 4, tile bits 11).
 struct BatchBlock {
@@ -115,7 +131,7 @@ struct LayerPayload {
     uint32_t rpmask = 0;      // rotation mode: rounds whose exit phases are not all 1
     uint32_t rswap = 0;       // rotation mode: tile bits whose halves the pass leaves exchanged
     bool generate = false;    // write-only: the input is taken as 1 for every amplitude (not read)
-    size_t off_fac = 0, off_cross = 0, off_out = 0, off_din = 0, off_qph = 0, off_rp = 0, bytes = 0;
+    size_t off_fac = 0, off_cross = 0, off_out = 0, off_din = 0, off_qph = 0, off_rp = 0, off_sph = 0, bytes = 0;
 };
 size_t layer_smem_bytes(bool with_din);
 // Rotation-mode passes with per-tile phases first write one record per tile

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "qsa.h"
+#include "qsa_costmodel.h"
 #include "qsa_internal.h"
 
 struct qsa_state_s {
@@ -36,6 +37,7 @@ struct qsa_state_s {
     void* d_lrec = nullptr;           // per-tile records of layer passes
     size_t lrec_cap = 0;
     int* d_err = nullptr;             // device error word written by bounded waits
+    qsa::CostModel cm;                // cost model attached to this state (qsa_costmodel_load), or null
     // CUDA-event timers
     struct Pending {
         cudaEvent_t a, b;
@@ -112,6 +114,19 @@ qsa_status check_state(qsa_state s);
 qsa_status sync_and_check(qsa_state s, const char* where);
 qsa_status ensure_dev(qsa_state s, void** ptr, size_t* cap, size_t bytes);
 void to_float_matrix(const double* m, int k, float* out);
+// Running sum of the modulus errors left by the FP32 constants of one plan,
+// each weighted by the share of the state it multiplies (see f2_modulus).
+struct ModulusCarry {
+    double acc = 0.0;
+};
+// FP32 complex number within a few ulps of z whose squared modulus, weighted
+// by `weight` and added to the carry, leaves the carry nearest zero (with no
+// carry: whose squared modulus is nearest m2); the carry is updated.  See
+// layer_host.cpp.
+float2 f2_modulus(std::complex<double> z, double m2, double weight = 1.0, ModulusCarry* carry = nullptr);
+// A table of `count` interleaved complex numbers rounded that way, each with
+// its own modulus as the target and the given weight.
+void to_float_moduli(const double* z, size_t count, float* out, double weight, ModulusCarry* carry);
 qsa_status validate_targets(int n, const int32_t* targets, int k, int kmax = QSA_MAX_K);
 qsa_status apply_logical(qsa_state s, const int32_t* targets, int k, const float* d_mat, int lowering,
                          int precision, qsa_run_stats* rs);
@@ -140,7 +155,7 @@ bool layer_fits(int n, const int* pos, int k);
 // groups that fit a tile (in target order), the diagonal ops in the first;
 // payloads appended to *bytes (16-byte aligned), dev_off relative to its start.
 std::vector<LayerLaunch> prepare_layer(int n, const int32_t* L, const LayerSpec& spec,
-                                       std::vector<unsigned char>* bytes);
+                                       std::vector<unsigned char>* bytes, ModulusCarry* carry = nullptr);
 qsa_status run_layer_launches(qsa_state s, const std::vector<LayerLaunch>& ls, const unsigned char* d_base,
                               qsa_run_stats* rs);
 // Prepare for the state's current layout, upload to scratch and run (N < 12:
@@ -169,5 +184,9 @@ class Timer {
     bool stopped_ = false;
 };
 void collect_timers(qsa_state s, double* total);
+// qsa_plan_create with an explicit cost model for QSA_PLAN_DP_MLP (null: the
+// width-limit heuristic).
+qsa_status plan_create(const qsa_op* ops, size_t n_ops, int n_qubits, const qsa_plan_opts* opts,
+                       const int32_t* layout, const CostModel& model, qsa_plan* out);
 
 }  // namespace qsa

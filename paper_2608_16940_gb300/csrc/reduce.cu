@@ -629,12 +629,9 @@ cudaError_t launch_batch_sample(const float2* states, int n, int n_traj, uint32_
     const uint64_t nb = (1ull << n) / bsz;
     const uint32_t P = static_cast<uint32_t>(next_pow2(shots));
     const size_t smem = sizeof(uint64_t) * nb + sizeof(uint32_t) * P;
-    static size_t attr = 0;
-    if (smem > attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_batch_sample, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem));
+    {
+        cudaError_t e = set_smem_attr(reinterpret_cast<const void*>(k_batch_sample), static_cast<int>(smem));
         if (e != cudaSuccess) return e;
-        attr = smem;
     }
     k_batch_sample<<<n_traj, kBatchSampleThreads, smem, st>>>(states, n, shots, P, seed, out_keys, out_counts,
                                                               n_distinct);

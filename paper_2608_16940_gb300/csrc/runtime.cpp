@@ -9,7 +9,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -20,9 +22,40 @@
 
 namespace {
 thread_local std::string g_err;
-}
+
+// Allocations to go before an injected failure (-1: none) and the number of
+// device allocations the library holds.
+std::atomic<int64_t> g_alloc_fail_in{-1};
+std::atomic<int64_t> g_live_allocs{0};
+// QSA_FAULT_ALLOC=<n> at load time: the n-th device allocation (0 = the
+// first) fails.
+struct FaultEnv {
+    FaultEnv() {
+        if (const char* v = std::getenv("QSA_FAULT_ALLOC")) g_alloc_fail_in.store(std::atoll(v));
+    }
+} g_fault_env;
+}  // namespace
 
 namespace qsa {
+
+cudaError_t dev_malloc_raw(void** p, size_t bytes) {
+    int64_t left = g_alloc_fail_in.load();
+    while (left >= 0 && !g_alloc_fail_in.compare_exchange_weak(left, left - 1)) {
+    }
+    if (left == 0) {   // the injected failure: nothing is allocated
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) g_live_allocs.fetch_add(1);
+    return e;
+}
+
+void dev_free(void* p) {
+    if (!p) return;
+    cudaFree(p);
+    g_live_allocs.fetch_sub(1);
+}
 
 qsa_status fail(qsa_status st, const std::string& msg) {
     g_err = msg;
@@ -37,14 +70,15 @@ qsa_status cuda_fail(qsa_state s, cudaError_t e, const char* where) {
 // Synchronise the state's stream and report a device-side give-up recorded
 // in the error word by a bounded wait (QSA_E_TIMEOUT; the state is then failed).
 qsa_status sync_and_check(qsa_state s, const char* where) {
-    int h = 0;
-    cudaError_t e = cudaMemcpyAsync(&h, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    int h[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(h, s->d_err, sizeof(h), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, where);
-    if (h != 0) {
+    if (h[0] != 0) {
         s->failed = true;
         return fail(QSA_E_TIMEOUT, std::string(where) + ": a kernel gave up a bounded wait (code " +
-                                       std::to_string(h) + "); the amplitudes are invalid");
+                                       std::to_string(h[0]) + ", work item " + std::to_string(h[1]) + ", block " +
+                                       std::to_string(h[2]) + "); the amplitudes are invalid");
     }
     return QSA_OK;
 }
@@ -59,12 +93,12 @@ qsa_status ensure_dev(qsa_state s, void** ptr, size_t* cap, size_t bytes) {
     if (*cap >= bytes && *ptr) return QSA_OK;
     if (*ptr) {
         cudaStreamSynchronize(s->stream);
-        cudaFree(*ptr);
+        dev_free(*ptr);
         *ptr = nullptr;
         *cap = 0;
     }
     size_t want = std::max<size_t>(bytes, 4096);
-    cudaError_t e = cudaMalloc(ptr, want);
+    cudaError_t e = dev_malloc(ptr, want);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *ptr = nullptr;
@@ -286,6 +320,16 @@ using namespace qsa;
 
 extern "C" {
 
+qsa_status qsa_debug_fail_alloc(int64_t nth) {
+    g_alloc_fail_in.store(nth < 0 ? -1 : nth);
+    return QSA_OK;
+}
+
+uint64_t qsa_debug_live_allocations(void) {
+    const int64_t v = g_live_allocs.load();
+    return v < 0 ? 0 : static_cast<uint64_t>(v);
+}
+
 const char* qsa_last_error(void) { return g_err.c_str(); }
 
 qsa_status qsa_state_create_ex(int n_qubits, qsa_dtype dtype, void* dev_buf, size_t bytes, void* cuda_stream,
@@ -313,7 +357,7 @@ qsa_status qsa_state_create_ex(int n_qubits, qsa_dtype dtype, void* dev_buf, siz
         s->owned = false;
     } else {
         void* p = nullptr;
-        cudaError_t e = cudaMalloc(&p, need);
+        cudaError_t e = dev_malloc(&p, need);
         if (e != cudaSuccess) {
             cudaGetLastError();
             delete s;
@@ -323,20 +367,28 @@ qsa_status qsa_state_create_ex(int n_qubits, qsa_dtype dtype, void* dev_buf, siz
         s->owned = true;
         init_zero = 1;
     }
-    cudaError_t e = cudaMalloc(&s->d_err, sizeof(int) * 4);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, sizeof(int) * 4, s->stream);
+    auto discard = [&]() {
+        if (s->owned) dev_free(s->psi);
+        dev_free(s->d_err);
+        delete s;
+    };
+    cudaError_t e = dev_malloc(&s->d_err, sizeof(int) * 4);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        if (s->owned) cudaFree(s->psi);
-        delete s;
-        return fail(QSA_E_NOMEM, "cudaMalloc of the error word failed");
+        discard();
+        return fail(QSA_E_NOMEM, std::string("cudaMalloc of the error word failed: ") + cudaGetErrorString(e));
+    }
+    e = cudaMemsetAsync(s->d_err, 0, sizeof(int) * 4, s->stream);
+    if (e != cudaSuccess) {
+        qsa_status st = cuda_fail(s, e, "error word");
+        discard();
+        return st;
     }
     if (init_zero) {
         e = launch_init_zero(s->psi, s->n, s->stream, &s->launches);
         if (e != cudaSuccess) {
             qsa_status st = cuda_fail(s, e, "init");
-            if (s->owned) cudaFree(s->psi);
-            delete s;
+            discard();
             return st;
         }
         s->known_zero = true;
@@ -353,14 +405,14 @@ qsa_status qsa_state_destroy(qsa_state s) {
     if (!s) return fail(QSA_E_ARG, "state is NULL");
     cudaStreamSynchronize(s->stream);
     cudaGetLastError();
-    if (s->owned && s->psi) cudaFree(s->psi);
-    if (s->d_mat) cudaFree(s->d_mat);
-    if (s->d_red) cudaFree(s->d_red);
-    if (s->d_dm) cudaFree(s->d_dm);
-    if (s->d_lrec) cudaFree(s->d_lrec);
-    if (s->d_samp) cudaFree(s->d_samp);
-    if (s->d_err) cudaFree(s->d_err);
-    if (s->d_mlp) cudaFree(s->d_mlp);
+    if (s->owned && s->psi) dev_free(s->psi);
+    if (s->d_mat) dev_free(s->d_mat);
+    if (s->d_red) dev_free(s->d_red);
+    if (s->d_dm) dev_free(s->d_dm);
+    if (s->d_lrec) dev_free(s->d_lrec);
+    if (s->d_samp) dev_free(s->d_samp);
+    if (s->d_err) dev_free(s->d_err);
+    if (s->d_mlp) dev_free(s->d_mlp);
     for (auto& p : s->ev_free) {
         cudaEventDestroy(p.first);
         cudaEventDestroy(p.second);
@@ -515,7 +567,8 @@ qsa_status qsa_apply_diag(qsa_state s, const int32_t* targets, int k, const doub
     if (!diag) return fail(QSA_E_ARG, "diag is NULL");
     const size_t cnt = 2ull << k;
     std::vector<float> hd(cnt);
-    for (size_t i = 0; i < cnt; ++i) hd[i] = static_cast<float>(diag[i]);
+    ModulusCarry carry;
+    to_float_moduli(diag, cnt / 2, hd.data(), 1.0 / static_cast<double>(cnt / 2), &carry);
     st = ensure_dev(s, reinterpret_cast<void**>(&s->d_mat), &s->mat_cap, cnt * sizeof(float));
     if (st != QSA_OK) return st;
     // pageable source: the copy is staged before the call returns
@@ -591,7 +644,7 @@ qsa_status qsa_probabilities(qsa_state s, double* out_host, double* norm_out) {
     if (out_host) {
         const size_t bytes = sizeof(double) << s->n;
         double* tmp = nullptr;
-        cudaError_t e = cudaMalloc(&tmp, bytes);
+        cudaError_t e = dev_malloc(&tmp, bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(QSA_E_NOMEM, "cudaMalloc of the probability buffer failed");
@@ -599,11 +652,11 @@ qsa_status qsa_probabilities(qsa_state s, double* out_host, double* norm_out) {
         e = launch_probs_logical(s->psi, s->n, s->L, tmp, s->stream, &s->launches);
         if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, tmp, bytes, cudaMemcpyDeviceToHost, s->stream);
         if (e != cudaSuccess) {
-            cudaFree(tmp);
+            dev_free(tmp);
             return cuda_fail(s, e, "probabilities");
         }
         st = sync_and_check(s, "probabilities");
-        cudaFree(tmp);
+        dev_free(tmp);
         if (st != QSA_OK) return st;
     }
     if (norm_out) return qsa_expectation_z(s, 0, norm_out);

@@ -33,7 +33,10 @@ class GState:
 
 
 def check_close(ref, got, fid_tol=FID_TOL, amp_tol=AMP_TOL):
+    """1 - F within fid_tol on both sides (F is not renormalised, so a norm
+    that grew counts like one that shrank) and the largest amplitude
+    difference within amp_tol."""
     f = oracle.fidelity(ref, got)
     e = oracle.max_abs_diff(ref, got)
-    assert 1 - f <= fid_tol and e <= amp_tol, (1 - f, e)
+    assert abs(1 - f) <= fid_tol and e <= amp_tol, (1 - f, e)
     return 1 - f, e

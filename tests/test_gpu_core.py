@@ -52,7 +52,7 @@ class GState:
 def _check_close(ref, got):
     f = oracle.fidelity(ref, got)
     e = oracle.max_abs_diff(ref, got)
-    assert 1 - f <= FID_TOL and e <= AMP_TOL, (1 - f, e)
+    assert abs(1 - f) <= FID_TOL and e <= AMP_TOL, (1 - f, e)
 
 
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6])
