@@ -184,6 +184,10 @@ def run_reference(args):
         picks, _, what = _dm_oracle_picks(n_s // 2, args.dm_p)
         n_s = 2 * (n_s // 2)
         wl = f"dm_ghz{args.dm_n}"
+    elif args.workload == "wide":
+        n_s = min(n_s, 24)   # a k = 6 operator costs 64 complex products per amplitude on the host
+        picks = W.wide_circuit(n_s, n_ops=2, widths=(5, 6), seed=args.seed)
+        wl, what = f"wide{args.n}", "k=5 / k=6 Haar operator of the wide workload"
     else:
         ops, _ = W.qaoa_circuit(n=n_s, p=args.p, seed=args.seed)
         picks = [ops[0], ops[n_s]]   # alternate a one-qubit and a two-qubit gate of the circuit
@@ -231,6 +235,10 @@ def cpu_baseline(n_s: int, seed: int, p: int, workload: str = "qaoa", p_dep: flo
     if workload == "dm_ghz":
         picks, _, what = _dm_oracle_picks(n_s // 2, p_dep)
         n_s = 2 * (n_s // 2)
+    elif workload == "wide":
+        n_s = min(n_s, 24)
+        picks = W.wide_circuit(n_s, n_ops=2, widths=(5, 6), seed=seed)
+        what = "2 operators (k=5, k=6) of the wide workload"
     else:
         ops, _ = W.qaoa_circuit(n=n_s, p=p, seed=seed)
         picks = [ops[0], ops[n_s]]
@@ -263,6 +271,152 @@ def step_dtype(agg):
     if agg["permutes"]:
         ran.append("bit permutations")
     return "c64 state; " + ", ".join(ran) + "; f64 reductions"
+
+
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def tc_record(q, torch, buf, stream, n, seed, hbm_peak, n_ops=40):
+    """The wide workload's operators at N = n: alternating Haar k = 5 / 6
+    operators on random target sets, one pass each, on the split-TF32 tensor
+    cores and on the FP32 CUDA cores.  Per precision: ms per operator (CUDA
+    events around each launch), operator-level amplitude updates per second
+    over the whole run, and the fused kernel's HBM roofline (16 B per
+    amplitude per launch)."""
+    ops = W.wide_circuit(n, n_ops=n_ops, widths=(5, 6), seed=seed)
+    s = q.qsa_state_create_ex(n, buf.data_ptr(), 8 << n, stream, 1)
+    out = {"workload": f"wide{n}: {n_ops} Haar k=5/6 operators on random targets, N={n} complex64"}
+    try:
+        for name, prec in (("tf32x3", q.QSA_PREC_TF32X3), ("fp32", q.QSA_PREC_FP32)):
+            plan = q.qsa_plan_create(ops, n, q.make_opts(planner=q.QSA_PLAN_PER_GATE, kmax=6, kmax_diag=6,
+                                                         precision=prec, timing=1))
+            try:
+                q.qsa_plan_execute(s, plan)   # warm-up
+                e0, e1 = _events(torch)
+                torch.cuda.synchronize()
+                e0.record()
+                st = q.qsa_plan_execute(s, plan)
+                e1.record()
+                torch.cuda.synchronize()
+            finally:
+                q.qsa_plan_destroy(plan)
+            t = e0.elapsed_time(e1) * 1e-3
+            kt = st["tc_seconds"] if prec else st["apply_seconds"]
+            per_op = kt / n_ops
+            gbs = 16.0 * (1 << n) / per_op / 1e9
+            out[name] = {"value": n_ops * float(1 << n) / t, "unit": UNIT, "ms_per_op": per_op * 1e3,
+                         "tc_blocks": st["tc_blocks"], "kernel": "k_apply_tc" if prec else "k_apply_fp32",
+                         "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                                      "frac": gbs / hbm_peak}}
+        out["tc_speedup_vs_fp32"] = out["fp32"]["ms_per_op"] / out["tf32x3"]["ms_per_op"]
+        # per width: FP32 CUDA-core k = 1..6 and split-TF32 k = 5, 6, 8 operators each on random targets
+        per_k = {}
+        for name, prec, ks in (("fp32", q.QSA_PREC_FP32, range(1, 7)), ("tf32x3", q.QSA_PREC_TF32X3, (5, 6))):
+            for k in ks:
+                kops = W.wide_circuit(n, n_ops=8, widths=(k,), seed=seed + 100 + k)
+                plan = q.qsa_plan_create(kops, n, q.make_opts(planner=q.QSA_PLAN_PER_GATE, kmax=6, kmax_diag=6,
+                                                              precision=prec, timing=1))
+                try:
+                    q.qsa_plan_execute(s, plan)
+                    st = q.qsa_plan_execute(s, plan)
+                finally:
+                    q.qsa_plan_destroy(plan)
+                kt = (st["tc_seconds"] if st["tc_blocks"] else st["apply_seconds"]) / len(kops)
+                per_k[f"{name}_k{k}"] = {"ms_per_op": kt * 1e3, "frac": 16.0 * (1 << n) / kt / 1e9 / hbm_peak}
+        out["per_width"] = per_k
+    finally:
+        q.qsa_state_destroy(s)
+    return out
+
+
+def batch_record(q, torch, buf, stream, seed, n=20, n_traj=256, shots=10000, p=1e-3):
+    """Batched noisy trajectories: n_traj states of N = n, depths uniform in
+    10..60 of U(2) + CZ brick layers with depolarising branches (probability p
+    per gate), one persistent launch replayed from a CUDA graph, then shots
+    sampled counts per trajectory.  Metrics: trajectories/s and gate-level
+    amplitude updates per second (input gates x 2^n per trajectory)."""
+    trajs, depths = W.trajectory_batch(n_traj=n_traj, n=n, dmin=10, dmax=60, seed=seed, p=p)
+    b = q.qsa_batch_create(n, trajs, q.make_opts(planner=q.QSA_PLAN_DP, kmax=4, kmax_diag=4))
+    nbytes = n_traj * (8 << n)
+    if buf.numel() * 8 < nbytes:
+        buf = torch.empty(nbytes // 8, dtype=torch.complex64, device=buf.device)
+    try:
+        info = q.qsa_batch_info(b)
+        q.qsa_batch_run(b, buf.data_ptr(), nbytes, shots, seed, 0, 1, stream)   # capture + warm-up
+        e0, e1 = _events(torch)
+        times = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            e0.record()
+            st = q.qsa_batch_run(b, buf.data_ptr(), nbytes, shots, seed, 0, 1, stream)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) * 1e-3)
+        t = statistics.median(times)
+    finally:
+        q.qsa_batch_destroy(b)
+    gates = sum(len(x) for x in trajs)
+    l2 = torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size
+    return {"workload": f"{n_traj} trajectories N={n}, depths 10..60, depolarising p={p:g}, {shots} shots each",
+            "trajectories_per_s": n_traj / t, "value": gates * float(1 << n) / t, "unit": UNIT,
+            "ms_per_batch": t * 1e3, "launch_seconds": st["seconds"], "gates": gates, "fused_blocks": info["blocks"],
+            "states_bytes": nbytes, "l2_bytes": l2,
+            "bound": "hbm" if nbytes > l2 else "l2",
+            "hbm_gbs_if_streamed": info["blocks"] * 16.0 * (1 << n) / t / 1e9}
+
+
+def planner_record(q, torch, buf, stream, seed, n=28, layers=40, n_samples=600):
+    """The learned planner against the method without it on the fusion
+    workload at N = n: QFT of a seeded basis state, `layers` layers of Haar
+    U(2) on every qubit and Haar U(4) on a random matching, then the inverse
+    of everything (the state returns to |0...0>).  Plans with kmax 6, diagonal
+    blocks up to 12 qubits and split-TF32 for k = 5, 6: the width-limit
+    heuristic (greedy), Eq. dp-recurrence with Gamma = 4^k, and the same DP
+    scored by the cost model trained here on this state's own kernel timings.
+    Each plan's run is timed with CUDA events (median of 3)."""
+    ops, _ = W.fusion_circuit(n=n, layers=layers, seed=seed, with_inverse=True)
+    if buf.numel() < (1 << n):
+        buf = torch.empty(1 << n, dtype=torch.complex64, device=buf.device)
+    s = q.qsa_state_create_ex(n, buf.data_ptr(), 8 << n, stream, 1)
+    out = {"workload": f"fusion{n}: QFT + {layers} Haar U(2)/U(4) layers + inverse, {len(ops)} gates, "
+                       f"N={n} complex64", "kmax": 6, "kmax_diag": 12, "precision": "tf32x3"}
+    try:
+        out["cost_model"] = train_cost_model(q, s, q.QSA_PREC_TF32X3, seed, n_samples)
+        for name, planner in (("greedy", q.QSA_PLAN_GREEDY), ("dp_4k", q.QSA_PLAN_DP),
+                              ("dp_mlp", q.QSA_PLAN_DP_MLP)):
+            opts = q.make_opts(planner=planner, kmax=6, kmax_diag=12, precision=q.QSA_PREC_TF32X3)
+            t0 = time.perf_counter()
+            plan = q.qsa_plan_create(ops, n, opts)
+            plan_s = time.perf_counter() - t0
+            try:
+                q.qsa_state_reset(s)
+                q.qsa_plan_execute(s, plan)   # warm-up
+                times = []
+                for _ in range(3):
+                    q.qsa_state_reset(s)
+                    e0, e1 = _events(torch)
+                    torch.cuda.synchronize()
+                    e0.record()
+                    st = q.qsa_plan_execute(s, plan)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1) * 1e-3)
+                q.qsa_state_sync(s)
+                p0 = float(abs(complex(buf[0].item())) ** 2)   # logical |0...0> sits at index 0 in any layout
+            finally:
+                blocks = q.qsa_plan_info(plan)["blocks"]
+                q.qsa_plan_destroy(plan)
+            out[name] = {"seconds": statistics.median(times), "blocks": blocks, "passes": st["passes"],
+                         "tc_blocks": st["tc_blocks"], "diag_blocks": st["diag_blocks"], "plan_seconds": plan_s,
+                         "return_probability": p0, "value": len(ops) * float(1 << n) / statistics.median(times),
+                         "unit": UNIT}
+        out["gain_vs_greedy"] = out["greedy"]["seconds"] / out["dp_mlp"]["seconds"]
+        out["gain_vs_dp_4k"] = out["dp_4k"]["seconds"] / out["dp_mlp"]["seconds"]
+    finally:
+        q.qsa_costmodel_set(None)
+        q.qsa_state_destroy(s)
+    return out
 
 
 def interleaved_layout(n: int, ways: int = 3):
@@ -298,7 +452,11 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="qaoa", choices=["qaoa", "dm_ghz"])
+    ap.add_argument("--workload", default="qaoa", choices=["qaoa", "dm_ghz", "wide"],
+                    help="qaoa: the N=30 QAOA circuit; dm_ghz: noisy GHZ density matrix; wide: --wide-ops Haar "
+                         "k=5/6 operators on random targets, one pass each (--precision picks the tensor-core or "
+                         "CUDA-core path)")
+    ap.add_argument("--wide-ops", type=int, default=40, help="operators per step of --workload wide")
     ap.add_argument("--dm-n", type=int, default=15, help="density-matrix qubits of --workload dm_ghz (2..17)")
     ap.add_argument("--dm-p", type=float, default=1e-2, help="depolarising rate of --workload dm_ghz")
     ap.add_argument("--n", type=int, default=30)
@@ -325,6 +483,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the per-gate comparison run")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--records", default="tc,planner,batch",
+                    help="comma list of sub-records measured after the timed region on rank 0 "
+                         "(tc: split-TF32 vs FP32 k=5/6 operators at N=30; planner: greedy / 4^k DP / learned DP "
+                         "on the N=28 fusion circuit; batch: 256 noisy trajectories at N=20); "
+                         "'' for none")
     args = ap.parse_args()
 
     if args.impl == "reference":
@@ -342,12 +505,20 @@ def main():
     dev = torch.device(f"cuda:{local}")
 
     dm = args.workload == "dm_ghz"
+    wide = args.workload == "wide"
+    if wide:
+        # each operator is one fused block already (k = 5, 6): no fusion, no layer units, no cost model
+        args.planner, args.layer, args.zero_init, args.layout = "per_gate", 0, 0, "identity"
     if dm:
         n_dm = args.dm_n
         n = 2 * n_dm
         chans = W.noisy_ghz_channels(n_dm, args.dm_p)
         ops = [q.qsa_dm_superoperator(n_dm, c.targets, c.kraus) for c in chans]
         edges = [(0, n_dm - 1)]
+    elif wide:
+        n = args.n
+        ops = W.wide_circuit(n, n_ops=args.wide_ops, widths=(5, 6), seed=args.seed + rank)
+        edges = [(0, 1)]
     else:
         n = args.n
         ops, edges = W.qaoa_circuit(n=n, p=args.p, seed=args.seed + rank)
@@ -502,6 +673,14 @@ def main():
                              "hbm_gbs": pst["passes"] * bytes_per_launch / pg_t / 1e9,
                              "fused_speedup": (amp_updates / per_step) / (amp_updates / pg_t)}
 
+    recs = [r for r in args.records.split(",") if r] if (rank == 0 and not dm and not wide) else []
+    if "tc" in recs:
+        extra["tc"] = tc_record(q, torch, buf, stream, n, args.seed, hbm_peak)
+    if "planner" in recs:
+        extra["planner"] = planner_record(q, torch, buf, stream, args.seed)
+    if "batch" in recs:
+        extra["batch"] = batch_record(q, torch, buf, stream, args.seed)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_qubits, args.seed, args.p, args.workload, args.dm_p)
@@ -515,7 +694,10 @@ def main():
                 "vs_baseline": None,
                 "dtype": step_dtype(agg),
                 "data": "synthetic",
-                "config": {"workload": (f"dm_ghz{n_dm}: noisy GHZ density matrix, {len(ops)} channels "
+                "config": {"workload": (f"wide{n}: {len(ops)} Haar k=5/6 operators on random targets, N={n} "
+                                        f"complex64 ({8 * (1 << n) / 2**30:g} GiB), from |0...0> (reset included), "
+                                        f"norm + <Z0 Z1> + {args.shots} shots per step") if wide else
+                                       (f"dm_ghz{n_dm}: noisy GHZ density matrix, {len(ops)} channels "
                                         f"(depolarising p={args.dm_p:g} after each gate) lowered to superoperators, "
                                         f"vec(rho) on 2n={n} qubits complex64 ({8 * (1 << n) / 2**30:g} GiB), "
                                         f"trace + Tr(rho Z0 Z{n_dm - 1}) per step") if dm else
@@ -527,7 +709,11 @@ def main():
                            "precision": args.precision,
                            "lowering": args.lowering, "victim": args.victim, "fused_blocks": pinfo["blocks"],
                            "layout": args.layout,
-                           "l2": "state 8 GiB > 129 MB L2; no flush needed", "parallelism": f"replicas x{ws}"},
+                           "l2": (f"state {8 * (1 << n) / 2**30:g} GiB > L2 "
+                                  f"{torch.cuda.get_device_properties(dev).L2_cache_size / 2**20:.0f} MiB; no flush needed"
+                                  if (8 << n) > torch.cuda.get_device_properties(dev).L2_cache_size else
+                                  "state smaller than L2: timings include L2 reuse"),
+                           "parallelism": f"replicas x{ws}"},
                 "gpu_launches": launches, "clocks": clocks, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "passes_per_step": agg["passes"] / args.steps,
                 "hbm_gbs_step": agg["passes"] / args.steps * bytes_per_launch / per_step / 1e9,

@@ -147,3 +147,27 @@ def test_learned_planner_gain_over_heuristics(q, capsys):
     finally:
         q.qsa_costmodel_set(None)
         st.close()
+
+
+def test_learned_planner_on_the_fusion_workload(q, capsys):
+    """The fusion workload at N = 28 (QFT of a seeded basis state, 40 layers of
+    Haar U(2) on every qubit and U(4) on random matchings, then the inverse;
+    4.2k gates), kmax 6, diagonal blocks up to 12 qubits, split-TF32 for
+    k = 5, 6: the width-limit heuristic, the 4^k DP and the DP scored by a
+    cost model trained on this state's own kernel timings (600 samples), each
+    plan timed with CUDA events.  Every plan returns the state to |0...0>."""
+    import bench
+    buf = torch.empty(1 << 28, dtype=torch.complex64, device="cuda:0")
+    try:
+        rec = bench.planner_record(q, torch, buf, torch.cuda.current_stream().cuda_stream, 0)
+    finally:
+        del buf
+        torch.cuda.empty_cache()
+    with capsys.disabled():
+        print(f"\nfusion28 planners: greedy {rec['greedy']['seconds']:.4f} s ({rec['greedy']['blocks']} blocks), "
+              f"dp_4k {rec['dp_4k']['seconds']:.4f} s ({rec['dp_4k']['blocks']}), "
+              f"dp_mlp {rec['dp_mlp']['seconds']:.4f} s ({rec['dp_mlp']['blocks']}); gain vs greedy "
+              f"{rec['gain_vs_greedy']:.2f}x, vs 4^k DP {rec['gain_vs_dp_4k']:.2f}x; held-out median error "
+              f"{rec['cost_model']['heldout_median_rel_err']:.3f}")
+    for name in ("greedy", "dp_4k", "dp_mlp"):
+        assert rec[name]["return_probability"] > 1 - 1e-4, (name, rec[name]["return_probability"])
