@@ -35,27 +35,39 @@
 // (about 2^-9 of the result) accumulate in tensor memory, where their
 // rounding is far below FP32 resolution of the output.
 //
-// CTA roles (one persistent CTA per SM, 320 threads):
-//   warp 8      producer: copies each chunk from HBM into an NR-stage ring
-//               with 16-byte cp.async (mbarrier-tracked), in an XOR layout
-//               chosen per launch so that the converters' reads are free of
-//               bank conflicts for any target positions;
-//   warps 0-3   converters in two teams of two warps; team t converts chunks
-//               t, t + 2, ... into B buffer t (so each buffer has one owner
-//               and every parity wait on it is for the next completion).  A
-//               lane holds one K half (32 amplitudes) of one row: the values
-//               into registers (the raw stage is released right away), the
-//               half's quantum, the hi / lo split and the B operand (K-major,
-//               128-byte swizzle) in shared memory;
-//   warp 9      allocates tensor memory and issues the MMAs (one thread);
-//               A (hi and lo) stays in tensor memory for the whole launch;
-//   warps 4-7   epilogue, warp w on tensor-memory lanes 32 (w % 4) ...: sums
-//               the accumulators, transposes its 16 outputs x 32 rows through
-//               its own shared staging area and writes them back (one row
-//               block of consecutive addresses per warp store).  At the start
-//               the same warps build A in tensor memory.
-// Tensor memory (512 columns): A_hi 128, A_lo 128, and two accumulator sets
-// of 96 columns (two exact main halves and the corrections, 32 rows each).
+// CTA roles (one persistent CTA per SM, 736 threads).  Chunks go through the
+// tensor core in pairs (chunks 2p and 2p + 1 of the CTA's list): each MMA has
+// N = 64, the B rows of both chunks, which halves the MMA instructions per
+// chunk against N = 32.
+//   warps 16-19 producers: copy each chunk from HBM into a 4-stage ring with
+//               16-byte cp.async (mbarrier-tracked; each warp a quarter of
+//               the chunk's copies), in an XOR layout chosen per launch so
+//               that the converters' reads are free of bank conflicts for any
+//               target positions;
+//   warps 0-7   converters in two teams of four; team t converts chunk
+//               2p + t of every pair into rows 32 t .. 32 t + 31 of B buffer
+//               p mod 2 (two buffers, so the conversion of a pair overlaps
+//               the MMAs of the previous one).  A lane holds one K quarter
+//               (16 amplitudes) of one row: the values into registers (the
+//               raw stage is released right away), the K half's quantum
+//               (maximum shared with the lane holding the other quarter), the
+//               hi / lo split and the B operand (K-major, 128-byte swizzle);
+//   warps 20-22 one thread each issues one of the pair's three products
+//               (16 MMAs, N = 64) into its own accumulator columns: a single
+//               issuing thread left the tensor pipe idle most of the time.
+//               Warp 20 allocates tensor memory; A (hi and lo) stays there for
+//               the whole launch;
+//   warps 8-15  epilogue in two groups of four; group g takes chunk 2p + g of
+//               every pair (accumulator columns 32 g .. 32 g + 31), warp w on
+//               tensor-memory lanes 32 (w % 4) ...: sums the accumulators into
+//               the group's staging area in a second XOR layout (chunk-local
+//               order), then stores the chunk back in 16-byte units exactly as
+//               the producers read it, so every warp store covers 512
+//               consecutive bytes whatever the target positions.  At the
+//               start group 0 builds A in tensor memory.
+// Tensor memory (512 columns): A_hi 128, A_lo 128, and one accumulator set of
+// 256 columns (two exact main halves and the two correction products, 64
+// columns each for the pair).
 // Every mbarrier wait is bounded; on timeout the CTA records an error code,
 // drains its copies and MMAs, frees tensor memory and returns.
 #include <cuda_runtime.h>
@@ -70,41 +82,51 @@ namespace qsa {
 
 namespace {
 
-constexpr int kThreads = 320;
-constexpr int kConvWarps = 4;                // warps 0-3
-constexpr int kProdWarp = 8;
-constexpr int kMmaWarp = 9;                  // warps 4-7: epilogue
+constexpr int kThreads = 736;
+constexpr int kConvWarps = 8;                // warps 0-7: converters, two teams of four
+constexpr int kEpiWarp = 8;                  // warps 8-15: epilogue, two groups of four
+constexpr int kProdWarp = 16;                // warps 16-19: producers
+constexpr int kProducers = 4;
+constexpr int kMmaWarp = 20;                 // warps 20-22: MMA issuers (warp 20 owns tensor memory)
+constexpr int kIssuers = 3;
 constexpr int kChunkBits = 11;               // amplitudes per chunk: 2^11
-constexpr int kNR = 8;                       // raw chunk stages
-constexpr int kNB = 2;                       // B operand stages: one per converter team
-constexpr int kND = 2;                       // accumulator sets
-constexpr uint32_t kWaitLimit = 1u << 22;    // try_wait rounds before giving up
+constexpr int kNR = 4;                       // raw chunk stages
+// chunks go through the MMA in pairs: a B operand holds 64 rows, two chunks
+// of 32 (one per converter team), and each MMA has N = 64; two B buffers
+// (pair p in buffer p mod 2) let the conversion of a pair overlap the MMAs
+// of the one before
+constexpr int kNB = 2;
+constexpr uint64_t kWaitNs = 1000000000ull;   // a wait gives up after one second
+constexpr uint32_t kSuspendNs = 100000;        // a try_wait may sleep this long before it returns
 
 constexpr uint32_t kRawBytes = (1u << kChunkBits) * 8;   // 16 KiB
-constexpr uint32_t kHalfB = 32 * 128 * 4;                // one split part of B: 32 rows x 128 floats
+constexpr uint32_t kKBlock = 64 * 128;                   // one K block of B: 64 rows x 32 floats (128 B)
+constexpr uint32_t kHalfB = 4 * kKBlock;                 // one split part of B: 64 rows x 128 floats
 constexpr uint32_t kBBytes = 2 * kHalfB;                 // hi + lo
-constexpr uint32_t kStgPitch = 33;                       // float2 per staged output (32 rows + 1 pad)
-constexpr uint32_t kStgWarpBytes = 16 * kStgPitch * 8;   // 16 outputs per epilogue warp
+// epilogue staging: one chunk per epilogue group, in the output layout
+constexpr uint32_t kOutBytes = kRawBytes;
 // shared memory carve-up (from a 1024-byte aligned base)
 constexpr uint32_t OFF_B = 0;
 constexpr uint32_t OFF_RAW = OFF_B + kNB * kBBytes;
 constexpr uint32_t OFF_STG = OFF_RAW + kNR * kRawBytes;
-constexpr uint32_t OFF_GI = OFF_STG + 4 * kStgWarpBytes;   // producer: 32 global offsets
+constexpr uint32_t OFF_GI = OFF_STG + 2 * kOutBytes;     // 32 global offsets of copy units (in and out)
 constexpr uint32_t OFF_SI = OFF_GI + 32 * 8;               // producer: 32 stage offsets
-constexpr uint32_t OFF_GNU = OFF_SI + 32 * 4;              // epilogue: 64 global output offsets
-constexpr uint32_t OFF_BARS = OFF_GNU + 64 * 8;
+constexpr uint32_t OFF_OI = OFF_SI + 32 * 4;               // epilogue: 32 output staging offsets
+constexpr uint32_t OFF_BARS = OFF_OI + 32 * 4;
 constexpr int BAR_RFULL = 0, BAR_REMPTY = kNR, BAR_BFULL = 2 * kNR, BAR_BEMPTY = BAR_BFULL + kNB,
-              BAR_DFULL = BAR_BEMPTY + kNB, BAR_DEMPTY = BAR_DFULL + kND, BAR_AREADY = BAR_DEMPTY + kND,
+              BAR_DFULL = BAR_BEMPTY + kNB, BAR_DEMPTY = BAR_DFULL + 1, BAR_AREADY = BAR_DEMPTY + 1,
               BAR_FIN = BAR_AREADY + 1, NBARS = BAR_FIN + 1;
 constexpr uint32_t OFF_MISC = OFF_BARS + NBARS * 8;        // tensor-memory address, abort word
 constexpr size_t kSmem = 1024 + OFF_MISC + 16;
 static_assert(kSmem <= 232448, "shared memory per CTA");
 // tensor memory columns
-constexpr uint32_t COL_AHI = 0, COL_ALO = 128, COL_D = 256, D_COLS = 96;
+// accumulators of a pair: main K half 0, main K half 1, A_hi B_lo, A_lo B_hi
+// (64 columns each: chunk 2p in the first 32, chunk 2p + 1 in the next 32)
+constexpr uint32_t COL_AHI = 0, COL_ALO = 128, COL_D = 256, D_COLS = 256;
 constexpr uint32_t kTmemCols = 512;
-static_assert(COL_D + kND * D_COLS <= kTmemCols, "tensor memory");
-// instruction descriptor: D FP32, A and B TF32, both K-major, N = 32, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+static_assert(COL_D + D_COLS <= kTmemCols, "tensor memory");
+// instruction descriptor: D FP32, A and B TF32, both K-major, N = 64, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -119,20 +141,30 @@ __device__ __forceinline__ void mbar_arrive(uint32_t a) {
 __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.b32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(a), "r"(parity)
+        : "r"(a), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
-// Bounded wait; gives up (and raises the CTA abort word) after kWaitLimit
-// rounds or as soon as another role has aborted.  The first give-up on the
-// device records its code, the chunk it waited for and the CTA in gerr[0..2].
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+// Bounded wait; gives up (and raises the CTA abort word) after kWaitNs or as
+// soon as another role has aborted.  The thread sleeps inside try_wait until
+// the phase completes (or kSuspendNs passes), so waiting warps take few issue
+// slots from the working ones.  The first give-up on the device records its
+// code, the chunk it waited for and the CTA in gerr[0..2].
 __device__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag, int* gerr, int code,
                           uint64_t item = 0) {
-    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    if (mbar_try(a, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
         if (mbar_try(a, parity)) return true;
         if (*abort_flag) return false;
+        if (global_ns() - t0 > kWaitNs) break;
     }
     *abort_flag = 1;
     if (atomicCAS(gerr, 0, code) == 0) {
@@ -142,6 +174,21 @@ __device__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag,
     return false;
 }
 
+// Named barrier over nthreads threads; group_all also returns the AND of v
+// over them.  Every thread of the group reaches each call the same number of
+// times (the group's exits are decided by group_all).
+__device__ __forceinline__ void group_sync(uint32_t id, uint32_t nthreads) {
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ bool group_all(uint32_t id, uint32_t nthreads, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"(static_cast<uint32_t>(v)), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
@@ -183,6 +230,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
+}
+// 32 lanes x 16 consecutive 32-bit columns (one row per thread).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+// 32 lanes x 8 consecutive 32-bit columns (one row per thread).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 // 32 lanes x 16 consecutive 32-bit columns (one row per thread).
@@ -260,6 +322,7 @@ struct TcArgs {
     uint64_t nchunks;
     uint64_t gbit[kChunkBits];   // global amplitude offset of chunk-local position p
     uint32_t sbit[kChunkBits];   // stage byte address (XOR) contribution of chunk-local position p
+    uint32_t obit[kChunkBits];   // the same for the output staging
     int m, nx;                   // chunk-local positions: 0..m-1 and xpos[0..nx-1]
     int xpos[6];
     int kp[6];                   // chunk-local position of K bit b
@@ -305,7 +368,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_apply_tc(TcArgs a) {
     unsigned char* Raw = sm + OFF_RAW;
     uint64_t* gi_tab = reinterpret_cast<uint64_t*>(sm + OFF_GI);
     uint32_t* si_tab = reinterpret_cast<uint32_t*>(sm + OFF_SI);
-    uint64_t* gnu_tab = reinterpret_cast<uint64_t*>(sm + OFF_GNU);
+    uint32_t* oi_tab = reinterpret_cast<uint32_t*>(sm + OFF_OI);
     const uint32_t bar0 = smem_u32(sm + OFF_BARS);
     auto bar = [&](int i) { return bar0 + 8u * static_cast<uint32_t>(i); };
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_MISC);
@@ -313,42 +376,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_apply_tc(TcArgs a) {
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // Producer copy units: unit U = lane + 32 i (16 bytes: elements 2U, 2U+1);
-    // the bits of i are chunk-local positions 6..10.
+    // Copy units (producers in, epilogue out): unit U = lane + 32 i (16
+    // bytes: elements 2U, 2U+1); the bits of i are chunk-local positions 6..10.
     if (tid < 32) {
         uint64_t g = 0;
-        uint32_t s = 0;
+        uint32_t s = 0, o = 0;
 #pragma unroll
         for (int b = 0; b < 5; ++b)
             if ((tid >> b) & 1) {
                 g |= a.gbit[6 + b];
                 s ^= a.sbit[6 + b];
+                o ^= a.obit[6 + b];
             }
         gi_tab[tid] = g;
         si_tab[tid] = s;
-    } else if (tid >= 64 && tid < 128) {   // global offset of output nu within its row
-        const int nu = tid - 64;
-        uint64_t g = 0;
-#pragma unroll
-        for (int b = 0; b < 6; ++b)
-            if ((nu >> b) & 1) g |= a.gbit[a.kp[b]];
-        gnu_tab[nu] = g;
+        oi_tab[tid] = o;
     }
     if (tid == 0) {
         for (int i = 0; i < kNR; ++i) {
-            mbar_init(bar(BAR_RFULL + i), 32);
-            mbar_init(bar(BAR_REMPTY + i), 64);   // the converting team
+            mbar_init(bar(BAR_RFULL + i), 32 * kProducers);   // every producer lane
+            mbar_init(bar(BAR_REMPTY + i), 128);   // the converting team
         }
         for (int i = 0; i < kNB; ++i) {
-            mbar_init(bar(BAR_BFULL + i), 64);
-            mbar_init(bar(BAR_BEMPTY + i), 1);
+            mbar_init(bar(BAR_BFULL + i), 256);         // both converter teams
+            mbar_init(bar(BAR_BEMPTY + i), kIssuers);   // one commit per issuer
         }
-        for (int i = 0; i < kND; ++i) {
-            mbar_init(bar(BAR_DFULL + i), 1);
-            mbar_init(bar(BAR_DEMPTY + i), 128);
-        }
+        mbar_init(bar(BAR_DFULL), kIssuers);
+        mbar_init(bar(BAR_DEMPTY), 256);        // both epilogue groups
         mbar_init(bar(BAR_AREADY), 128);
-        mbar_init(bar(BAR_FIN), 1);
+        mbar_init(bar(BAR_FIN), kIssuers);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -364,8 +420,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_apply_tc(TcArgs a) {
     const uint64_t nch = a.nchunks;
     const uint64_t my = nch > blockIdx.x ? (nch - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
 
-    if (warp == kProdWarp) {
-        // ---------------- producer ----------------
+    if (warp >= kProdWarp && warp < kProdWarp + kProducers) {
+        // ---------------- producers ----------------
+        constexpr int kU = 32 / kProducers;
+        const int u0 = kU * (warp - kProdWarp);   // this warp's copies: units lane + 32 u, u0 <= u < u0 + kU
         uint64_t gl = 0;   // this lane's part of its units (unit bits 0..4 = positions 1..5)
         uint32_t sl = 0;
 #pragma unroll
@@ -384,181 +442,235 @@ __global__ void __launch_bounds__(kThreads, 1) k_apply_tc(TcArgs a) {
             }
             const uint64_t base = chunk_base(a, blockIdx.x + i * gridDim.x) | gl;
             const uint32_t d0 = raw0 + static_cast<uint32_t>(s) * kRawBytes;
-#pragma unroll 8
-            for (int u = 0; u < 32; ++u) cp_async16(d0 + (sl ^ si_tab[u]), a.psi + (base | gi_tab[u]));
+#pragma unroll
+            for (int u = u0; u < u0 + kU; ++u) cp_async16(d0 + (sl ^ si_tab[u]), a.psi + (base | gi_tab[u]));
             cp_async_arrive_noinc(bar(BAR_RFULL + s));
         }
         cp_async_wait_all();   // no copy may land after the CTA has left
     } else if (warp < kConvWarps) {
         // ---------------- converters ----------------
-        const int team = warp >> 1;
-        const int rho = 16 * (warp & 1) + (lane & 15), h = lane >> 4;   // row and K half of this lane
+        const int team = warp >> 2, wt = warp & 3;
+        // this lane: row rho, K quarter 2 h + sub (16 amplitudes); the two
+        // quarters of a K half sit in lanes l and l ^ 16 of one warp
+        const int rho = 16 * (wt & 1) + (lane & 15), h = wt >> 1, sub = lane >> 4;
         uint32_t srow = 0;
 #pragma unroll
         for (int b = 0; b < 5; ++b)
             if ((rho >> b) & 1) srow ^= a.sbit[a.rp[b]];
         if (h) srow ^= a.sbit[a.kp[5]];
-        uint32_t ks[5];
+        if (sub) srow ^= a.sbit[a.kp[4]];
+        uint32_t ks[4];
 #pragma unroll
-        for (int b = 0; b < 5; ++b) ks[b] = a.sbit[a.kp[b]];
-        auto kaddr = [&](int c) {   // c < 32 is a compile-time constant in the unrolled loops
+        for (int b = 0; b < 4; ++b) ks[b] = a.sbit[a.kp[b]];
+        auto kaddr = [&](int c) {   // c < 16 is a compile-time constant in the unrolled loops
             uint32_t o = 0;
 #pragma unroll
-            for (int b = 0; b < 5; ++b)
+            for (int b = 0; b < 4; ++b)
                 if ((c >> b) & 1) o ^= ks[b];
             return o;
         };
         const uint32_t brow = static_cast<uint32_t>(rho >> 3) * 1024u + static_cast<uint32_t>(rho & 7) * 128u;
         const uint32_t bsw = static_cast<uint32_t>(rho & 7);
-        for (uint64_t i = static_cast<uint64_t>(team); i < my; i += 2) {
-            const int s = static_cast<int>(i % kNR), bb = static_cast<int>(i % kNB);   // bb == team
-            bool ok = mbar_wait(bar(BAR_RFULL + s), static_cast<uint32_t>(i / kNR) & 1u, abort_flag, a.err, 22, i);
-            if (!__all_sync(0xffffffffu, ok)) break;
-            // x[2 c + t] = part t of amplitude 32 h + c of the row
-            const unsigned char* stg = Raw + static_cast<uint32_t>(s) * kRawBytes;   // element at srow ^ kaddr
-            float x[64];
-            if (PAIR) {
+        const uint64_t npairs = (my + 1) / 2;
+        unsigned char* Bteam = Bsm + 4096u * static_cast<uint32_t>(team);   // rows 32 team .. 32 team + 31
+        for (uint64_t pr = 0; pr < npairs; ++pr) {
+            const int bb = static_cast<int>(pr & 1);
+            const uint64_t i = 2 * pr + static_cast<uint64_t>(team);   // this team's chunk of the pair
+            float x[32];
+            const bool have = i < my;   // the last pair of an odd count has one chunk
+            if (have) {
+                const int s = static_cast<int>(i % kNR);
+                const bool ok =
+                    mbar_wait(bar(BAR_RFULL + s), static_cast<uint32_t>(i / kNR) & 1u, abort_flag, a.err, 22, i);
+                if (!__all_sync(0xffffffffu, ok)) break;
+                // x[2 c + t] = part t of amplitude 32 h + 16 sub + c of the row
+                const unsigned char* stg = Raw + static_cast<uint32_t>(s) * kRawBytes;   // element at srow ^ kaddr
+                if (PAIR) {
 #pragma unroll
-                for (int c2 = 0; c2 < 16; ++c2) {
-                    const float4 v = *reinterpret_cast<const float4*>(stg + (srow ^ kaddr(2 * c2)));
-                    x[4 * c2] = v.x;
-                    x[4 * c2 + 1] = v.y;
-                    x[4 * c2 + 2] = v.z;
-                    x[4 * c2 + 3] = v.w;
-                }
-            } else {
+                    for (int c2 = 0; c2 < 8; ++c2) {
+                        const float4 v = *reinterpret_cast<const float4*>(stg + (srow ^ kaddr(2 * c2)));
+                        x[4 * c2] = v.x;
+                        x[4 * c2 + 1] = v.y;
+                        x[4 * c2 + 2] = v.z;
+                        x[4 * c2 + 3] = v.w;
+                    }
+                } else {
 #pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    const float2 v = *reinterpret_cast<const float2*>(stg + (srow ^ kaddr(c)));
-                    x[2 * c] = v.x;
-                    x[2 * c + 1] = v.y;
+                    for (int c = 0; c < 16; ++c) {
+                        const float2 v = *reinterpret_cast<const float2*>(stg + (srow ^ kaddr(c)));
+                        x[2 * c] = v.x;
+                        x[2 * c + 1] = v.y;
+                    }
                 }
+                mbar_arrive(bar(BAR_REMPTY + s));   // the values are in registers: the stage may refill
             }
-            mbar_arrive(bar(BAR_REMPTY + s));   // the values are in registers: the stage may refill
-            if (i >= kNB) {
-                ok = mbar_wait(bar(BAR_BEMPTY + bb), static_cast<uint32_t>(i / kNB - 1) & 1u, abort_flag, a.err, 23,
-                               i);
+            if (pr >= kNB) {   // the MMAs of pair pr - 2 have read this buffer
+                const bool ok = mbar_wait(bar(BAR_BEMPTY + bb), static_cast<uint32_t>(pr / kNB - 1) & 1u, abort_flag,
+                                          a.err, 23, i);
                 if (!__all_sync(0xffffffffu, ok)) break;
             }
-            unsigned char* Bhi = Bsm + static_cast<uint32_t>(bb) * kBBytes;
+            unsigned char* Bhi = Bteam + static_cast<uint32_t>(bb) * kBBytes;
             unsigned char* Blo = Bhi + kHalfB;
+            // the segment maximum spans the K half: both quarters (uniform across the warp)
             float mx = 0.f;
+            if (have) {
+                float m4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int j = 0; j < 64; ++j) mx = fmaxf(mx, fabsf(x[j]));
-            const float magic = seg_magic<kSplitB>(mx);
-            // K = 64 h + 4 u16 + (0..3): K block 2 h + (u16 >> 3), 16-byte unit u16 & 7
-#pragma unroll
-            for (int u16 = 0; u16 < 16; ++u16) {
-                float4 hv, lv;
-                split_one(x[4 * u16], magic, hv.x, lv.x);
-                split_one(x[4 * u16 + 1], magic, hv.y, lv.y);
-                split_one(x[4 * u16 + 2], magic, hv.z, lv.z);
-                split_one(x[4 * u16 + 3], magic, hv.w, lv.w);
-                const uint32_t off = static_cast<uint32_t>(2 * h + (u16 >> 3)) * 4096u + brow +
-                                     ((static_cast<uint32_t>(u16 & 7) ^ bsw) << 4);
-                *reinterpret_cast<float4*>(Bhi + off) = hv;
-                *reinterpret_cast<float4*>(Blo + off) = lv;
+                for (int j = 0; j < 32; ++j) m4[j & 3] = fmaxf(m4[j & 3], fabsf(x[j]));
+                mx = fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3]));
             }
-            fence_async_smem();   // the operand, visible to the tensor core
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+            if (have) {
+                const float magic = seg_magic<kSplitB>(mx);
+                // K = 64 h + 32 sub + 4 u + (0..3): K block 2 h + sub, 16-byte unit u
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    float4 hv, lv;
+                    split_one(x[4 * u], magic, hv.x, lv.x);
+                    split_one(x[4 * u + 1], magic, hv.y, lv.y);
+                    split_one(x[4 * u + 2], magic, hv.z, lv.z);
+                    split_one(x[4 * u + 3], magic, hv.w, lv.w);
+                    const uint32_t off = static_cast<uint32_t>(2 * h + sub) * kKBlock + brow +
+                                         ((static_cast<uint32_t>(u) ^ bsw) << 4);
+                    *reinterpret_cast<float4*>(Bhi + off) = hv;
+                    *reinterpret_cast<float4*>(Blo + off) = lv;
+                }
+                fence_async_smem();   // the operand, visible to the tensor core
+            }
             mbar_arrive(bar(BAR_BFULL + bb));
         }
-    } else if (warp == kMmaWarp) {
-        // ---------------- MMA issuer ----------------
+    } else if (warp >= kMmaWarp && warp < kMmaWarp + kIssuers) {
+        // ---------------- MMA issuers: product mi of every chunk ----------------
         if (lane == 0) {
+            const int mi = warp - kMmaWarp;   // 0: A_hi B_hi (two exact halves), 1: A_hi B_lo, 2: A_lo B_hi
             bool ok = mbar_wait(bar(BAR_AREADY), 0, abort_flag, a.err, 24);
             tc_fence_after();
             const uint32_t b0 = smem_u32(Bsm);
-            for (uint64_t i = 0; i < my && ok; ++i) {
-                const int bb = static_cast<int>(i % kNB), d = static_cast<int>(i % kND);
-                if (!mbar_wait(bar(BAR_BFULL + bb), static_cast<uint32_t>(i / kNB) & 1u, abort_flag, a.err, 25, i))
+            const uint32_t acol = tmem + (mi == 2 ? COL_ALO : COL_AHI);
+            const uint64_t npairs = (my + 1) / 2;
+            const uint32_t dcol = tmem + COL_D + (mi == 0 ? 0u : 64u + 64u * mi);
+            // B: hi for the main product and A_lo B_hi, lo for A_hi B_lo; the descriptor's
+            // address field is addr / 16 below 2^14, so a K-step adds a constant to it
+            const uint64_t bdesc0 = sw128_desc(b0 + (mi == 1 ? kHalfB : 0u));
+            for (uint64_t pr = 0; pr < npairs && ok; ++pr) {
+                const int bb = static_cast<int>(pr & 1);
+                if (!mbar_wait(bar(BAR_BFULL + bb), static_cast<uint32_t>(pr / kNB) & 1u, abort_flag, a.err, 25, 2 * pr))
                     break;
-                if (i >= kND &&
-                    !mbar_wait(bar(BAR_DEMPTY + d), static_cast<uint32_t>(i / kND - 1) & 1u, abort_flag, a.err, 26, i))
+                if (pr >= 1 &&
+                    !mbar_wait(bar(BAR_DEMPTY), static_cast<uint32_t>(pr - 1) & 1u, abort_flag, a.err, 26, 2 * pr))
                     break;
                 tc_fence_after();
-                const uint32_t dm = tmem + COL_D + static_cast<uint32_t>(d) * D_COLS;
-                const uint32_t bhi = b0 + static_cast<uint32_t>(bb) * kBBytes, blo = bhi + kHalfB;
+                const uint64_t bdesc = bdesc0 + ((static_cast<uint64_t>(bb) * kBBytes) >> 4);
 #pragma unroll
                 for (int kk = 0; kk < 16; ++kk) {   // K-steps of 8
-                    const uint32_t boff = static_cast<uint32_t>(kk >> 2) * 4096u + 32u * static_cast<uint32_t>(kk & 3);
-                    const uint64_t dhi = sw128_desc(bhi + boff), dlo = sw128_desc(blo + boff);
-                    mma_tf32_ts(dm + 32u * static_cast<uint32_t>(kk >> 3), tmem + COL_AHI + 8u * kk, dhi, kIdesc,
-                                (kk & 7) != 0);
-                    mma_tf32_ts(dm + 64u, tmem + COL_AHI + 8u * kk, dlo, kIdesc, kk != 0);
-                    mma_tf32_ts(dm + 64u, tmem + COL_ALO + 8u * kk, dhi, kIdesc, 1);
+                    const uint64_t boff = (static_cast<uint64_t>(kk >> 2) * kKBlock + 32u * static_cast<uint64_t>(kk & 3)) >> 4;
+                    const uint32_t dk = mi == 0 ? dcol + 64u * static_cast<uint32_t>(kk >> 3) : dcol;
+                    const uint32_t acc = mi == 0 ? static_cast<uint32_t>((kk & 7) != 0) : static_cast<uint32_t>(kk != 0);
+                    mma_tf32_ts(dk, acol + 8u * kk, bdesc + boff, kIdesc, acc);
                 }
                 mma_commit(bar(BAR_BEMPTY + bb));
-                mma_commit(bar(BAR_DFULL + d));
+                mma_commit(bar(BAR_DFULL));
             }
             // drain: no MMA may be in flight when the CTA tears down
             mma_commit(bar(BAR_FIN));
-            for (uint32_t it = 0; it < kWaitLimit; ++it)
-                if (mbar_try(bar(BAR_FIN), 0)) break;
+            const uint64_t t0 = global_ns();
+            while (!mbar_try(bar(BAR_FIN), 0) && global_ns() - t0 < kWaitNs) {
+            }
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue (warps 4-7) ----------------
-        const int q = warp & 3;   // tensor-memory lane quarter
+        // ---------------- epilogue (warps 4-11) ----------------
+        const int q = warp & 3;                  // tensor-memory lane quarter
+        const int grp = (warp - kEpiWarp) >> 2;  // accumulator set / chunk parity of this group
         const uint32_t lane_t = tmem + (static_cast<uint32_t>(q * 32) << 16);
-        {
+        if (grp == 0) {
             // A: row n = 32 q + lane of the embedding, hi and lo per K half
             const int n = 32 * q + lane, nu = n >> 1, s = n & 1;
 #pragma unroll 1
             for (int h = 0; h < 2; ++h) {
-                float x[64];
-                float mx = 0.f;
-#pragma unroll
-                for (int j = 0; j < 64; ++j) {
-                    x[j] = a_entry(a, nu, 32 * h + (j >> 1), s, j & 1);
-                    mx = fmaxf(mx, fabsf(x[j]));
-                }
+                float mx = 0.f;   // entry 2 kap + t of the half: kap = 32 h + (j >> 1), t = j & 1
+#pragma unroll 4
+                for (int j = 0; j < 64; ++j) mx = fmaxf(mx, fabsf(a_entry(a, nu, 32 * h + (j >> 1), s, j & 1)));
                 const float magic = seg_magic<kSplitA>(mx);
-                float hi[64], lo[64];
-#pragma unroll
-                for (int j = 0; j < 64; ++j) split_one(x[j], magic, hi[j], lo[j]);
-#pragma unroll
+#pragma unroll 1
                 for (int c = 0; c < 4; ++c) {
-                    tmem_st16(lane_t + COL_AHI + 64u * h + 16u * c, hi + 16 * c);
-                    tmem_st16(lane_t + COL_ALO + 64u * h + 16u * c, lo + 16 * c);
+                    float hi[16], lo[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        split_one(a_entry(a, nu, 32 * h + 8 * c + (j >> 1), s, j & 1), magic, hi[j], lo[j]);
+                    tmem_st16(lane_t + COL_AHI + 64u * h + 16u * c, hi);
+                    tmem_st16(lane_t + COL_ALO + 64u * h + 16u * c, lo);
                 }
             }
             tmem_st_wait();
             tc_fence_before();
             mbar_arrive(bar(BAR_AREADY));
         }
-        uint64_t grow = 0;   // row `lane` within the chunk
+        // The group writes its chunk into its staging area in the output
+        // layout (lane: output part lane & 1 of amplitude nu, register: row),
+        // then each warp stores a quarter of the chunk's 16-byte units in
+        // chunk-local order, mirroring the producers' copies.
+        unsigned char* ost = sm + OFF_STG + static_cast<uint32_t>(grp) * kOutBytes;
+        const int nu = 16 * q + (lane >> 1);
+        uint32_t onu = 4u * static_cast<uint32_t>(lane & 1);
+#pragma unroll
+        for (int b = 0; b < 6; ++b)
+            if ((nu >> b) & 1) onu ^= a.obit[a.kp[b]];
+        uint32_t orow[5];
+#pragma unroll
+        for (int b = 0; b < 5; ++b) orow[b] = a.obit[a.rp[b]];
+        uint64_t gl = 0;   // this lane's part of its units (positions 1..5)
+        uint32_t ol = 0;
 #pragma unroll
         for (int b = 0; b < 5; ++b)
-            if ((lane >> b) & 1) grow |= a.gbit[a.rp[b]];
-        float* stg = reinterpret_cast<float*>(sm + OFF_STG + static_cast<uint32_t>(q) * kStgWarpBytes);
-        const float2* stg2 = reinterpret_cast<const float2*>(stg);
-        const uint32_t wslot = static_cast<uint32_t>(lane >> 1) * kStgPitch * 2u + static_cast<uint32_t>(lane & 1);
-        for (uint64_t i = 0; i < my; ++i) {
-            const int d = static_cast<int>(i % kND);
-            const bool ok =
-                mbar_wait(bar(BAR_DFULL + d), static_cast<uint32_t>(i / kND) & 1u, abort_flag, a.err, 27, i);
-            // tcgen05.ld is warp-collective: leave together if any lane gave up
-            if (!__all_sync(0xffffffffu, ok)) break;
+            if ((lane >> b) & 1) {
+                gl |= a.gbit[1 + b];
+                ol ^= a.obit[1 + b];
+            }
+        const uint32_t gbar = 1u + static_cast<uint32_t>(grp);   // named barrier of the group (128 threads)
+        const uint32_t dcol = lane_t + COL_D + 32u * static_cast<uint32_t>(grp);   // this group's chunk of a pair
+        const uint64_t npairs = (my + 1) / 2;
+        for (uint64_t pr = 0; pr < npairs; ++pr) {
+            const uint64_t i = 2 * pr + static_cast<uint64_t>(grp);
+            bool ok = mbar_wait(bar(BAR_DFULL), static_cast<uint32_t>(pr) & 1u, abort_flag, a.err, 27, i);
+            // one decision for the whole group (its warps meet at a named barrier
+            // below); as a barrier it also means that the group's stores of its
+            // previous chunk have read the staging area
+            if (!group_all(gbar, 128, ok)) break;
+            if (i >= my) {   // the last pair of an odd count has one chunk
+                mbar_arrive(bar(BAR_DEMPTY));
+                continue;
+            }
             tc_fence_after();
-            uint32_t m0[32], m1[32], c[32];
-            const uint32_t dcol = lane_t + COL_D + static_cast<uint32_t>(d) * D_COLS;
-            tmem_ld32(dcol, m0);
-            tmem_ld32(dcol + 32u, m1);
-            tmem_ld32(dcol + 64u, c);
-            tmem_ld_wait();
-            tc_fence_before();
-            mbar_arrive(bar(BAR_DEMPTY + d));
-            // output part (lane & 1) of amplitude 16 q + (lane >> 1), rows 0..31
+            // output part (lane & 1) of amplitude nu, rows 8 hh .. 8 hh + 7
 #pragma unroll
-            for (int r = 0; r < 32; ++r)
-                stg[wslot + 2u * r] =
-                    __fadd_rn(__fadd_rn(__uint_as_float(m0[r]), __uint_as_float(m1[r])), __uint_as_float(c[r]));
-            __syncwarp();
-            // back out with lane = row: one warp store per output amplitude
-            const uint64_t base = chunk_base(a, blockIdx.x + i * gridDim.x) | grow;
-#pragma unroll 4
-            for (int j = 0; j < 16; ++j) __stcs(a.psi + (base | gnu_tab[16 * q + j]), stg2[j * kStgPitch + lane]);
-            __syncwarp();
+            for (int hh = 0; hh < 4; ++hh) {
+                uint32_t m0[8], m1[8], ca[8], cb[8];
+                tmem_ld8(dcol + 8u * hh, m0);
+                tmem_ld8(dcol + 64u + 8u * hh, m1);
+                tmem_ld8(dcol + 128u + 8u * hh, ca);
+                tmem_ld8(dcol + 192u + 8u * hh, cb);
+                tmem_ld_wait();
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int row = 8 * hh + r;
+                    uint32_t ad = onu;
+#pragma unroll
+                    for (int b = 0; b < 5; ++b)
+                        if ((row >> b) & 1) ad ^= orow[b];
+                    *reinterpret_cast<float*>(ost + ad) =
+                        __fadd_rn(__fadd_rn(__uint_as_float(m0[r]), __uint_as_float(m1[r])),
+                                  __fadd_rn(__uint_as_float(ca[r]), __uint_as_float(cb[r])));
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(bar(BAR_DEMPTY));
+            group_sync(gbar, 128);   // the chunk is staged
+            const uint64_t base = chunk_base(a, blockIdx.x + i * gridDim.x) | gl;
+#pragma unroll
+            for (int u = 8 * q; u < 8 * q + 8; ++u)
+                __stcs(reinterpret_cast<float4*>(a.psi + (base | gi_tab[u])),
+                       *reinterpret_cast<const float4*>(ost + (ol ^ oi_tab[u])));
         }
     }
     tc_fence_before();
@@ -595,6 +707,35 @@ void stage_layout(const int* rp, bool pair, uint32_t* sbit) {
             sbit[p] = 16u << (p - 1);
         else
             sbit[p] = (128u << (p - 4)) ^ (fvec[p] << 4);
+    }
+}
+
+// Output staging: the same element-in-unit and slot bits for positions 0..3
+// (16-byte units read back in chunk-local order, 8 lanes on distinct slots),
+// and slot vectors for the K positions at 4 and above among K bits 0..3 (the
+// bits that vary across an epilogue warp's lanes), so that a warp's staging
+// writes meet at most two to a bank.
+void out_layout(const int* kp, uint32_t* obit) {
+    uint32_t fvec[kChunkBits] = {};
+    uint32_t used = 0;
+    for (int b = 0; b < 4; ++b)
+        if (kp[b] >= 1 && kp[b] <= 3) used |= 1u << (kp[b] - 1);
+    for (int b = 0; b < 4; ++b)
+        if (kp[b] >= 4) {
+            int j = 0;
+            while (j < 3 && ((used >> j) & 1u)) ++j;
+            if (j < 3) {
+                used |= 1u << j;
+                fvec[kp[b]] = 1u << j;
+            }
+        }
+    for (int p = 0; p < kChunkBits; ++p) {
+        if (p == 0)
+            obit[p] = 8u;
+        else if (p <= 3)
+            obit[p] = 16u << (p - 1);
+        else
+            obit[p] = (128u << (p - 4)) ^ (fvec[p] << 4);
     }
 }
 
@@ -660,6 +801,7 @@ cudaError_t launch_apply_tc(float2* psi, int n, const int* phys, int k, const fl
     for (int b = 0; b < 5; ++b) a.rp[b] = np[b];
     const bool pair = tls[0] == 0;
     stage_layout(a.rp, pair, a.sbit);
+    out_layout(a.kp, a.obit);
     return pair ? launch_pair<true>(a, g.ntiles, st, launches) : launch_pair<false>(a, g.ntiles, st, launches);
 }
 
