@@ -52,9 +52,9 @@ UNIT = "amp-updates/s"
 # 4.260 GB; profiles/k_apply_layer_n28.md: 4.265 GB (a regular pass); each /
 # 2^28).  Traffic scales with the state size, so a launch at N moves this many
 # bytes times 2^N.
-DRAM_BYTES_PER_AMP = {"k_apply_tc": 4.241e9 / 2**28, "k_apply_fp32": 4.234e9 / 2**28,
+DRAM_BYTES_PER_AMP = {"k_apply_tc": 4.234e9 / 2**28, "k_apply_fp32": 4.234e9 / 2**28,
                       "k_apply_diag": 4.234e9 / 2**28, "k_apply_prod": 4.260e9 / 2**28,
-                      "k_apply_layer": 4.265e9 / 2**28}
+                      "k_apply_layer": 4.266e9 / 2**28}
 
 
 def _peaks():
@@ -330,14 +330,14 @@ def tc_record(q, torch, buf, stream, n, seed, hbm_peak, n_ops=40):
     return out
 
 
-def batch_record(q, torch, buf, stream, seed, n=20, n_traj=256, shots=10000, p=1e-3):
+def batch_record(q, torch, buf, stream, seed, n=20, n_traj=256, shots=10000, p=1e-3, kmax=4):
     """Batched noisy trajectories: n_traj states of N = n, depths uniform in
     10..60 of U(2) + CZ brick layers with depolarising branches (probability p
     per gate), one persistent launch replayed from a CUDA graph, then shots
     sampled counts per trajectory.  Metrics: trajectories/s and gate-level
     amplitude updates per second (input gates x 2^n per trajectory)."""
     trajs, depths = W.trajectory_batch(n_traj=n_traj, n=n, dmin=10, dmax=60, seed=seed, p=p)
-    b = q.qsa_batch_create(n, trajs, q.make_opts(planner=q.QSA_PLAN_DP, kmax=4, kmax_diag=4))
+    b = q.qsa_batch_create(n, trajs, q.make_opts(planner=q.QSA_PLAN_DP, kmax=kmax, kmax_diag=kmax))
     nbytes = n_traj * (8 << n)
     if buf.numel() * 8 < nbytes:
         buf = torch.empty(nbytes // 8, dtype=torch.complex64, device=buf.device)
@@ -359,6 +359,7 @@ def batch_record(q, torch, buf, stream, seed, n=20, n_traj=256, shots=10000, p=1
     gates = sum(len(x) for x in trajs)
     l2 = torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size
     return {"workload": f"{n_traj} trajectories N={n}, depths 10..60, depolarising p={p:g}, {shots} shots each",
+            "kmax": kmax,
             "trajectories_per_s": n_traj / t, "value": gates * float(1 << n) / t, "unit": UNIT,
             "ms_per_batch": t * 1e3, "launch_seconds": st["seconds"], "gates": gates, "fused_blocks": info["blocks"],
             "states_bytes": nbytes, "l2_bytes": l2,
@@ -483,6 +484,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the per-gate comparison run")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-n", type=int, default=20, help="qubits per trajectory of the batch sub-record")
+    ap.add_argument("--batch-traj", type=int, default=256, help="trajectories of the batch sub-record")
+    ap.add_argument("--batch-kmax", type=int, default=4, choices=[1, 2, 3, 4], help="fused-block cap of the batch sub-record")
     ap.add_argument("--records", default="tc,planner,batch",
                     help="comma list of sub-records measured after the timed region on rank 0 "
                          "(tc: split-TF32 vs FP32 k=5/6 operators at N=30; planner: greedy / 4^k DP / learned DP "
@@ -679,7 +683,8 @@ def main():
     if "planner" in recs:
         extra["planner"] = planner_record(q, torch, buf, stream, args.seed)
     if "batch" in recs:
-        extra["batch"] = batch_record(q, torch, buf, stream, args.seed)
+        extra["batch"] = batch_record(q, torch, buf, stream, args.seed, n=args.batch_n, n_traj=args.batch_traj,
+                                      kmax=args.batch_kmax)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

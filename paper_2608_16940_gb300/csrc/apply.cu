@@ -86,19 +86,85 @@ struct ApplyArgs {
     const float* mat;   // 2 * 4^K floats
     int tl[6];          // tile-local position of target j (V order)
     int tls[6];         // the same positions, ascending
+    uint8_t fv[16];     // stage layout: slot vector of tile-local position p >= 4 (k <= 4)
 };
+
+// Stage layout of the k <= 4 kernels: tile-local element j sits at
+// j ^ (h(j >> 4) << 1), h linear with h(bit i) = fv[4 + i].  Position 0 stays
+// the element within a 16-byte unit and positions 1..3 its slot in a 128-byte
+// line, so the copies in and out move whole 16-byte units with eight lanes on
+// eight slots; the slot vectors of higher positions are chosen per launch so
+// that the lowest non-target positions (the bits that vary across a
+// half-warp's groups) land on distinct banks.
+__device__ __forceinline__ uint32_t stage_xor(const uint8_t* htab, uint32_t j) {
+    return static_cast<uint32_t>(htab[j >> 4]) << 1;
+}
+
+__device__ __forceinline__ void build_htab(const ApplyArgs& a, uint8_t* htab) {
+    const int n = 1 << (a.t.T - 4);
+    for (int x = threadIdx.x; x < n; x += blockDim.x) {
+        uint32_t h = 0;
+#pragma unroll
+        for (int i = 0; i < 12; ++i)   // constant indices keep the arguments in parameter space
+            if (i < a.t.T - 4 && ((x >> i) & 1)) h ^= a.fv[4 + i];
+        htab[x] = static_cast<uint8_t>(h);
+    }
+}
+
+__device__ __forceinline__ void load_tile_swz(const TileArgs& a, const uint64_t* runoff, const uint8_t* htab, uint64_t t,
+                                              float2* st) {
+    const uint64_t base = tile_base(a, t);
+    const uint32_t chunks = 1u << (a.T - 1);
+    for (uint32_t q = threadIdx.x; q < chunks; q += blockDim.x) {
+        const uint32_t j = q << 1;
+        cp_async16(st + (j ^ stage_xor(htab, j)), a.psi + tile_global(a, runoff, base, j));
+    }
+}
+
+// Write a transformed tile back in address order (16-byte units).  All of a
+// thread's shared-memory reads come before its stores, which they could not
+// pass otherwise.
+template <int UNITS>
+__device__ __forceinline__ void store_tile_swz(const TileArgs& a, const uint64_t* runoff, const uint8_t* htab,
+                                               uint64_t t, const float2* st) {
+    const uint64_t base = tile_base(a, t);
+    float4 v[UNITS];
+    uint64_t g[UNITS];
+#pragma unroll
+    for (int u = 0; u < UNITS; ++u) {
+        const uint32_t j = (threadIdx.x + u * blockDim.x) << 1;
+        v[u] = *reinterpret_cast<const float4*>(st + (j ^ stage_xor(htab, j)));
+        g[u] = tile_global(a, runoff, base, j);
+    }
+#pragma unroll
+    for (int u = 0; u < UNITS; ++u) __stcs(reinterpret_cast<float4*>(a.psi + g[u]), v[u]);
+}
 
 // The tile pipeline of one fused operator over tiles t0, t0 + stride, ...
 // Ms (G as float2[D][D]), runoff and loff are set up in shared memory.
-template <int K, int R, int S>
+// SWZ (k <= 4): the stage takes the swizzled layout (htab; sloff holds the
+// swizzled group offsets), so a half-warp's gathers meet at most two to a
+// bank wherever the targets sit.  WB (with SWZ, one item per group): each
+// item writes its outputs in place and the tile goes back in address order
+// (16-byte units of 2^TB-amplitude tiles), for target sets whose direct
+// stores would give every lane its own sector.
+template <int K, int R, int S, bool SWZ = false, bool WB = false, int TB = 11>
 __device__ __forceinline__ void apply_tiles(const ApplyArgs& a, float2* stage, const float2* Ms,
-                                            const uint64_t* runoff, const int* loff, uint64_t t0, uint64_t stride) {
+                                            const uint64_t* runoff, const int* loff, uint64_t t0, uint64_t stride,
+                                            const uint8_t* htab = nullptr, const int* sloff = nullptr) {
     constexpr int D = 1 << K;
+    static_assert(!WB || (SWZ && R == D), "in-place outputs: swizzled stage, the whole group in one item");
     const int tileAmps = 1 << a.t.T;
+    auto load = [&](uint64_t t, float2* st) {
+        if constexpr (SWZ)
+            load_tile_swz(a.t, runoff, htab, t, st);
+        else
+            load_tile(a.t, runoff, t, st);
+    };
 #pragma unroll
     for (int s = 0; s < S - 1; ++s) {
         uint64_t t = t0 + s * stride;
-        if (t < a.t.ntiles) load_tile(a.t, runoff, t, stage + s * tileAmps);
+        if (t < a.t.ntiles) load(t, stage + s * tileAmps);
         cp_async_commit();
     }
     const int G = tileAmps >> K;                  // groups per tile
@@ -109,12 +175,12 @@ __device__ __forceinline__ void apply_tiles(const ApplyArgs& a, float2* stage, c
         uint64_t tn = t + (S - 1) * stride;
         int ld_stage = it_stage + (S - 1);
         if (ld_stage >= S) ld_stage -= S;
-        if (tn < a.t.ntiles) load_tile(a.t, runoff, tn, stage + ld_stage * tileAmps);
+        if (tn < a.t.ntiles) load(tn, stage + ld_stage * tileAmps);
         cp_async_commit();
         cp_async_wait<S - 1>();
         __syncthreads();
 
-        const float2* st = stage + it_stage * tileAmps;
+        float2* st = stage + it_stage * tileAmps;
         const uint64_t base = tile_base(a.t, t);
         for (int it = threadIdx.x; it < items; it += blockDim.x) {
             const int g = it & (G - 1);
@@ -122,6 +188,7 @@ __device__ __forceinline__ void apply_tiles(const ApplyArgs& a, float2* stage, c
             uint32_t lb = static_cast<uint32_t>(g);
 #pragma unroll
             for (int j = 0; j < K; ++j) lb = static_cast<uint32_t>(insert_zero(lb, a.tls[j]));
+            const uint32_t lbs = SWZ ? (lb ^ stage_xor(htab, lb)) : lb;   // the group's base in the stage
             if constexpr (K <= 5) {
                 // Packed FP32 pairs: with x2_c = (Re v_c, Re v_c), y2_c = (Im v_c, Im v_c)
                 // and g = (Re G, Im G), p = sum x2_c * g and q = sum y2_c * g give
@@ -130,7 +197,7 @@ __device__ __forceinline__ void apply_tiles(const ApplyArgs& a, float2* stage, c
                 uint64_t x2[D], y2[D];
 #pragma unroll
                 for (int c = 0; c < D; ++c) {
-                    const float2 f = st[lb | loff[c]];
+                    const float2 f = SWZ ? st[lbs ^ sloff[c]] : st[lb | loff[c]];
                     x2[c] = pack2(f.x, f.x);
                     y2[c] = pack2(f.y, f.y);
                 }
@@ -148,8 +215,12 @@ __device__ __forceinline__ void apply_tiles(const ApplyArgs& a, float2* stage, c
                         qv = fma2(y2[c + 1], gg.y, qv);
                     }
                     const float2 P = unpack2(p), Q = unpack2(qv);
-                    const uint32_t lj = lb | loff[r];
-                    __stcs(a.t.psi + tile_global(a.t, runoff, base, lj), make_float2(P.x - Q.y, P.y + Q.x));
+                    if constexpr (WB) {
+                        st[lbs ^ sloff[r]] = make_float2(P.x - Q.y, P.y + Q.x);   // in place: inputs are in registers
+                    } else {
+                        const uint32_t lj = lb | loff[r];
+                        __stcs(a.t.psi + tile_global(a.t, runoff, base, lj), make_float2(P.x - Q.y, P.y + Q.x));
+                    }
                 }
             } else {
                 float2 v[D];
@@ -177,6 +248,10 @@ __device__ __forceinline__ void apply_tiles(const ApplyArgs& a, float2* stage, c
                 }
             }
         }
+        if constexpr (WB) {
+            __syncthreads();
+            store_tile_swz<(1 << (TB - 1)) / kThreads>(a.t, runoff, htab, t, st);
+        }
         __syncthreads();
         if (++it_stage == S) it_stage = 0;
     }
@@ -195,7 +270,7 @@ __device__ __forceinline__ void build_loff(const int* tl, int* loff) {
     }
 }
 
-template <int K, int R, int S>
+template <int K, int R, int S, bool SWZ, bool WB, int TB>
 __global__ void __launch_bounds__(kThreads) k_apply_fp32(ApplyArgs a) {
     constexpr int D = 1 << K;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -204,25 +279,85 @@ __global__ void __launch_bounds__(kThreads) k_apply_fp32(ApplyArgs a) {
     float2* Ms = stage + S * tileAmps;
     uint64_t* runoff = reinterpret_cast<uint64_t*>(Ms + D * D);
     int* loff = reinterpret_cast<int*>(runoff + 64);
+    int* sloff = loff + 64;
+    uint8_t* htab = reinterpret_cast<uint8_t*>(sloff + 64);
 
     const float2* gm = reinterpret_cast<const float2*>(a.mat);
     for (int i = threadIdx.x; i < D * D; i += blockDim.x) Ms[i] = gm[i];
     build_runoff(a.t, runoff);
     build_loff<K>(a.tl, loff);
+    if constexpr (SWZ) {
+        build_htab(a, htab);
+        __syncthreads();
+        for (int c = threadIdx.x; c < D; c += blockDim.x) sloff[c] = loff[c] ^ static_cast<int>(stage_xor(htab, loff[c]));
+    }
     __syncthreads();
-    apply_tiles<K, R, S>(a, stage, Ms, runoff, loff, blockIdx.x, gridDim.x);
+    apply_tiles<K, R, S, SWZ, WB, TB>(a, stage, Ms, runoff, loff, blockIdx.x, gridDim.x, htab, sloff);
 }
 
 template <int K>
 struct ApplyCfg;
-template <> struct ApplyCfg<1> { static constexpr int T = 11, R = 2, S = 3; };
-template <> struct ApplyCfg<2> { static constexpr int T = 11, R = 4, S = 3; };
-template <> struct ApplyCfg<3> { static constexpr int T = 11, R = 8, S = 3; };
+// SWZ: the swizzled stage and, where the targets call for it, in-place outputs
+// with an address-order write-back are available (k <= 4).
+template <> struct ApplyCfg<1> { static constexpr int T = 11, R = 2, S = 2; static constexpr bool SWZ = true; };
+template <> struct ApplyCfg<2> { static constexpr int T = 11, R = 4, S = 2; static constexpr bool SWZ = true; };
+template <> struct ApplyCfg<3> { static constexpr int T = 11, R = 8, S = 2; static constexpr bool SWZ = true; };
 // k = 4: 2^12-amplitude tiles, so that a tile has one 16-row item per thread
-// (2^11 left half of the CTA idle in the compute phase)
-template <> struct ApplyCfg<4> { static constexpr int T = 12, R = 16, S = 3; };
-template <> struct ApplyCfg<5> { static constexpr int T = 12, R = 8, S = 2; };
-template <> struct ApplyCfg<6> { static constexpr int T = 12, R = 8, S = 2; };
+// (2^11 left half of the CTA idle in the compute phase), two stages so that
+// three CTAs fit an SM (faster than three stages at two CTAs)
+template <> struct ApplyCfg<4> { static constexpr int T = 12, R = 16, S = 2; static constexpr bool SWZ = true; };
+template <> struct ApplyCfg<5> { static constexpr int T = 12, R = 8, S = 2; static constexpr bool SWZ = false; };
+template <> struct ApplyCfg<6> { static constexpr int T = 12, R = 8, S = 2; static constexpr bool SWZ = false; };
+
+// Form of a k <= 4 launch from its lowest non-target tile positions np[0..4]
+// (the group-index bits that vary across a warp).  With the plain layout a
+// half-warp's gathers spread over 2^(#np[0..3] below 4) of the 16 bank pairs,
+// and a warp's direct 8-byte stores over 32 / 2^(#np[0..4] below 2) sectors.
+// 0: plain layout, direct stores; 1: swizzled gathers, direct stores (gathers
+// four or more to a bank); 2: swizzled gathers and in-place write-back (one
+// sector per lane).  The thresholds follow CUDA-event timings of all three
+// forms on target sets at N = 30.
+int apply_form(int T, const int* tls, int k) {
+    int np[5], nn = 0;
+    for (int p = 0; p < T && nn < 5; ++p) {
+        bool tgt = false;
+        for (int j = 0; j < k; ++j) tgt = tgt || tls[j] == p;
+        if (!tgt) np[nn++] = p;
+    }
+    int low4 = 0, low2 = 0;
+    for (int b = 0; b < nn; ++b) {
+        if (b < 4 && np[b] < 4) ++low4;
+        if (np[b] < 2) ++low2;
+    }
+    if (low2 == 0) return 2;
+    if (low4 <= 2) return 1;
+    return 0;
+}
+
+// Slot vectors of the swizzled stage: the four lowest non-target tile
+// positions take distinct slot bits where they can (positions 1..3 own theirs;
+// a higher one takes a free one; position 0 is the element within a unit).
+void stage_slots(int T, const int* tls, int k, uint8_t* fv) {
+    for (int p = 0; p < 16; ++p) fv[p] = 0;
+    int np[4], nn = 0;
+    for (int p = 0; p < T && nn < 4; ++p) {
+        bool tgt = false;
+        for (int j = 0; j < k; ++j) tgt = tgt || tls[j] == p;
+        if (!tgt) np[nn++] = p;
+    }
+    uint32_t used = 0;
+    for (int b = 0; b < nn; ++b)
+        if (np[b] >= 1 && np[b] <= 3) used |= 1u << (np[b] - 1);
+    for (int b = 0; b < nn; ++b)
+        if (np[b] >= 4) {
+            int j = 0;
+            while (j < 3 && ((used >> j) & 1u)) ++j;
+            if (j < 3) {
+                used |= 1u << j;
+                fv[np[b]] = static_cast<uint8_t>(1u << j);
+            }
+        }
+}
 
 // Tile-local positions of the targets for geometry g.
 void local_targets(const TileGeom& g, const int* phys, int k, int* tl, int* tls) {
@@ -255,13 +390,18 @@ cudaError_t launch_apply_k(float2* psi, int n, const int* phys, const float* d_m
     for (int e = 0; e < 6; ++e) a.t.xpos[e] = g.xpos[e];
     a.mat = d_mat;
     local_targets(g, phys, K, a.tl, a.tls);
+    // the write-back is unrolled for full tiles (states of at least 2^T
+    // amplitudes); smaller states take the plain form
+    const int form = C::SWZ && g.T == C::T ? apply_form(g.T, a.tls, K) : 0;
+    if (form) stage_slots(g.T, a.tls, K, a.fv);
     const int D = 1 << K;
-    const size_t smem = sizeof(float2) * (static_cast<size_t>(C::S) << g.T) + sizeof(float2) * D * D +
-                        sizeof(uint64_t) * 64 + sizeof(int) * 64;
-    auto kern = k_apply_fp32<K, C::R, C::S>;
+    constexpr size_t tables = sizeof(uint64_t) * 64 + 2 * sizeof(int) * 64 + 256;
+    const size_t smem = sizeof(float2) * (static_cast<size_t>(C::S) << g.T) + sizeof(float2) * D * D + tables;
+    auto kern = form == 2   ? k_apply_fp32<K, C::R, C::S, C::SWZ, C::SWZ, C::T>
+                : form == 1 ? k_apply_fp32<K, C::R, C::S, C::SWZ, false, C::T>
+                            : k_apply_fp32<K, C::R, C::S, false, false, C::T>;
     {
-        const size_t full = sizeof(float2) * (static_cast<size_t>(C::S) << C::T) + sizeof(float2) * D * D +
-                            sizeof(uint64_t) * 64 + sizeof(int) * 64;
+        const size_t full = sizeof(float2) * (static_cast<size_t>(C::S) << C::T) + sizeof(float2) * D * D + tables;
         cudaError_t e = set_smem_attr(reinterpret_cast<const void*>(kern), static_cast<int>(full));
         if (e != cudaSuccess) return e;
     }
@@ -517,6 +657,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch_evolve(BatchArgs a) {
     float2* Ms = stage + (kBatchS << kBatchT);
     uint64_t* runoff = reinterpret_cast<uint64_t*>(Ms + 256);
     int* loff = reinterpret_cast<int*>(runoff + 64);
+    int* sloff = loff + 64;
+    uint8_t* htab = reinterpret_cast<uint8_t*>(sloff + 64);
     __shared__ int s_slot;
     __shared__ int s_stop;
     const long long t_start = clock64();
@@ -548,6 +690,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch_evolve(BatchArgs a) {
                 aa.tl[e] = d.tl[e];
                 aa.tls[e] = d.tls[e];
             }
+#pragma unroll
+            for (int e = 0; e < 16; ++e) aa.fv[e] = d.fv[e];
             const int D = 1 << d.k;
             const float2* gm = reinterpret_cast<const float2*>(a.mats + d.mat_off);
             for (int i = threadIdx.x; i < D * D; i += blockDim.x) Ms[i] = gm[i];
@@ -558,13 +702,34 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch_evolve(BatchArgs a) {
                 case 3: build_loff<3>(aa.tl, loff); break;
                 default: build_loff<4>(aa.tl, loff); break;
             }
+            if (d.form) build_htab(aa, htab);
             __syncthreads();
-            switch (d.k) {
-                case 1: apply_tiles<1, 2, kBatchS>(aa, stage, Ms, runoff, loff, 0, 1); break;
-                case 2: apply_tiles<2, 4, kBatchS>(aa, stage, Ms, runoff, loff, 0, 1); break;
-                case 3: apply_tiles<3, 8, kBatchS>(aa, stage, Ms, runoff, loff, 0, 1); break;
-                default: apply_tiles<4, 8, kBatchS>(aa, stage, Ms, runoff, loff, 0, 1); break;
+            if (d.form) {
+                for (int c = threadIdx.x; c < D; c += blockDim.x)
+                    sloff[c] = loff[c] ^ static_cast<int>(stage_xor(htab, loff[c]));
+                __syncthreads();
             }
+            // the stage forms of the single-state kernel (k = 4 takes two items
+            // per group here, so no in-place write-back)
+#define QSA_BATCH_FORMS(K, R)                                                                                     \
+    if (d.form == 2)                                                                                              \
+        apply_tiles<K, R, kBatchS, true, true, kBatchT>(aa, stage, Ms, runoff, loff, 0, 1, htab, sloff);          \
+    else if (d.form == 1)                                                                                         \
+        apply_tiles<K, R, kBatchS, true, false, kBatchT>(aa, stage, Ms, runoff, loff, 0, 1, htab, sloff);         \
+    else                                                                                                          \
+        apply_tiles<K, R, kBatchS>(aa, stage, Ms, runoff, loff, 0, 1);
+            switch (d.k) {
+                case 1: QSA_BATCH_FORMS(1, 2) break;
+                case 2: QSA_BATCH_FORMS(2, 4) break;
+                case 3: QSA_BATCH_FORMS(3, 8) break;
+                default:
+                    if (d.form)
+                        apply_tiles<4, 8, kBatchS, true, false, kBatchT>(aa, stage, Ms, runoff, loff, 0, 1, htab, sloff);
+                    else
+                        apply_tiles<4, 8, kBatchS>(aa, stage, Ms, runoff, loff, 0, 1);
+                    break;
+            }
+#undef QSA_BATCH_FORMS
             // watchdog: thread 0 decides for the whole CTA
             if (threadIdx.x == 0)
                 s_stop = (a.budget != 0 && static_cast<unsigned long long>(clock64() - t_start) > a.budget) ? 1 : 0;
@@ -649,12 +814,15 @@ bool make_batch_block(int n, const int* phys, int k, uint32_t mat_off, BatchBloc
     for (int e = 0; e < 6; ++e) b->xpos[e] = g.xpos[e];
     local_targets(g, phys, k, b->tl, b->tls);
     b->mat_off = mat_off;
+    b->form = g.T == kBatchT ? apply_form(g.T, b->tls, k) : 0;
+    if (k == 4 && b->form == 2) b->form = 1;   // two items per group: gathers only
+    if (b->form) stage_slots(g.T, b->tls, k, b->fv);
     return true;
 }
 
 cudaError_t launch_batch_evolve(const BatchArgs& a, cudaStream_t st, uint64_t* launches) {
     const size_t smem = sizeof(float2) * (static_cast<size_t>(kBatchS) << kBatchT) + sizeof(float2) * 256 +
-                        sizeof(uint64_t) * 64 + sizeof(int) * 64;
+                        sizeof(uint64_t) * 64 + 2 * sizeof(int) * 64 + 256;
     {
         cudaError_t e = set_smem_attr(reinterpret_cast<const void*>(k_batch_evolve), static_cast<int>(smem));
         if (e != cudaSuccess) return e;

@@ -52,7 +52,8 @@ struct BatchBlock {
     int32_t k, T, m, nx;
     int32_t xpos[6], tl[6], tls[6];
     uint32_t mat_off;   // float offset of G in the matrix table
-    uint32_t pad;
+    int32_t form;       // 0 plain stage, 1 swizzled gathers, 2 swizzled with in-place write-back
+    uint8_t fv[16];     // slot vectors of the swizzled stage
 };
 
 struct BatchArgs {

@@ -93,6 +93,36 @@ def test_low_and_high_target_mixes(q, targets):
         st.close()
 
 
+# Target sets that select each stage form of the FP32 k <= 4 kernels (from the
+# five lowest non-target positions, the bits that vary across a warp): plain
+# layout (no target among the low positions), swizzled gathers (two or more of
+# positions 0..3 are targets, not both 0 and 1), and swizzled gathers with the
+# in-place write-back (positions 0 and 1 are both targets).
+FORM_TARGETS = {
+    "plain": {1: (11,), 2: (10, 11), 3: (9, 10, 11), 4: (8, 9, 10, 11)},
+    "swizzled": {2: (2, 3), 3: (1, 2, 3), 4: (1, 3, 5, 7)},
+    "write_back": {2: (0, 1), 3: (1, 0, 7), 4: (3, 0, 2, 1)},
+}
+
+
+@pytest.mark.parametrize("form,k", [(f, k) for f, d in FORM_TARGETS.items() for k in d])
+@pytest.mark.parametrize("n", [12, 15])
+def test_fp32_stage_forms_match_oracle(q, form, k, n):
+    targets = FORM_TARGETS[form][k]
+    rng = np.random.default_rng(7 * k + n)
+    psi = W.random_state(n, 11 + k)
+    st = GState(q, n, init=psi.astype(np.complex64))
+    ref = psi.astype(np.complex64).astype(np.complex128)
+    try:
+        for _ in range(2):
+            G = W.haar_unitary(1 << k, rng)
+            q.qsa_apply_fused_ex(st.h, targets, G, 0, q.QSA_PREC_FP32)
+            oracle.apply(ref, targets, G)
+        _check_close(ref, st.logical())
+    finally:
+        st.close()
+
+
 def test_brick_circuit_per_gate_matches_oracle(q):
     """Plain per-gate path at N=12 (20 brick layers of Haar U(2) + CZ)."""
     n = 12
