@@ -367,26 +367,30 @@ def batch_record(q, torch, buf, stream, seed, n=20, n_traj=256, shots=10000, p=1
             "hbm_gbs_if_streamed": info["blocks"] * 16.0 * (1 << n) / t / 1e9}
 
 
-def planner_record(q, torch, buf, stream, seed, n=28, layers=40, n_samples=600):
+def planner_record(q, torch, buf, stream, seed, n=28, layers=40, n_samples=1000, precision="tf32x3"):
     """The learned planner against the method without it on the fusion
     workload at N = n: QFT of a seeded basis state, `layers` layers of Haar
     U(2) on every qubit and Haar U(4) on a random matching, then the inverse
-    of everything (the state returns to |0...0>).  Plans with kmax 6, diagonal
-    blocks up to 12 qubits and split-TF32 for k = 5, 6: the width-limit
-    heuristic (greedy), Eq. dp-recurrence with Gamma = 4^k, and the same DP
-    scored by the cost model trained here on this state's own kernel timings.
-    Each plan's run is timed with CUDA events (median of 3)."""
+    of everything (the state returns to |0...0>).  Plans with kmax 6 and
+    diagonal blocks up to 12 qubits: the width-limit heuristic (greedy),
+    Eq. dp-recurrence with Gamma = 4^k, and the same DP scored by the cost
+    model trained here on this state's own kernel timings.  precision
+    "tf32x3" runs k = 5, 6 on the tensor cores (every width then costs about
+    one memory pass, the heuristic's own assumption); "fp32" keeps them on the
+    CUDA cores, where a 6-qubit block costs several passes.  Each plan's run
+    is timed with CUDA events (median of 3)."""
+    prec = q.QSA_PREC_TF32X3 if precision == "tf32x3" else q.QSA_PREC_FP32
     ops, _ = W.fusion_circuit(n=n, layers=layers, seed=seed, with_inverse=True)
     if buf.numel() < (1 << n):
         buf = torch.empty(1 << n, dtype=torch.complex64, device=buf.device)
     s = q.qsa_state_create_ex(n, buf.data_ptr(), 8 << n, stream, 1)
     out = {"workload": f"fusion{n}: QFT + {layers} Haar U(2)/U(4) layers + inverse, {len(ops)} gates, "
-                       f"N={n} complex64", "kmax": 6, "kmax_diag": 12, "precision": "tf32x3"}
+                       f"N={n} complex64", "kmax": 6, "kmax_diag": 12, "precision": precision}
     try:
-        out["cost_model"] = train_cost_model(q, s, q.QSA_PREC_TF32X3, seed, n_samples)
+        out["cost_model"] = train_cost_model(q, s, prec, seed, n_samples)
         for name, planner in (("greedy", q.QSA_PLAN_GREEDY), ("dp_4k", q.QSA_PLAN_DP),
                               ("dp_mlp", q.QSA_PLAN_DP_MLP)):
-            opts = q.make_opts(planner=planner, kmax=6, kmax_diag=12, precision=q.QSA_PREC_TF32X3)
+            opts = q.make_opts(planner=planner, kmax=6, kmax_diag=12, precision=prec)
             t0 = time.perf_counter()
             plan = q.qsa_plan_create(ops, n, opts)
             plan_s = time.perf_counter() - t0
@@ -438,7 +442,7 @@ def train_cost_model(q, s, precision, seed, n_samples):
     perm = np.random.default_rng(seed).permutation(len(y))
     n_tr = int(0.85 * len(y))
     tr, te = perm[:n_tr], perm[n_tr:]
-    params, losses = q.qsa_costmodel_train(X[tr], y[tr], epochs=200, batch=32, lr=2e-3, seed=seed + 7,
+    params, losses = q.qsa_costmodel_train(X[tr], y[tr], epochs=400, batch=32, lr=2e-3, seed=seed + 7,
                                            weight_decay=1e-2)
     q.qsa_costmodel_set(params)
     pred = q.qsa_costmodel_predict(X[te])
@@ -682,6 +686,7 @@ def main():
         extra["tc"] = tc_record(q, torch, buf, stream, n, args.seed, hbm_peak)
     if "planner" in recs:
         extra["planner"] = planner_record(q, torch, buf, stream, args.seed)
+        extra["planner_fp32"] = planner_record(q, torch, buf, stream, args.seed, precision="fp32")
     if "batch" in recs:
         extra["batch"] = batch_record(q, torch, buf, stream, args.seed, n=args.batch_n, n_traj=args.batch_traj,
                                       kmax=args.batch_kmax)

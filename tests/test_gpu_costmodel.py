@@ -116,7 +116,11 @@ def test_learned_planner_gain_over_heuristics(q, capsys):
     """Collect timings from the library's own kernels at N = 26, train the
     model on the GPU, then plan the QAOA workload (3-regular graph, p = 8) with
     the width-limit greedy heuristic, the 4^k DP and the model-scored DP; the
-    measured time of each plan is what the model is scored against."""
+    measured time of each plan is what the model is scored against.  FP32 with
+    kmax 6 is a setting where both heuristics mispredict: a 5- or 6-qubit
+    block on the CUDA cores costs several memory passes (greedy takes them
+    whenever they fit), and 4^k overprices the 2- to 4-qubit blocks that all
+    cost about one pass; the learned DP must beat both by 5 %."""
     n = 26
     st = GState(q, torch, n)
     try:
@@ -132,7 +136,7 @@ def test_learned_planner_gain_over_heuristics(q, capsys):
         ops, _ = W.qaoa_circuit(n=n, p=8, seed=0)
         times, blocks = {}, {}
         for name, planner in [("greedy", q.QSA_PLAN_GREEDY), ("dp_4k", q.QSA_PLAN_DP), ("dp_mlp", q.QSA_PLAN_DP_MLP)]:
-            plan = q.qsa_plan_create(ops, n, q.make_opts(planner=planner, kmax=4, kmax_diag=4))
+            plan = q.qsa_plan_create(ops, n, q.make_opts(planner=planner, kmax=6, kmax_diag=6))
             blocks[name] = q.qsa_plan_info(plan)["blocks"]
             _time_plan(q, st, plan, reps=1)
             times[name] = _time_plan(q, st, plan)
@@ -143,31 +147,40 @@ def test_learned_planner_gain_over_heuristics(q, capsys):
                   f"gain vs greedy {times['greedy'] / times['dp_mlp']:.2f}x, vs 4^k DP "
                   f"{times['dp_4k'] / times['dp_mlp']:.2f}x")
         assert np.median(rel) < 0.10
-        assert times["dp_mlp"] <= 1.05 * min(times["greedy"], times["dp_4k"])
+        assert times["dp_mlp"] <= 0.95 * min(times["greedy"], times["dp_4k"])
     finally:
         q.qsa_costmodel_set(None)
         st.close()
 
 
-def test_learned_planner_on_the_fusion_workload(q, capsys):
+@pytest.mark.parametrize("precision", ["tf32x3", "fp32"])
+def test_learned_planner_on_the_fusion_workload(q, capsys, precision):
     """The fusion workload at N = 28 (QFT of a seeded basis state, 40 layers of
     Haar U(2) on every qubit and U(4) on random matchings, then the inverse;
-    4.2k gates), kmax 6, diagonal blocks up to 12 qubits, split-TF32 for
-    k = 5, 6: the width-limit heuristic, the 4^k DP and the DP scored by a
-    cost model trained on this state's own kernel timings (600 samples), each
-    plan timed with CUDA events.  Every plan returns the state to |0...0>."""
+    4.2k gates), kmax 6, diagonal blocks up to 12 qubits: the width-limit
+    heuristic, the 4^k DP and the DP scored by a cost model trained on this
+    state's own kernel timings (1000 samples), each plan timed with CUDA
+    events.  Every plan returns the state to |0...0>.  With split-TF32 for
+    k = 5, 6 every width costs about one pass, so the learned DP can at best
+    match the greedy plan (within 5 %); in FP32 the wide blocks cost several
+    passes and the learned DP must beat greedy by 10 % and the 4^k DP by 5 %."""
     import bench
     buf = torch.empty(1 << 28, dtype=torch.complex64, device="cuda:0")
     try:
-        rec = bench.planner_record(q, torch, buf, torch.cuda.current_stream().cuda_stream, 0)
+        rec = bench.planner_record(q, torch, buf, torch.cuda.current_stream().cuda_stream, 0, precision=precision)
     finally:
         del buf
         torch.cuda.empty_cache()
     with capsys.disabled():
-        print(f"\nfusion28 planners: greedy {rec['greedy']['seconds']:.4f} s ({rec['greedy']['blocks']} blocks), "
-              f"dp_4k {rec['dp_4k']['seconds']:.4f} s ({rec['dp_4k']['blocks']}), "
+        print(f"\nfusion28 {precision} planners: greedy {rec['greedy']['seconds']:.4f} s "
+              f"({rec['greedy']['blocks']} blocks), dp_4k {rec['dp_4k']['seconds']:.4f} s ({rec['dp_4k']['blocks']}), "
               f"dp_mlp {rec['dp_mlp']['seconds']:.4f} s ({rec['dp_mlp']['blocks']}); gain vs greedy "
               f"{rec['gain_vs_greedy']:.2f}x, vs 4^k DP {rec['gain_vs_dp_4k']:.2f}x; held-out median error "
               f"{rec['cost_model']['heldout_median_rel_err']:.3f}")
     for name in ("greedy", "dp_4k", "dp_mlp"):
         assert rec[name]["return_probability"] > 1 - 1e-4, (name, rec[name]["return_probability"])
+    assert rec["cost_model"]["heldout_median_rel_err"] < 0.10
+    if precision == "fp32":
+        assert rec["gain_vs_greedy"] >= 1.10 and rec["gain_vs_dp_4k"] >= 1.05
+    else:
+        assert rec["gain_vs_greedy"] >= 0.95
