@@ -537,6 +537,9 @@ def main():
     victim = {"first_free": 0, "farthest": 1}[args.victim]
     opts = q.make_opts(planner=planner, kmax=args.kmax, kmax_diag=kdiag, precision=prec, lowering=low, timing=1,
                        victim=victim, kmax_prod=args.kmax_prod, layer=args.layer, zero_init=args.zero_init)
+    # the same plan without per-launch timing, as a user builds it (end-to-end measurement)
+    opts_user = q.make_opts(planner=planner, kmax=args.kmax, kmax_diag=kdiag, precision=prec, lowering=low,
+                            victim=victim, kmax_prod=args.kmax_prod, layer=args.layer, zero_init=args.zero_init)
 
     buf = torch.empty(1 << n, dtype=torch.complex64, device=dev)
     stream = torch.cuda.current_stream(dev).cuda_stream
@@ -643,11 +646,13 @@ def main():
         for _ in range(max(1, min(3, args.steps))):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            reset()
-            st = q.qsa_apply_circuit(s, ops, q.make_opts(planner=planner, kmax=args.kmax, kmax_diag=kdiag,
-                                                          precision=prec, lowering=low, victim=victim,
-                                                          kmax_prod=args.kmax_prod, layer=args.layer,
-                                                          zero_init=args.zero_init))
+            # the plan from the host op list (fusion, FP64 block products, FP32 constants), its upload, and
+            # the run from |0...0> (cleared first unless the plan's first pass writes every amplitude)
+            p_e2e = q.qsa_plan_create(ops, n, opts_user, layout=layout)
+            try:
+                st = q.qsa_plan_execute_from_zero(s, p_e2e)
+            finally:
+                q.qsa_plan_destroy(p_e2e)
             if dm:
                 q.qsa_dm_probabilities(s, n_dm, want_probs=False)
                 q.qsa_dm_expectation_z(s, n_dm, edge_mask)

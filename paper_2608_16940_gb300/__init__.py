@@ -259,20 +259,42 @@ def qsa_apply_diag(s: int, targets: Sequence[int], diag) -> None:
 
 class OpArray:
     """A qsa_op[] built from objects with ``targets``, ``matrix`` (complex,
-    2^k x 2^k) and optional ``diag``; keeps the matrices alive."""
+    2^k x 2^k) and optional ``diag``; the matrices are copied into one
+    contiguous buffer that the array keeps alive.  The records are filled
+    through a numpy view of the C layout (per-op ctypes calls cost several
+    microseconds each)."""
+
+    _dtype = np.dtype({"names": ["k", "targets", "matrix", "flags"],
+                       "formats": ["<i4", ("<i4", 6), "<u8", "<u4"],
+                       "offsets": [qsa_op.k.offset, qsa_op.targets.offset, qsa_op.matrix.offset,
+                                   qsa_op.flags.offset],
+                       "itemsize": _c.sizeof(qsa_op)})
 
     def __init__(self, ops: Iterable):
         ops = list(ops)
-        self.mats = [_cmat(o.matrix) for o in ops]
-        self.arr = (qsa_op * max(1, len(ops)))()
-        for i, o in enumerate(ops):
-            t = list(o.targets)
-            self.arr[i].k = len(t)
-            for j, q in enumerate(t):
-                self.arr[i].targets[j] = int(q)
-            self.arr[i].matrix = self.mats[i].view(np.float64).ctypes.data_as(_dp)
-            self.arr[i].flags = QSA_OP_DIAG if getattr(o, "diag", False) else 0
-        self.n = len(ops)
+        n = len(ops)
+        targets = [tuple(o.targets) for o in ops]
+        ks = np.fromiter((len(t) for t in targets), dtype=np.int64, count=n)
+        offs = np.zeros(n + 1, dtype=np.int64)
+        np.cumsum(np.left_shift(1, 2 * ks), out=offs[1:])
+        self.mats = np.empty(max(1, int(offs[-1])), dtype=np.complex128)
+        tg = np.zeros((max(1, n), 6), dtype=np.int32)
+        by_k = {}
+        for i, t in enumerate(targets):
+            by_k.setdefault(len(t), []).append(i)
+        for k, idx in by_k.items():   # one numpy call per width
+            d = 1 << (2 * k)
+            m = np.asarray([ops[i].matrix for i in idx], dtype=np.complex128).reshape(len(idx), d)
+            self.mats[offs[idx][:, None] + np.arange(d)] = m
+            tg[idx, :k] = np.asarray([targets[i] for i in idx], dtype=np.int32).reshape(len(idx), k)
+        rec = np.zeros(max(1, n), dtype=self._dtype)
+        rec["k"][:n] = ks
+        rec["targets"] = tg
+        rec["matrix"][:n] = self.mats.ctypes.data + 16 * offs[:n]
+        rec["flags"][:n] = [QSA_OP_DIAG if getattr(o, "diag", False) else 0 for o in ops]
+        self.rec = rec
+        self.arr = (qsa_op * max(1, n)).from_buffer(rec)
+        self.n = n
 
 
 def qsa_plan_opts_default() -> qsa_plan_opts:

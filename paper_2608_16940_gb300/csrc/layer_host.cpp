@@ -277,30 +277,60 @@ bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vec
 // up (weight = the share of the state's indices the constant multiplies).
 // Without a carry: the smallest modulus error.  Ties go to the smaller error,
 // then to the candidate nearer z.
+namespace {
+// The FP32 neighbour of a finite float toward -inf (up = false) or +inf: the
+// same value as std::nextafter, by stepping the bit pattern.
+inline float step_float(float x, bool up) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7fffffffu) == 0)
+        u = up ? 0x00000001u : 0x80000001u;
+    else if ((u >> 31) == (up ? 1u : 0u))
+        --u;
+    else
+        ++u;
+    float y;
+    std::memcpy(&y, &u, 4);
+    return y;
+}
+}  // namespace
+
 float2 f2_modulus(std::complex<double> z, double m2, double weight, ModulusCarry* carry) {
-    constexpr float kInf = std::numeric_limits<float>::infinity();
     const float r0 = static_cast<float>(z.real()), i0 = static_cast<float>(z.imag());
-    const float rs[3] = {std::nextafter(r0, -kInf), r0, std::nextafter(r0, kInf)};
-    const float is[3] = {std::nextafter(i0, -kInf), i0, std::nextafter(i0, kInf)};
+    const float rs[3] = {step_float(r0, false), r0, step_float(r0, true)};
+    const float is[3] = {step_float(i0, false), i0, step_float(i0, true)};
     const double acc = carry ? carry->acc : 0.0;
-    float best_r = r0, best_i = i0;
-    double bk = 0.0, be = 0.0, bd = 0.0;
+    const double zr = z.real(), zi = z.imag();
+    double rr[3], ii[3];
+    for (int a = 0; a < 3; ++a) {
+        rr[a] = static_cast<double>(rs[a]) * rs[a];
+        ii[a] = static_cast<double>(is[a]) * is[a];
+    }
+    auto dist = [&](int a, int b) {
+        return (rs[a] - zr) * (rs[a] - zr) + (is[b] - zi) * (is[b] - zi);
+    };
+    int br = 0, bi = 0;
+    double bk = 0.0, be = 0.0;
     bool first = true;
-    for (const float r : rs)
-        for (const float i : is) {
-            const double e = static_cast<double>(r) * r + static_cast<double>(i) * i - m2;
-            const double key = std::fabs(acc + weight * e), d = std::norm(std::complex<double>(r, i) - z);
-            if (first || key < bk || (key == bk && (std::fabs(e) < std::fabs(be) || (std::fabs(e) == std::fabs(be) && d < bd)))) {
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const double e = rr[a] + ii[b] - m2;
+            const double key = std::fabs(acc + weight * e);
+            bool take = first || key < bk;
+            if (!take && key == bk) {
+                const double ae = std::fabs(e), abe = std::fabs(be);
+                take = ae < abe || (ae == abe && dist(a, b) < dist(br, bi));
+            }
+            if (take) {
                 first = false;
                 bk = key;
                 be = e;
-                bd = d;
-                best_r = r;
-                best_i = i;
+                br = a;
+                bi = b;
             }
         }
     if (carry) carry->acc += weight * be;
-    return make_float2(best_r, best_i);
+    return make_float2(rs[br], is[bi]);
 }
 
 void to_float_moduli(const double* z, size_t count, float* out, double weight, ModulusCarry* carry) {
