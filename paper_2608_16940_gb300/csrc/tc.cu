@@ -64,7 +64,9 @@
 //               order), then stores the chunk back in 16-byte units exactly as
 //               the producers read it, so every warp store covers 512
 //               consecutive bytes whatever the target positions.  At the
-//               start group 0 builds A in tensor memory.
+//               start group g builds K half g of A in tensor memory, from G
+//               staged in B buffer 0 (the converters start writing B once A
+//               is ready).
 // Tensor memory (512 columns): A_hi 128, A_lo 128, and one accumulator set of
 // 256 columns (two exact main halves and the two correction products, 64
 // columns each for the pair).
@@ -340,20 +342,14 @@ __device__ __forceinline__ uint64_t chunk_base(const TcArgs& a, uint64_t t) {
 }
 
 // Entry [2 nu + s][2 kap + t] of A: the real embedding of G in the K-bit
-// numbering (k = 5: blockdiag(R, R), the block given by bit 5).
-__device__ float a_entry(const TcArgs& a, int nu, int kap, int s, int t) {
-    int r = nu, c = kap;
-    if (a.k == 5) {
-        if ((nu >> 5) != (kap >> 5)) return 0.f;
-        r &= 31;
-        c &= 31;
-    }
-    int ro = 0, co = 0;
-    for (int b = 0; b < a.k; ++b) {
-        ro |= ((r >> b) & 1) << a.vbit[b];
-        co |= ((c >> b) & 1) << a.vbit[b];
-    }
-    const float2 g = reinterpret_cast<const float2*>(a.mat)[(ro << a.k) + co];
+// numbering (k = 5: blockdiag(R, R), the block given by bit 5).  perm maps a
+// K-bit index to the operator index (bit b to bit vbit[b]); gs is G in shared
+// memory.
+__device__ __forceinline__ float a_entry(const TcArgs& a, const float2* gs, const int* perm, int nu, int kap, int s,
+                                         int t) {
+    if (a.k == 5 && (nu >> 5) != (kap >> 5)) return 0.f;
+    const int m = a.k == 5 ? 31 : 63;
+    const float2 g = gs[(perm[nu & m] << a.k) + perm[kap & m]];
     return s == 0 ? (t == 0 ? g.x : -g.y) : (t == 0 ? g.y : g.x);
 }
 
@@ -403,7 +399,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_apply_tc(TcArgs a) {
         }
         mbar_init(bar(BAR_DFULL), kIssuers);
         mbar_init(bar(BAR_DEMPTY), 256);        // both epilogue groups
-        mbar_init(bar(BAR_AREADY), 128);
+        mbar_init(bar(BAR_AREADY), 256);   // both epilogue groups build A
         mbar_init(bar(BAR_FIN), kIssuers);
         *abort_flag = 0;
         fence_mbar_init();
@@ -411,6 +407,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_apply_tc(TcArgs a) {
     if (warp == kMmaWarp) {
         tmem_alloc(smem_u32(tmem_slot), kTmemCols);
         tmem_relinquish();
+    }
+    // G into B buffer 0 with coalesced loads; the epilogue builds A from
+    // there (scattered reads of G from global memory took about 0.17 ms per
+    // launch), and the converters write B only once A is ready
+    const float2* g_sm = reinterpret_cast<const float2*>(Bsm);
+    int* perm = reinterpret_cast<int*>(Bsm + 32768);   // after G (at most 32 KiB)
+    for (int i = tid; i < (1 << (2 * a.k)); i += kThreads)
+        reinterpret_cast<float2*>(Bsm)[i] = reinterpret_cast<const float2*>(a.mat)[i];
+    if (tid < 64) {
+        int o = 0;
+#pragma unroll
+        for (int b = 0; b < 6; ++b)
+            if (b < a.k && ((tid >> b) & 1)) o |= 1 << a.vbit[b];
+        perm[tid] = o;
     }
     tc_fence_before();
     __syncthreads();
@@ -504,6 +514,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_apply_tc(TcArgs a) {
                 }
                 mbar_arrive(bar(BAR_REMPTY + s));   // the values are in registers: the stage may refill
             }
+            if (pr == 0) {   // B buffer 0 holds G until A is built
+                const bool ok = mbar_wait(bar(BAR_AREADY), 0, abort_flag, a.err, 28, i);
+                if (!__all_sync(0xffffffffu, ok)) break;
+            }
             if (pr >= kNB) {   // the MMAs of pair pr - 2 have read this buffer
                 const bool ok = mbar_wait(bar(BAR_BEMPTY + bb), static_cast<uint32_t>(pr / kNB - 1) & 1u, abort_flag,
                                           a.err, 23, i);
@@ -583,24 +597,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_apply_tc(TcArgs a) {
         const int q = warp & 3;                  // tensor-memory lane quarter
         const int grp = (warp - kEpiWarp) >> 2;  // accumulator set / chunk parity of this group
         const uint32_t lane_t = tmem + (static_cast<uint32_t>(q * 32) << 16);
-        if (grp == 0) {
-            // A: row n = 32 q + lane of the embedding, hi and lo per K half
-            const int n = 32 * q + lane, nu = n >> 1, s = n & 1;
+        {
+            // A: row n = 32 q + lane of the embedding, hi and lo of K half grp
+            const int n = 32 * q + lane, nu = n >> 1, s = n & 1, h = grp;
+            float mx = 0.f;   // entry 2 kap + t of the half: kap = 32 h + (j >> 1), t = j & 1
+#pragma unroll 8
+            for (int j = 0; j < 64; ++j) mx = fmaxf(mx, fabsf(a_entry(a, g_sm, perm, nu, 32 * h + (j >> 1), s, j & 1)));
+            const float magic = seg_magic<kSplitA>(mx);
 #pragma unroll 1
-            for (int h = 0; h < 2; ++h) {
-                float mx = 0.f;   // entry 2 kap + t of the half: kap = 32 h + (j >> 1), t = j & 1
-#pragma unroll 4
-                for (int j = 0; j < 64; ++j) mx = fmaxf(mx, fabsf(a_entry(a, nu, 32 * h + (j >> 1), s, j & 1)));
-                const float magic = seg_magic<kSplitA>(mx);
-#pragma unroll 1
-                for (int c = 0; c < 4; ++c) {
-                    float hi[16], lo[16];
+            for (int c = 0; c < 4; ++c) {
+                float hi[16], lo[16];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        split_one(a_entry(a, nu, 32 * h + 8 * c + (j >> 1), s, j & 1), magic, hi[j], lo[j]);
-                    tmem_st16(lane_t + COL_AHI + 64u * h + 16u * c, hi);
-                    tmem_st16(lane_t + COL_ALO + 64u * h + 16u * c, lo);
-                }
+                for (int j = 0; j < 16; ++j)
+                    split_one(a_entry(a, g_sm, perm, nu, 32 * h + 8 * c + (j >> 1), s, j & 1), magic, hi[j], lo[j]);
+                tmem_st16(lane_t + COL_AHI + 64u * h + 16u * c, hi);
+                tmem_st16(lane_t + COL_ALO + 64u * h + 16u * c, lo);
             }
             tmem_st_wait();
             tc_fence_before();
