@@ -188,6 +188,9 @@ def run_reference(args):
         n_s = min(n_s, 24)   # a k = 6 operator costs 64 complex products per amplitude on the host
         picks = W.wide_circuit(n_s, n_ops=2, widths=(5, 6), seed=args.seed)
         wl, what = f"wide{args.n}", "k=5 / k=6 Haar operator of the wide workload"
+    elif args.workload == "fusion":
+        picks = _fusion_picks(n_s, args.seed)
+        wl, what = f"fusion{args.n}", "U(2) / U(4) gate of the fusion workload"
     else:
         ops, _ = W.qaoa_circuit(n=n_s, p=args.p, seed=args.seed)
         picks = [ops[0], ops[n_s]]   # alternate a one-qubit and a two-qubit gate of the circuit
@@ -211,6 +214,14 @@ def run_reference(args):
                              "sample": f"alternating {what} at N={n_s}, {args.steps} timed gates", **host_cpu()},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _fusion_picks(n: int, seed: int):
+    """A one-qubit and a two-qubit Haar gate of the fusion workload's layers."""
+    ops, _ = W.fusion_circuit(n=n, layers=1, seed=seed, with_inverse=False)
+    one = next(o for o in reversed(ops) if len(o.targets) == 1)
+    two = next(o for o in reversed(ops) if len(o.targets) == 2)
+    return [one, two]
 
 
 class _LoweredOp:
@@ -239,6 +250,9 @@ def cpu_baseline(n_s: int, seed: int, p: int, workload: str = "qaoa", p_dep: flo
         n_s = min(n_s, 24)
         picks = W.wide_circuit(n_s, n_ops=2, widths=(5, 6), seed=seed)
         what = "2 operators (k=5, k=6) of the wide workload"
+    elif workload == "fusion":
+        picks = _fusion_picks(n_s, seed)
+        what = "2 gates (U(2), U(4)) of the fusion workload"
     else:
         ops, _ = W.qaoa_circuit(n=n_s, p=p, seed=seed)
         picks = [ops[0], ops[n_s]]
@@ -457,11 +471,15 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="qaoa", choices=["qaoa", "dm_ghz", "wide"],
+    ap.add_argument("--workload", default="qaoa", choices=["qaoa", "dm_ghz", "wide", "fusion"],
                     help="qaoa: the N=30 QAOA circuit; dm_ghz: noisy GHZ density matrix; wide: --wide-ops Haar "
                          "k=5/6 operators on random targets, one pass each (--precision picks the tensor-core or "
-                         "CUDA-core path)")
+                         "CUDA-core path); fusion: QFT + Haar U(2)/U(4) layers + inverse, planned like the QAOA "
+                         "step (dense blocks up to k = 6, split-TF32 for k = 5, 6)")
     ap.add_argument("--wide-ops", type=int, default=40, help="operators per step of --workload wide")
+    ap.add_argument("--fusion-layers", type=int, default=40,
+                    help="Haar U(2)/U(4) layers of --workload fusion (QFT + layers + inverse; use --n 28 for the "
+                         "N=28 fusion configuration)")
     ap.add_argument("--dm-n", type=int, default=15, help="density-matrix qubits of --workload dm_ghz (2..17)")
     ap.add_argument("--dm-p", type=float, default=1e-2, help="depolarising rate of --workload dm_ghz")
     ap.add_argument("--n", type=int, default=30)
@@ -482,7 +500,7 @@ def main():
                     help="eviction rule of --lowering permute promotions")
     ap.add_argument("--layout", default="interleave", choices=["identity", "interleave"],
                     help="initial layout, set on |0...0> as a metadata-only relabel before each step")
-    ap.add_argument("--cm-samples", type=int, default=240)
+    ap.add_argument("--cm-samples", type=int, default=1000, help="timings the cost model of the bench plan trains on")
     ap.add_argument("--ref-qubits", type=int, default=28)
     ap.add_argument("--cpu-qubits", type=int, default=28)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -514,6 +532,7 @@ def main():
 
     dm = args.workload == "dm_ghz"
     wide = args.workload == "wide"
+    fusion = args.workload == "fusion"
     if wide:
         # each operator is one fused block already (k = 5, 6): no fusion, no layer units, no cost model
         args.planner, args.layer, args.zero_init, args.layout = "per_gate", 0, 0, "identity"
@@ -526,6 +545,10 @@ def main():
     elif wide:
         n = args.n
         ops = W.wide_circuit(n, n_ops=args.wide_ops, widths=(5, 6), seed=args.seed + rank)
+        edges = [(0, 1)]
+    elif fusion:
+        n = args.n
+        ops, _ = W.fusion_circuit(n=n, layers=args.fusion_layers, seed=args.seed + rank, with_inverse=True)
         edges = [(0, 1)]
     else:
         n = args.n
@@ -686,7 +709,7 @@ def main():
                              "hbm_gbs": pst["passes"] * bytes_per_launch / pg_t / 1e9,
                              "fused_speedup": (amp_updates / per_step) / (amp_updates / pg_t)}
 
-    recs = [r for r in args.records.split(",") if r] if (rank == 0 and not dm and not wide) else []
+    recs = [r for r in args.records.split(",") if r] if (rank == 0 and not dm and not wide and not fusion) else []
     if "tc" in recs:
         extra["tc"] = tc_record(q, torch, buf, stream, n, args.seed, hbm_peak)
     if "planner" in recs:
@@ -716,6 +739,10 @@ def main():
                                         f"(depolarising p={args.dm_p:g} after each gate) lowered to superoperators, "
                                         f"vec(rho) on 2n={n} qubits complex64 ({8 * (1 << n) / 2**30:g} GiB), "
                                         f"trace + Tr(rho Z0 Z{n_dm - 1}) per step") if dm else
+                                       (f"fusion{n}: QFT of a seeded basis state + {args.fusion_layers} Haar U(2)/U(4) "
+                                        f"layers + the inverse of everything, {len(ops)} gates, N={n} complex64 "
+                                        f"({8 * (1 << n) / 2**30:g} GiB), returns to |0...0>; norm + <Z0 Z1> + "
+                                        f"{args.shots} shots per step") if fusion else
                                        (f"qaoa{n}_p{args.p}: random 3-regular graph, {len(ops)} gates, N={n} "
                                         f"complex64 ({8 * (1 << n) / 2**30:g} GiB), {args.shots} shots + norm + "
                                         f"<ZZ> per step"),
