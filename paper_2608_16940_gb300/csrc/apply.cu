@@ -18,6 +18,7 @@
 //           sampled as explicit Pauli branches) in one persistent launch: each
 //           CTA pops a trajectory from an atomic queue (longest first), resets
 //           it to |0...0> and applies all of its fused blocks.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -650,8 +651,15 @@ __global__ void k_set_one(float2* psi) { psi[0] = make_float2(1.f, 0.f); }
 // ---------------------------------------------------------------------------
 constexpr int kBatchT = 11;
 constexpr int kBatchS = 3;
+// A trajectory's blocks run one after another, so the batch ends when its
+// deepest trajectory does: each trajectory is run by a cluster of CTAs that
+// split every pass's tiles (rank r takes tiles r, r + C, ...) and meet at a
+// cluster barrier between blocks.
+constexpr int kBatchCluster = 4;
 
-__global__ void __launch_bounds__(kThreads, 4) k_batch_evolve(BatchArgs a) {
+namespace cg = cooperative_groups;
+
+__global__ void __cluster_dims__(kBatchCluster, 1, 1) __launch_bounds__(kThreads, 4) k_batch_evolve(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* stage = reinterpret_cast<float2*>(smem_raw);
     float2* Ms = stage + (kBatchS << kBatchT);
@@ -659,23 +667,33 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch_evolve(BatchArgs a) {
     int* loff = reinterpret_cast<int*>(runoff + 64);
     int* sloff = loff + 64;
     uint8_t* htab = reinterpret_cast<uint8_t*>(sloff + 64);
+    // Rank 0 of the cluster pops the queue and makes the watchdog's decision;
+    // the others read them from its shared memory after a cluster barrier, so
+    // every CTA of a cluster takes the same path and meets the same barriers
+    // (s_stop alternates by block so a value is never rewritten before all
+    // have read it; s_slot is rewritten only after the trajectory's barriers).
     __shared__ int s_slot;
-    __shared__ int s_stop;
+    __shared__ int s_stop[2];
+    cg::cluster_group cluster = cg::this_cluster();
+    const unsigned crank = cluster.block_rank();
     const long long t_start = clock64();
     for (;;) {
-        if (threadIdx.x == 0) s_slot = static_cast<int>(atomicAdd(a.queue, 1u));
-        __syncthreads();
-        const int slot = s_slot;
-        __syncthreads();
-        if (slot >= a.n_traj) break;
+        if (crank == 0 && threadIdx.x == 0) s_slot = static_cast<int>(atomicAdd(a.queue, 1u));
+        cluster.sync();
+        const int slot = *cluster.map_shared_rank(&s_slot, 0);
+        if (slot >= a.n_traj) {
+            cluster.sync();   // no CTA leaves while another may still read its shared memory
+            break;
+        }
         const int traj = a.order[slot];
         float2* psi = a.states + (static_cast<uint64_t>(traj) << a.n);
-        // |0...0>
+        // |0...0>, a share per CTA
         float4* p4 = reinterpret_cast<float4*>(psi);
         const uint64_t npairs = (1ull << a.n) >> 1;
-        for (uint64_t i = threadIdx.x; i < npairs; i += blockDim.x)
+        for (uint64_t i = crank * blockDim.x + threadIdx.x; i < npairs; i += kBatchCluster * blockDim.x)
             p4[i] = make_float4(i == 0 ? 1.f : 0.f, 0.f, 0.f, 0.f);
-        __syncthreads();
+        __threadfence();
+        cluster.sync();
         for (uint32_t b = a.bstart[traj]; b < a.bstart[traj + 1]; ++b) {
             const BatchBlock d = a.blocks[b];
             ApplyArgs aa{};
@@ -713,29 +731,35 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch_evolve(BatchArgs a) {
             // per group here, so no in-place write-back)
 #define QSA_BATCH_FORMS(K, R)                                                                                     \
     if (d.form == 2)                                                                                              \
-        apply_tiles<K, R, kBatchS, true, true, kBatchT>(aa, stage, Ms, runoff, loff, 0, 1, htab, sloff);          \
+        apply_tiles<K, R, kBatchS, true, true, kBatchT>(aa, stage, Ms, runoff, loff, crank, kBatchCluster, htab,  \
+                                                        sloff);                                                   \
     else if (d.form == 1)                                                                                         \
-        apply_tiles<K, R, kBatchS, true, false, kBatchT>(aa, stage, Ms, runoff, loff, 0, 1, htab, sloff);         \
+        apply_tiles<K, R, kBatchS, true, false, kBatchT>(aa, stage, Ms, runoff, loff, crank, kBatchCluster, htab, \
+                                                         sloff);                                                  \
     else                                                                                                          \
-        apply_tiles<K, R, kBatchS>(aa, stage, Ms, runoff, loff, 0, 1);
+        apply_tiles<K, R, kBatchS>(aa, stage, Ms, runoff, loff, crank, kBatchCluster);
             switch (d.k) {
                 case 1: QSA_BATCH_FORMS(1, 2) break;
                 case 2: QSA_BATCH_FORMS(2, 4) break;
                 case 3: QSA_BATCH_FORMS(3, 8) break;
                 default:
                     if (d.form)
-                        apply_tiles<4, 8, kBatchS, true, false, kBatchT>(aa, stage, Ms, runoff, loff, 0, 1, htab, sloff);
+                        apply_tiles<4, 8, kBatchS, true, false, kBatchT>(aa, stage, Ms, runoff, loff, crank,
+                                                                         kBatchCluster, htab, sloff);
                     else
-                        apply_tiles<4, 8, kBatchS>(aa, stage, Ms, runoff, loff, 0, 1);
+                        apply_tiles<4, 8, kBatchS>(aa, stage, Ms, runoff, loff, crank, kBatchCluster);
                     break;
             }
 #undef QSA_BATCH_FORMS
-            // watchdog: thread 0 decides for the whole CTA
-            if (threadIdx.x == 0)
-                s_stop = (a.budget != 0 && static_cast<unsigned long long>(clock64() - t_start) > a.budget) ? 1 : 0;
-            __syncthreads();
-            if (s_stop) {
-                if (threadIdx.x == 0) atomicExch(a.err, 7);
+            // the pass's tiles are written before any CTA of the cluster reads
+            // them in the next block; the watchdog's decision travels with it
+            if (crank == 0 && threadIdx.x == 0)
+                s_stop[b & 1] = (a.budget != 0 && static_cast<unsigned long long>(clock64() - t_start) > a.budget) ? 1 : 0;
+            __threadfence();
+            cluster.sync();
+            if (*cluster.map_shared_rank(&s_stop[b & 1], 0)) {
+                if (crank == 0 && threadIdx.x == 0) atomicExch(a.err, 7);
+                cluster.sync();
                 return;
             }
         }
@@ -831,10 +855,12 @@ cudaError_t launch_batch_evolve(const BatchArgs& a, cudaStream_t st, uint64_t* l
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_evolve, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
-    unsigned grid = static_cast<unsigned>(num_sms() * occ);
-    if (grid > static_cast<unsigned>(a.n_traj)) grid = static_cast<unsigned>(a.n_traj);
-    if (grid == 0) grid = 1;
-    k_batch_evolve<<<grid, kThreads, smem, st>>>(a);
+    // one cluster per trajectory in flight (clusters that find the queue
+    // empty leave at once)
+    unsigned clusters = static_cast<unsigned>(num_sms() * occ / kBatchCluster);
+    if (clusters > static_cast<unsigned>(a.n_traj)) clusters = static_cast<unsigned>(a.n_traj);
+    if (clusters == 0) clusters = 1;
+    k_batch_evolve<<<clusters * kBatchCluster, kThreads, smem, st>>>(a);
     ++*launches;
     return cudaGetLastError();
 }
