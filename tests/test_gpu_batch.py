@@ -58,6 +58,26 @@ def test_batch_matches_oracle(q, use_graph):
         q.qsa_batch_destroy(b)
 
 
+@pytest.mark.parametrize("n", [6, 11, 13, 15])
+def test_cluster_edge_cases(q, n):
+    """A trajectory runs on a cluster of CTAs that split each pass's tiles:
+    states of one tile (all but one CTA idle), of a few tiles, and of more
+    tiles than CTAs; empty trajectories (the clear and nothing else), a single
+    trajectory, and more trajectories than clusters in flight."""
+    deep, _ = W.trajectory_batch(n_traj=3, n=n, dmin=4, dmax=9, seed=n, p=0.05)
+    cases = [[deep[0]], [[], deep[1], [], deep[2], []]]
+    for trajs in cases:
+        b = q.qsa_batch_create(n, trajs, q.make_opts(planner=q.QSA_PLAN_DP, kmax=4, kmax_diag=4))
+        states = torch.full((len(trajs) << n,), 7.0 + 1j, dtype=torch.complex64, device="cuda:0")
+        try:
+            q.qsa_batch_run(b, states.data_ptr(), states.numel() * 8, 100, 3, 0, 1)
+            got = states.cpu().numpy().reshape(len(trajs), 1 << n).astype(np.complex128)
+            for t, ops in enumerate(trajs):
+                check_close(oracle.run_circuit(n, ops), got[t])
+        finally:
+            q.qsa_batch_destroy(b)
+
+
 def test_graph_and_direct_paths_agree(q):
     n, n_traj, shots = 12, 20, 1000
     trajs, _ = W.trajectory_batch(n_traj=n_traj, n=n, dmin=3, dmax=12, seed=8, p=0.02)
