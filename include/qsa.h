@@ -482,11 +482,13 @@ qsa_status qsa_sample_counts(qsa_state s, uint64_t shots, uint64_t seed, uint64_
 /* ---- batched trajectories ---------------------------------------------------
  * Many independent small states (noisy trajectories: the per-gate Pauli
  * channels of §IV-A sampled into explicit Pauli branches, so every trajectory
- * is a unitary circuit) evolved in ONE persistent kernel launch: each CTA pops
- * a trajectory from an atomic queue (longest first), resets it to |0..0> and
- * applies all of its fused blocks; a second kernel samples every state (one
- * CTA per trajectory, Philox stream id = trajectory index, identity layout),
- * and both can be replayed as one captured CUDA graph. */
+ * is a unitary circuit) evolved in ONE persistent kernel launch: each
+ * thread-block cluster of four CTAs pops a trajectory from an atomic queue
+ * (longest first), resets it to |0..0> and applies all of its fused blocks,
+ * the four CTAs splitting every pass's tiles and meeting at a cluster barrier
+ * between blocks; a second kernel samples every state (one CTA per
+ * trajectory, Philox stream id = trajectory index, identity layout), and both
+ * can be replayed as one captured CUDA graph. */
 typedef struct qsa_batch_s* qsa_batch;
 
 /* Host planning + one-time upload: trajectory t is ops[op_offsets[t] ..
@@ -503,8 +505,9 @@ qsa_status qsa_batch_info(qsa_batch b, size_t* total_blocks, size_t* total_ops, 
  * draw `shots` (1..16384) samples of each with the rule of qsa_sample_counts
  * (stream id t).  use_graph = 1 captures the launches into a CUDA graph on
  * first use (re-captured when an argument changes) and replays it.
- * budget_cycles > 0 bounds each CTA's run time in SM clock cycles: a CTA that
- * runs over stops between blocks and the call returns QSA_E_TIMEOUT.
+ * budget_cycles > 0 bounds each cluster's run time in SM clock cycles (as seen
+ * by its first CTA): a cluster that runs over stops between blocks and the
+ * call returns QSA_E_TIMEOUT.
  * Synchronises cuda_stream; stats->seconds is the device time of the launch. */
 qsa_status qsa_batch_run(qsa_batch b, void* dev_states, size_t bytes, uint64_t shots, uint64_t seed,
                          uint64_t budget_cycles, int use_graph, void* cuda_stream, qsa_run_stats* stats);
