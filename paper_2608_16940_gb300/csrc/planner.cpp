@@ -423,18 +423,28 @@ void left_multiply(std::vector<std::complex<double>>& M, int u, const int* pos, 
             if ((c >> j) & 1) o |= size_t(1) << pos[j];
         off[c] = o;
     }
-    std::vector<std::complex<double>> v(d);
-    for (size_t col = 0; col < D; ++col)
-        for (size_t x = 0; x < D; ++x) {
-            if (x & opmask) continue;
-            for (size_t c = 0; c < d; ++c) v[c] = M[(x | off[c]) * D + col];
-            for (size_t r = 0; r < d; ++r) {
-                std::complex<double> acc = 0;
-                for (size_t c = 0; c < d; ++c)
-                    acc += std::complex<double>(g[2 * (r * d + c)], g[2 * (r * d + c) + 1]) * v[c];
-                M[(x | off[r]) * D + col] = acc;
+    // whole rows at a time (contiguous, real arithmetic): rows x | off[r] of
+    // the product are sum_c g[r][c] * rows x | off[c], summed in c order
+    double* m = reinterpret_cast<double*>(M.data());
+    std::vector<double> in(2 * d * D);
+    for (size_t x = 0; x < D; ++x) {
+        if (x & opmask) continue;
+        for (size_t c = 0; c < d; ++c)
+            std::copy(m + 2 * (x | off[c]) * D, m + 2 * ((x | off[c]) * D + D), in.data() + 2 * c * D);
+        for (size_t r = 0; r < d; ++r) {
+            double* out = m + 2 * (x | off[r]) * D;
+            std::fill(out, out + 2 * D, 0.0);
+            for (size_t c = 0; c < d; ++c) {
+                const double gr = g[2 * (r * d + c)], gi = g[2 * (r * d + c) + 1];
+                const double* v = in.data() + 2 * c * D;
+                for (size_t col = 0; col < D; ++col) {
+                    const double vr = v[2 * col], vi = v[2 * col + 1];
+                    out[2 * col] += gr * vr - gi * vi;
+                    out[2 * col + 1] += gr * vi + gi * vr;
+                }
             }
         }
+    }
 }
 
 // Fused matrix of ops[s..e) on the ascending union of their targets.
