@@ -635,6 +635,18 @@ qsa_status qsa_debug_fail_alloc(int64_t nth);
  * and batch uploads, scratch): a leak check for the error paths. */
 uint64_t qsa_debug_live_allocations(void);
 
+/* Debug-build bounds checks.  A library built with -DQSA_DEBUG_BOUNDS
+ * (paper_2608_16940_gb300/build.py --debug-bounds: libqsa_debug.so) checks the
+ * state indices of the fused-update, permutation, product, batched, layer and
+ * tensor-core kernels' global loads and stores; an out-of-range access is
+ * skipped (no trap, no assert) and the first one of each kernel file is kept.
+ * qsa_debug_bounds_status returns the first record found as
+ * (check code << 48) | index, 0 when no check has failed (always 0 in a
+ * release build); it reads device memory, so call it after the stream is
+ * synchronised.  qsa_debug_bounds_enabled returns 1 in the debug build. */
+uint64_t qsa_debug_bounds_status(void);
+int qsa_debug_bounds_enabled(void);
+
 const char* qsa_last_error(void);
 
 #ifdef __cplusplus

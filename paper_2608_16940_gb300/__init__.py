@@ -19,7 +19,9 @@ from typing import Iterable, List, Optional, Sequence, Tuple
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libqsa.so")
+# QSA_LIB_VARIANT=debug loads the bounds-checked build (libqsa_debug.so, from
+# build.py --debug-bounds) instead of the release library
+LIB_PATH = os.path.join(_HERE, "libqsa_debug.so" if os.environ.get("QSA_LIB_VARIANT") == "debug" else "libqsa.so")
 
 QSA_OK, QSA_E_ARG, QSA_E_RANGE, QSA_E_NOMEM, QSA_E_CUDA, QSA_E_TIMEOUT, QSA_E_UNSUPPORTED, QSA_E_STATE = range(8)
 QSA_C64, QSA_C128 = 0, 1
@@ -583,6 +585,8 @@ _f["qsa_costmodel_save"] = _sig("qsa_costmodel_save", [_c.c_char_p])
 _f["qsa_costmodel_load"] = _sig("qsa_costmodel_load", [_vp, _c.c_char_p])
 _f["qsa_debug_fail_alloc"] = _sig("qsa_debug_fail_alloc", [_c.c_int64])
 _f["qsa_debug_live_allocations"] = _sig("qsa_debug_live_allocations", [], _c.c_uint64)
+_f["qsa_debug_bounds_status"] = _sig("qsa_debug_bounds_status", [], _c.c_uint64)
+_f["qsa_debug_bounds_enabled"] = _sig("qsa_debug_bounds_enabled", [], _c.c_int)
 
 
 def qsa_costmodel_save(path: str) -> None:
@@ -600,6 +604,16 @@ def qsa_debug_fail_alloc(nth: int) -> None:
 
 def qsa_debug_live_allocations() -> int:
     return int(_f["qsa_debug_live_allocations"]())
+
+
+def qsa_debug_bounds_status() -> Tuple[int, int]:
+    """(check code, index) of the first failed bounds check, (0, 0) if none."""
+    w = int(_f["qsa_debug_bounds_status"]())
+    return w >> 48, w & ((1 << 48) - 1)
+
+
+def qsa_debug_bounds_enabled() -> bool:
+    return bool(_f["qsa_debug_bounds_enabled"]())
 
 
 def qsa_costmodel_init(seed: int) -> np.ndarray:

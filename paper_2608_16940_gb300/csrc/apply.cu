@@ -27,6 +27,7 @@
 #include <mutex>
 #include <utility>
 
+#include "qsa_bounds.cuh"
 #include "qsa_device.cuh"
 #include "qsa_internal.h"
 
@@ -75,7 +76,8 @@ __device__ __forceinline__ void load_tile(const TileArgs& a, const uint64_t* run
     const uint32_t chunks = 1u << (a.T - 1);
     for (uint32_t q = threadIdx.x; q < chunks; q += blockDim.x) {
         uint32_t j = q << 1;
-        cp_async16(st + j, a.psi + tile_global(a, runoff, base, j));
+        const uint64_t gi = tile_global(a, runoff, base, j);
+        if (dbg::in_bounds(gi, 2, a.ntiles << a.T, 1)) cp_async16(st + j, a.psi + gi);
     }
 }
 
@@ -118,7 +120,8 @@ __device__ __forceinline__ void load_tile_swz(const TileArgs& a, const uint64_t*
     const uint32_t chunks = 1u << (a.T - 1);
     for (uint32_t q = threadIdx.x; q < chunks; q += blockDim.x) {
         const uint32_t j = q << 1;
-        cp_async16(st + (j ^ stage_xor(htab, j)), a.psi + tile_global(a, runoff, base, j));
+        const uint64_t gi = tile_global(a, runoff, base, j);
+        if (dbg::in_bounds(gi, 2, a.ntiles << a.T, 2)) cp_async16(st + (j ^ stage_xor(htab, j)), a.psi + gi);
     }
 }
 
@@ -138,7 +141,8 @@ __device__ __forceinline__ void store_tile_swz(const TileArgs& a, const uint64_t
         g[u] = tile_global(a, runoff, base, j);
     }
 #pragma unroll
-    for (int u = 0; u < UNITS; ++u) __stcs(reinterpret_cast<float4*>(a.psi + g[u]), v[u]);
+    for (int u = 0; u < UNITS; ++u)
+        if (dbg::in_bounds(g[u], 2, a.ntiles << a.T, 3)) __stcs(reinterpret_cast<float4*>(a.psi + g[u]), v[u]);
 }
 
 // The tile pipeline of one fused operator over tiles t0, t0 + stride, ...
@@ -219,8 +223,9 @@ __device__ __forceinline__ void apply_tiles(const ApplyArgs& a, float2* stage, c
                     if constexpr (WB) {
                         st[lbs ^ sloff[r]] = make_float2(P.x - Q.y, P.y + Q.x);   // in place: inputs are in registers
                     } else {
-                        const uint32_t lj = lb | loff[r];
-                        __stcs(a.t.psi + tile_global(a.t, runoff, base, lj), make_float2(P.x - Q.y, P.y + Q.x));
+                        const uint64_t gj = tile_global(a.t, runoff, base, lb | loff[r]);
+                        if (dbg::in_bounds(gj, 1, a.t.ntiles << a.t.T, 4))
+                            __stcs(a.t.psi + gj, make_float2(P.x - Q.y, P.y + Q.x));
                     }
                 }
             } else {
@@ -244,8 +249,8 @@ __device__ __forceinline__ void apply_tiles(const ApplyArgs& a, float2* stage, c
                         ai = fmaf(m2.z, v[c + 1].y, ai);
                         ai = fmaf(m2.w, v[c + 1].x, ai);
                     }
-                    const uint32_t lj = lb | loff[r];
-                    __stcs(a.t.psi + tile_global(a.t, runoff, base, lj), make_float2(ar, ai));
+                    const uint64_t gj = tile_global(a.t, runoff, base, lb | loff[r]);
+                    if (dbg::in_bounds(gj, 1, a.t.ntiles << a.t.T, 4)) __stcs(a.t.psi + gj, make_float2(ar, ai));
                 }
             }
         }
@@ -497,14 +502,14 @@ __device__ __forceinline__ void prod_round(const ProdArgs& a, float2* st, const 
             }
         }
         if (last) {
-            float2* g0 = a.t.psi + tile_global(a.t, runoff, base, ub);
+            const uint64_t g0 = tile_global(a.t, runoff, base, ub);
 #pragma unroll
             for (int c = 0; c < G; ++c) {
                 uint64_t go = 0;
 #pragma unroll
                 for (int j = 0; j < H; ++j)
                     if ((c >> j) & 1) go += gb[j];
-                __stcs(g0 + go, v[c]);
+                if (dbg::in_bounds(g0 + go, 1, a.t.ntiles << a.t.T, 5)) __stcs(a.t.psi + g0 + go, v[c]);
             }
         } else {
 #pragma unroll
@@ -635,8 +640,9 @@ __global__ void __launch_bounds__(kThreads) k_permute(PermArgs a) {
                 s1 ^= (x1 << a.la[i]) | (x1 << a.lb[i]);
             }
             float2 v0 = st[s0], v1 = st[s1];
-            float4* dst = reinterpret_cast<float4*>(a.t.psi + tile_global(a.t, runoff, base, d0));
-            __stcs(dst, make_float4(v0.x, v0.y, v1.x, v1.y));
+            const uint64_t gd = tile_global(a.t, runoff, base, d0);
+            if (dbg::in_bounds(gd, 2, a.t.ntiles << a.t.T, 6))
+                __stcs(reinterpret_cast<float4*>(a.t.psi + gd), make_float4(v0.x, v0.y, v1.x, v1.y));
         }
         __syncthreads();
         if (++it_stage == S) it_stage = 0;
@@ -767,6 +773,8 @@ __global__ void __cluster_dims__(kBatchCluster, 1, 1) __launch_bounds__(kThreads
 }
 
 }  // namespace
+
+QSA_BOUNDS_READER(bounds_word_apply)
 
 int num_sms() {
     static std::mutex mu;

@@ -40,6 +40,7 @@
 #include <cstdint>
 
 #include "qsa_device.cuh"
+#include "qsa_bounds.cuh"
 #include "qsa_internal.h"
 
 namespace qsa {
@@ -236,7 +237,8 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
         // (round 0 never stores: as the last round it goes through the stage)
         static_assert(R > 0, "round 0 writes to the stage");
 #pragma unroll
-        for (int i = 0; i < 16; ++i) __stcs(a.psi + (gb | goff[16 * R + i]), v[i]);
+        for (int i = 0; i < 16; ++i)
+            if (dbg::in_bounds(gb | goff[16 * R + i], 1, a.ntiles << 12, 11)) __stcs(a.psi + (gb | goff[16 * R + i]), v[i]);
     } else {
         if constexpr (R == 0) {
 #pragma unroll
@@ -448,7 +450,8 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
         if (GEN == 0 || (GEN == 2 && !a.generate))
 #pragma unroll
             for (int k = 0; k < kLAmps / 2 / kLThreads; ++k)
-                cp_async16(st + (sld ^ lsw(512 * k)), a.psi + (base | goff[48 + k]));
+                if (dbg::in_bounds(base | goff[48 + k], 2, a.ntiles << 12, 12))
+                    cp_async16(st + (sld ^ lsw(512 * k)), a.psi + (base | goff[48 + k]));
         if (use_rec && threadIdx.x < static_cast<int>(sizeof(LayerRec) / 16))
             cp_async16(reinterpret_cast<float4*>(recs + sidx) + threadIdx.x,
                        reinterpret_cast<const float4*>(a.rec + t) + threadIdx.x);
@@ -489,7 +492,8 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
                 for (int k = 0; k < kLAmps / 2 / kLThreads; ++k) {
                     float4 c = *reinterpret_cast<const float4*>(st + (sx ^ lsw(512 * k)));
                     if (hx) c = make_float4(c.z, c.w, c.x, c.y);
-                    __stcs(reinterpret_cast<float4*>(a.psi + (base | gld | goff[48 + k])), c);
+                    if (dbg::in_bounds(base | gld | goff[48 + k], 2, a.ntiles << 12, 13))
+                        __stcs(reinterpret_cast<float4*>(a.psi + (base | gld | goff[48 + k])), c);
                 }
             } else if (r1) {
                 __syncwarp();
@@ -607,5 +611,7 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
     ++*launches;
     return cudaGetLastError();
 }
+
+QSA_BOUNDS_READER(bounds_word_layer)
 
 }  // namespace qsa

@@ -40,6 +40,12 @@ cudaError_t dev_malloc(T** p, size_t bytes) {
 }
 void dev_free(void* p);
 
+// First bounds-check record of each checked translation unit ((code << 48) |
+// index, 0 if none; always 0 unless built with -DQSA_DEBUG_BOUNDS).
+uint64_t bounds_word_apply();
+uint64_t bounds_word_layer();
+uint64_t bounds_word_tc();
+
 // Number of SMs of the current device (cached per device).
 int num_sms();
 // cudaFuncSetAttribute(kernel, MaxDynamicSharedMemorySize, bytes) on the

@@ -330,6 +330,20 @@ uint64_t qsa_debug_live_allocations(void) {
     return v < 0 ? 0 : static_cast<uint64_t>(v);
 }
 
+uint64_t qsa_debug_bounds_status(void) {
+    for (uint64_t w : {bounds_word_apply(), bounds_word_layer(), bounds_word_tc()})
+        if (w) return w;
+    return 0;
+}
+
+int qsa_debug_bounds_enabled(void) {
+#ifdef QSA_DEBUG_BOUNDS
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 const char* qsa_last_error(void) { return g_err.c_str(); }
 
 qsa_status qsa_state_create_ex(int n_qubits, qsa_dtype dtype, void* dev_buf, size_t bytes, void* cuda_stream,

@@ -77,6 +77,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "qsa_bounds.cuh"
 #include "qsa_internal.h"
 #include "qsa_runtime.h"
 
@@ -453,7 +454,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_apply_tc(TcArgs a) {
             const uint64_t base = chunk_base(a, blockIdx.x + i * gridDim.x) | gl;
             const uint32_t d0 = raw0 + static_cast<uint32_t>(s) * kRawBytes;
 #pragma unroll
-            for (int u = u0; u < u0 + kU; ++u) cp_async16(d0 + (sl ^ si_tab[u]), a.psi + (base | gi_tab[u]));
+            for (int u = u0; u < u0 + kU; ++u)
+                if (dbg::in_bounds(base | gi_tab[u], 2, a.nchunks << kChunkBits, 21))
+                    cp_async16(d0 + (sl ^ si_tab[u]), a.psi + (base | gi_tab[u]));
             cp_async_arrive_noinc(bar(BAR_RFULL + s));
         }
         cp_async_wait_all();   // no copy may land after the CTA has left
@@ -680,8 +683,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_apply_tc(TcArgs a) {
             const uint64_t base = chunk_base(a, blockIdx.x + i * gridDim.x) | gl;
 #pragma unroll
             for (int u = 8 * q; u < 8 * q + 8; ++u)
-                __stcs(reinterpret_cast<float4*>(a.psi + (base | gi_tab[u])),
-                       *reinterpret_cast<const float4*>(ost + (ol ^ oi_tab[u])));
+                if (dbg::in_bounds(base | gi_tab[u], 2, a.nchunks << kChunkBits, 22))
+                    __stcs(reinterpret_cast<float4*>(a.psi + (base | gi_tab[u])),
+                           *reinterpret_cast<const float4*>(ost + (ol ^ oi_tab[u])));
         }
     }
     tc_fence_before();
@@ -763,6 +767,8 @@ cudaError_t launch_pair(const TcArgs& a, uint64_t nchunks, cudaStream_t st, uint
 }
 
 }  // namespace
+
+QSA_BOUNDS_READER(bounds_word_tc)
 
 bool tc_available(qsa_state s, int k) { return (k == 5 || k == 6) && s->n >= kChunkBits; }
 
