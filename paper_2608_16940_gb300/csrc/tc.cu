@@ -557,7 +557,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_apply_tc(TcArgs a) {
             mbar_arrive(bar(BAR_BFULL + bb));
         }
     } else if (warp >= kMmaWarp && warp < kMmaWarp + kIssuers) {
-        // ---------------- MMA issuers: product mi of every chunk ----------------
+        // ---------------- MMA issuers: product mi of every pair ----------------
         if (lane == 0) {
             const int mi = warp - kMmaWarp;   // 0: A_hi B_hi (two exact halves), 1: A_hi B_lo, 2: A_lo B_hi
             bool ok = mbar_wait(bar(BAR_AREADY), 0, abort_flag, a.err, 24);
@@ -596,7 +596,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_apply_tc(TcArgs a) {
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue (warps 4-11) ----------------
+        // ---------------- epilogue (warps 8-15) ----------------
         const int q = warp & 3;                  // tensor-memory lane quarter
         const int grp = (warp - kEpiWarp) >> 2;  // accumulator set / chunk parity of this group
         const uint32_t lane_t = tmem + (static_cast<uint32_t>(q * 32) << 16);
