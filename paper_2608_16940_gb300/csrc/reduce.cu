@@ -214,22 +214,46 @@ __device__ __forceinline__ void square_pair(float x, float y, float& hi, float& 
     lo = __fadd_rn(e, __fadd_rn(l1, l2));
 }
 
-// s + c += (-1)^sign (hi + lo), sign given as the FP32 sign bit.
-__device__ __forceinline__ void add_signed(float& s, float& c, float hi, float lo, uint32_t signbit) {
-    const float h = __uint_as_float(__float_as_uint(hi) ^ signbit);
-    const float l = __uint_as_float(__float_as_uint(lo) ^ signbit);
-    const float t = __fadd_rn(s, h);
+// Weight of one component from its bits when its biased exponent e is at most
+// 127 (|v| < 2): the product (M 2^8)(M 2^7) and the right shift by 255 - 2e of
+// sq_fixed60, with the shift left unclamped (PTX shr.b64 takes shifts above 64
+// as 64 and gives 0, as the clamped shift does: the product is below 2^63).
+// The implicit bit is set unconditionally; for e = 0 (zero, subnormals) the
+// shift is 255, so the result is 0 as in sq_fixed60.  255 - 2e = 2e ^ 255
+// since 2e < 256.
+__device__ __forceinline__ uint64_t sq_fixed60_small(uint32_t bits) {
+    const uint32_t mp = (bits << 8) | 0x80000000u;
+    const uint32_t sh = ((bits >> 22) & 0x1feu) ^ 0xffu;
+    const uint64_t prod = static_cast<uint64_t>(mp) * (mp >> 1);
+    uint64_t r;
+    asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(prod), "r"(sh));
+    return r;
+}
+
+// s + c += g (hi + lo) for g = +-1, in double-float: Knuth's two-sum of s and
+// g hi (its rounding error to c with g lo), the sign taken inside FMAs (g hi
+// and g lo are exact products, so each FMA rounds once, like an addition of
+// the negated term).
+__device__ __forceinline__ void add_scaled(float& s, float& c, float hi, float lo, float g) {
+    const float t = __fmaf_rn(g, hi, s);
     const float bp = __fsub_rn(t, s);
-    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(h, bp));
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fmaf_rn(g, hi, -bp));
     s = t;
-    c = __fadd_rn(c, __fadd_rn(e, l));
+    c = __fadd_rn(c, __fmaf_rn(g, lo, e));
 }
 
 // Blocks of 1024 amplitudes: the block weights and the <Z_mask> sums of NM
 // masks in one read.  A warp takes a block; lane l loads the 16-byte pairs
 // l + 32 k (k = 0..15) up front, so 8 KiB per warp are in flight.  Amplitude
 // y = 1024 w + 2 (l + 32 k) + b has its index bits split over (w, l, k, b), so
-// its sign parity is a per-block, a per-lane, a per-k and a per-b part.  Per
+// its sign parity is a per-block, a per-lane, a per-k and a per-b part.
+// Weights: when no component of the block has |v| >= 2 (always, for a state
+// of norm about 1) the warp takes sq_fixed60_small, else sq_fixed60 (equal
+// values where both apply).  Sums: each thread keeps its mask-m pair in the
+// frame of its own block-and-lane sign (the pair negated when that sign
+// changes between blocks; round-to-nearest is symmetric, so the values are
+// those of summing in the true signs, up to the sign of zeros), so the sign
+// left per amplitude, of its k and b bits, is the same across the warp.  Per
 // CTA partials of mask m at m * gridDim.x.
 template <int NM>
 __global__ void __launch_bounds__(kRedThreads, 2) k_weights_z1024(const float4* __restrict__ psi2, uint64_t nblocks,
@@ -239,35 +263,58 @@ __global__ void __launch_bounds__(kRedThreads, 2) k_weights_z1024(const float4* 
     const int lane = threadIdx.x & 31;
     const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x >> 5);
     float zs[NA] = {}, zc[NA] = {};
-    uint32_t kb[NA] = {}, lb[NA] = {}, b1[NA] = {};
+    uint32_t kb[NA] = {}, lb[NA] = {}, fr[NA] = {};
+    float bf[NA] = {};
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
         for (int k = 0; k < 16; ++k) kb[m] |= static_cast<uint32_t>(__popcll((64ull * k) & masks.m[m]) & 1) << k;
         lb[m] = __popcll((2ull * lane) & masks.m[m]) & 1;
-        b1[m] = static_cast<uint32_t>(masks.m[m] & 1ull) << 31;
+        bf[m] = (masks.m[m] & 1ull) ? -1.f : 1.f;
     }
     for (uint64_t w = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; w < nblocks; w += warps) {
         const float4* p = psi2 + w * 512 + lane;
         float4 a[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) a[k] = __ldcs(p + 32 * k);
-        uint32_t pb[NA] = {};
+        if constexpr (NM > 0) {
 #pragma unroll
-        for (int m = 0; m < NM; ++m) pb[m] = (__popcll((w << 10) & masks.m[m]) & 1) ^ lb[m];
+            for (int m = 0; m < NM; ++m) {
+                // this thread's sign for the block; the pair follows it into the new frame
+                const uint32_t f = (__popcll((w << 10) & masks.m[m]) & 1) ^ lb[m];
+                if (f != fr[m]) {
+                    zs[m] = -zs[m];
+                    zc[m] = -zc[m];
+                    fr[m] = f;
+                }
+            }
+        }
+        uint32_t any = 0;
         uint64_t s = 0;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-            s += sq_fixed60(a[k].x) + sq_fixed60(a[k].y) + sq_fixed60(a[k].z) + sq_fixed60(a[k].w);
+            const uint32_t x0 = __float_as_uint(a[k].x), y0 = __float_as_uint(a[k].y);
+            const uint32_t x1 = __float_as_uint(a[k].z), y1 = __float_as_uint(a[k].w);
+            any |= x0 | y0 | x1 | y1;
+            s += sq_fixed60_small(x0) + sq_fixed60_small(y0) + sq_fixed60_small(x1) + sq_fixed60_small(y1);
             if constexpr (NM > 0) {
                 float h0, l0, h1, l1;
                 square_pair(a[k].x, a[k].y, h0, l0);
                 square_pair(a[k].z, a[k].w, h1, l1);
 #pragma unroll
                 for (int m = 0; m < NM; ++m) {
-                    const uint32_t s0 = ((pb[m] ^ (kb[m] >> k)) & 1u) << 31;
-                    add_signed(zs[m], zc[m], h0, l0, s0);
-                    add_signed(zs[m], zc[m], h1, l1, s0 ^ b1[m]);
+                    const float g0 = __uint_as_float(0x3f800000u | (((kb[m] >> k) & 1u) << 31));
+                    add_scaled(zs[m], zc[m], h0, l0, g0);
+                    add_scaled(zs[m], zc[m], h1, l1, g0 * bf[m]);
                 }
+            }
+        }
+        if (!__all_sync(0xffffffffu, (any & 0x40000000u) == 0u)) {
+            // a component with |v| >= 2 (or not finite) in the block: the weights again, by sq_fixed60
+            s = 0;
+#pragma unroll 4
+            for (int k = 0; k < 16; ++k) {
+                const float4 v = __ldcs(p + 32 * k);
+                s += sq_fixed60(v.x) + sq_fixed60(v.y) + sq_fixed60(v.z) + sq_fixed60(v.w);
             }
         }
         s = warp_sum_u64(s);
@@ -277,7 +324,9 @@ __global__ void __launch_bounds__(kRedThreads, 2) k_weights_z1024(const float4* 
         __shared__ double ws[kRedThreads / 32];
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
-            double acc = static_cast<double>(zs[m]) + static_cast<double>(zc[m]);
+            // back from the thread's frame (the last block's sign)
+            const double sg = fr[m] ? -1.0 : 1.0;
+            double acc = sg * static_cast<double>(zs[m]) + sg * static_cast<double>(zc[m]);
             acc = warp_sum_d(acc);
             if (lane == 0) ws[threadIdx.x >> 5] = acc;
             __syncthreads();

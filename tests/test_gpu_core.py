@@ -300,6 +300,35 @@ def test_sampler_bit_exact_vs_oracle(q, n, shots, perm, zero_frac):
         st.close()
 
 
+@pytest.mark.parametrize("n", [12, 16])
+def test_sampler_components_at_two(q, n):
+    """Blocks holding a component of magnitude 2 (the largest the weights are
+    defined for: floor(2^2 2^60) = 2^62) beside blocks without one: the
+    weights pass takes its general per-component path for those blocks only,
+    and the draws, counts and <Z> sums still match the oracle."""
+    psi = W.random_state(n, 90 + n)
+    rng = np.random.default_rng(n)
+    for y in rng.choice(1 << n, size=2, replace=False):
+        if rng.random() < 0.5:
+            psi[y] = complex(-2.0 if rng.random() < 0.5 else 2.0, psi[y].imag)
+        else:
+            psi[y] = complex(psi[y].real, -2.0 if rng.random() < 0.5 else 2.0)
+    psi = psi.astype(np.complex64)
+    st = GState(q, n, init=psi)
+    p64 = psi.astype(np.complex128)
+    L = list(range(n))
+    try:
+        masks = [0, 1 << (n - 1), 0b1011]
+        z, vals, cnts = q.qsa_measure(st.h, masks, 4000, seed=5)
+        rv, rc = oracle.sample_counts(p64, L, 4000, 5)
+        assert np.array_equal(vals, rv) and np.array_equal(cnts, rc)
+        for m, g in zip(masks, z):
+            ref = oracle.expect_z(p64, m)
+            assert abs(g - ref) < 1e-12 * max(1.0, abs(ref))
+    finally:
+        st.close()
+
+
 @pytest.mark.parametrize("n,perm", [(12, True), (23, False)])
 def test_measure_equals_expectations_and_sampling(q, n, perm):
     """qsa_measure: the same counts as qsa_sample_counts (bit for bit) and the
