@@ -84,19 +84,27 @@ struct LayerArgs {
     const float2* din;        // table of the gates with every qubit in the tile: 2^12 entries in
                               // tile-local order (copied to shared memory), or nullptr
     const float2* qph;        // rotation mode: each tile bit's entry phases q (kLT x 2)
-    const float2* rp;         // rotation mode: per round, the product of its factor bits' exit
-                              // phases p over the round's 16 local amplitudes (3 x 16)
     const float2* sph;        // rotation mode without per-tile phases: per round, the product of
                               // its bits' entry phases q (3 x 16, the LayerRec layout), formed on
                               // the host
     const LayerRec* rec;      // rotation mode with per-tile phases: one record per tile, or nullptr
+    // Read with compile-time indices, so they enter the instructions from the parameter bank
+    // (no shared-memory loads):
+    uint64_t goff[56];        // offsets of a round's local bits (goff[16 R + i] for tile-local
+                              // (i ^ exchanged round bits) << 4R) and of the load loop's chunk
+                              // strides (goff[48 + k] for tile-local 512 k)
+    float rot[kLT];           // rotation mode: each tile bit's coefficient (t or u; 0 without a factor)
+    float rpe[96];            // rotation mode: per round, the exit phases of its 16 places (interleaved)
 };
 
 struct LayerShared {
     float2 tf[kLT][4];        // general mode: this tile's factors (cross phases folded in)
     LayerRec ph;              // per-tile phases (general mode and static rotation mode)
-    float2 rp[3][16];         // rotation mode: per-round exit phases
 };
+// round 0 reads the phase tables two entries at a time (16-byte loads): every
+// array of the shared layout in k_apply_layer starts on a 16-byte boundary
+static_assert(sizeof(LayerShared) % 16 == 0 && offsetof(LayerShared, ph) % 16 == 0 && sizeof(LayerRec) % 16 == 0,
+              "16-byte aligned shared tables");
 
 // Slot of tile-local amplitude j: 16-byte chunk c = j / 2 is stored at
 // c ^ ((c >> 3) & 7), which spreads each round's warp accesses over all banks.
@@ -162,8 +170,7 @@ __device__ __forceinline__ void rotation(float2 (&v)[16], float coef) {
 // or (last round) to HBM.
 template <bool ROT, int R, int DIN, int PH, int RP, int GEN, bool LAST>
 __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, const float2* din_s,
-                                            const LayerShared& sh, const LayerRec& pr,
-                                            const float2* rot, const uint64_t* runoff, const uint64_t* goff,
+                                            const LayerShared& sh, const LayerRec& pr, const uint64_t* runoff,
                                             uint64_t base, bool phase) {
     const int t = threadIdx.x;
     const int jb = (t & ((1 << (4 * R)) - 1)) | ((t >> (4 * R)) << (4 * R + 4));
@@ -193,7 +200,11 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
             // phases of tile bits 4..11 (fixed for this thread) times those of the 16 local amplitudes
             const float2 ph = cmulf(pr.pa[(jb >> 4) & 15], pr.pb[(jb >> 8) & 15]);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = cmulf(v[i], cmulf(ph, pr.pl[i]));
+            for (int i = 0; i < 16; i += 2) {
+                const float4 q = reinterpret_cast<const float4*>(pr.pl)[i >> 1];   // two entries per load
+                v[i] = cmulf(v[i], cmulf(ph, make_float2(q.x, q.y)));
+                v[i + 1] = cmulf(v[i + 1], cmulf(ph, make_float2(q.z, q.w)));
+            }
         }
     } else {
 #pragma unroll
@@ -206,22 +217,22 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
         // only, on tile bit 3 (the lowest position above the run), and
         // otherwise branches per bit
         if (R > 0 || act == 15u) {
-            rotation<0>(v, rot[4 * R + 0].x);
-            rotation<1>(v, rot[4 * R + 1].x);
-            rotation<2>(v, rot[4 * R + 2].x);
-            rotation<3>(v, rot[4 * R + 3].x);
+            rotation<0>(v, a.rot[4 * R + 0]);
+            rotation<1>(v, a.rot[4 * R + 1]);
+            rotation<2>(v, a.rot[4 * R + 2]);
+            rotation<3>(v, a.rot[4 * R + 3]);
         } else if (act == 8u) {
-            rotation<3>(v, rot[3].x);
+            rotation<3>(v, a.rot[3]);
         } else {
-            if (act & 1u) rotation<0>(v, rot[0].x);
-            if (act & 2u) rotation<1>(v, rot[1].x);
-            if (act & 4u) rotation<2>(v, rot[2].x);
-            if (act & 8u) rotation<3>(v, rot[3].x);
+            if (act & 1u) rotation<0>(v, a.rot[0]);
+            if (act & 2u) rotation<1>(v, a.rot[1]);
+            if (act & 4u) rotation<2>(v, a.rot[2]);
+            if (act & 8u) rotation<3>(v, a.rot[3]);
         }
         if (RP != 0 && act && ((a.rpmask >> R) & 1u)) {
             // exit phases of the round's factor bits (they follow only their own rotations)
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = cmulf(v[i], sh.rp[R][i]);
+            for (int i = 0; i < 16; ++i) v[i] = cmulf(v[i], make_float2(a.rpe[32 * R + 2 * i], a.rpe[32 * R + 2 * i + 1]));
         }
     } else {
         if (act & 1u) butterfly<0>(v, sh.tf[4 * R + 0]);
@@ -231,14 +242,14 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
     }
     if constexpr (LAST) {
         // global offset of (jb | x) = offset(jb) | offset(x) at the exchanged index:
-        // goff[R][i] holds offset((i ^ exchanged round bits) << 4R)
+        // goff[16 R + i] holds offset((i ^ exchanged round bits) << 4R)
         const uint64_t gb =
             layer_global(a, runoff, base, jb ^ static_cast<int>(a.rswap & ~(15u << (4 * R)) & 0xfffu));
         // (round 0 never stores: as the last round it goes through the stage)
         static_assert(R > 0, "round 0 writes to the stage");
 #pragma unroll
         for (int i = 0; i < 16; ++i)
-            if (dbg::in_bounds(gb | goff[16 * R + i], 1, a.ntiles << 12, 11)) __stcs(a.psi + (gb | goff[16 * R + i]), v[i]);
+            if (dbg::in_bounds(gb | a.goff[16 * R + i], 1, a.ntiles << 12, 11)) __stcs(a.psi + (gb | a.goff[16 * R + i]), v[i]);
     } else {
         if constexpr (R == 0) {
 #pragma unroll
@@ -387,10 +398,8 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
     float2* stage = reinterpret_cast<float2*>(smem_raw);                        // kLStages x 4096
     uint64_t* runoff = reinterpret_cast<uint64_t*>(stage + kLStages * kLAmps);  // 512
     LayerShared& sh = *reinterpret_cast<LayerShared*>(runoff + 512);
-    float2* rot = reinterpret_cast<float2*>(&sh + 1);                           // kLT
-    LayerRec* recs = reinterpret_cast<LayerRec*>(rot + kLT);                    // kLStages
-    uint64_t* goff = reinterpret_cast<uint64_t*>(recs + kLStages);              // 48 + 8
-    uint64_t* dep = goff + 56;                                                  // 3 x 256
+    LayerRec* recs = reinterpret_cast<LayerRec*>(&sh + 1);                      // kLStages
+    uint64_t* dep = reinterpret_cast<uint64_t*>(recs + kLStages);               // 3 x 256
     float2* din_s = a.din ? reinterpret_cast<float2*>(dep + 768) : nullptr;     // 4096, swizzled
 
     for (int r = threadIdx.x; r < (1 << a.nx); r += blockDim.x) {
@@ -399,15 +408,6 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
             if ((r >> e) & 1) off |= 1ull << a.xpos[e];
         runoff[r] = off;
     }
-    __syncthreads();
-    // offsets of a round's local bits (goff[16 R + i] for tile-local i << 4R) and of
-    // the load loop's chunk strides (goff[48 + k] for tile-local 512 k)
-    if (threadIdx.x < 56) {
-        const int R = threadIdx.x >> 4;
-        const int j = threadIdx.x < 48 ? ((threadIdx.x & 15) ^ static_cast<int>((a.rswap >> (4 * R)) & 15u)) << (4 * R)
-                                       : (threadIdx.x - 48) << 9;
-        goff[threadIdx.x] = layer_global(a, runoff, 0, j);
-    }
     // tile bases: the tile index's bits deposited into the positions outside the
     // tile, ascending; dep[c][v] deposits v << 8c, so base(t) is an OR of three
     for (int i = threadIdx.x; i < 768; i += blockDim.x)
@@ -415,8 +415,6 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
     const bool dynamic = a.ncross > 0 || a.nout > 0;
     const bool phase = a.pmask != 0 || a.nout > 0;
     if (ROT) {
-        if (threadIdx.x < kLT) rot[threadIdx.x] = a.fac[threadIdx.x];
-        for (int i = threadIdx.x; i < 48; i += blockDim.x) sh.rp[i >> 4][i & 15] = a.rp[i];
         if (!dynamic)   // static phases: the rotations' entry phases only, tables from the host
             for (int i = threadIdx.x; i < 48; i += blockDim.x) reinterpret_cast<float2*>(&sh.ph)[i] = a.sph[i];
     } else if (!dynamic) {
@@ -450,8 +448,8 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
         if (GEN == 0 || (GEN == 2 && !a.generate))
 #pragma unroll
             for (int k = 0; k < kLAmps / 2 / kLThreads; ++k)
-                if (dbg::in_bounds(base | goff[48 + k], 2, a.ntiles << 12, 12))
-                    cp_async16(st + (sld ^ lsw(512 * k)), a.psi + (base | goff[48 + k]));
+                if (dbg::in_bounds(base | a.goff[48 + k], 2, a.ntiles << 12, 12))
+                    cp_async16(st + (sld ^ lsw(512 * k)), a.psi + (base | a.goff[48 + k]));
         if (use_rec && threadIdx.x < static_cast<int>(sizeof(LayerRec) / 16))
             cp_async16(reinterpret_cast<float4*>(recs + sidx) + threadIdx.x,
                        reinterpret_cast<const float4*>(a.rec + t) + threadIdx.x);
@@ -481,7 +479,7 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
             // round 0 always writes to the stage: its threads hold 16 consecutive
             // amplitudes, so when it is the last round the tile is copied out in
             // 16-byte chunks by consecutive threads instead (coalesced stores)
-            layer_round<ROT, 0, DIN, PH, RP, GEN, false>(a, st, din_s, sh, pr, rot, runoff, goff, base, phase);
+            layer_round<ROT, 0, DIN, PH, RP, GEN, false>(a, st, din_s, sh, pr, runoff, base, phase);
             if (last == 0) {
                 // the amplitudes of tile-local j, j + 1 are in place (j ^ rswap),
                 // (j + 1) ^ rswap: chunk (j ^ rswap) / 2, halves exchanged if bit 0 is
@@ -492,8 +490,8 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
                 for (int k = 0; k < kLAmps / 2 / kLThreads; ++k) {
                     float4 c = *reinterpret_cast<const float4*>(st + (sx ^ lsw(512 * k)));
                     if (hx) c = make_float4(c.z, c.w, c.x, c.y);
-                    if (dbg::in_bounds(base | gld | goff[48 + k], 2, a.ntiles << 12, 13))
-                        __stcs(reinterpret_cast<float4*>(a.psi + (base | gld | goff[48 + k])), c);
+                    if (dbg::in_bounds(base | gld | a.goff[48 + k], 2, a.ntiles << 12, 13))
+                        __stcs(reinterpret_cast<float4*>(a.psi + (base | gld | a.goff[48 + k])), c);
                 }
             } else if (r1) {
                 __syncwarp();
@@ -503,12 +501,12 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
         }
         if (first <= 1 && last >= 1 && r1) {
             if (last == 1)
-                layer_round<ROT, 1, DIN, PH, RP, GEN, true>(a, st, din_s, sh, pr, rot, runoff, goff, base, phase);
+                layer_round<ROT, 1, DIN, PH, RP, GEN, true>(a, st, din_s, sh, pr, runoff, base, phase);
             else
-                layer_round<ROT, 1, DIN, PH, RP, GEN, false>(a, st, din_s, sh, pr, rot, runoff, goff, base, phase);
+                layer_round<ROT, 1, DIN, PH, RP, GEN, false>(a, st, din_s, sh, pr, runoff, base, phase);
             if (last > 1) __syncthreads();
         }
-        if (last == 2) layer_round<ROT, 2, DIN, PH, RP, GEN, true>(a, st, din_s, sh, pr, rot, runoff, goff, base, phase);
+        if (last == 2) layer_round<ROT, 2, DIN, PH, RP, GEN, true>(a, st, din_s, sh, pr, runoff, base, phase);
         if (end_sync) __syncthreads();
         cur ^= 1;
     }
@@ -519,8 +517,7 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
 
 size_t layer_smem_bytes(bool with_din) {
     return sizeof(float2) * kLStages * kLAmps + sizeof(uint64_t) * 512 + sizeof(LayerShared) +
-           sizeof(float2) * kLT + sizeof(LayerRec) * kLStages + sizeof(uint64_t) * (56 + 768) +
-           (with_din ? sizeof(float2) * kLAmps : 0);
+           sizeof(LayerRec) * kLStages + sizeof(uint64_t) * 768 + (with_din ? sizeof(float2) * kLAmps : 0);
 }
 
 size_t layer_record_bytes(int n) { return n < kLT ? 0 : sizeof(LayerRec) << (n - kLT); }
@@ -551,8 +548,21 @@ bool layer_args(float2* psi, int n, const LayerGeom& g, const unsigned char* d_p
     a.outg = reinterpret_cast<const LayerGate*>(d_payload + p.off_out);
     a.din = p.has_din ? reinterpret_cast<const float2*>(d_payload + p.off_din) : nullptr;
     a.qph = reinterpret_cast<const float2*>(d_payload + p.off_qph);
-    a.rp = reinterpret_cast<const float2*>(d_payload + p.off_rp);
     a.sph = reinterpret_cast<const float2*>(d_payload + p.off_sph);
+    // global offsets of tile-local indices: the low m bits in place, bit m + e at xpos[e]
+    auto offset = [&](int j) {
+        uint64_t off = static_cast<uint64_t>(j & ((1 << g.m) - 1));
+        for (int e = 0; e < g.nx; ++e)
+            if ((j >> (g.m + e)) & 1) off |= 1ull << g.xpos[e];
+        return off;
+    };
+    for (int t = 0; t < 56; ++t) {
+        const int R = t >> 4;
+        a.goff[t] = offset(t < 48 ? ((t & 15) ^ static_cast<int>((p.rswap >> (4 * R)) & 15u)) << (4 * R)
+                                  : (t - 48) << 9);
+    }
+    for (int b = 0; b < kLT; ++b) a.rot[b] = p.rot[b];
+    for (int i = 0; i < 96; ++i) a.rpe[i] = p.rp[i];
     return true;
 }
 

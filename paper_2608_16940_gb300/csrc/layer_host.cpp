@@ -241,6 +241,13 @@ bool prepare_pass(int n, const int32_t* L, const LayerSpec& spec, const std::vec
         else
             for (int c = 0; c < 4; ++c) facf[4 * b + c] = f2(fac[b][c]);
     }
+    if (p.rotation) {
+        for (int b = 0; b < kTile; ++b) p.rot[b] = facf[b].x;
+        for (int i = 0; i < 48; ++i) {
+            p.rp[2 * i] = rpt[i].x;
+            p.rp[2 * i + 1] = rpt[i].y;
+        }
+    }
     p.off_fac = append(bytes, facf.data(), facf.size()) - base;
     p.off_qph = append(bytes, qph.data(), qph.size()) - base;
     p.off_rp = append(bytes, rpt.data(), rpt.size()) - base;

@@ -139,6 +139,10 @@ struct LayerPayload {
     uint32_t rswap = 0;       // rotation mode: tile bits whose halves the pass leaves exchanged
     bool generate = false;    // write-only: the input is taken as 1 for every amplitude (not read)
     size_t off_fac = 0, off_cross = 0, off_out = 0, off_din = 0, off_qph = 0, off_rp = 0, off_sph = 0, bytes = 0;
+    // rotation mode: host copies of the payload's FP32 rotation coefficients (t or u per tile bit)
+    // and per-round exit phases (3 x 16 complex, interleaved), passed with the launch
+    float rot[12] = {};
+    float rp[96] = {};
 };
 size_t layer_smem_bytes(bool with_din);
 // Rotation-mode passes with per-tile phases first write one record per tile
