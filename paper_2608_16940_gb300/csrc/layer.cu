@@ -95,6 +95,10 @@ struct LayerArgs {
                               // strides (goff[48 + k] for tile-local 512 k)
     float rot[kLT];           // rotation mode: each tile bit's coefficient (t or u; 0 without a factor)
     float rpe[96];            // rotation mode: per round, the exit phases of its 16 places (interleaved)
+    // Tile bases: base(t) deposits t's bits into the positions outside the tile (omask, ascending);
+    // base(t + s) = ((base(t) | ~omask) + dstride) & omask with dstride = base(s) (the carries run
+    // through the tile's positions), s the launch's grid size.
+    uint64_t omask, dstride;
 };
 
 struct LayerShared {
@@ -168,9 +172,18 @@ __device__ __forceinline__ void rotation(float2 (&v)[16], float coef) {
 // entry table and the per-tile phases; apply the round's factors; (last
 // round, rotation mode) multiply by the exit table; write back to the stage
 // or (last round) to HBM.
+// This thread's part of the global offsets of round R's stores: tile-local
+// jb at the exchanged index, jb its amplitudes' common bits outside the round.
+template <int R>
+__device__ __forceinline__ uint64_t store_offset(const LayerArgs& a, const uint64_t* runoff) {
+    const int t = threadIdx.x;
+    const int jb = (t & ((1 << (4 * R)) - 1)) | ((t >> (4 * R)) << (4 * R + 4));
+    return layer_global(a, runoff, 0, jb ^ static_cast<int>(a.rswap & ~(15u << (4 * R)) & 0xfffu));
+}
+
 template <bool ROT, int R, int DIN, int PH, int RP, int GEN, bool LAST>
 __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, const float2* din_s,
-                                            const LayerShared& sh, const LayerRec& pr, const uint64_t* runoff,
+                                            const LayerShared& sh, const LayerRec& pr, uint64_t soff,
                                             uint64_t base, bool phase) {
     const int t = threadIdx.x;
     const int jb = (t & ((1 << (4 * R)) - 1)) | ((t >> (4 * R)) << (4 * R + 4));
@@ -242,9 +255,9 @@ __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, c
     }
     if constexpr (LAST) {
         // global offset of (jb | x) = offset(jb) | offset(x) at the exchanged index:
-        // goff[16 R + i] holds offset((i ^ exchanged round bits) << 4R)
-        const uint64_t gb =
-            layer_global(a, runoff, base, jb ^ static_cast<int>(a.rswap & ~(15u << (4 * R)) & 0xfffu));
+        // soff = offset(jb ^ exchanged bits outside the round), formed once per thread
+        // (store_offset); goff[16 R + i] holds offset((i ^ exchanged round bits) << 4R)
+        const uint64_t gb = base | soff;
         // (round 0 never stores: as the last round it goes through the stage)
         static_assert(R > 0, "round 0 writes to the stage");
 #pragma unroll
@@ -399,8 +412,7 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
     uint64_t* runoff = reinterpret_cast<uint64_t*>(stage + kLStages * kLAmps);  // 512
     LayerShared& sh = *reinterpret_cast<LayerShared*>(runoff + 512);
     LayerRec* recs = reinterpret_cast<LayerRec*>(&sh + 1);                      // kLStages
-    uint64_t* dep = reinterpret_cast<uint64_t*>(recs + kLStages);               // 3 x 256
-    float2* din_s = a.din ? reinterpret_cast<float2*>(dep + 768) : nullptr;     // 4096, swizzled
+    float2* din_s = a.din ? reinterpret_cast<float2*>(recs + kLStages) : nullptr;   // 4096, swizzled
 
     for (int r = threadIdx.x; r < (1 << a.nx); r += blockDim.x) {
         uint64_t off = 0;
@@ -408,10 +420,6 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
             if ((r >> e) & 1) off |= 1ull << a.xpos[e];
         runoff[r] = off;
     }
-    // tile bases: the tile index's bits deposited into the positions outside the
-    // tile, ascending; dep[c][v] deposits v << 8c, so base(t) is an OR of three
-    for (int i = threadIdx.x; i < 768; i += blockDim.x)
-        dep[i] = layer_base(a, static_cast<uint64_t>(i & 255) << (8 * (i >> 8)));
     const bool dynamic = a.ncross > 0 || a.nout > 0;
     const bool phase = a.pmask != 0 || a.nout > 0;
     if (ROT) {
@@ -438,12 +446,11 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
     const bool use_rec = ROT && a.rec;
     // this thread's chunks are 2 * threadIdx.x + 512 k, k = 0..7
     const uint64_t gld = layer_global(a, runoff, 0, 2 * threadIdx.x);
+    // this thread's store offsets for a last round 1 or 2
+    const uint64_t soff1 = store_offset<1>(a, runoff), soff2 = store_offset<2>(a, runoff);
     const int sld = lsw(2 * threadIdx.x);
-    auto tile_base = [&](uint64_t t) {
-        return dep[t & 255] | dep[256 + ((t >> 8) & 255)] | dep[512 + ((t >> 16) & 255)];
-    };
-    auto load = [&](uint64_t t, int sidx) {
-        const uint64_t base = tile_base(t) | gld;
+    auto load = [&](uint64_t t, uint64_t tbase, int sidx) {
+        const uint64_t base = tbase | gld;
         float2* st = stage + sidx * kLAmps;
         if (GEN == 0 || (GEN == 2 && !a.generate))
 #pragma unroll
@@ -462,16 +469,18 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
     // rewrites the shared factors each tile and keeps an end-of-tile barrier.
     const bool r1 = ((a.fmask >> 4) & 15u) != 0;
     const bool end_sync = dynamic && !use_rec;
-    if (blockIdx.x < a.ntiles) load(blockIdx.x, 0);
+    uint64_t nbase = layer_base(a, blockIdx.x);   // base of the next tile to load
+    if (blockIdx.x < a.ntiles) load(blockIdx.x, nbase, 0);
     cp_async_commit();
     int cur = 0;
     for (uint64_t t = blockIdx.x; t < a.ntiles; t += stride) {
-        const uint64_t base = tile_base(t);
+        const uint64_t base = nbase;
+        nbase = ((nbase | ~a.omask) + a.dstride) & a.omask;
         if (end_sync && threadIdx.x < 32) tile_phases<ROT>(a, base, sh);
         cp_async_wait<0>();
         __syncthreads();
         const uint64_t tn = t + stride;
-        if (tn < a.ntiles) load(tn, cur ^ 1);
+        if (tn < a.ntiles) load(tn, nbase, cur ^ 1);
         cp_async_commit();
         float2* st = stage + cur * kLAmps;
         const LayerRec& pr = use_rec ? recs[cur] : sh.ph;
@@ -479,7 +488,7 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
             // round 0 always writes to the stage: its threads hold 16 consecutive
             // amplitudes, so when it is the last round the tile is copied out in
             // 16-byte chunks by consecutive threads instead (coalesced stores)
-            layer_round<ROT, 0, DIN, PH, RP, GEN, false>(a, st, din_s, sh, pr, runoff, base, phase);
+            layer_round<ROT, 0, DIN, PH, RP, GEN, false>(a, st, din_s, sh, pr, 0, base, phase);
             if (last == 0) {
                 // the amplitudes of tile-local j, j + 1 are in place (j ^ rswap),
                 // (j + 1) ^ rswap: chunk (j ^ rswap) / 2, halves exchanged if bit 0 is
@@ -501,12 +510,12 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
         }
         if (first <= 1 && last >= 1 && r1) {
             if (last == 1)
-                layer_round<ROT, 1, DIN, PH, RP, GEN, true>(a, st, din_s, sh, pr, runoff, base, phase);
+                layer_round<ROT, 1, DIN, PH, RP, GEN, true>(a, st, din_s, sh, pr, soff1, base, phase);
             else
-                layer_round<ROT, 1, DIN, PH, RP, GEN, false>(a, st, din_s, sh, pr, runoff, base, phase);
+                layer_round<ROT, 1, DIN, PH, RP, GEN, false>(a, st, din_s, sh, pr, 0, base, phase);
             if (last > 1) __syncthreads();
         }
-        if (last == 2) layer_round<ROT, 2, DIN, PH, RP, GEN, true>(a, st, din_s, sh, pr, runoff, base, phase);
+        if (last == 2) layer_round<ROT, 2, DIN, PH, RP, GEN, true>(a, st, din_s, sh, pr, soff2, base, phase);
         if (end_sync) __syncthreads();
         cur ^= 1;
     }
@@ -517,7 +526,7 @@ __global__ void __launch_bounds__(kLThreads, 2) k_apply_layer(LayerArgs a) {
 
 size_t layer_smem_bytes(bool with_din) {
     return sizeof(float2) * kLStages * kLAmps + sizeof(uint64_t) * 512 + sizeof(LayerShared) +
-           sizeof(LayerRec) * kLStages + sizeof(uint64_t) * 768 + (with_din ? sizeof(float2) * kLAmps : 0);
+           sizeof(LayerRec) * kLStages + (with_din ? sizeof(float2) * kLAmps : 0);
 }
 
 size_t layer_record_bytes(int n) { return n < kLT ? 0 : sizeof(LayerRec) << (n - kLT); }
@@ -561,6 +570,10 @@ bool layer_args(float2* psi, int n, const LayerGeom& g, const unsigned char* d_p
         a.goff[t] = offset(t < 48 ? ((t & 15) ^ static_cast<int>((p.rswap >> (4 * R)) & 15u)) << (4 * R)
                                   : (t - 48) << 9);
     }
+    uint64_t tmask = (1ull << g.m) - 1;
+    for (int e = 0; e < g.nx; ++e) tmask |= 1ull << g.xpos[e];
+    a.omask = ((1ull << n) - 1) & ~tmask;
+    a.dstride = 0;   // set with the grid size
     for (int b = 0; b < kLT; ++b) a.rot[b] = p.rot[b];
     for (int i = 0; i < 96; ++i) a.rpe[i] = p.rp[i];
     return true;
@@ -617,6 +630,12 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
     if (occ < 1) occ = 1;
     uint64_t grid = static_cast<uint64_t>(num_sms()) * occ;
     if (grid > a.ntiles) grid = a.ntiles;
+    // the grid size deposited into the positions outside the tile
+    for (uint64_t v = grid, pos = 0; v && pos < 64; ++pos)
+        if ((a.omask >> pos) & 1) {
+            if (v & 1) a.dstride |= 1ull << pos;
+            v >>= 1;
+        }
     kern<<<static_cast<unsigned>(grid), kLThreads, smem, st>>>(a);
     ++*launches;
     return cudaGetLastError();
