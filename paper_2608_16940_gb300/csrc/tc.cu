@@ -76,6 +76,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "qsa_bounds.cuh"
 #include "qsa_internal.h"
@@ -90,6 +91,7 @@ constexpr int kConvWarps = 8;                // warps 0-7: converters, two teams
 constexpr int kEpiWarp = 8;                  // warps 8-15: epilogue, two groups of four
 constexpr int kProdWarp = 16;                // warps 16-19: producers
 constexpr int kProducers = 4;
+static_assert(kProducers == 4, "the producers' unit loops are specialised for four warps");
 constexpr int kMmaWarp = 20;                 // warps 20-22: MMA issuers (warp 20 owns tensor memory)
 constexpr int kIssuers = 3;
 constexpr int kChunkBits = 11;               // amplitudes per chunk: 2^11
@@ -112,10 +114,7 @@ constexpr uint32_t kOutBytes = kRawBytes;
 constexpr uint32_t OFF_B = 0;
 constexpr uint32_t OFF_RAW = OFF_B + kNB * kBBytes;
 constexpr uint32_t OFF_STG = OFF_RAW + kNR * kRawBytes;
-constexpr uint32_t OFF_GI = OFF_STG + 2 * kOutBytes;     // 32 global offsets of copy units (in and out)
-constexpr uint32_t OFF_SI = OFF_GI + 32 * 8;               // producer: 32 stage offsets
-constexpr uint32_t OFF_OI = OFF_SI + 32 * 4;               // epilogue: 32 output staging offsets
-constexpr uint32_t OFF_BARS = OFF_OI + 32 * 4;
+constexpr uint32_t OFF_BARS = OFF_STG + 2 * kOutBytes;
 constexpr int BAR_RFULL = 0, BAR_REMPTY = kNR, BAR_BFULL = 2 * kNR, BAR_BEMPTY = BAR_BFULL + kNB,
               BAR_DFULL = BAR_BEMPTY + kNB, BAR_DEMPTY = BAR_DFULL + 1, BAR_AREADY = BAR_DEMPTY + 1,
               BAR_FIN = BAR_AREADY + 1, NBARS = BAR_FIN + 1;
@@ -222,27 +221,6 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
                  : "memory");
 }
 
-// 32 lanes x 32 consecutive 32-bit columns (one row per thread).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-}
-// 32 lanes x 16 consecutive 32-bit columns (one row per thread).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
 // 32 lanes x 8 consecutive 32-bit columns (one row per thread).
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
@@ -332,6 +310,12 @@ struct TcArgs {
     int rp[5];                   // chunk-local position of row bit b
     int vbit[6];                 // operator bit of K bit b (b < k; for k = 5, K bit 5 is the group bit)
     int k;
+    // Copy unit U = lane + 32 u (16 bytes: elements 2U, 2U+1): the parts of its global offset, stage
+    // address and output staging address given by u's bits (chunk-local positions 6..10), read at
+    // compile-time u, so they enter the instructions from the parameter bank
+    uint64_t gi[32];
+    uint32_t si[32];
+    uint32_t oi[32];
 };
 
 __device__ __forceinline__ uint64_t chunk_base(const TcArgs& a, uint64_t t) {
@@ -363,9 +347,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_apply_tc(TcArgs a) {
     unsigned char* sm = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
     unsigned char* Bsm = sm + OFF_B;
     unsigned char* Raw = sm + OFF_RAW;
-    uint64_t* gi_tab = reinterpret_cast<uint64_t*>(sm + OFF_GI);
-    uint32_t* si_tab = reinterpret_cast<uint32_t*>(sm + OFF_SI);
-    uint32_t* oi_tab = reinterpret_cast<uint32_t*>(sm + OFF_OI);
     const uint32_t bar0 = smem_u32(sm + OFF_BARS);
     auto bar = [&](int i) { return bar0 + 8u * static_cast<uint32_t>(i); };
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_MISC);
@@ -373,22 +354,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_apply_tc(TcArgs a) {
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // Copy units (producers in, epilogue out): unit U = lane + 32 i (16
-    // bytes: elements 2U, 2U+1); the bits of i are chunk-local positions 6..10.
-    if (tid < 32) {
-        uint64_t g = 0;
-        uint32_t s = 0, o = 0;
-#pragma unroll
-        for (int b = 0; b < 5; ++b)
-            if ((tid >> b) & 1) {
-                g |= a.gbit[6 + b];
-                s ^= a.sbit[6 + b];
-                o ^= a.obit[6 + b];
-            }
-        gi_tab[tid] = g;
-        si_tab[tid] = s;
-        oi_tab[tid] = o;
-    }
     if (tid == 0) {
         for (int i = 0; i < kNR; ++i) {
             mbar_init(bar(BAR_RFULL + i), 32 * kProducers);   // every producer lane
@@ -453,10 +418,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_apply_tc(TcArgs a) {
             }
             const uint64_t base = chunk_base(a, blockIdx.x + i * gridDim.x) | gl;
             const uint32_t d0 = raw0 + static_cast<uint32_t>(s) * kRawBytes;
+            // this warp's units at compile-time indices (one copy of the loop per producer warp)
+            auto copy_units = [&](auto pw) {
+                constexpr int v0 = kU * decltype(pw)::value;
 #pragma unroll
-            for (int u = u0; u < u0 + kU; ++u)
-                if (dbg::in_bounds(base | gi_tab[u], 2, a.nchunks << kChunkBits, 21))
-                    cp_async16(d0 + (sl ^ si_tab[u]), a.psi + (base | gi_tab[u]));
+                for (int u = v0; u < v0 + kU; ++u)
+                    if (dbg::in_bounds(base | a.gi[u], 2, a.nchunks << kChunkBits, 21))
+                        cp_async16(d0 + (sl ^ a.si[u]), a.psi + (base | a.gi[u]));
+            };
+            switch (u0 / kU) {
+                case 0: copy_units(std::integral_constant<int, 0>{}); break;
+                case 1: copy_units(std::integral_constant<int, 1>{}); break;
+                case 2: copy_units(std::integral_constant<int, 2>{}); break;
+                default: copy_units(std::integral_constant<int, 3>{}); break;
+            }
             cp_async_arrive_noinc(bar(BAR_RFULL + s));
         }
         cp_async_wait_all();   // no copy may land after the CTA has left
@@ -681,11 +656,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_apply_tc(TcArgs a) {
             mbar_arrive(bar(BAR_DEMPTY));
             group_sync(gbar, 128);   // the chunk is staged
             const uint64_t base = chunk_base(a, blockIdx.x + i * gridDim.x) | gl;
+            // this warp's quarter of the units at compile-time indices
+            auto store_units = [&](auto qq) {
+                constexpr int v0 = 8 * decltype(qq)::value;
 #pragma unroll
-            for (int u = 8 * q; u < 8 * q + 8; ++u)
-                if (dbg::in_bounds(base | gi_tab[u], 2, a.nchunks << kChunkBits, 22))
-                    __stcs(reinterpret_cast<float4*>(a.psi + (base | gi_tab[u])),
-                           *reinterpret_cast<const float4*>(ost + (ol ^ oi_tab[u])));
+                for (int u = v0; u < v0 + 8; ++u)
+                    if (dbg::in_bounds(base | a.gi[u], 2, a.nchunks << kChunkBits, 22))
+                        __stcs(reinterpret_cast<float4*>(a.psi + (base | a.gi[u])),
+                               *reinterpret_cast<const float4*>(ost + (ol ^ a.oi[u])));
+            };
+            switch (q) {
+                case 0: store_units(std::integral_constant<int, 0>{}); break;
+                case 1: store_units(std::integral_constant<int, 1>{}); break;
+                case 2: store_units(std::integral_constant<int, 2>{}); break;
+                default: store_units(std::integral_constant<int, 3>{}); break;
+            }
         }
     }
     tc_fence_before();
@@ -819,6 +804,16 @@ cudaError_t launch_apply_tc(float2* psi, int n, const int* phys, int k, const fl
     const bool pair = tls[0] == 0;
     stage_layout(a.rp, pair, a.sbit);
     out_layout(a.kp, a.obit);
+    for (int u = 0; u < 32; ++u) {
+        a.gi[u] = 0;
+        a.si[u] = a.oi[u] = 0;
+        for (int b = 0; b < 5; ++b)
+            if ((u >> b) & 1) {
+                a.gi[u] |= a.gbit[6 + b];
+                a.si[u] ^= a.sbit[6 + b];
+                a.oi[u] ^= a.obit[6 + b];
+            }
+    }
     return pair ? launch_pair<true>(a, g.ntiles, st, launches) : launch_pair<false>(a, g.ntiles, st, launches);
 }
 
