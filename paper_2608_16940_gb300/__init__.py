@@ -13,6 +13,7 @@ Status codes other than QSA_OK raise :class:`QsaError` carrying the code and
 from __future__ import annotations
 
 import ctypes
+import itertools
 import os
 from typing import Iterable, List, Optional, Sequence, Tuple
 
@@ -275,20 +276,21 @@ class OpArray:
     def __init__(self, ops: Iterable):
         ops = list(ops)
         n = len(ops)
-        targets = [tuple(o.targets) for o in ops]
-        ks = np.fromiter((len(t) for t in targets), dtype=np.int64, count=n)
+        targets = [o.targets for o in ops]
+        ks = np.fromiter(map(len, targets), dtype=np.int64, count=n)
+        flat = [np.asarray(o.matrix, dtype=np.complex128).ravel() for o in ops]
+        dims = np.left_shift(1, 2 * ks)
+        if not np.array_equal(np.fromiter(map(len, flat), dtype=np.int64, count=n), dims):
+            raise ValueError("every op's matrix must be 2^k x 2^k for its k targets")
         offs = np.zeros(n + 1, dtype=np.int64)
-        np.cumsum(np.left_shift(1, 2 * ks), out=offs[1:])
-        self.mats = np.empty(max(1, int(offs[-1])), dtype=np.complex128)
+        np.cumsum(dims, out=offs[1:])
+        self.mats = np.concatenate(flat) if n else np.empty(1, dtype=np.complex128)
         tg = np.zeros((max(1, n), 6), dtype=np.int32)
-        by_k = {}
-        for i, t in enumerate(targets):
-            by_k.setdefault(len(t), []).append(i)
-        for k, idx in by_k.items():   # one numpy call per width
-            d = 1 << (2 * k)
-            m = np.asarray([ops[i].matrix for i in idx], dtype=np.complex128).reshape(len(idx), d)
-            self.mats[offs[idx][:, None] + np.arange(d)] = m
-            tg[idx, :k] = np.asarray([targets[i] for i in idx], dtype=np.int32).reshape(len(idx), k)
+        nt = int(offs.size and ks.sum())
+        if nt:   # row i, columns 0..k_i - 1 from the flattened target lists
+            rows = np.repeat(np.arange(n), ks)
+            cols = np.arange(nt) - np.repeat(np.cumsum(ks) - ks, ks)
+            tg[rows, cols] = np.fromiter(itertools.chain.from_iterable(targets), dtype=np.int32, count=nt)
         rec = np.zeros(max(1, n), dtype=self._dtype)
         rec["k"][:n] = ks
         rec["targets"] = tg
