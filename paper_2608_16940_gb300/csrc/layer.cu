@@ -533,7 +533,9 @@ size_t layer_record_bytes(int n) { return n < kLT ? 0 : sizeof(LayerRec) << (n -
 
 namespace {
 
-// three deposit tables of 8 tile-index bits cover N - 12 <= 24 bits
+// The launch's arguments: geometry, payload pointers and the tables read from
+// the parameter bank (N - 12 <= 24 tile-index bits: states of up to 2^36
+// amplitudes, beyond QSA_MAX_QUBITS)
 bool layer_args(float2* psi, int n, const LayerGeom& g, const unsigned char* d_payload, const LayerPayload& p,
                 LayerArgs* out) {
     if (n < kLT || n - kLT > 24 || g.m + g.nx != kLT || g.m < 3) return false;
