@@ -164,14 +164,6 @@ __device__ __forceinline__ void rotation(float2 (&v)[16], float coef) {
     }
 }
 
-// Whether a pass has a diagonal table (DIN), per-tile phases (PH) and exit
-// phases (RP), and whether it generates its input (GEN): known at compile
-// time (1 present, 0 absent) or read at run time (2); LAST: the round stores
-// to HBM.
-// One round over tile bits 4R..4R+3: read the stage; (R = 0) multiply by the
-// entry table and the per-tile phases; apply the round's factors; (last
-// round, rotation mode) multiply by the exit table; write back to the stage
-// or (last round) to HBM.
 // This thread's part of the global offsets of round R's stores: tile-local
 // jb at the exchanged index, jb its amplitudes' common bits outside the round.
 template <int R>
@@ -181,6 +173,14 @@ __device__ __forceinline__ uint64_t store_offset(const LayerArgs& a, const uint6
     return layer_global(a, runoff, 0, jb ^ static_cast<int>(a.rswap & ~(15u << (4 * R)) & 0xfffu));
 }
 
+// Whether a pass has a diagonal table (DIN), per-tile phases (PH) and exit
+// phases (RP), and whether it generates its input (GEN): known at compile
+// time (1 present, 0 absent) or read at run time (2); LAST: the round stores
+// to HBM (soff: this thread's store_offset for the round).
+// One round over tile bits 4R..4R+3: read the stage; (R = 0) multiply by the
+// entry table and the per-tile phases; apply the round's factors; (last
+// round, rotation mode) multiply by the exit table; write back to the stage
+// or (last round) to HBM.
 template <bool ROT, int R, int DIN, int PH, int RP, int GEN, bool LAST>
 __device__ __forceinline__ void layer_round(const LayerArgs& a, float2* stage, const float2* din_s,
                                             const LayerShared& sh, const LayerRec& pr, uint64_t soff,
