@@ -90,6 +90,11 @@ struct ApplyArgs {
     int tl[6];          // tile-local position of target j (V order)
     int tls[6];         // the same positions, ascending
     uint8_t fv[16];     // stage layout: slot vector of tile-local position p >= 4 (k <= 4)
+    // k <= 4 launches: the tile-local offsets of a group's D members in the plain (loffc) and the
+    // swizzled (sloffc) stage, formed on the host and read at compile-time member indices from the
+    // parameter bank
+    int loffc[16];
+    int sloffc[16];
 };
 
 // Stage layout of the k <= 4 kernels: tile-local element j sits at
@@ -153,12 +158,16 @@ __device__ __forceinline__ void store_tile_swz(const TileArgs& a, const uint64_t
 // item writes its outputs in place and the tile goes back in address order
 // (16-byte units of 2^TB-amplitude tiles), for target sets whose direct
 // stores would give every lane its own sector.
-template <int K, int R, int S, bool SWZ = false, bool WB = false, int TB = 11>
+template <int K, int R, int S, bool SWZ = false, bool WB = false, int TB = 11, bool PO = false>
 __device__ __forceinline__ void apply_tiles(const ApplyArgs& a, float2* stage, const float2* Ms,
                                             const uint64_t* runoff, const int* loff, uint64_t t0, uint64_t stride,
                                             const uint8_t* htab = nullptr, const int* sloff = nullptr) {
     constexpr int D = 1 << K;
     static_assert(!WB || (SWZ && R == D), "in-place outputs: swizzled stage, the whole group in one item");
+    // PO: member offsets from the parameter bank (k <= 4)
+    static_assert(!PO || D <= 16, "parameter-bank member offsets: k <= 4");
+    auto moff = [&](int c) { return PO ? a.loffc[c] : loff[c]; };
+    auto msoff = [&](int c) { return PO ? a.sloffc[c] : sloff[c]; };
     const int tileAmps = 1 << a.t.T;
     auto load = [&](uint64_t t, float2* st) {
         if constexpr (SWZ)
@@ -202,7 +211,7 @@ __device__ __forceinline__ void apply_tiles(const ApplyArgs& a, float2* stage, c
                 uint64_t x2[D], y2[D];
 #pragma unroll
                 for (int c = 0; c < D; ++c) {
-                    const float2 f = SWZ ? st[lbs ^ sloff[c]] : st[lb | loff[c]];
+                    const float2 f = SWZ ? st[lbs ^ msoff(c)] : st[lb | moff(c)];
                     x2[c] = pack2(f.x, f.x);
                     y2[c] = pack2(f.y, f.y);
                 }
@@ -221,9 +230,9 @@ __device__ __forceinline__ void apply_tiles(const ApplyArgs& a, float2* stage, c
                     }
                     const float2 P = unpack2(p), Q = unpack2(qv);
                     if constexpr (WB) {
-                        st[lbs ^ sloff[r]] = make_float2(P.x - Q.y, P.y + Q.x);   // in place: inputs are in registers
+                        st[lbs ^ msoff(r)] = make_float2(P.x - Q.y, P.y + Q.x);   // in place: inputs are in registers
                     } else {
-                        const uint64_t gj = tile_global(a.t, runoff, base, lb | loff[r]);
+                        const uint64_t gj = tile_global(a.t, runoff, base, lb | moff(r));
                         if (dbg::in_bounds(gj, 1, a.t.ntiles << a.t.T, 4))
                             __stcs(a.t.psi + gj, make_float2(P.x - Q.y, P.y + Q.x));
                     }
@@ -298,7 +307,7 @@ __global__ void __launch_bounds__(kThreads) k_apply_fp32(ApplyArgs a) {
         for (int c = threadIdx.x; c < D; c += blockDim.x) sloff[c] = loff[c] ^ static_cast<int>(stage_xor(htab, loff[c]));
     }
     __syncthreads();
-    apply_tiles<K, R, S, SWZ, WB, TB>(a, stage, Ms, runoff, loff, blockIdx.x, gridDim.x, htab, sloff);
+    apply_tiles<K, R, S, SWZ, WB, TB, (K <= 4)>(a, stage, Ms, runoff, loff, blockIdx.x, gridDim.x, htab, sloff);
 }
 
 template <int K>
@@ -401,6 +410,17 @@ cudaError_t launch_apply_k(float2* psi, int n, const int* phys, const float* d_m
     const int form = C::SWZ && g.T == C::T ? apply_form(g.T, a.tls, K) : 0;
     if (form) stage_slots(g.T, a.tls, K, a.fv);
     const int D = 1 << K;
+    for (int c = 0; c < D && c < 16; ++c) {
+        int o = 0;
+        for (int j = 0; j < K; ++j)
+            if ((c >> j) & 1) o |= 1 << a.tl[j];
+        a.loffc[c] = o;
+        // swizzled stage: o ^ (h(o >> 4) << 1), h the XOR of the slot vectors of o's bits from 4 on
+        uint32_t h = 0;
+        for (int i = 0; i < g.T - 4; ++i)
+            if ((o >> (4 + i)) & 1) h ^= a.fv[4 + i];
+        a.sloffc[c] = o ^ static_cast<int>(h << 1);
+    }
     constexpr size_t tables = sizeof(uint64_t) * 64 + 2 * sizeof(int) * 64 + 256;
     const size_t smem = sizeof(float2) * (static_cast<size_t>(C::S) << g.T) + sizeof(float2) * D * D + tables;
     auto kern = form == 2   ? k_apply_fp32<K, C::R, C::S, C::SWZ, C::SWZ, C::T>
