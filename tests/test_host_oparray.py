@@ -71,3 +71,15 @@ def test_plan_from_records_equals_plan_from_ops(q):
     finally:
         q.qsa_plan_destroy(p1)
         q.qsa_plan_destroy(p2)
+
+
+def test_matrix_size_must_match_the_targets(q):
+    """A matrix that is not 2^k x 2^k for its k targets is refused before any
+    record is written (the records index one shared buffer by the widths)."""
+    good = _Op([0, 1], np.eye(4))
+    with pytest.raises(ValueError):
+        q.OpArray([good, _Op([2], np.eye(4))])
+    with pytest.raises(ValueError):
+        q.OpArray([_Op([3, 4, 5], np.eye(4)), good])
+    oa = q.OpArray([good, _Op([2], [[0, 1], [1, 0]])])
+    assert oa.n == 2 and _read(oa.arr[1])[1] == [2]
