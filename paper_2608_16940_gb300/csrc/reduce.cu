@@ -215,16 +215,16 @@ __device__ __forceinline__ void square_pair(float x, float y, float& hi, float& 
 }
 
 // Weight of one component from its bits when its biased exponent e is at most
-// 127 (|v| < 2): the product (M 2^8)(M 2^7) and the right shift by 255 - 2e of
-// sq_fixed60, with the shift left unclamped (PTX shr.b64 takes shifts above 64
-// as 64 and gives 0, as the clamped shift does: the product is below 2^63).
+// 127 (|v| < 2): floor(v^2 2^60) = floor(M^2 2^(2e - 240)) as (M 2^7)^2 =
+// M^2 2^14 < 2^62 shifted right by 254 - 2e, the shift left unclamped (PTX
+// shr.b64 takes shifts above 64 as 64 and gives 0, the exact result there).
 // The implicit bit is set unconditionally; for e = 0 (zero, subnormals) the
-// shift is 255, so the result is 0 as in sq_fixed60.  255 - 2e = 2e ^ 255
-// since 2e < 256.
+// shift is 254, so the result is 0 as in sq_fixed60.  254 - 2e = 2e ^ 254
+// since 2e is even and below 256.
 __device__ __forceinline__ uint64_t sq_fixed60_small(uint32_t bits) {
-    const uint32_t mp = (bits << 8) | 0x80000000u;
-    const uint32_t sh = ((bits >> 22) & 0x1feu) ^ 0xffu;
-    const uint64_t prod = static_cast<uint64_t>(mp) * (mp >> 1);
+    const uint32_t mq = ((bits & 0x7fffffu) | 0x800000u) << 7;
+    const uint32_t sh = ((bits >> 22) & 0x1feu) ^ 0xfeu;
+    const uint64_t prod = static_cast<uint64_t>(mq) * mq;
     uint64_t r;
     asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(prod), "r"(sh));
     return r;
