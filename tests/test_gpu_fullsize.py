@@ -148,21 +148,22 @@ def test_wide_200_ops_fidelity_vs_oracle(q, prec, capsys):
         st.close()
 
 
-def test_diag33_beyond_2_32_closed_form_and_inverse(q):
-    """N = 33: H on qubits 0 and 32, then a 12-qubit diagonal that includes
-    qubit 32 (index bit beyond 2^32) and bits 0, 11, 12, 23, 24: the four
-    populated amplitudes are d[c] / 2 at their target bits; the conjugate
-    table returns the state."""
-    n = 33
+@pytest.mark.parametrize("n", [33, 34])
+def test_diag33_beyond_2_32_closed_form_and_inverse(q, n):
+    """N = 33 and 34 (the largest state, 128 GiB): H on qubits 0 and N - 1,
+    then a 12-qubit diagonal that includes qubit N - 1 (index bit beyond 2^32)
+    and bits 0, 11, 12, 23, 24: the four populated amplitudes are d[c] / 2 at
+    their target bits; the conjugate table returns the state."""
+    top = n - 1
     st = Big(q, n)
     rng = np.random.default_rng(33)
     try:
-        for qb in (0, 32):
+        for qb in (0, top):
             q.qsa_apply_fused(st.h, [qb], W.H)
-        t = [32, 0, 11, 12, 23, 24, 5, 17, 29, 30, 2, 8]
+        t = [top, 0, 11, 12, 23, 24, 5, 17, 29, 30, 2, 8]
         d = np.exp(1j * rng.uniform(0, 2 * np.pi, size=1 << len(t)))
         q.qsa_apply_diag(st.h, t, d)
-        idx = np.array([0, 1, 1 << 32, (1 << 32) | 1], dtype=np.int64)
+        idx = np.array([0, 1, 1 << top, (1 << top) | 1], dtype=np.int64)
         c = np.array([sum(((int(x) >> tq) & 1) << j for j, tq in enumerate(t)) for x in idx])
         got = st.amps(idx)
         assert np.max(np.abs(got - 0.5 * d[c])) < 1e-6
@@ -174,26 +175,28 @@ def test_diag33_beyond_2_32_closed_form_and_inverse(q):
         st.close()
 
 
-def test_layer33_beyond_2_32_closed_form_and_inverse(q):
-    """N = 33 layer blocks whose factors and phase gates reach qubit 32 (indices
-    beyond 2^32): after H on qubits 0, 17, 32 with ZZ(32, 5), ZZ(17, 32) and a
-    phase on 32 the populated amplitudes match their closed form; the inverse
-    blocks (factors first, then the conjugate phases) return to |0...0>."""
-    n = 33
+@pytest.mark.parametrize("n", [33, 34])
+def test_layer33_beyond_2_32_closed_form_and_inverse(q, n):
+    """N = 33 and 34 layer blocks whose factors and phase gates reach qubit
+    N - 1 (indices beyond 2^32): after H on qubits 0, 17, N - 1 with
+    ZZ(N - 1, 5), ZZ(17, N - 1) and a phase on N - 1 the populated amplitudes
+    match their closed form; the inverse blocks (factors first, then the
+    conjugate phases) return to |0...0>."""
+    top = n - 1
     zz = lambda g: np.diag(np.exp(-0.5j * g * np.array([1, -1, -1, 1])))
-    diag = [W.Op((32, 5), zz(0.7), True), W.Op((17, 32), zz(1.9), True),
-            W.Op((32,), np.diag([1, np.exp(0.3j)]), True)]
-    t = [0, 17, 32]
+    diag = [W.Op((top, 5), zz(0.7), True), W.Op((17, top), zz(1.9), True),
+            W.Op((top,), np.diag([1, np.exp(0.3j)]), True)]
+    t = [0, 17, top]
     st = Big(q, n)
     try:
         q.qsa_apply_layer(st.h, [], t, [W.H] * 3)
         q.qsa_apply_layer(st.h, diag, [], [])
-        xs = np.array([0, 1, 1 << 17, 1 << 32, (1 << 32) | 1, (1 << 32) | (1 << 17) | 1, 1 << 5], dtype=np.int64)
+        xs = np.array([0, 1, 1 << 17, 1 << top, (1 << top) | 1, (1 << top) | (1 << 17) | 1, 1 << 5], dtype=np.int64)
         got = st.amps(xs)
         ref = []
         for x in xs:
-            populated = (int(x) & ~((1 << 0) | (1 << 17) | (1 << 32))) == 0
-            b = [(int(x) >> k) & 1 for k in (32, 5, 17)]
+            populated = (int(x) & ~((1 << 0) | (1 << 17) | (1 << top))) == 0
+            b = [(int(x) >> k) & 1 for k in (top, 5, 17)]
             ph = np.exp(-0.5j * 0.7 * (1 - 2 * (b[0] ^ b[1]))) * np.exp(-0.5j * 1.9 * (1 - 2 * (b[2] ^ b[0])))
             ph *= np.exp(0.3j) if b[0] else 1.0
             ref.append(ph / np.sqrt(8) if populated else 0.0)
