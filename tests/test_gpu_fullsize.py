@@ -116,7 +116,7 @@ def test_qaoa30_symmetries_and_fused_equals_per_gate(q, kmax, kdiag, kprod, prec
         st.close()
 
 
-@pytest.mark.parametrize("n,n_ops", [(32, 20), (33, 8)])
+@pytest.mark.parametrize("n,n_ops", [(32, 20), (33, 8), (34, 4)])
 def test_wide_tensor_core_ops_then_inverse_return(q, n, n_ops):
     ops = W.wide_circuit(n, n_ops=n_ops, widths=(5, 6), seed=n)
     st = Big(q, n)
