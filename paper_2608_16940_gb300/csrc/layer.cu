@@ -608,7 +608,7 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
         for (auto kern : {k_apply_layer<true, 0, 0, 0, 0>, k_apply_layer<true, 0, 1, 0, 0>, k_apply_layer<true, 1, 0, 0, 0>,
                           k_apply_layer<true, 1, 1, 0, 0>, k_apply_layer<true, 0, 0, 2, 0>, k_apply_layer<true, 0, 1, 2, 0>,
                           k_apply_layer<true, 1, 0, 2, 0>, k_apply_layer<true, 1, 1, 2, 0>, k_apply_layer<true, 2, 2, 2, 1>,
-                          k_apply_layer<false, 2, 2, 2, 2>}) {
+                          k_apply_layer<true, 1, 1, 0, 1>, k_apply_layer<false, 2, 2, 2, 2>}) {
             cudaError_t e = set_smem_attr(reinterpret_cast<const void*>(kern), static_cast<int>(layer_smem_bytes(true)));
             if (e != cudaSuccess) return e;
         }
@@ -617,10 +617,12 @@ cudaError_t launch_apply_layer(float2* psi, int n, const LayerGeom& g, const uns
         if (!d_rec) return cudaErrorInvalidValue;
         a.rec = static_cast<const LayerRec*>(d_rec);   // written by launch_layer_records before
     }
-    // rotation mode: the diagonal table and the per-tile phases fixed at compile time
+    // rotation mode: the diagonal table and the per-tile phases fixed at compile time (the write-only
+    // pass too in its usual form: a diagonal table, per-tile phases, exit phases handed on)
     const bool ph = p.pmask != 0 || p.nout > 0;
     auto kern = !p.rotation ? k_apply_layer<false, 2, 2, 2, 2>
-                : p.generate ? k_apply_layer<true, 2, 2, 2, 1>
+                : p.generate ? (p.has_din && ph && p.rpmask == 0 ? k_apply_layer<true, 1, 1, 0, 1>
+                                                                 : k_apply_layer<true, 2, 2, 2, 1>)
                 : p.rpmask == 0
                     ? (p.has_din ? (ph ? k_apply_layer<true, 1, 1, 0, 0> : k_apply_layer<true, 1, 0, 0, 0>)
                                  : (ph ? k_apply_layer<true, 0, 1, 0, 0> : k_apply_layer<true, 0, 0, 0, 0>))
